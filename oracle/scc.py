@@ -1,0 +1,105 @@
+"""Similarity-constraint pieces of SCCSD in the FP64 oracle (test infrastructure).
+
+This file is part of the oracle. Only tests, the smoke check and the
+benchmark's CPU-baseline leg may import it; the product path never does.
+
+SCCSD adds zeta X3 to the cluster operator, X3 = R1^a R2^b - R1^b R2^a
+(Sec. 2.4.1), and the only surviving correction to the projected equations
+is zeta <mu~|[Hhat, X3]|HF> = zeta <mu~|Hhat X3|HF> (Sec. 2.4.2; X3 Hhat|HF>
+has rank >= 3). For a product R1 R2 of commuting excitation operators,
+
+  <mu~|Hhat R1 R2|HF> = <mu~|[[Hhat,R1],R2]|HF>
+                        + [mu single] r1_mu <HF|Hhat R2|HF>
+                        + [mu double] ( (r1 (x) s1)_mu + r2_mu <HF|Hhat R1|HF> )
+
+with s1_kappa = <kappa~|Hhat R2|HF> over singles and (r1 (x) s1) the doubles
+amplitude r1_P s1_Q + s1_P r1_Q. This follows from Hhat R1 R2 =
+[[Hhat,R1],R2] + R2 [Hhat,R1] + R1 Hhat R2 and a resolution of the identity
+in the biorthonormal excitation basis. Each piece is a derivative of the
+CCSD functions at T2 = 0 with the current T1 dressing:
+
+  <mu~|[[Hhat,R1],R2]|HF> = d^2/ds du Omega(t1 + s r1, u r2),
+  <kappa~|Hhat R2|HF>      = d/du Omega_1(t1, u r2),
+  <HF|Hhat R2|HF>          = d/du E0(t1, u r2),
+  <HF|Hhat R1|HF>          = d/ds E0(t1 + s r1, 0).
+
+The orthogonality O_ab = <psi_a|P|psi_b> of the natural projection
+(Sec. 2.4.1, 2.4.2) is the Hilbert-space inner product of the HF+S+D parts
+of psi = exp(T)(R0 + R)|HF>, T without X3 (the triples part of the cluster
+operator does not reach the projected space).
+"""
+from __future__ import annotations
+
+import torch
+from torch.func import jvp
+
+from . import ccsd as cc
+
+DT = torch.float64
+
+
+def _cc(t1, t2, h, L, o):
+    E0, O1, O2 = cc.ccsd_energy_residual(t1, t2, h, L, o)
+    return E0, cc.pack(O1, O2)
+
+
+def xi(t1, Rx, Ry, h, L, o, v):
+    """<mu~|Hhat R1(Rx) R2(Ry)|HF> in the packed layout."""
+    ov = o * v
+    r1, r2 = cc.unpack(Rx, o, v)[0], cc.unpack(Ry, o, v)[1]
+    z2 = torch.zeros(v, o, v, o, dtype=DT)
+
+    def f_u(t1_, u):
+        return _cc(t1_, u * r2, h, L, o)
+
+    # d/du at u = 0 for a given t1
+    def du(t1_):
+        one = torch.ones((), dtype=DT)
+        zero = torch.zeros((), dtype=DT)
+        (_, _), (dE, dO) = jvp(lambda u: f_u(t1_, u), (zero,), (one,))
+        return dE, dO
+
+    # mixed derivative d/ds of du(t1 + s r1)
+    zero = torch.zeros((), dtype=DT)
+    one = torch.ones((), dtype=DT)
+    (e2, s_all), (_, dd) = jvp(lambda s: du(t1 + s * r1), (zero,), (one,))
+    (_, _), (e1, _) = jvp(lambda s: _cc(t1 + s * r1, z2, h, L, o), (zero,), (one,))
+    s1 = s_all[:ov].reshape(v, o)
+    out = dd.clone()
+    out[:ov] = out[:ov] + r1.reshape(-1) * e2
+    prod = torch.einsum("ai,bj->aibj", r1, s1)
+    prod = prod + prod.permute(2, 3, 0, 1)
+    extra2 = cc.pack(torch.zeros(v, o, dtype=DT), prod)[ov:] + r2_packed(Ry, ov) * e1
+    out[ov:] = out[ov:] + extra2
+    return out
+
+
+def r2_packed(R, ov):
+    return torch.as_tensor(R, dtype=DT)[ov:]
+
+
+def projected_state(x_t, R0, R, o, v):
+    """(c0, c1[a,i], c2[a,i,b,j]): HF+S+D part of exp(T)(R0 + R)|HF>."""
+    t1, t2 = cc.unpack(x_t, o, v)
+    r1, r2 = cc.unpack(R, o, v)
+    c0 = torch.as_tensor(R0, dtype=DT)
+    c1 = r1 + c0 * t1
+    tr = torch.einsum("ai,bj->aibj", t1, r1)
+    tt = torch.einsum("ai,bj->aibj", t1, t1)
+    c2 = r2 + tr + tr.permute(2, 3, 0, 1) + c0 * (t2 + tt)
+    return c0, c1, c2
+
+
+def metric_product(x, y):
+    """Hilbert-space inner product of two HF+S+D kets given as (c0, c1, c2):
+    <S|S'> = 2 sum c1 c1', <D|D'> = sum c2 (2 c2' - c2' exchanged)."""
+    x0, x1, x2 = x
+    y0, y1, y2 = y
+    return (x0 * y0 + 2.0 * torch.sum(x1 * y1)
+            + torch.sum(x2 * (2.0 * y2 - y2.permute(0, 3, 2, 1))))
+
+
+def overlap(x_t, Ra0, Ra, Rb0, Rb, o, v):
+    """O_ab of the natural projection (Sec. 2.4.2)."""
+    return metric_product(projected_state(x_t, Ra0, Ra, o, v),
+                          projected_state(x_t, Rb0, Rb, o, v))

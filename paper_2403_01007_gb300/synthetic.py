@@ -1,0 +1,107 @@
+"""Seeded synthetic inputs for the SCCSD hot path.
+
+This module only draws random numbers. It holds none of the method's
+arithmetic: no Hamiltonian, no dressing, no contraction. Both the CUDA path
+(through its tests and the benchmark) and the FP64 CPU oracle take their
+inputs from here, so the two sides see identical arrays.
+
+Input recipe (the paper uses molecular integrals from a Hartree-Fock
+calculation, Sec. 2.3.2; here they are replaced by a synthetic canonical
+Hartree-Fock reference):
+
+* orbital energies: occupied eps ~ U[-1.5, -0.3] Eh, virtual eps ~ U[0.2, 3.0]
+  Eh, each block sorted ascending, occupied first;
+* Cholesky-factored two-electron integrals g_pqrs = sum_J L^J_pq L^J_rs with
+  L^J symmetric in pq and the upper-triangle entries ~ N(0, sd^2);
+* amplitude-like vectors (t, R, L) drawn N(0, 1) in the packed layout and
+  scaled or normalised by the caller.
+
+Seeds follow  seed = 240301007 * 100 + config * 10 + instance,  drawn with
+NumPy's PCG64 in the order eps_occ, eps_vir, L (upper triangle, J-major).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+SEED_BASE = 240301007 * 100
+
+
+@dataclass(frozen=True)
+class Workload:
+    """Sizes and distribution of one synthetic system."""
+    name: str
+    o: int      # doubly occupied spatial orbitals
+    v: int      # virtual spatial orbitals
+    J: int      # Cholesky rank
+    sd: float   # standard deviation of the Cholesky entries
+    config: int  # config number used in the seed
+
+    @property
+    def n(self) -> int:
+        return self.o + self.v
+
+
+# Workloads of the paper-scale benchmark ladder (small, medium, large).
+SMALL = Workload("o5_v19_J72", 5, 19, 72, 0.05, 1)
+MEDIUM = Workload("o10_v90_J300", 10, 90, 300, 0.03, 2)
+LARGE = Workload("o21_v200_J663", 21, 200, 663, 0.03, 3)
+
+
+def seed_of(config: int, instance: int = 0) -> int:
+    return SEED_BASE + 10 * config + instance
+
+
+def orbital_energies(rng: np.random.Generator, o: int, v: int) -> np.ndarray:
+    eo = np.sort(rng.uniform(-1.5, -0.3, size=o))
+    ev = np.sort(rng.uniform(0.2, 3.0, size=v))
+    return np.concatenate([eo, ev]).astype(np.float64)
+
+
+def cholesky_vectors(rng: np.random.Generator, n: int, J: int, sd: float) -> np.ndarray:
+    """L[J][n][n], symmetric in the last two indices."""
+    iu = np.triu_indices(n)
+    L = np.zeros((J, n, n), dtype=np.float64)
+    vals = rng.normal(0.0, sd, size=(J, iu[0].size))
+    L[:, iu[0], iu[1]] = vals
+    L[:, iu[1], iu[0]] = vals
+    return L
+
+
+def system(o: int, v: int, J: int, sd: float, seed: int):
+    """Return (eps[n], L[J][n][n]) for one seeded synthetic system."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    eps = orbital_energies(rng, o, v)
+    L = cholesky_vectors(rng, o + v, J, sd)
+    return eps, L
+
+
+def workload_system(w: Workload, instance: int = 0):
+    return system(w.o, w.v, w.J, w.sd, seed_of(w.config, instance))
+
+
+def packed_dim(o: int, v: int) -> int:
+    ov = o * v
+    return ov + ov * (ov + 1) // 2
+
+
+def random_vectors(o: int, v: int, count: int, seed: int, scale: float = 1.0,
+                   normalise: bool = False) -> np.ndarray:
+    """count vectors in the packed singles+doubles layout, N(0,1) * scale.
+
+    With normalise=True each vector has unit Euclidean norm over the packed
+    singles and doubles.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = rng.normal(0.0, 1.0, size=(count, packed_dim(o, v)))
+    if normalise:
+        x /= np.linalg.norm(x, axis=1, keepdims=True)
+    else:
+        x *= scale
+    return x
+
+
+def random_scalars(count: int, seed: int) -> np.ndarray:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.normal(0.0, 1.0, size=count)
