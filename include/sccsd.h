@@ -1,0 +1,112 @@
+/* C ABI of the SCCSD hot path (closed-shell similarity constrained CCSD).
+ *
+ * Paper: "Nuclear gradients and nonadiabatic couplings for similarity
+ * constrained coupled cluster singles and doubles" (arXiv 2403.01007).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * o, v, J  occupied and virtual spatial orbitals, Cholesky rank; n = o + v.
+ * eps[n]   orbital energies of a canonical closed-shell HF reference, the o
+ *          occupied first; the Fock matrix is diag(eps) (Brillouin condition
+ *          F_ai = 0, the last constraint of the Lagrangian of Sec. 2.3.1).
+ * L[J][n][n]  Cholesky vectors, g_pqrs = sum_J L^J_pq L^J_rs, each L^J
+ *          symmetric in pq. The one-electron integrals are derived so that
+ *          F = diag(eps):  h_pq = eps_p d_pq - sum_k (2 g_pqkk - g_pkkq).
+ * packed vectors (length dim = ov + ov(ov+1)/2, double):
+ *          singles first, x[a*o + i]; then the doubles over unique compound
+ *          pairs P = a*o + i <= Q = b*o + j at x[ov + Q(Q+1)/2 + P].
+ *          Kets (t, R): T = sum_ai t_ai E_ai + 1/2 sum_{ai,bj} t_aibj E_ai E_bj
+ *          with t_aibj = t_bjai (= t_ij^ab = t_ji^ba).
+ *          Bras (Omega, L, sigma of the left transform) live in the
+ *          biorthonormal basis <mu~|nu> = d_mu,nu, so <L|R> = sum_mu L_mu R_mu.
+ * pointers: every array argument may be host or device memory (detected per
+ *          call); the caller owns all of them. The context owns its internal
+ *          device buffers. Work is queued on the stream given to sccsd_init and
+ *          every call returns after that stream has finished the call's work.
+ * errors:  0 on success, a negative SCCSD_E* code otherwise; the text of the
+ *          last failure is returned by sccsd_last_error(ctx). No exception
+ *          crosses this interface. A failed call leaves the outputs undefined.
+ */
+#ifndef SCCSD_H
+#define SCCSD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sccsd_ctx sccsd_ctx;
+
+enum {
+  SCCSD_OK = 0,
+  SCCSD_EINVAL = -1,   /* bad size, NULL pointer, bad mode */
+  SCCSD_ENOMEM = -2,   /* device allocation failed */
+  SCCSD_ECUDA = -3,    /* a CUDA call or kernel failed */
+  SCCSD_ESTATE = -4,   /* call order: e.g. a Jacobian before any residual */
+  SCCSD_EINTERNAL = -5
+};
+
+/* Precision of the tensor-core-eligible contractions (ladder, rings,
+ * integral products). SCCSD_FP64: all arithmetic in FP64 on CUDA cores.
+ * SCCSD_BF16X3: each FP64 operand split into three BF16 slices (each the BF16
+ * rounding of what the previous slices left over), the six leading slice
+ * products on tcgen05 tensor cores with FP32 accumulation, summed in FP64
+ * (about FP32 accuracy). SCCSD_BF16: one BF16 slice per operand. */
+enum { SCCSD_FP64 = 0, SCCSD_BF16X3 = 1, SCCSD_BF16 = 2 };
+
+/* Create a context for one synthetic system (sizes, eps, L as above).
+ * Computes h (the integrals of a canonical reference) and the HF energy.
+ * stream: a cudaStream_t, or NULL for the default stream. */
+int sccsd_init(sccsd_ctx** ctx, int o, int v, int J, const double* eps, const double* L,
+               int precision, void* stream);
+
+/* Ground-state energy and residual at amplitudes t (packed ket):
+ *   E0 = <HF|Hbar|HF>,  omega_mu = <mu~|Hbar|HF>   (Sec. 2.1),
+ * with Hbar = exp(-T) H exp(T). With Ra and Rb non-NULL (packed kets of the two
+ * constrained states a, b) the cluster operator is T + zeta X3,
+ * X3 = R1^a R2^b - R1^b R2^a (Sec. 2.4.1), which adds
+ * zeta <mu~|[Hhat, X3]|HF> to omega (Sec. 2.4.2); E0 is unchanged by it.
+ * Outputs: omega (packed bra, may be NULL), e_corr = E0 - E_HF (may be NULL).
+ * The call also fixes t (and zeta, Ra, Rb) as the state at which the
+ * Jacobians and densities below are evaluated. */
+int sccsd_residual(sccsd_ctx* ctx, const double* t, double zeta, const double* Ra,
+                   const double* Rb, double* omega, double* e_corr);
+
+/* sigma_k = A R_k for nvec packed kets R[nvec][dim], with
+ * A_mu,nu = <mu~|[Hbar, tau_nu]|HF> (Sec. 2.3.3), at the state fixed by the
+ * last sccsd_residual call (SCC terms included when it had them).
+ * Also returns eta.R_k in etaR[nvec] when etaR is non-NULL (eta of Sec. 2.3.3). */
+int sccsd_jacobian_right(sccsd_ctx* ctx, int nvec, const double* R, double* sigma,
+                         double* etaR);
+
+/* sigma_k = A^T L_k (the left transformation) for nvec packed bras. */
+int sccsd_jacobian_left(sccsd_ctx* ctx, int nvec, const double* L, double* sigma);
+
+/* One- and two-particle (transition) densities of Sec. 2.3.2 for the bra
+ * (l0, L) and ket (r0, R) at the fixed state:
+ *   D1[p][q]       = d_pq = <L|exp(-T) E_pq exp(T)|R>
+ *   Gamma[J][p][q] = sum_rs d_pqrs L^J_rs,  d_pqrs = <L|exp(-T) e_pqrs exp(T)|R>
+ * (with the SCC state the cluster operator includes zeta X3, which gives the
+ * Delta d corrections of Sec. 2.4.2). Gamma may be NULL. */
+int sccsd_densities(sccsd_ctx* ctx, double l0, const double* L, double r0, const double* R,
+                    double* D1, double* Gamma);
+
+/* Dense contraction utility on the library's own kernels:
+ *   C[m][n] = alpha * sum_k A[m][k] B[n][k]   (row-major, FP64 in and out)
+ * on CUDA cores (SCCSD_FP64) or on tcgen05 tensor cores with BF16 slices
+ * (SCCSD_BF16X3 / SCCSD_BF16, used when the product is large enough). All three
+ * pointers must be device memory; the call returns after the work finished.
+ * This is the contraction primitive of the hot path, exposed for validation. */
+int sccsd_gemm_tn(int precision, long long M, long long N, long long K, double alpha,
+                  const double* A, const double* B, double* C, void* stream);
+
+/* Size of a packed vector. */
+long long sccsd_dim(int o, int v);
+const char* sccsd_last_error(sccsd_ctx* ctx);
+const char* sccsd_strerror(int code);
+void sccsd_destroy(sccsd_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCCSD_H */

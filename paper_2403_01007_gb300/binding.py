@@ -1,0 +1,167 @@
+"""Thin ctypes binding of the C ABI declared in include/sccsd.h.
+
+Argument marshalling only: arrays are passed as raw pointers (NumPy arrays
+for host memory, CUDA torch tensors for device memory), every computation
+happens in the compiled library. Importing fails loudly when the library
+has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libsccsd.so")
+
+FP64, BF16X3, BF16 = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "bf16x3": BF16X3, "bf16": BF16}
+
+_dp = ctypes.c_void_p
+
+
+def _declare(lib):
+    lib.sccsd_init.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int,
+                               ctypes.c_int, _dp, _dp, ctypes.c_int, _dp]
+    lib.sccsd_residual.argtypes = [_dp, _dp, ctypes.c_double, _dp, _dp, _dp, _dp]
+    lib.sccsd_jacobian_right.argtypes = [_dp, ctypes.c_int, _dp, _dp, _dp]
+    lib.sccsd_jacobian_left.argtypes = [_dp, ctypes.c_int, _dp, _dp]
+    lib.sccsd_densities.argtypes = [_dp, ctypes.c_double, _dp, ctypes.c_double, _dp, _dp, _dp]
+    lib.sccsd_gemm_tn.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong,
+                                  ctypes.c_longlong, ctypes.c_double, _dp, _dp, _dp, _dp]
+    lib.sccsd_gemm_tn.restype = ctypes.c_int
+    lib.sccsd_dim.argtypes = [ctypes.c_int, ctypes.c_int]
+    lib.sccsd_dim.restype = ctypes.c_longlong
+    lib.sccsd_last_error.argtypes = [_dp]
+    lib.sccsd_last_error.restype = ctypes.c_char_p
+    lib.sccsd_strerror.argtypes = [ctypes.c_int]
+    lib.sccsd_strerror.restype = ctypes.c_char_p
+    lib.sccsd_destroy.argtypes = [_dp]
+    lib.sccsd_destroy.restype = None
+    for f in ("sccsd_init", "sccsd_residual", "sccsd_jacobian_right",
+              "sccsd_jacobian_left", "sccsd_densities"):
+        getattr(lib, f).restype = ctypes.c_int
+    return lib
+
+
+_LIB = None
+
+
+def load(path: str | None = None):
+    """Load the compiled library (raises if it is missing)."""
+    global _LIB
+    if path is None and _LIB is not None:
+        return _LIB
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"compiled SCCSD library not found at {p}; run the build first")
+    lib = _declare(ctypes.CDLL(p))
+    if path is None:
+        _LIB = lib
+    return lib
+
+
+class SccsdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"sccsd error {code}: {msg}")
+        self.code = code
+
+
+def _ptr(x):
+    """Pointer of a float64 array: NumPy (host) or torch tensor (host/device)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags.c_contiguous:
+            raise TypeError("arrays must be C-contiguous float64")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        import torch
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise TypeError("tensors must be contiguous float64")
+        return x.data_ptr()
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def dim(o: int, v: int) -> int:
+    ov = o * v
+    return ov + ov * (ov + 1) // 2
+
+
+def gemm_tn(A, B, C, alpha=1.0, precision="fp64", lib=None):
+    """C = alpha * A @ B.T on device tensors through the library's kernels."""
+    lib = lib or load()
+    M, K = A.shape
+    N = B.shape[0]
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    rc = lib.sccsd_gemm_tn(prec, M, N, K, float(alpha), _ptr(A), _ptr(B), _ptr(C), None)
+    if rc != 0:
+        raise SccsdError(rc, lib.sccsd_strerror(rc).decode())
+    return C
+
+
+class Context:
+    """One system: orbital energies eps[n] and Cholesky vectors L[J][n][n]."""
+
+    def __init__(self, o, v, J, eps, L, precision="fp64", stream=None, lib=None):
+        self.lib = lib or load()
+        self.o, self.v, self.J = o, v, J
+        self.n = o + v
+        self.dim = dim(o, v)
+        h = ctypes.c_void_p()
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        s = None if stream is None else ctypes.c_void_p(stream)
+        rc = self.lib.sccsd_init(ctypes.byref(h), o, v, J, _ptr(eps), _ptr(L), prec, s)
+        if rc != 0:
+            raise SccsdError(rc, self.lib.sccsd_strerror(rc).decode())
+        self.h = h
+        self._keep = (eps, L)
+
+    def _check(self, rc):
+        if rc != 0:
+            raise SccsdError(rc, self.lib.sccsd_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sccsd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def residual(self, t, omega=None, scc=None):
+        """Return (e_corr, omega); scc = (zeta, Ra, Rb) or None."""
+        if omega is None:
+            omega = np.empty(self.dim)
+        e = ctypes.c_double()
+        zeta, Ra, Rb = (0.0, None, None) if scc is None else scc
+        self._check(self.lib.sccsd_residual(self.h, _ptr(t), float(zeta), _ptr(Ra), _ptr(Rb),
+                                            _ptr(omega), ctypes.addressof(e)))
+        return e.value, omega
+
+    def jacobian_right(self, R, sigma=None, with_eta=False):
+        nvec = 1 if R.ndim == 1 else R.shape[0]
+        if sigma is None:
+            sigma = np.empty_like(R) if isinstance(R, np.ndarray) else R.new_empty(R.shape)
+        eta = np.empty(nvec) if with_eta else None
+        self._check(self.lib.sccsd_jacobian_right(self.h, nvec, _ptr(R), _ptr(sigma), _ptr(eta)))
+        return (sigma, eta) if with_eta else sigma
+
+    def jacobian_left(self, L, sigma=None):
+        nvec = 1 if L.ndim == 1 else L.shape[0]
+        if sigma is None:
+            sigma = np.empty_like(L) if isinstance(L, np.ndarray) else L.new_empty(L.shape)
+        self._check(self.lib.sccsd_jacobian_left(self.h, nvec, _ptr(L), _ptr(sigma)))
+        return sigma
+
+    def densities(self, l0, L, r0, R, gamma=True):
+        n = self.n
+        D1 = np.empty((n, n))
+        G = np.empty((self.J, n, n)) if gamma else None
+        self._check(self.lib.sccsd_densities(self.h, float(l0), _ptr(L), float(r0), _ptr(R),
+                                             _ptr(D1), _ptr(G)))
+        return D1, G

@@ -1,0 +1,53 @@
+// Device backend used by the graph executor. Every method launches kernels
+// of this library on the context's CUDA stream; there is no host path.
+#pragma once
+
+#include <cstdint>
+#include <stdexcept>
+
+namespace sccsd {
+
+struct CudaError : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+struct OomError : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+
+class Graph;
+
+class Backend {
+ public:
+  virtual ~Backend() {}
+  virtual double* alloc(int64_t n) = 0;
+  virtual void release(double* p) = 0;
+  // dst (device, n doubles) <- src (host or device)
+  virtual void upload(double* dst, const double* src, int64_t n, bool src_on_device) = 0;
+  virtual void fill(double* p, int64_t n, double v) = 0;
+  // dst (host or device) <- src (device)
+  virtual void download(double* dst, const double* src, int64_t n, bool dst_on_device) = 0;
+  // true when p is a device (or managed) pointer usable by kernels
+  virtual bool is_device(const void* p) = 0;
+  virtual void sync() = 0;
+  // packed singles+doubles vector <-> t1[a][i], full t2[i][j][a][b].
+  // ket: t2 = t_mu on both (P,Q) and (Q,P);  bra: off-diagonal pairs halved
+  // on unpack and summed on pack, so that sum_packed L X = sum_full L~ X.
+  virtual void unpack(const double* x, int o, int v, double* t1, double* t2, bool bra) = 0;
+  virtual void pack(const double* t1, const double* t2, int o, int v, double* x, bool bra) = 0;
+  // out[i] (+)= coef * in[i] over a rank-r index box; both sides strided.
+  virtual void copy_view(int rank, const int64_t* dims, double* out, const int64_t* ostr,
+                         const double* in, const int64_t* istr, double coef, bool accumulate) = 0;
+  // C[b][m][n] = alpha * sum_k A[b][m][k] B[b][n][k]; C dense and overwritten.
+  // tc: the contraction may use tensor cores when the precision mode allows.
+  virtual void gemm_tn(int64_t batch, int64_t M, int64_t N, int64_t K, double alpha,
+                       const double* A, const double* B, double* C, bool tc) = 0;
+  // Reusable temporary device buffers (slot 0..7), grown on demand.
+  virtual double* scratch(int slot, int64_t n) = 0;
+  // Particle-particle ladder with the vv block of L (see Graph::ladder).
+  virtual void ladder(const Graph& g, const double* L, int64_t L_version, const double* X,
+                      double* Y) = 0;
+  virtual void ladder_adj_l(const Graph& g, const double* L, const double* Ybar,
+                            const double* X, double* out) = 0;
+};
+
+}  // namespace sccsd

@@ -1,0 +1,392 @@
+// tcgen05 BF16 GEMM with TMA loads and TMEM accumulators (sm_103a).
+//
+// One CTA computes a 128 x 256 FP32 tile of A * B^T (both operands K-major
+// BF16 in global memory, padded to whole tiles) and writes alpha * tile into
+// an FP64 output (overwrite or accumulate). Warp roles:
+//   warp 4    : TMA producer, 4-stage ring of (A 128x64, B 256x64) tiles,
+//               128-byte swizzle, completion on mbarriers (expect_tx)
+//   warp 5    : one elected thread issues tcgen05.mma.kind::f16 (M=128,
+//               N=256, K=16 per instruction, 4 per stage), commits each stage
+//               back to the producer and finally the accumulator
+//   warps 0-3 : epilogue, tcgen05.ld 32 lanes x 32 columns at a time, staged
+//               through shared memory for coalesced FP64 stores
+// Every mbarrier wait is bounded; on expiry the kernel records an error code
+// and the remaining roles skip their work, so a fault in the pipeline shows
+// up as an error status instead of a hang. TMEM is always freed.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <stdexcept>
+#include <string>
+
+#include "backend.h"
+#include "tc_gemm.h"
+
+namespace sccsd {
+
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;
+constexpr int B_BYTES = BN * BK * 2;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int EPI_FLOATS = 4 * 32 * 33;
+constexpr int SMEM_BYTES = 1024 /*align slack*/ + STAGES * STAGE_BYTES + 256 /*barriers*/ +
+                           EPI_FLOATS * 4;
+constexpr int TMEM_COLS = 256;
+constexpr uint32_t WAIT_LIMIT = 1u << 24;  // polls before a wait is declared failed
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n"
+      " selp.b32 %0, 1, 0, P;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait; returns false (and records code) when the limit is reached
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+  for (uint32_t i = 0; i < WAIT_LIMIT; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if (i > 32) __nanosleep(64);
+  }
+  atomicCAS(err, 0, code);
+  return false;
+}
+
+__device__ __forceinline__ uint64_t make_desc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);   // start address
+  d |= (uint64_t)(16u >> 4) << 16;           // leading byte offset (unused, K-major SW128)
+  d |= (uint64_t)(1024u >> 4) << 32;         // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                    // descriptor version (tcgen05)
+  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  return d;
+}
+
+// kind::f16 instruction descriptor: BF16 x BF16 -> FP32, both K-major
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
+  return (1u << 4)                      // D format FP32
+         | (1u << 7)                    // A format BF16
+         | (1u << 10)                   // B format BF16
+         | ((uint32_t)(N >> 3) << 17)   // N / 8
+         | ((uint32_t)(M >> 4) << 24);  // M / 16
+}
+
+__global__ void __launch_bounds__(192, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              int64_t M, int64_t N, int nk, double alpha, double* __restrict__ C, int64_t ldc,
+              int accumulate, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * A_BYTES;
+  uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accf = empty + STAGES;
+  uint32_t* tmem_slot = (uint32_t*)(accf + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  float* epi = (float*)(smem + STAGES * STAGE_BYTES + 256);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(accf)));
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 4) {
+    if (lane == 0) {
+      int issued_last[STAGES];
+      for (int s = 0; s < STAGES; ++s) issued_last[s] = -1;
+      for (int kb = 0; kb < nk; ++kb) {
+        const int s = kb % STAGES;
+        if (kb >= STAGES) {
+          if (!mbar_wait(smem_u32(&empty[s]), ((kb / STAGES) - 1) & 1, err, 1)) {
+            *abort_flag = 1;
+            break;
+          }
+        }
+        if (*abort_flag) break;
+        const uint32_t fb = smem_u32(&full[s]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                     "r"(STAGE_BYTES)
+                     : "memory");
+        const int x = kb * BK;
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(sA + s * A_BYTES)),
+            "l"((uint64_t)&tmA), "r"(fb), "r"(x), "r"((int)m0)
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(sB + s * B_BYTES)),
+            "l"((uint64_t)&tmB), "r"(fb), "r"(x), "r"((int)n0)
+            : "memory");
+        issued_last[s] = kb;
+      }
+      // make sure no copy issued by this CTA is still in flight at exit
+      for (int s = 0; s < STAGES; ++s)
+        if (issued_last[s] >= 0)
+          mbar_wait(smem_u32(&full[s]), (issued_last[s] / STAGES) & 1, err, 2);
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = make_idesc(BM, BN);
+      for (int kb = 0; kb < nk; ++kb) {
+        const int s = kb % STAGES;
+        if (!mbar_wait(smem_u32(&full[s]), (kb / STAGES) & 1, err, 3) || *abort_flag) {
+          *abort_flag = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k) {
+          const uint64_t ad = make_desc_sw128(a0 + k * 32);
+          const uint64_t bd = make_desc_sw128(b0 + k * 32);
+          const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        }
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&empty[s]))
+            : "memory");
+      }
+      // accumulator ready (or the pipeline was abandoned)
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(accf))
+          : "memory");
+    }
+  } else {
+    // epilogue warps 0..3: TMEM lanes 32*warp .. 32*warp+31
+    bool ok = mbar_wait(smem_u32(accf), 0, err, 4);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok && !*abort_flag) {
+      float* buf = epi + warp * 32 * 33;
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+            "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, "
+            "[%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+              "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+              "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
+              "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+              "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 32; ++j) buf[lane * 33 + j] = __uint_as_float(r[j]);
+        __syncwarp();
+        const int64_t col = n0 + c0 + lane;
+        for (int rr = 0; rr < 32; ++rr) {
+          const int64_t row = m0 + warp * 32 + rr;
+          if (row < M && col < N) {
+            double v = alpha * (double)buf[rr * 33 + lane];
+            double* p = C + row * ldc + col;
+            *p = accumulate ? *p + v : v;
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS));
+  }
+}
+
+// x = sum_s slice_s with slice_s = bf16(x - sum_{r<s} slice_r); padded with zeros
+__global__ void k_split_bf16(const double* __restrict__ X, int64_t rows, int64_t K,
+                             int64_t rows_pad, int64_t k_pad, int slices,
+                             __nv_bfloat16* __restrict__ out) {
+  const int64_t total = rows_pad * k_pad;
+  const int64_t sstride = rows_pad * k_pad;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / k_pad, k = e % k_pad;
+    double x = (r < rows && k < K) ? X[r * K + k] : 0.0;
+    for (int s = 0; s < slices; ++s) {
+      __nv_bfloat16 b = __double2bfloat16(x);
+      out[s * sstride + e] = b;
+      x -= (double)__bfloat162float(b);
+    }
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p)
+      throw CudaError("cuTensorMapEncodeTiled entry point unavailable");
+    fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+CUtensorMap make_map(const void* base, int64_t rows_pad, int64_t k_pad, int box_rows) {
+  CUtensorMap m;
+  cuuint64_t dims[2] = {(cuuint64_t)k_pad, (cuuint64_t)rows_pad};
+  cuuint64_t strides[1] = {(cuuint64_t)(k_pad * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+                           strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw CudaError("cuTensorMapEncodeTiled failed: " + std::to_string(r));
+  return m;
+}
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+TcGemm::TcGemm(cudaStream_t st, int precision) : st_(st) {
+  nslices_ = precision == 1 ? 3 : 1;
+  if (cudaMalloc(&d_err_, sizeof(int)) != cudaSuccess) throw OomError("tc error flag");
+  cudaMemsetAsync(d_err_, 0, sizeof(int), st_);
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       SMEM_BYTES);
+  if (e != cudaSuccess) throw CudaError(std::string("tc smem attribute: ") + cudaGetErrorString(e));
+}
+
+TcGemm::~TcGemm() {
+  release(a_tmp_);
+  release(b_tmp_);
+  if (d_err_) cudaFree(d_err_);
+}
+
+void TcGemm::release(TcOperand& op) {
+  if (op.data) cudaFree(op.data);
+  op = TcOperand();
+}
+
+bool TcGemm::worthwhile(int64_t nb, int64_t M, int64_t N, int64_t K) const {
+  return nb == 1 && M >= 64 && N >= 64 && K >= 64 && (double)M * N * K >= 6.7e7;
+}
+
+void TcGemm::convert(const double* X, int64_t rows, int64_t K, TcOperand& out) {
+  const int64_t rp = round_up(rows, BN), kp = round_up(K, BK);
+  const size_t need = (size_t)rp * kp * 2 * nslices_;
+  if (out.bytes < need) {
+    if (out.data) {
+      cudaStreamSynchronize(st_);
+      cudaFree(out.data);
+      out.data = nullptr;
+    }
+    if (cudaMalloc(&out.data, need) != cudaSuccess) {
+      cudaGetLastError();
+      throw OomError("tensor-core operand buffer of " + std::to_string(need) + " bytes");
+    }
+    out.bytes = need;
+  }
+  out.rows = rows;
+  out.k = K;
+  out.rows_pad = rp;
+  out.k_pad = kp;
+  out.slices = nslices_;
+  const int64_t total = rp * kp;
+  int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
+  k_split_bf16<<<grid, 256, 0, st_>>>(X, rows, K, rp, kp, nslices_, (__nv_bfloat16*)out.data);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw CudaError(std::string("split_bf16: ") + cudaGetErrorString(e));
+}
+
+void TcGemm::prepare_operand(const double* X, int64_t rows, int64_t K, TcOperand& out) {
+  convert(X, rows, K, out);
+}
+
+void TcGemm::check_error() {
+  int h = 0;
+  cudaMemcpyAsync(&h, d_err_, sizeof(int), cudaMemcpyDeviceToHost, st_);
+  cudaStreamSynchronize(st_);
+  if (h != 0) {
+    cudaMemsetAsync(d_err_, 0, sizeof(int), st_);
+    throw CudaError("tensor-core pipeline wait expired (code " + std::to_string(h) + ")");
+  }
+}
+
+void TcGemm::run(const TcOperand& A, int sa, const TcOperand& B, int sb, int64_t M, int64_t N,
+                 double alpha, double* C, bool accumulate) {
+  if (A.k_pad != B.k_pad) throw std::runtime_error("tc: K mismatch");
+  const __nv_bfloat16* a = (const __nv_bfloat16*)A.data + (size_t)sa * A.rows_pad * A.k_pad;
+  const __nv_bfloat16* b = (const __nv_bfloat16*)B.data + (size_t)sb * B.rows_pad * B.k_pad;
+  CUtensorMap ma = make_map(a, A.rows_pad, A.k_pad, BM);
+  CUtensorMap mb = make_map(b, B.rows_pad, B.k_pad, BN);
+  dim3 grid((unsigned)(B.rows_pad / BN), (unsigned)((M + BM - 1) / BM));
+  const int nk = (int)(A.k_pad / BK);
+  k_tc_gemm<<<grid, 192, SMEM_BYTES, st_>>>(ma, mb, M, N, nk, alpha, C, N, accumulate ? 1 : 0,
+                                           d_err_);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw CudaError(std::string("tc_gemm launch: ") + cudaGetErrorString(e));
+}
+
+// slice pairs (i, j) with i + j < slices, largest first
+static void slice_pairs(int s, std::vector<std::pair<int, int>>& out) {
+  out.clear();
+  for (int tot = 0; tot < s; ++tot)
+    for (int i = 0; i <= tot; ++i) out.push_back({i, tot - i});
+}
+
+void TcGemm::gemm_prepared_b(int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+                             const TcOperand& B, double* C) {
+  convert(A, M, K, a_tmp_);
+  std::vector<std::pair<int, int>> pairs;
+  slice_pairs(nslices_, pairs);
+  // accumulate the small products first, the leading one last
+  for (size_t p = pairs.size(); p-- > 0;)
+    run(a_tmp_, pairs[p].first, B, pairs[p].second, M, N, alpha, C, p + 1 != pairs.size());
+  check_error();
+}
+
+void TcGemm::gemm(int64_t nb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+                  const double* B, double* C) {
+  if (nb != 1) throw std::runtime_error("tc: batched GEMM not supported");
+  convert(B, N, K, b_tmp_);
+  gemm_prepared_b(M, N, K, alpha, A, b_tmp_, C);
+}
+
+}  // namespace sccsd

@@ -1,0 +1,50 @@
+// Tensor-core (tcgen05 / TMEM / TMA) contraction path for sm_103a.
+//
+// FP64 operands are split into BF16 slices x = x_0 + x_1 + ... (each slice the
+// BF16 rounding of what the previous ones left over); slice products run as
+// BF16 x BF16 -> FP32 GEMMs on the tensor cores and are summed into the FP64
+// result. One slice (SCCSD_BF16) keeps about 8 significant bits per operand,
+// three slices with the six leading products (SCCSD_BF16X3) about 24.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+namespace sccsd {
+
+// A matrix already converted to BF16 slices, rows padded to 256 and K to 64.
+struct TcOperand {
+  void* data = nullptr;   // slices back to back, each [rows_pad][k_pad] bf16
+  int64_t rows = 0, k = 0, rows_pad = 0, k_pad = 0;
+  int slices = 0;
+  size_t bytes = 0;
+};
+
+class TcGemm {
+ public:
+  TcGemm(cudaStream_t st, int precision);
+  ~TcGemm();
+  bool worthwhile(int64_t nb, int64_t M, int64_t N, int64_t K) const;
+  // C[m][n] = alpha * sum_k A[m][k] B[n][k]  (FP64 in and out)
+  void gemm(int64_t nb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+            const double* B, double* C);
+  void prepare_operand(const double* X, int64_t rows, int64_t K, TcOperand& out);
+  void gemm_prepared_b(int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+                       const TcOperand& B, double* C);
+  void release(TcOperand& op);
+  int slices() const { return nslices_; }
+
+ private:
+  void convert(const double* X, int64_t rows, int64_t K, TcOperand& out);
+  void run(const TcOperand& A, int sa, const TcOperand& B, int sb, int64_t M, int64_t N,
+           double alpha, double* C, bool accumulate);
+  void check_error();
+  cudaStream_t st_;
+  int nslices_;
+  TcOperand a_tmp_, b_tmp_;
+  int* d_err_ = nullptr;
+};
+
+}  // namespace sccsd

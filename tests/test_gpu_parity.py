@@ -1,0 +1,132 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import ccsd as cc
+from oracle import response as rp
+from paper_2403_01007_gb300 import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2403_01007_gb300 import binding
+    return binding
+
+
+def dev(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda:0")
+
+
+def maxrel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.abs(a - b).max() / max(1.0, np.abs(b).max())
+
+
+# ----------------------------------------------------------- contraction primitive
+
+def test_tc_gemm_exact_integers(B):
+    """Small integers are exact in BF16 and their FP32 sums stay below 2^24,
+    so the tensor-core GEMM must agree bit for bit (ragged M, N, K)."""
+    rng = np.random.default_rng(5)
+    M, N, K = 300, 517, 704
+    A = rng.integers(-8, 9, size=(M, K)).astype(np.float64)
+    Bm = rng.integers(-8, 9, size=(N, K)).astype(np.float64)
+    C = torch.empty((M, N), dtype=torch.float64, device="cuda:0")
+    B.gemm_tn(dev(A), dev(Bm), C, precision="bf16")
+    assert np.array_equal(C.cpu().numpy(), A @ Bm.T)
+
+
+def test_tc_gemm_split_accuracy(B):
+    rng = np.random.default_rng(6)
+    M, N, K = 1000, 777, 1300
+    A = rng.normal(size=(M, K))
+    Bm = rng.normal(size=(N, K))
+    ref = A @ Bm.T
+    C = torch.empty((M, N), dtype=torch.float64, device="cuda:0")
+    B.gemm_tn(dev(A), dev(Bm), C, precision="bf16x3")
+    err3 = np.abs(C.cpu().numpy() - ref).max() / np.abs(ref).max()
+    B.gemm_tn(dev(A), dev(Bm), C, precision="bf16")
+    err1 = np.abs(C.cpu().numpy() - ref).max() / np.abs(ref).max()
+    B.gemm_tn(dev(A), dev(Bm), C, precision="fp64")
+    err0 = np.abs(C.cpu().numpy() - ref).max() / np.abs(ref).max()
+    assert err0 < 1e-14
+    assert err1 < 2e-2
+    assert err3 < 1e-6
+
+
+# ----------------------------------------------------------------- FP64 parity
+
+def run_all(B, o, v, J, sd, seed, precision="fp64", scc=False, on_device=False):
+    eps, L = syn.system(o, v, J, sd, seed)
+    prob = cc.Problem(eps, L, o)
+    t = syn.random_vectors(o, v, 1, seed + 1, scale=0.02)[0]
+    R, Lv, Ra, Rb = syn.random_vectors(o, v, 4, seed + 2, normalise=True)
+    conv = dev if on_device else (lambda x: np.ascontiguousarray(x))
+    ctx = B.Context(o, v, J, conv(eps), conv(L), precision=precision)
+    sccarg = (0.31, conv(Ra), conv(Rb)) if scc else None
+    scct = (0.31, torch.tensor(Ra), torch.tensor(Rb)) if scc else None
+    out = {}
+    om = torch.empty(prob.dim, dtype=torch.float64, device="cuda:0") if on_device else None
+    e, om = ctx.residual(conv(t), omega=om, scc=sccarg)
+    om = om.cpu().numpy() if on_device else om
+    E0, Om = rp.residual(prob, t, scc=scct)
+    Ehf = float(rp.residual(prob, np.zeros(prob.dim))[0])
+    out["E"] = (e, float(E0) - Ehf)
+    out["omega"] = (om, Om.numpy())
+    sig, eta = ctx.jacobian_right(np.ascontiguousarray(R), with_eta=True)
+    out["AR"] = (sig, rp.jacobian_right(prob, t, R, scc=scct).numpy())
+    out["etaR"] = (eta[0], float(rp.eta(prob, t, scc=scct) @ torch.tensor(R)))
+    out["ATL"] = (ctx.jacobian_left(np.ascontiguousarray(Lv)),
+                  rp.jacobian_left(prob, t, Lv, scc=scct).numpy())
+    D1, G = ctx.densities(0.6, np.ascontiguousarray(Lv), -0.3, np.ascontiguousarray(R))
+    D1r, Gr = rp.densities(prob, t, 0.6, Lv, -0.3, R, scc=scct)
+    out["D1"] = (D1, D1r.numpy())
+    out["Gamma"] = (G, Gr.numpy())
+    ctx.close()
+    return out
+
+
+@pytest.mark.parametrize("scc", [False, True], ids=["ccsd", "sccsd"])
+@pytest.mark.parametrize("size", [(1, 1, 3), (2, 3, 6), (3, 5, 9)], ids=lambda s: "o%d_v%d" % s[:2])
+def test_fp64_parity_tiny(B, size, scc):
+    o, v, J = size
+    out = run_all(B, o, v, J, 0.3, 1234 + o * 10 + v, scc=scc)
+    for k, (a, b) in out.items():
+        assert maxrel(a, b) < 1e-12, k
+
+
+def test_fp64_parity_small_device_pointers(B):
+    w = syn.SMALL
+    out = run_all(B, w.o, w.v, w.J, w.sd, syn.seed_of(w.config), scc=True, on_device=True)
+    for k, (a, b) in out.items():
+        assert maxrel(a, b) < 1e-11, k
+
+
+def test_fp64_parity_ragged(B):
+    """Sizes that are not multiples of any tile (v = 37, o = 7)."""
+    out = run_all(B, 7, 37, 41, 0.05, 777)
+    for k, (a, b) in out.items():
+        assert maxrel(a, b) < 1e-11, k
+
+
+# --------------------------------------------------------------- error paths
+
+def test_error_codes(B):
+    import ctypes
+    lib = B.load()
+    h = ctypes.c_void_p()
+    eps = np.linspace(-1, 1, 4)
+    L = np.zeros((2, 4, 4))
+    assert lib.sccsd_init(ctypes.byref(h), 0, 4, 2, eps.ctypes.data, L.ctypes.data, 0, None) == -1
+    assert lib.sccsd_init(ctypes.byref(h), 2, 2, 2, eps.ctypes.data, L.ctypes.data, 7, None) == -1
+    bad = np.array([-1.0, -2.0, 0.5, 1.0])   # occupied eps not ascending
+    assert lib.sccsd_init(ctypes.byref(h), 2, 2, 2, bad.ctypes.data, L.ctypes.data, 0, None) == -1
+    ctx = B.Context(2, 2, 2, eps, L)
+    R = np.zeros(B.dim(2, 2))
+    with pytest.raises(B.SccsdError) as ei:
+        ctx.jacobian_right(R)
+    assert ei.value.code == -4
+    ctx.close()
