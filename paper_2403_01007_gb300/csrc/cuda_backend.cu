@@ -496,7 +496,7 @@ class CudaBackend : public Backend {
       int64_t dims[4] = {v, v, v, v};  // a c b d
       int64_t ostr[4] = {v * vv, vv, v, 1};
       int64_t i1[4] = {v * vv, v, vv, 1};  // D[a][b][c][d]
-      int64_t i2[4] = {v, 1, v * vv, vv};  // D[b][a][d][c]
+      int64_t i2[4] = {vv, 1, v * vv, v};  // D[b][a][d][c]
       copy_view(4, dims, M2, ostr, D, i1, 1.0, false);
       copy_view(4, dims, M2, ostr, D, i2, 1.0, true);
     }

@@ -54,7 +54,8 @@ def test_tc_gemm_split_accuracy(B):
     err0 = np.abs(C.cpu().numpy() - ref).max() / np.abs(ref).max()
     assert err0 < 1e-14
     assert err1 < 2e-2
-    assert err3 < 1e-6
+    # three slices leave FP32 accumulation (24-bit) as the limit: |err| <~ sqrt(K) u32 |C|
+    assert err3 < 1e-5
 
 
 # ----------------------------------------------------------------- FP64 parity
