@@ -99,6 +99,17 @@ int sccsd_densities(sccsd_ctx* ctx, double l0, const double* L, double r0, const
 int sccsd_gemm_tn(int precision, long long M, long long N, long long K, double alpha,
                   const double* A, const double* B, double* C, void* stream);
 
+/* Profiling. sccsd_profile(ctx, 1) resets the counters and starts timing
+ * every particle-particle ladder contraction (o^2 v^4 part) with CUDA events
+ * on the context's stream; 0 stops it. sccsd_profile_read returns the summed
+ * ladder time in ms, the number of ladder contractions, their algorithmic
+ * flop count (2 o^2 v^4 each) and the number of kernels this library
+ * launched since the reset (any output may be NULL). Timing adds one stream
+ * synchronisation per read. */
+int sccsd_profile(sccsd_ctx* ctx, int enable);
+int sccsd_profile_read(sccsd_ctx* ctx, double* ladder_ms, long long* ladder_calls,
+                       double* ladder_flops, long long* launches);
+
 /* Size of a packed vector. */
 long long sccsd_dim(int o, int v);
 const char* sccsd_last_error(sccsd_ctx* ctx);

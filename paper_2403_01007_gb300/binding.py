@@ -31,6 +31,10 @@ def _declare(lib):
     lib.sccsd_gemm_tn.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong,
                                   ctypes.c_longlong, ctypes.c_double, _dp, _dp, _dp, _dp]
     lib.sccsd_gemm_tn.restype = ctypes.c_int
+    lib.sccsd_profile.argtypes = [_dp, ctypes.c_int]
+    lib.sccsd_profile.restype = ctypes.c_int
+    lib.sccsd_profile_read.argtypes = [_dp, _dp, _dp, _dp, _dp]
+    lib.sccsd_profile_read.restype = ctypes.c_int
     lib.sccsd_dim.argtypes = [ctypes.c_int, ctypes.c_int]
     lib.sccsd_dim.restype = ctypes.c_longlong
     lib.sccsd_last_error.argtypes = [_dp]
@@ -157,6 +161,17 @@ class Context:
             sigma = np.empty_like(L) if isinstance(L, np.ndarray) else L.new_empty(L.shape)
         self._check(self.lib.sccsd_jacobian_left(self.h, nvec, _ptr(L), _ptr(sigma)))
         return sigma
+
+    def profile(self, enable=True):
+        self._check(self.lib.sccsd_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """(ladder_ms, ladder_calls, ladder_flops, kernel_launches) since the reset."""
+        ms, fl = ctypes.c_double(), ctypes.c_double()
+        calls, launches = ctypes.c_longlong(), ctypes.c_longlong()
+        self._check(self.lib.sccsd_profile_read(self.h, ctypes.addressof(ms), ctypes.addressof(calls),
+                                                ctypes.addressof(fl), ctypes.addressof(launches)))
+        return ms.value, calls.value, fl.value, launches.value
 
     def densities(self, l0, L, r0, R, gamma=True):
         n = self.n

@@ -1,5 +1,7 @@
 // C ABI of the SCCSD hot path: contexts, graph assembly and marshalling.
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -131,6 +133,10 @@ struct sccsd_ctx {
   double e_hf = 0.0;
   std::string err;
   ~sccsd_ctx() {
+    if (getenv("SCCSD_TRACE")) {
+      for (Model* m : {plain.get(), scc.get()})
+        if (m) fprintf(stderr, "%s", m->g.trace_report(60).c_str());
+    }
     plain.reset();
     scc.reset();
     if (be) {
@@ -171,6 +177,7 @@ Model& model(sccsd_ctx* c, bool scc) {
   std::unique_ptr<Model>& m = scc ? c->scc : c->plain;
   if (!m) {
     m = build_model(c->be.get(), c->o, c->v, c->J, scc);
+    m->g.trace = getenv("SCCSD_TRACE") != nullptr;
     m->g.set_input(m->L, c->L, true);
     m->g.set_input(m->h, c->h, true);
     m->g.set_input(m->delta, c->delta, true);
@@ -428,6 +435,23 @@ int sccsd_densities(sccsd_ctx* c, double l0, const double* L, double r0, const d
 }
 
 void sccsd_destroy(sccsd_ctx* c) { delete c; }
+
+int sccsd_profile(sccsd_ctx* c, int enable) {
+  if (!c) return SCCSD_EINVAL;
+  return guarded(c, [&] { c->be->profile(enable != 0); });
+}
+
+int sccsd_profile_read(sccsd_ctx* c, double* ladder_ms, long long* ladder_calls,
+                       double* ladder_flops, long long* launches) {
+  if (!c) return SCCSD_EINVAL;
+  return guarded(c, [&] {
+    long long calls = 0;
+    c->be->profile_read(ladder_ms, &calls, launches);
+    if (ladder_calls) *ladder_calls = calls;
+    const double oo = (double)c->o * c->o, vv = (double)c->v * c->v;
+    if (ladder_flops) *ladder_flops = 2.0 * oo * vv * vv * (double)calls;
+  });
+}
 
 int sccsd_gemm_tn(int precision, long long M, long long N, long long K, double alpha,
                   const double* A, const double* B, double* C, void* stream) {

@@ -46,6 +46,14 @@ class Backend {
   // Particle-particle ladder with the vv block of L (see Graph::ladder).
   virtual void ladder(const Graph& g, const double* L, int64_t L_version, const double* X,
                       double* Y) = 0;
+  // Profiling: CUDA-event timing of the ladder contractions and a count of
+  // kernel launches since the last reset.
+  virtual void profile(bool enable) = 0;
+  // Per-operation tracing support: record an event on the stream, and the
+  // elapsed milliseconds between two recorded events (synchronises).
+  virtual void* record_event() = 0;
+  virtual double elapsed_ms(void* a, void* b) = 0;
+  virtual void profile_read(double* ladder_ms, long long* ladder_calls, long long* launches) = 0;
   virtual void ladder_adj_l(const Graph& g, const double* L, const double* Ybar,
                             const double* X, double* out) = 0;
 };

@@ -39,9 +39,9 @@ EnergyResidual build_energy_residual(Graph& g, int t1, int t2, int L, int h, int
 
   // T1-transformed Cholesky vectors and one-electron integrals
   int Lhoo = g.add("Jkl", {{Loo, "Jkl", 1.0}, {g.contract(Lov, "Jka", t1, "al", "Jkl"), "Jkl", 1.0}});
-  int Lhvv = g.add("Jab", {{Lvv, "Jab", 1.0}, {g.contract(t1, "ak", Lov, "Jkb", "Jab"), "Jab", -1.0}});
+  int Lhvv = g.add("Jab", {{Lvv, "Jab", 1.0}, {g.contract(t1, "ak", Lov, "Jkb", "Jab", 1.0, true), "Jab", -1.0}});
   int Lhvo = g.add("Jai", {{Lvo, "Jai", 1.0},
-                           {g.contract(Lvv, "Jac", t1, "ci", "Jai"), "Jai", 1.0},
+                           {g.contract(Lvv, "Jac", t1, "ci", "Jai", 1.0, true), "Jai", 1.0},
                            {g.contract(t1, "ak", Lhoo, "Jki", "Jai"), "Jai", -1.0}});
   int hhoo = g.add("kl", {{hoo, "kl", 1.0}, {g.contract(hov, "ka", t1, "al", "kl"), "kl", 1.0}});
   int hhvo = g.add("ai", {{hvo, "ai", 1.0},
@@ -61,8 +61,8 @@ EnergyResidual build_energy_residual(Graph& g, int t1, int t2, int L, int h, int
                          {g.contract(Lhvo, "Jai", s, "J", "ai"), "ai", 2.0},
                          {g.contract(Lhvo, "Jam", Lhoo, "Jmi", "ai"), "ai", -1.0}});
   int Fvv = g.add("ab", {{hhvv, "ab", 1.0},
-                         {g.contract(Lhvv, "Jab", s, "J", "ab"), "ab", 2.0},
-                         {g.contract(Lhvo, "Jam", Lov, "Jmb", "ab"), "ab", -1.0}});
+                         {g.contract(Lhvv, "Jab", s, "J", "ab", 1.0, true), "ab", 2.0},
+                         {g.contract(Lhvo, "Jam", Lov, "Jmb", "ab", 1.0, true), "ab", -1.0}});
 
   // u_ij^ab = 2 t_ij^ab - t_ij^ba
   int u = g.add("ijab", {{t2, "ijab", 2.0}, {t2, "ijba", -1.0}});
@@ -79,10 +79,10 @@ EnergyResidual build_energy_residual(Graph& g, int t1, int t2, int L, int h, int
 
   // ---- singles
   int Z = g.contract(Lov, "Jkc", u, "kicd", "Jid", 1.0, true);
-  int A1 = g.contract(Lhvv, "Jad", Z, "Jid", "ai");
-  int Gooov = g.contract(Lhoo, "Jki", Lov, "Jlc", "kilc");
+  int A1 = g.contract(Lhvv, "Jad", Z, "Jid", "ai", 1.0, true);
+  int Gooov = g.contract(Lhoo, "Jki", Lov, "Jlc", "kilc", 1.0, true);
   int B1 = g.contract(u, "klac", Gooov, "kilc", "ai", 1.0, true);
-  int C1 = g.contract(u, "ikac", Fov, "kc", "ai");
+  int C1 = g.contract(u, "ikac", Fov, "kc", "ai", 1.0, true);
   r.O1 = g.add("ai", {{Fvo, "ai", 1.0}, {A1, "ai", 1.0}, {B1, "ai", -1.0}, {C1, "ai", 1.0}});
 
   // ---- doubles
@@ -91,10 +91,10 @@ EnergyResidual build_energy_residual(Graph& g, int t1, int t2, int L, int h, int
   int lad = g.ladder(t2, L);
   int Govvv = g.contract(Lov, "Jkc", Lvv, "Jbd", "kcbd", 1.0, true);
   int W0 = g.contract(t2, "ijcd", Govvv, "kcbd", "ijkb", 1.0, true);
-  int l2 = g.contract(t1, "ak", W0, "ijkb", "ijab");
-  int l3 = g.contract(t1, "bl", W0, "jila", "ijab");
+  int l2 = g.contract(t1, "ak", W0, "ijkb", "ijab", 1.0, true);
+  int l3 = g.contract(t1, "bl", W0, "jila", "ijab", 1.0, true);
   int Zl = g.contract(t2, "ijcd", Govov, "klcd", "ijkl", 1.0, true);
-  int l4 = g.contract(g.contract(t1, "ak", Zl, "ijkl", "ijal"), "ijal", t1, "bl", "ijab");
+  int l4 = g.contract(g.contract(t1, "ak", Zl, "ijkl", "ijal", 1.0, true), "ijal", t1, "bl", "ijab", 1.0, true);
   // hole-hole ladder
   int Goooo = g.contract(Lhoo, "Jki", Lhoo, "Jlj", "kilj");
   int Bint = g.add("ijkl", {{Goooo, "kilj", 1.0}, {Zl, "ijkl", 1.0}});
@@ -116,8 +116,8 @@ EnergyResidual build_energy_residual(Graph& g, int t1, int t2, int L, int h, int
                           {g.contract(u, "klbd", Govov, "lkdc", "bc", 1.0, true), "bc", -1.0}});
   int Fooi = g.add("kj", {{Foo, "kj", 1.0},
                           {g.contract(u, "ljcd", Govov, "kldc", "kj", 1.0, true), "kj", 1.0}});
-  int E2 = g.add("ijab", {{g.contract(t2, "ijac", Fvvi, "bc", "ijab"), "ijab", 1.0},
-                          {g.contract(t2, "ikab", Fooi, "kj", "ijab"), "ijab", -1.0}});
+  int E2 = g.add("ijab", {{g.contract(t2, "ijac", Fvvi, "bc", "ijab", 1.0, true), "ijab", 1.0},
+                          {g.contract(t2, "ikab", Fooi, "kj", "ijab", 1.0, true), "ijab", -1.0}});
   int Pp = g.add("ijab", {{C2, "ijab", 1.0}, {D2, "ijab", 1.0}, {E2, "ijab", 1.0}});
   r.O2 = g.add("ijab", {{A2, "ijab", 1.0},
                         {lad, "ijab", 1.0},

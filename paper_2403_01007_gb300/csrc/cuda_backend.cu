@@ -23,7 +23,13 @@ namespace sccsd {
       throw CudaError(std::string(#call) + ": " + cudaGetErrorString(e_));            \
   } while (0)
 
+static long long g_launches = 0;  // kernel launches issued by this library
+
+void count_launch() { ++g_launches; }
+long long launch_count() { return g_launches; }
+
 static void check_launch(const char* what) {
+  ++g_launches;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw CudaError(std::string(what) + ": " + cudaGetErrorString(e));
 }
@@ -41,6 +47,30 @@ struct ViewArgs {
   int64_t ostr[kMaxRank];
   int64_t istr[kMaxRank];
 };
+
+// same with 32-bit index arithmetic (all extents and offsets below 2^31)
+struct ViewArgs32 {
+  int rank;
+  uint32_t dims[kMaxRank];
+  uint32_t ostr[kMaxRank];
+  uint32_t istr[kMaxRank];
+};
+
+__global__ void k_copy_view32(ViewArgs32 a, uint32_t total, double* __restrict__ out,
+                              const double* __restrict__ in, double coef, int acc) {
+  for (uint32_t lin = blockIdx.x * blockDim.x + threadIdx.x; lin < total;
+       lin += gridDim.x * blockDim.x) {
+    uint32_t r = lin, oo = 0, ii = 0;
+    for (int k = a.rank - 1; k >= 0; --k) {
+      uint32_t c = r % a.dims[k];
+      r /= a.dims[k];
+      oo += c * a.ostr[k];
+      ii += c * a.istr[k];
+    }
+    double v = coef * in[ii];
+    out[oo] = acc ? out[oo] + v : v;
+  }
+}
 
 __global__ void k_copy_view(ViewArgs a, int64_t total, double* __restrict__ out,
                             const double* __restrict__ in, double coef, int acc) {
@@ -213,6 +243,110 @@ __global__ void __launch_bounds__(256) k_dgemm_tn(int64_t M, int64_t N, int64_t 
   }
 }
 
+// Split-K variant for outputs with few tiles: blockIdx.z selects a K chunk,
+// part[z][m][n] receives the chunk's sum.
+__global__ void __launch_bounds__(256) k_dgemm_splitk(int64_t M, int64_t N, int64_t K, int64_t kc,
+                                                      const double* __restrict__ A,
+                                                      const double* __restrict__ B,
+                                                      double* __restrict__ part) {
+  __shared__ double As[DBK][DBM + 1];
+  __shared__ double Bs[DBK][DBN + 1];
+  const int64_t kbeg = (int64_t)blockIdx.z * kc;
+  const int64_t kend = (K < kbeg + kc) ? K : kbeg + kc;
+  const int64_t m0 = (int64_t)blockIdx.y * DBM, n0 = (int64_t)blockIdx.x * DBN;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (int64_t k0 = kbeg; k0 < kend; k0 += DBK) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int e = tid + 256 * q;
+      int row = e >> 4, kk = e & 15;
+      int64_t gk = k0 + kk;
+      int64_t gm = m0 + row, gn = n0 + row;
+      As[kk][row] = (gm < M && gk < kend) ? A[gm * K + gk] : 0.0;
+      Bs[kk][row] = (gn < N && gk < kend) ? B[gn * K + gk] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < DBK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double* P = part + (int64_t)blockIdx.z * M * N;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int64_t gm = m0 + ty + 16 * i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int64_t gn = n0 + tx + 16 * j;
+      if (gn < N) P[gm * N + gn] = acc[i][j];
+    }
+  }
+}
+
+// Outputs of at most 32 x 32 with a long contraction: 32x32 tile, K chunk per
+// block (blockIdx.z), each thread 2x2 outputs; partial tiles go to part[z].
+__global__ void __launch_bounds__(256) k_dgemm_small(int64_t M, int64_t N, int64_t K, int64_t kc,
+                                                     const double* __restrict__ A,
+                                                     const double* __restrict__ B,
+                                                     double* __restrict__ part) {
+  __shared__ double As[32][33];
+  __shared__ double Bs[32][33];
+  const int64_t kbeg = (int64_t)blockIdx.z * kc;
+  const int64_t kend = (K < kbeg + kc) ? K : kbeg + kc;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  double acc00 = 0, acc01 = 0, acc10 = 0, acc11 = 0;
+  for (int64_t k0 = kbeg; k0 < kend; k0 += 32) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int e = tid + 256 * q;
+      int row = e >> 5, kk = e & 31;
+      int64_t gk = k0 + kk;
+      As[kk][row] = (row < M && gk < kend) ? A[row * K + gk] : 0.0;
+      Bs[kk][row] = (row < N && gk < kend) ? B[row * K + gk] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+      double a0 = As[kk][ty], a1 = As[kk][ty + 16], b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+      acc00 = fma(a0, b0, acc00);
+      acc01 = fma(a0, b1, acc01);
+      acc10 = fma(a1, b0, acc10);
+      acc11 = fma(a1, b1, acc11);
+    }
+    __syncthreads();
+  }
+  double* P = part + (int64_t)blockIdx.z * M * N;
+  if (ty < M && tx < N) P[ty * N + tx] = acc00;
+  if (ty < M && tx + 16 < N) P[ty * N + tx + 16] = acc01;
+  if (ty + 16 < M && tx < N) P[(ty + 16) * N + tx] = acc10;
+  if (ty + 16 < M && tx + 16 < N) P[(ty + 16) * N + tx + 16] = acc11;
+}
+
+__global__ void k_sum_parts(int64_t n, int splits, const double* __restrict__ part, double alpha,
+                            double* __restrict__ C) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int z = 0; z < splits; ++z) s += part[(int64_t)z * n + e];
+    C[e] = alpha * s;
+  }
+}
+
 // Split-K dot products for outputs with few elements: partial sums per
 // (output, chunk), then a fixed-order final sum (deterministic).
 __global__ void k_dot_partial(int64_t M, int64_t N, int64_t K, const double* __restrict__ A,
@@ -261,6 +395,10 @@ class CudaBackend : public Backend {
   const double* G_src = nullptr;
   std::unique_ptr<TcGemm> tc;
   TcOperand G_tc;
+  bool prof = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  double prof_ms = 0.0;
+  long long prof_calls = 0, launches0 = 0;
 
   CudaBackend(void* stream, int prec) : st((cudaStream_t)stream), precision(prec) {
     int dev = 0;
@@ -268,6 +406,10 @@ class CudaBackend : public Backend {
     if (precision != 0) tc = std::make_unique<TcGemm>(st, precision);
   }
   ~CudaBackend() override {
+    for (auto& e : ev) {
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
     for (double* p : slots)
       if (p) cudaFree(p);
     if (G) cudaFree(G);
@@ -306,7 +448,10 @@ class CudaBackend : public Backend {
     }
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
   }
-  void sync() override { CK(cudaStreamSynchronize(st)); }
+  void sync() override {
+    CK(cudaStreamSynchronize(st));
+    if (tc) tc->check_error();
+  }
   void fill(double* p, int64_t n, double v) override {
     if (n <= 0) return;
     k_fill<<<grid_for(n, 256), 256, 0, st>>>(p, n, v);
@@ -371,6 +516,24 @@ class CudaBackend : public Backend {
       check_launch("copy_transpose");
       return;
     }
+    int64_t omax = 0, imax = 0;
+    for (int k = 0; k < r; ++k) {
+      omax += (d[k] - 1) * os[k];
+      imax += (d[k] - 1) * is[k];
+    }
+    if (total < (1LL << 31) && omax < (1LL << 31) && imax < (1LL << 31)) {
+      ViewArgs32 a;
+      a.rank = r;
+      for (int k = 0; k < r; ++k) {
+        a.dims[k] = (uint32_t)d[k];
+        a.ostr[k] = (uint32_t)os[k];
+        a.istr[k] = (uint32_t)is[k];
+      }
+      k_copy_view32<<<grid_for(total, 256), 256, 0, st>>>(a, (uint32_t)total, out, in, coef,
+                                                           acc ? 1 : 0);
+      check_launch("copy_view32");
+      return;
+    }
     ViewArgs a;
     a.rank = r;
     for (int k = 0; k < r; ++k) {
@@ -399,6 +562,35 @@ class CudaBackend : public Backend {
       k_dot_final<<<(unsigned)((nb * M * N + 127) / 128), 128, 0, st>>>(nb * M * N, chunks, part,
                                                                        alpha, C);
       check_launch("dot_final");
+      return;
+    }
+    if (nb == 1 && M <= 32 && N <= 32 && K >= 4096) {
+      int64_t splits = std::min<int64_t>(1216, (K + 1023) / 1024);
+      int64_t kc = (K + splits - 1) / splits;
+      kc = (kc + 31) / 32 * 32;
+      splits = (K + kc - 1) / kc;
+      double* part = scratch(7, splits * M * N);
+      k_dgemm_small<<<dim3(1, 1, (unsigned)splits), 256, 0, st>>>(M, N, K, kc, A, B, part);
+      check_launch("dgemm_small");
+      k_sum_parts<<<grid_for(M * N, 256), 256, 0, st>>>(M * N, (int)splits, part, alpha, C);
+      check_launch("sum_parts");
+      return;
+    }
+    const int64_t tiles = nb * ((M + DBM - 1) / DBM) * ((N + DBN - 1) / DBN);
+    if (nb == 1 && tiles < 2 * 152 && K >= 4096) {
+      // split K so that the grid fills the GPU; partial tiles are summed in a
+      // fixed order afterwards (deterministic)
+      int64_t splits = std::min<int64_t>((4 * 152 + tiles - 1) / tiles, K / 1024);
+      splits = std::max<int64_t>(2, std::min<int64_t>(splits, 64));
+      int64_t kc = (K + splits - 1) / splits;
+      kc = (kc + DBK - 1) / DBK * DBK;
+      splits = (K + kc - 1) / kc;
+      double* part = scratch(7, splits * M * N);
+      dim3 grid((unsigned)((N + DBN - 1) / DBN), (unsigned)((M + DBM - 1) / DBM), (unsigned)splits);
+      k_dgemm_splitk<<<grid, 256, 0, st>>>(M, N, K, kc, A, B, part);
+      check_launch("dgemm_splitk");
+      k_sum_parts<<<grid_for(M * N, 256), 256, 0, st>>>(M * N, (int)splits, part, alpha, C);
+      check_launch("sum_parts");
       return;
     }
     for (int64_t b0 = 0; b0 < nb; b0 += 65535) {
@@ -453,13 +645,55 @@ class CudaBackend : public Backend {
     }
     if (!G) G = alloc(vv * vv);
     double* Gp = scratch(4, vv * vv);  // Gp[(ac)][(bd)]
-    dgemm(1, vv, vv, J, 1.0, Lt, Lt, Gp);
+    gemm_tn(1, vv, vv, J, 1.0, Lt, Lt, Gp, true);
     // G[a][b][c][d] = Gp[a][c][b][d]
     int64_t dims[4] = {v, v, v, v};
     int64_t ostr[4] = {v * vv, vv, v, 1};
     int64_t istr[4] = {v * vv, v, vv, 1};
     copy_view(4, dims, G, ostr, Gp, istr, 1.0, false);
     if (tc) tc->prepare_operand(G, vv, vv, G_tc);
+  }
+
+  void* record_event() override {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    CK(cudaEventRecord(e, st));
+    return (void*)e;
+  }
+  double elapsed_ms(void* a, void* b) override {
+    CK(cudaEventSynchronize((cudaEvent_t)b));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, (cudaEvent_t)a, (cudaEvent_t)b));
+    cudaEventDestroy((cudaEvent_t)a);
+    cudaEventDestroy((cudaEvent_t)b);
+    return ms;
+  }
+
+  void profile(bool enable) override {
+    sync();
+    for (auto& e : ev) {
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+    ev.clear();
+    prof = enable;
+    prof_ms = 0.0;
+    prof_calls = 0;
+    launches0 = g_launches;
+  }
+  void profile_read(double* ms, long long* calls, long long* launches) override {
+    sync();
+    for (auto& e : ev) {
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, e.first, e.second));
+      prof_ms += t;
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+    ev.clear();
+    if (ms) *ms = prof_ms;
+    if (calls) *calls = prof_calls;
+    if (launches) *launches = g_launches - launches0;
   }
 
   void ladder(const Graph& g, const double* L, int64_t ver, const double* X, double* Y) override {
@@ -469,12 +703,22 @@ class CudaBackend : public Backend {
       G_src = L;
     }
     const int64_t o = g.o, v = g.v, vv = v * v;
-    // Y[(ij)][(ab)] = sum_(cd) X[(ij)][(cd)] G[(ab)][(cd)]
-    if (tc && precision != 0) {
-      tc->gemm_prepared_b(o * o, vv, vv, 1.0, X, G_tc, Y);
-      return;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (prof) {
+      CK(cudaEventCreate(&e0));
+      CK(cudaEventCreate(&e1));
+      CK(cudaEventRecord(e0, st));
     }
-    dgemm(1, o * o, vv, vv, 1.0, X, G, Y);
+    // Y[(ij)][(ab)] = sum_(cd) X[(ij)][(cd)] G[(ab)][(cd)]
+    if (tc && precision != 0)
+      tc->gemm_prepared_b(o * o, vv, vv, 1.0, X, G_tc, Y, !prof);
+    else
+      dgemm(1, o * o, vv, vv, 1.0, X, G, Y);
+    if (prof) {
+      CK(cudaEventRecord(e1, st));
+      ev.push_back({e0, e1});
+      ++prof_calls;
+    }
   }
 
   void ladder_adj_l(const Graph& g, const double* L, const double* Yb, const double* X,

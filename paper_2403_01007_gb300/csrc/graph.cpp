@@ -2,6 +2,7 @@
 #include "graph.h"
 
 #include <algorithm>
+#include <cstdio>
 #include <stdexcept>
 
 #include "backend.h"
@@ -365,12 +366,46 @@ void Graph::run(const std::vector<int>& targets) {
     for (int x : op.in)
       if (t[x].kind == Kind::Input && !t[x].data)
         throw std::runtime_error("graph input '" + t[x].name + "' was never set");
+    void* e0 = trace ? be->record_event() : nullptr;
     exec(op);
+    if (trace) {
+      void* e1 = be->record_event();
+      op.trace_ms += be->elapsed_ms(e0, e1);
+      op.trace_calls += 1;
+    }
     op.seen.resize(op.in.size());
     for (size_t k = 0; k < op.in.size(); ++k) op.seen[k] = t[op.in[k]].version;
     op.ran = true;
     touch(op.out);
   }
+}
+
+std::string Graph::trace_report(int top) {
+  std::vector<size_t> idx;
+  double total = 0.0;
+  for (size_t i = 0; i < ops.size(); ++i)
+    if (ops[i].trace_calls) {
+      idx.push_back(i);
+      total += ops[i].trace_ms;
+    }
+  std::sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return ops[a].trace_ms > ops[b].trace_ms; });
+  static const char* names[] = {"contract", "add", "slice", "embed", "ladder", "ladder_adj_l"};
+  std::string out = "op trace: total " + std::to_string(total) + " ms\n";
+  for (int k = 0; k < top && k < (int)idx.size(); ++k) {
+    const Op& op = ops[idx[k]];
+    char line[512];
+    std::string dims;
+    for (int x : op.in) {
+      dims += "[";
+      for (auto d : t[x].dims) dims += std::to_string(d) + ",";
+      dims += "]";
+    }
+    snprintf(line, sizeof line, "%8.3f ms %6lld x  op%-5zu %-12s %s,%s->%s tc=%d %s\n", op.trace_ms,
+             (long long)op.trace_calls, idx[k], names[(int)op.kind], op.la.c_str(), op.lb.c_str(),
+             op.lc.c_str(), (int)op.tc, dims.c_str());
+    out += line;
+  }
+  return out;
 }
 
 void Graph::exec(Op& op) {

@@ -55,6 +55,8 @@ struct Op {
   // execution memo
   std::vector<int64_t> seen;
   bool ran = false;
+  double trace_ms = 0.0;
+  int64_t trace_calls = 0;
 };
 
 class Backend;
@@ -106,6 +108,10 @@ class Graph {
   // whose inputs did not change since their last execution.
   void run(const std::vector<int>& targets);
   double* data(int id) { return t[id].data; }
+  // Tracing: when enabled, every executed op is bracketed by events and its
+  // time accumulated per op; trace_report() lists the most expensive ops.
+  bool trace = false;
+  std::string trace_report(int top = 40);
 
  private:
   int new_tensor(const std::vector<int64_t>& dims, Kind k);

@@ -31,8 +31,10 @@ class TcGemm {
   void gemm(int64_t nb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
             const double* B, double* C);
   void prepare_operand(const double* X, int64_t rows, int64_t K, TcOperand& out);
+  // check: read back the pipeline error flag (synchronises the stream)
   void gemm_prepared_b(int64_t M, int64_t N, int64_t K, double alpha, const double* A,
-                       const TcOperand& B, double* C);
+                       const TcOperand& B, double* C, bool check = true);
+  void check_error();
   void release(TcOperand& op);
   int slices() const { return nslices_; }
 
@@ -40,7 +42,6 @@ class TcGemm {
   void convert(const double* X, int64_t rows, int64_t K, TcOperand& out);
   void run(const TcOperand& A, int sa, const TcOperand& B, int sb, int64_t M, int64_t N,
            double alpha, double* C, bool accumulate);
-  void check_error();
   cudaStream_t st_;
   int nslices_;
   TcOperand a_tmp_, b_tmp_;

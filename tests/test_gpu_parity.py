@@ -58,6 +58,18 @@ def test_tc_gemm_split_accuracy(B):
     assert err3 < 1e-5
 
 
+def test_fp64_gemm_split_k(B):
+    """Few output tiles and a long contraction take the split-K path."""
+    rng = np.random.default_rng(7)
+    for (M, N, K) in [(100, 30, 50000), (200, 21, 132600), (1, 1, 9000)]:
+        A = rng.normal(size=(M, K))
+        Bm = rng.normal(size=(N, K))
+        C = torch.empty((M, N), dtype=torch.float64, device="cuda:0")
+        B.gemm_tn(dev(A), dev(Bm), C, alpha=0.5, precision="fp64")
+        ref = 0.5 * A @ Bm.T
+        assert np.abs(C.cpu().numpy() - ref).max() < 1e-12 * np.abs(ref).max() * np.sqrt(K)
+
+
 # ----------------------------------------------------------------- FP64 parity
 
 def run_all(B, o, v, J, sd, seed, precision="fp64", scc=False, on_device=False):
