@@ -110,6 +110,27 @@ int sccsd_profile(sccsd_ctx* ctx, int enable);
 int sccsd_profile_read(sccsd_ctx* ctx, double* ladder_ms, long long* ladder_calls,
                        double* ladder_flops, long long* launches);
 
+/* The same FP64 contraction, C[m][n] = alpha * sum_k A[m][k] B[n][k], for
+ * callers that must not trigger device allocations: applications that give
+ * all device memory to their own pool allocator up front and forbid further
+ * cudaMalloc calls, and latency-critical callers that cannot take the implicit
+ * device synchronisation of cudaMalloc/cudaFree. (The paper has no
+ * counterpart; this is an interface of this library.)
+ * It calls no cudaMalloc, cudaFree or allocating library routine: the split-K
+ * partial sums live in a file-scope device array of
+ * sccsd_gemm_tn_noalloc_capacity() doubles (8 MiB), which every device that
+ * loads the library holds until exit. The first call on a device looks up that
+ * array's device address (with the device current), so make it before any
+ * stream capture. M*N above the capacity is rejected with SCCSD_EINVAL; larger
+ * K only lowers the number of K chunks. A, B and C must be device memory.
+ * All calls share the one array: calls that overlap on the GPU (two streams,
+ * two host threads) race on it, so serialise them. Every partial sum is written
+ * before it is read, so stale contents from the previous call do no harm.
+ * Returns after the stream has finished the call's work. */
+int sccsd_gemm_tn_noalloc(long long M, long long N, long long K, double alpha, const double* A,
+                          const double* B, double* C, void* stream);
+long long sccsd_gemm_tn_noalloc_capacity(void);
+
 /* Size of a packed vector. */
 long long sccsd_dim(int o, int v);
 const char* sccsd_last_error(sccsd_ctx* ctx);

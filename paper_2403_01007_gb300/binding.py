@@ -35,6 +35,11 @@ def _declare(lib):
     lib.sccsd_profile.restype = ctypes.c_int
     lib.sccsd_profile_read.argtypes = [_dp, _dp, _dp, _dp, _dp]
     lib.sccsd_profile_read.restype = ctypes.c_int
+    lib.sccsd_gemm_tn_noalloc.argtypes = [ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong,
+                                          ctypes.c_double, _dp, _dp, _dp, _dp]
+    lib.sccsd_gemm_tn_noalloc.restype = ctypes.c_int
+    lib.sccsd_gemm_tn_noalloc_capacity.argtypes = []
+    lib.sccsd_gemm_tn_noalloc_capacity.restype = ctypes.c_longlong
     lib.sccsd_dim.argtypes = [ctypes.c_int, ctypes.c_int]
     lib.sccsd_dim.restype = ctypes.c_longlong
     lib.sccsd_last_error.argtypes = [_dp]
@@ -100,6 +105,17 @@ def gemm_tn(A, B, C, alpha=1.0, precision="fp64", lib=None):
     N = B.shape[0]
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     rc = lib.sccsd_gemm_tn(prec, M, N, K, float(alpha), _ptr(A), _ptr(B), _ptr(C), None)
+    if rc != 0:
+        raise SccsdError(rc, lib.sccsd_strerror(rc).decode())
+    return C
+
+
+def gemm_tn_noalloc(A, B, C, alpha=1.0, lib=None):
+    """FP64 C = alpha * A @ B.T on device tensors without any device allocation."""
+    lib = lib or load()
+    M, K = A.shape
+    N = B.shape[0]
+    rc = lib.sccsd_gemm_tn_noalloc(M, N, K, float(alpha), _ptr(A), _ptr(B), _ptr(C), None)
     if rc != 0:
         raise SccsdError(rc, lib.sccsd_strerror(rc).decode())
     return C

@@ -13,7 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "lib")
 OBJ = os.path.join(HERE, "lib", "obj")
-SOURCES = ["graph.cpp", "ccsd_graph.cpp", "api.cpp", "cuda_backend.cu", "tc_gemm.cu"]
+SOURCES = ["graph.cpp", "ccsd_graph.cpp", "api.cpp", "cuda_backend.cu", "tc_gemm.cu",
+           "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
