@@ -276,7 +276,7 @@ def main():
                          f"scaled by the dense-flop ratio to o=21 v=200 J=663"}
 
     peak = peaks.get("bf16_tflops_sustained", 1700.0)
-    slices = {"bf16x3": 6, "bf16": 1, "fp64": 1}[args.precision]
+    slices = {"bf16x3": 3, "bf16": 1, "fp64": 1}[args.precision]
     achieved = lad_flops / (lad_ms / 1e3) / 1e12 if lad_ms > 0 else None
     if args.precision == "fp64":
         roof = {"bound": "alu", "achieved": achieved, "peak": 1.2, "unit": "TFLOP/s",

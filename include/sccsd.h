@@ -47,10 +47,11 @@ enum {
 
 /* Precision of the tensor-core-eligible contractions (ladder, rings,
  * integral products). SCCSD_FP64: all arithmetic in FP64 on CUDA cores.
- * SCCSD_BF16X3: each FP64 operand split into three BF16 slices (each the BF16
- * rounding of what the previous slices left over), the six leading slice
- * products on tcgen05 tensor cores with FP32 accumulation, summed in FP64
- * (about FP32 accuracy). SCCSD_BF16: one BF16 slice per operand. */
+ * SCCSD_BF16X3: each FP64 operand split into two BF16 slices x = x0 + x1 (x1
+ * the BF16 rounding of x - x0), the three products x0 y0 + x0 y1 + x1 y0 on
+ * tcgen05 tensor cores with FP32 accumulation, summed in FP64 (about 16
+ * significant bits per product; FP32 accumulation over long contractions then
+ * dominates the error). SCCSD_BF16: one BF16 slice per operand. */
 enum { SCCSD_FP64 = 0, SCCSD_BF16X3 = 1, SCCSD_BF16 = 2 };
 
 /* Create a context for one synthetic system (sizes, eps, L as above).
@@ -103,7 +104,8 @@ int sccsd_gemm_tn(int precision, long long M, long long N, long long K, double a
  * every particle-particle ladder contraction (o^2 v^4 part) with CUDA events
  * on the context's stream; 0 stops it. sccsd_profile_read returns the summed
  * ladder time in ms, the number of ladder contractions, their algorithmic
- * flop count (2 o^2 v^4 each) and the number of kernels this library
+ * flop count (2 o^2 v^4 per trial vector; trial vectors are batched up to 8
+ * per contraction) and the number of kernels this library
  * launched since the reset (any output may be NULL). Timing adds one stream
  * synchronisation per read. */
 int sccsd_profile(sccsd_ctx* ctx, int enable);

@@ -1,4 +1,5 @@
 // C ABI of the SCCSD hot path: contexts, graph assembly and marshalling.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -20,9 +21,20 @@ std::unique_ptr<Backend> make_backend(void* stream, int precision);
 
 // One graph holding the residual, both Jacobian transformations and the
 // densities, with or without the SCC X3 terms.
+struct RightSec {
+  int R1, R2, sig1, sig2, etaR;
+};
+struct LeftSec {
+  int Lb1, Lb2, lt1, lt2;
+};
+
 struct Model {
   Graph g;
   bool scc = false;
+  Graph::Ranges fwd;
+  std::vector<int> vol_inputs;
+  std::map<int64_t, RightSec> right;  // batched right transformations by batch size
+  std::map<int64_t, LeftSec> left;
   int t1, t2, L, h, delta;
   int R1, R2, Lb1, Lb2;
   int zeta = -1, Ra1 = -1, Ra2 = -1, Rb1 = -1, Rb2 = -1, t2zero = -1;
@@ -80,6 +92,7 @@ static std::unique_ptr<Model> build_model(Backend* be, int o, int v, int J, bool
                               {g.contract(M->zeta, "", d2, "ijab", "ijab"), "ijab", 1.0}});
   }
   Graph::Ranges fwd = {{0, g.ops.size()}};
+  M->fwd = fwd;
 
   // right transformation: forward-mode derivative along R
   size_t rb = g.ops.size();
@@ -112,7 +125,52 @@ static std::unique_ptr<Model> build_model(Backend* be, int o, int v, int J, bool
                         {M->h, M->L}, dr);
   M->D1 = dadj[M->h];
   M->Gam = dadj[M->L];
+  M->vol_inputs = {M->R1, M->R2, M->Lb1, M->Lb2, M->s_l0r0, M->s_l0, M->s_r0};
+  g.set_volatile_inputs(M->vol_inputs);
   return M;
+}
+
+// sigma = A R for nb trial vectors at once (forward mode with a batch label)
+static RightSec& right_section(Model& M, int64_t nb) {
+  auto it = M.right.find(nb);
+  if (it != M.right.end()) return it->second;
+  Graph& g = M.g;
+  const int64_t o = g.o, v = g.v;
+  RightSec S;
+  S.R1 = g.input({nb, v, o}, "R1b");
+  S.R2 = g.input({nb, o, o, v, v}, "R2b");
+  auto tan = g.tangent({{M.t1, S.R1}, {M.t2, S.R2}}, M.fwd, nb);
+  auto pick = [&](int id, std::vector<int64_t> d) {
+    auto f = tan.find(id);
+    if (f != tan.end()) return f->second;
+    d.insert(d.begin(), nb);
+    return g.zero(d);
+  };
+  S.sig1 = pick(M.er.O1, g.t[M.er.O1].dims);
+  S.sig2 = pick(M.er.O2, g.t[M.er.O2].dims);
+  S.etaR = pick(M.er.E0, g.t[M.er.E0].dims);
+  M.vol_inputs.push_back(S.R1);
+  M.vol_inputs.push_back(S.R2);
+  g.set_volatile_inputs(M.vol_inputs);
+  return M.right[nb] = S;
+}
+
+// sigma = A^T L for nb bras at once (reverse mode with a batch label)
+static LeftSec& left_section(Model& M, int64_t nb) {
+  auto it = M.left.find(nb);
+  if (it != M.left.end()) return it->second;
+  Graph& g = M.g;
+  const int64_t o = g.o, v = g.v;
+  LeftSec S;
+  S.Lb1 = g.input({nb, v, o}, "Lbar1b");
+  S.Lb2 = g.input({nb, o, o, v, v}, "Lbar2b");
+  auto adj = g.adjoint({{M.er.O1, S.Lb1}, {M.er.O2, S.Lb2}}, {M.t1, M.t2}, M.fwd, nb);
+  S.lt1 = adj[M.t1];
+  S.lt2 = adj[M.t2];
+  M.vol_inputs.push_back(S.Lb1);
+  M.vol_inputs.push_back(S.Lb2);
+  g.set_volatile_inputs(M.vol_inputs);
+  return M.left[nb] = S;
 }
 
 }  // namespace sccsd
@@ -131,6 +189,7 @@ struct sccsd_ctx {
   double* stage = nullptr;  // one packed vector
   double* stage2 = nullptr;
   double e_hf = 0.0;
+  int max_batch = 8;  // trial vectors per batched pass
   std::string err;
   ~sccsd_ctx() {
     if (getenv("SCCSD_TRACE")) {
@@ -210,6 +269,36 @@ void load_packed(sccsd_ctx* c, Graph& g, const double* src, int x1, int x2, bool
   c->be->unpack(d, c->o, c->v, input_buffer(g, x1), input_buffer(g, x2), bra);
   g.touch(x1);
   g.touch(x2);
+}
+
+// nb packed vectors (host or device) -> batched graph inputs [nb][...]
+void load_packed_batch(sccsd_ctx* c, Graph& g, const double* src, int64_t nb, int x1, int x2,
+                       bool bra) {
+  const int64_t ov = (int64_t)c->o * c->v, oovv = ov * ov;
+  double* b1 = input_buffer(g, x1);
+  double* b2 = input_buffer(g, x2);
+  const bool dev = c->be->is_device(src);
+  for (int64_t k = 0; k < nb; ++k) {
+    const double* d = src + k * c->dim;
+    if (!dev) {
+      c->be->upload(c->stage, d, c->dim, false);
+      d = c->stage;
+    }
+    c->be->unpack(d, c->o, c->v, b1 + k * ov, b2 + k * oovv, bra);
+  }
+  g.touch(x1);
+  g.touch(x2);
+}
+
+void store_packed_batch(sccsd_ctx* c, Graph& g, int64_t nb, int y1, int y2, double* dst, bool bra) {
+  const int64_t ov = (int64_t)c->o * c->v, oovv = ov * ov;
+  if (g.is_zero(y1) || g.is_zero(y2)) throw std::runtime_error("zero output node");
+  const bool dev = c->be->is_device(dst);
+  for (int64_t k = 0; k < nb; ++k) {
+    double* d = dev ? dst + k * c->dim : c->stage2;
+    c->be->pack(g.data(y1) + k * ov, g.data(y2) + k * oovv, c->o, c->v, d, bra);
+    if (!dev) c->be->download(dst + k * c->dim, d, c->dim, false);
+  }
 }
 
 void store_packed(sccsd_ctx* c, Graph& g, int y1, int y2, double* dst, bool bra) {
@@ -366,11 +455,13 @@ int sccsd_jacobian_right(sccsd_ctx* c, int nvec, const double* R, double* sigma,
   return guarded(c, [&] {
     Model& m = *c->cur;
     std::vector<double> er(nvec, 0.0);
-    for (int k = 0; k < nvec; ++k) {
-      load_packed(c, m.g, R + (int64_t)k * c->dim, m.R1, m.R2, false);
-      m.g.run({m.sig1, m.sig2, m.etaR});
-      store_packed(c, m.g, m.sig1, m.sig2, sigma + (int64_t)k * c->dim, false);
-      if (etaR) er[k] = get_scalar(c, m.g, m.etaR);
+    for (int k0 = 0; k0 < nvec; k0 += c->max_batch) {
+      const int nb = std::min(c->max_batch, nvec - k0);
+      RightSec& S = right_section(m, nb);
+      load_packed_batch(c, m.g, R + (int64_t)k0 * c->dim, nb, S.R1, S.R2, false);
+      m.g.run({S.sig1, S.sig2, S.etaR});
+      store_packed_batch(c, m.g, nb, S.sig1, S.sig2, sigma + (int64_t)k0 * c->dim, false);
+      if (etaR && !m.g.is_zero(S.etaR)) c->be->download(er.data() + k0, m.g.data(S.etaR), nb, false);
     }
     if (etaR) {
       if (c->be->is_device(etaR))
@@ -388,10 +479,12 @@ int sccsd_jacobian_left(sccsd_ctx* c, int nvec, const double* L, double* sigma) 
   if (!c->cur) return fail(c, SCCSD_ESTATE, "call sccsd_residual first");
   return guarded(c, [&] {
     Model& m = *c->cur;
-    for (int k = 0; k < nvec; ++k) {
-      load_packed(c, m.g, L + (int64_t)k * c->dim, m.Lb1, m.Lb2, true);
-      m.g.run({m.lt1, m.lt2});
-      store_packed(c, m.g, m.lt1, m.lt2, sigma + (int64_t)k * c->dim, true);
+    for (int k0 = 0; k0 < nvec; k0 += c->max_batch) {
+      const int nb = std::min(c->max_batch, nvec - k0);
+      LeftSec& S = left_section(m, nb);
+      load_packed_batch(c, m.g, L + (int64_t)k0 * c->dim, nb, S.Lb1, S.Lb2, true);
+      m.g.run({S.lt1, S.lt2});
+      store_packed_batch(c, m.g, nb, S.lt1, S.lt2, sigma + (int64_t)k0 * c->dim, true);
     }
     c->be->sync();
   });
@@ -446,10 +539,10 @@ int sccsd_profile_read(sccsd_ctx* c, double* ladder_ms, long long* ladder_calls,
   if (!c) return SCCSD_EINVAL;
   return guarded(c, [&] {
     long long calls = 0;
-    c->be->profile_read(ladder_ms, &calls, launches);
+    double fl = 0.0;
+    c->be->profile_read(ladder_ms, &calls, &fl, launches);
     if (ladder_calls) *ladder_calls = calls;
-    const double oo = (double)c->o * c->o, vv = (double)c->v * c->v;
-    if (ladder_flops) *ladder_flops = 2.0 * oo * vv * vv * (double)calls;
+    if (ladder_flops) *ladder_flops = fl;
   });
 }
 

@@ -16,6 +16,24 @@ struct OomError : std::runtime_error {
 
 class Graph;
 
+// A strided (batch, row, k) matrix view of a tensor: element (b, r, k) is at
+// p + b*sb + R(r) + K(k), with R(r) = (r / n2r) * sr1 + (r % n2r) * sr2 when
+// n2r > 0 and R(r) = r * sr2 otherwise (K(k) likewise with n2k, sk1, sk2).
+struct MatView {
+  const double* p = nullptr;
+  int64_t sb = 0;
+  int64_t n2r = 0, sr1 = 0, sr2 = 0;
+  int64_t n2k = 0, sk1 = 0, sk2 = 1;
+  static MatView dense(const double* p, int64_t rows, int64_t K) {
+    MatView v;
+    v.p = p;
+    v.sb = rows * K;
+    v.sr2 = K;
+    v.sk2 = 1;
+    return v;
+  }
+};
+
 class Backend {
  public:
   virtual ~Backend() {}
@@ -37,15 +55,38 @@ class Backend {
   // out[i] (+)= coef * in[i] over a rank-r index box; both sides strided.
   virtual void copy_view(int rank, const int64_t* dims, double* out, const int64_t* ostr,
                          const double* in, const int64_t* istr, double coef, bool accumulate) = 0;
-  // C[b][m][n] = alpha * sum_k A[b][m][k] B[b][n][k]; C dense and overwritten.
+  // C[b][m][n] = alpha * sum_k A(b,m,k) B(b,n,k); C dense and overwritten.
   // tc: the contraction may use tensor cores when the precision mode allows.
-  virtual void gemm_tn(int64_t batch, int64_t M, int64_t N, int64_t K, double alpha,
-                       const double* A, const double* B, double* C, bool tc) = 0;
+  virtual void gemm_view(int64_t batch, int64_t M, int64_t N, int64_t K, double alpha,
+                         const MatView& A, const MatView& B, double* C, bool tc) = 0;
+  void gemm_tn(int64_t batch, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+               const double* B, double* C, bool tc) {
+    gemm_view(batch, M, N, K, alpha, MatView::dense(A, M, K), MatView::dense(B, N, K), C, tc);
+  }
+  // Pool of recyclable device buffers keyed by exact size.
+  virtual double* pool_get(int64_t n) = 0;
+  virtual void pool_put(double* p, int64_t n) = 0;
+  // Tensor-core routing with a cache of converted operands. A key names an
+  // operand (graph, node, layout) at a version; the backend keeps its
+  // tensor-core form and reuses it while the version is unchanged.
+  struct OperandKey {
+    const void* graph;
+    int id;
+    int64_t version;
+    uint64_t layout;
+  };
+  virtual bool tc_will_use(int64_t nb, int64_t M, int64_t N, int64_t K) = 0;
+  virtual bool tc_cached(const OperandKey& k) = 0;
+  // A.p or B.p may be NULL when its key is cached.
+  virtual void gemm_tc_keyed(int64_t M, int64_t N, int64_t K, double alpha, const MatView& A,
+                             const OperandKey* ka, const MatView& B, const OperandKey* kb,
+                             double* C) = 0;
   // Reusable temporary device buffers (slot 0..7), grown on demand.
   virtual double* scratch(int slot, int64_t n) = 0;
   // Particle-particle ladder with the vv block of L (see Graph::ladder).
+  // rows = number of (ij) rows of X, o^2 times the batch size
   virtual void ladder(const Graph& g, const double* L, int64_t L_version, const double* X,
-                      double* Y) = 0;
+                      double* Y, int64_t rows) = 0;
   // Profiling: CUDA-event timing of the ladder contractions and a count of
   // kernel launches since the last reset.
   virtual void profile(bool enable) = 0;
@@ -53,7 +94,8 @@ class Backend {
   // elapsed milliseconds between two recorded events (synchronises).
   virtual void* record_event() = 0;
   virtual double elapsed_ms(void* a, void* b) = 0;
-  virtual void profile_read(double* ladder_ms, long long* ladder_calls, long long* launches) = 0;
+  virtual void profile_read(double* ladder_ms, long long* ladder_calls, double* ladder_flops,
+                            long long* launches) = 0;
   virtual void ladder_adj_l(const Graph& g, const double* L, const double* Ybar,
                             const double* X, double* out) = 0;
 };

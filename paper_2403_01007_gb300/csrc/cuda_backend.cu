@@ -6,11 +6,14 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <tuple>
 #include <memory>
 #include <string>
 #include <vector>
 
 #include "backend.h"
+#include "dgemm_view.cuh"
 #include "graph.h"
 #include "tc_gemm.h"
 
@@ -185,158 +188,6 @@ __global__ void k_pack(const double* __restrict__ t1, const double* __restrict__
 
 // ------------------------------------------------------------------ FP64 GEMM
 
-// C[b][m][n] = alpha * sum_k A[b][m][k] B[b][n][k], FP64 on CUDA cores.
-// 64x64 output tile per block, 256 threads with a 4x4 register tile each.
-constexpr int DBM = 64, DBN = 64, DBK = 16;
-
-__global__ void __launch_bounds__(256) k_dgemm_tn(int64_t M, int64_t N, int64_t K, double alpha,
-                                                  const double* __restrict__ A,
-                                                  const double* __restrict__ B,
-                                                  double* __restrict__ C) {
-  __shared__ double As[DBK][DBM + 1];
-  __shared__ double Bs[DBK][DBN + 1];
-  const int64_t bz = blockIdx.z;
-  A += bz * M * K;
-  B += bz * N * K;
-  C += bz * M * N;
-  const int64_t m0 = (int64_t)blockIdx.y * DBM, n0 = (int64_t)blockIdx.x * DBN;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  double acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-  for (int64_t k0 = 0; k0 < K; k0 += DBK) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      int e = tid + 256 * q;
-      int row = e >> 4, kk = e & 15;
-      int64_t gk = k0 + kk;
-      int64_t gm = m0 + row, gn = n0 + row;
-      As[kk][row] = (gm < M && gk < K) ? A[gm * K + gk] : 0.0;
-      Bs[kk][row] = (gn < N && gk < K) ? B[gn * K + gk] : 0.0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < DBK; ++kk) {
-      double a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    int64_t gm = m0 + ty + 16 * i;
-    if (gm >= M) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int64_t gn = n0 + tx + 16 * j;
-      if (gn < N) C[gm * N + gn] = alpha * acc[i][j];
-    }
-  }
-}
-
-// Split-K variant for outputs with few tiles: blockIdx.z selects a K chunk,
-// part[z][m][n] receives the chunk's sum.
-__global__ void __launch_bounds__(256) k_dgemm_splitk(int64_t M, int64_t N, int64_t K, int64_t kc,
-                                                      const double* __restrict__ A,
-                                                      const double* __restrict__ B,
-                                                      double* __restrict__ part) {
-  __shared__ double As[DBK][DBM + 1];
-  __shared__ double Bs[DBK][DBN + 1];
-  const int64_t kbeg = (int64_t)blockIdx.z * kc;
-  const int64_t kend = (K < kbeg + kc) ? K : kbeg + kc;
-  const int64_t m0 = (int64_t)blockIdx.y * DBM, n0 = (int64_t)blockIdx.x * DBN;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  double acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-  for (int64_t k0 = kbeg; k0 < kend; k0 += DBK) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      int e = tid + 256 * q;
-      int row = e >> 4, kk = e & 15;
-      int64_t gk = k0 + kk;
-      int64_t gm = m0 + row, gn = n0 + row;
-      As[kk][row] = (gm < M && gk < kend) ? A[gm * K + gk] : 0.0;
-      Bs[kk][row] = (gn < N && gk < kend) ? B[gn * K + gk] : 0.0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < DBK; ++kk) {
-      double a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-  double* P = part + (int64_t)blockIdx.z * M * N;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    int64_t gm = m0 + ty + 16 * i;
-    if (gm >= M) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int64_t gn = n0 + tx + 16 * j;
-      if (gn < N) P[gm * N + gn] = acc[i][j];
-    }
-  }
-}
-
-// Outputs of at most 32 x 32 with a long contraction: 32x32 tile, K chunk per
-// block (blockIdx.z), each thread 2x2 outputs; partial tiles go to part[z].
-__global__ void __launch_bounds__(256) k_dgemm_small(int64_t M, int64_t N, int64_t K, int64_t kc,
-                                                     const double* __restrict__ A,
-                                                     const double* __restrict__ B,
-                                                     double* __restrict__ part) {
-  __shared__ double As[32][33];
-  __shared__ double Bs[32][33];
-  const int64_t kbeg = (int64_t)blockIdx.z * kc;
-  const int64_t kend = (K < kbeg + kc) ? K : kbeg + kc;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  double acc00 = 0, acc01 = 0, acc10 = 0, acc11 = 0;
-  for (int64_t k0 = kbeg; k0 < kend; k0 += 32) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      int e = tid + 256 * q;
-      int row = e >> 5, kk = e & 31;
-      int64_t gk = k0 + kk;
-      As[kk][row] = (row < M && gk < kend) ? A[row * K + gk] : 0.0;
-      Bs[kk][row] = (row < N && gk < kend) ? B[row * K + gk] : 0.0;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int kk = 0; kk < 32; ++kk) {
-      double a0 = As[kk][ty], a1 = As[kk][ty + 16], b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
-      acc00 = fma(a0, b0, acc00);
-      acc01 = fma(a0, b1, acc01);
-      acc10 = fma(a1, b0, acc10);
-      acc11 = fma(a1, b1, acc11);
-    }
-    __syncthreads();
-  }
-  double* P = part + (int64_t)blockIdx.z * M * N;
-  if (ty < M && tx < N) P[ty * N + tx] = acc00;
-  if (ty < M && tx + 16 < N) P[ty * N + tx + 16] = acc01;
-  if (ty + 16 < M && tx < N) P[(ty + 16) * N + tx] = acc10;
-  if (ty + 16 < M && tx + 16 < N) P[(ty + 16) * N + tx + 16] = acc11;
-}
-
 __global__ void k_sum_parts(int64_t n, int splits, const double* __restrict__ part, double alpha,
                             double* __restrict__ C) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
@@ -345,39 +196,6 @@ __global__ void k_sum_parts(int64_t n, int splits, const double* __restrict__ pa
     for (int z = 0; z < splits; ++z) s += part[(int64_t)z * n + e];
     C[e] = alpha * s;
   }
-}
-
-// Split-K dot products for outputs with few elements: partial sums per
-// (output, chunk), then a fixed-order final sum (deterministic).
-__global__ void k_dot_partial(int64_t M, int64_t N, int64_t K, const double* __restrict__ A,
-                              const double* __restrict__ B, int64_t chunk, int chunks,
-                              double* __restrict__ part) {
-  const int64_t oidx = blockIdx.y;  // b*M*N + m*N + n
-  const int64_t n = oidx % N, bm = oidx / N;
-  const int64_t m = bm % M, b = bm / M;
-  const double* a = A + (b * M + m) * K;
-  const double* bb = B + (b * N + n) * K;
-  const int64_t k0 = (int64_t)blockIdx.x * chunk, k1 = (K < k0 + chunk) ? K : k0 + chunk;
-  double s = 0.0;
-  for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) s = fma(a[k], bb[k], s);
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-  __shared__ double ws[32];
-  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    s = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.0;
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-    if (threadIdx.x == 0) part[oidx * chunks + blockIdx.x] = s;
-  }
-}
-
-__global__ void k_dot_final(int64_t outs, int chunks, const double* __restrict__ part, double alpha,
-                            double* __restrict__ C) {
-  int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (o >= outs) return;
-  double s = 0.0;
-  for (int c = 0; c < chunks; ++c) s += part[o * chunks + c];
-  C[o] = alpha * s;
 }
 
 // ------------------------------------------------------------------ backend
@@ -397,8 +215,15 @@ class CudaBackend : public Backend {
   TcOperand G_tc;
   bool prof = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
-  double prof_ms = 0.0;
+  double prof_ms = 0.0, prof_flops = 0.0;
   long long prof_calls = 0, launches0 = 0;
+  std::map<int64_t, std::vector<double*>> pool;
+  struct CacheEntry {
+    int64_t version;
+    TcOperand op;
+  };
+  std::map<std::tuple<const void*, int, uint64_t>, CacheEntry> opcache;
+  TcOperand tmpA, tmpB;
 
   CudaBackend(void* stream, int prec) : st((cudaStream_t)stream), precision(prec) {
     int dev = 0;
@@ -406,6 +231,13 @@ class CudaBackend : public Backend {
     if (precision != 0) tc = std::make_unique<TcGemm>(st, precision);
   }
   ~CudaBackend() override {
+    if (tc) {
+      for (auto& kv : opcache) tc->release(kv.second.op);
+      tc->release(tmpA);
+      tc->release(tmpB);
+    }
+    for (auto& kv : pool)
+      for (double* p : kv.second) cudaFree(p);
     for (auto& e : ev) {
       cudaEventDestroy(e.first);
       cudaEventDestroy(e.second);
@@ -547,76 +379,121 @@ class CudaBackend : public Backend {
 
   void dgemm(int64_t nb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
              const double* B, double* C) {
+    dgemm_v(nb, M, N, K, alpha, MatView::dense(A, M, K), MatView::dense(B, N, K), C);
+  }
+
+  // FP64 contraction through strided views (see dgemm_view.cuh)
+  void dgemm_v(int64_t nb, int64_t M, int64_t N, int64_t K, double alpha, const MatView& A,
+               const MatView& B, double* C) {
     if (nb * M * N == 0) return;
     if (K == 0) {
       fill(C, nb * M * N, 0.0);
       return;
     }
-    if (nb * M * N <= 64 && K >= 4096) {
-      int chunks = (int)std::min<int64_t>(256, (K + 8191) / 8192);
-      int64_t chunk = (K + chunks - 1) / chunks;
-      double* part = scratch(7, nb * M * N * chunks);
-      k_dot_partial<<<dim3(chunks, (unsigned)(nb * M * N)), 256, 0, st>>>(M, N, K, A, B, chunk,
-                                                                          chunks, part);
-      check_launch("dot_partial");
-      k_dot_final<<<(unsigned)((nb * M * N + 127) / 128), 128, 0, st>>>(nb * M * N, chunks, part,
-                                                                       alpha, C);
-      check_launch("dot_final");
+    // FP64 FMAs are scarce on this part: shapes are routed so that padding
+    // wastes as few of them as possible
+    const int64_t outs = nb * M * N;
+    if (outs <= 4096 && K >= 512) {
+      int64_t chunks = std::max<int64_t>(1, std::min<int64_t>((4 * 152 + outs - 1) / outs, K / 2048));
+      int64_t kc = (K + chunks - 1) / chunks;
+      chunks = (K + kc - 1) / kc;
+      double* part = scratch(7, outs * chunks);
+      k_dot_view<<<dim3((unsigned)chunks, (unsigned)outs), 256, 0, st>>>(M, N, K, kc, (int)chunks,
+                                                                         A, B, part);
+      check_launch("dot_view");
+      k_dot_sum<<<(unsigned)((outs + 127) / 128), 128, 0, st>>>(outs, (int)chunks, part, alpha, C);
+      check_launch("dot_sum");
       return;
     }
-    if (nb == 1 && M <= 32 && N <= 32 && K >= 4096) {
-      int64_t splits = std::min<int64_t>(1216, (K + 1023) / 1024);
-      int64_t kc = (K + splits - 1) / splits;
-      kc = (kc + 31) / 32 * 32;
-      splits = (K + kc - 1) / kc;
-      double* part = scratch(7, splits * M * N);
-      k_dgemm_small<<<dim3(1, 1, (unsigned)splits), 256, 0, st>>>(M, N, K, kc, A, B, part);
-      check_launch("dgemm_small");
-      k_sum_parts<<<grid_for(M * N, 256), 256, 0, st>>>(M * N, (int)splits, part, alpha, C);
-      check_launch("sum_parts");
+    if (N == 1 || M == 1) {
+      // matrix-vector form; for M == 1 the roles swap (C^T has the same layout)
+      const MatView& Mv = (N == 1) ? A : B;
+      const MatView& Xv = (N == 1) ? B : A;
+      const int64_t rows = (N == 1) ? M : N;
+      const int wpr = Mv.sk2 == 1 ? 1 : 0;
+      int64_t threads = wpr ? rows * 32 : rows;
+      dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((threads + 255) / 256, 152 * 32)),
+                1, (unsigned)nb);
+      if (nb > 65535) throw std::runtime_error("gemv batch too large");
+      k_dgemv_view<<<grid, 256, 0, st>>>(rows, K, alpha, Mv, Xv, C, wpr);
+      check_launch("dgemv_view");
       return;
     }
-    const int64_t tiles = nb * ((M + DBM - 1) / DBM) * ((N + DBN - 1) / DBN);
-    if (nb == 1 && tiles < 2 * 152 && K >= 4096) {
-      // split K so that the grid fills the GPU; partial tiles are summed in a
-      // fixed order afterwards (deterministic)
-      int64_t splits = std::min<int64_t>((4 * 152 + tiles - 1) / tiles, K / 1024);
-      splits = std::max<int64_t>(2, std::min<int64_t>(splits, 64));
-      int64_t kc = (K + splits - 1) / splits;
-      kc = (kc + DBK - 1) / DBK * DBK;
-      splits = (K + kc - 1) / kc;
-      double* part = scratch(7, splits * M * N);
-      dim3 grid((unsigned)((N + DBN - 1) / DBN), (unsigned)((M + DBM - 1) / DBM), (unsigned)splits);
-      k_dgemm_splitk<<<grid, 256, 0, st>>>(M, N, K, kc, A, B, part);
-      check_launch("dgemm_splitk");
-      k_sum_parts<<<grid_for(M * N, 256), 256, 0, st>>>(M * N, (int)splits, part, alpha, C);
-      check_launch("sum_parts");
-      return;
-    }
-    for (int64_t b0 = 0; b0 < nb; b0 += 65535) {
-      int64_t bc = std::min<int64_t>(65535, nb - b0);
-      for (int64_t m0 = 0; m0 < M; m0 += 65535LL * DBM) {
-        int64_t mc = std::min<int64_t>(65535LL * DBM, M - m0);
-        dim3 grid((unsigned)((N + DBN - 1) / DBN), (unsigned)((mc + DBM - 1) / DBM), (unsigned)bc);
-        if (nb == 1) {
-          k_dgemm_tn<<<grid, 256, 0, st>>>(mc, N, K, alpha, A + m0 * K, B, C + m0 * N);
-        } else {
-          if (m0 != 0) throw std::runtime_error("batched GEMM with huge M");
-          k_dgemm_tn<<<grid, 256, 0, st>>>(M, N, K, alpha, A + b0 * M * K, B + b0 * N * K,
-                                           C + b0 * M * N);
-        }
-        check_launch("dgemm");
+    // tile shape: narrow tiles for skinny outputs
+    int shape = 0;  // 0: 64x64, 1: 32x32, 2: 32x64, 3: 64x32
+    if (M <= 32 && N <= 32)
+      shape = 1;
+    else if (M <= 32)
+      shape = 2;
+    else if (N <= 32)
+      shape = 3;
+    const int64_t bm = (shape == 1 || shape == 2) ? 32 : 64;
+    const int64_t bn = (shape == 1 || shape == 3) ? 32 : 64;
+    const int64_t bk = shape == 1 ? 32 : 16;
+    const int64_t tiles = ((M + bm - 1) / bm) * ((N + bn - 1) / bn);
+    auto launch = [&](dim3 grid, int64_t kc, double* o, int partial) {
+      switch (shape) {
+        case 1: k_dgemm_view<32, 32, 32><<<grid, 256, 0, st>>>(M, N, K, kc, alpha, A, B, o, partial); break;
+        case 2: k_dgemm_view<32, 64, 16><<<grid, 256, 0, st>>>(M, N, K, kc, alpha, A, B, o, partial); break;
+        case 3: k_dgemm_view<64, 32, 16><<<grid, 256, 0, st>>>(M, N, K, kc, alpha, A, B, o, partial); break;
+        default: k_dgemm_view<64, 64, 16><<<grid, 256, 0, st>>>(M, N, K, kc, alpha, A, B, o, partial);
       }
+      check_launch("dgemm_view");
+    };
+    if (nb == 1 && tiles < 2 * 152 && K >= 2048) {
+      // split K so that the grid fills the GPU; the partial tiles are summed
+      // in a fixed order afterwards (deterministic)
+      int64_t splits = std::min<int64_t>((4 * 152 + tiles - 1) / tiles, K / 512);
+      splits = std::max<int64_t>(2, std::min<int64_t>(splits, 1024));
+      int64_t kc = (K + splits - 1) / splits;
+      kc = (kc + bk - 1) / bk * bk;
+      splits = (K + kc - 1) / kc;
+      double* part = scratch(7, splits * M * N);
+      launch(dim3((unsigned)tiles, 1, (unsigned)splits), kc, part, 1);
+      k_sum_parts<<<grid_for(M * N, 256), 256, 0, st>>>(M * N, (int)splits, part, alpha, C);
+      check_launch("sum_parts");
+      return;
     }
+    if (nb > 65535) throw std::runtime_error("batched GEMM: batch too large");
+    if (tiles > (1LL << 31) - 1) throw std::runtime_error("GEMM: too many tiles");
+    launch(dim3((unsigned)tiles, 1, (unsigned)nb), 0, C, 0);
   }
 
-  void gemm_tn(int64_t nb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
-               const double* B, double* C, bool use_tc) override {
+  void gemm_view(int64_t nb, int64_t M, int64_t N, int64_t K, double alpha, const MatView& A,
+                 const MatView& B, double* C, bool use_tc) override {
     if (use_tc && tc && tc->worthwhile(nb, M, N, K)) {
-      tc->gemm(nb, M, N, K, alpha, A, B, C);
+      gemm_tc_keyed(M, N, K, alpha, A, nullptr, B, nullptr, C);
       return;
     }
-    dgemm(nb, M, N, K, alpha, A, B, C);
+    dgemm_v(nb, M, N, K, alpha, A, B, C);
+  }
+
+  bool tc_will_use(int64_t nb, int64_t M, int64_t N, int64_t K) override {
+    return tc && tc->worthwhile(nb, M, N, K);
+  }
+  bool tc_cached(const OperandKey& k) override {
+    auto it = opcache.find(std::make_tuple(k.graph, k.id, k.layout));
+    return it != opcache.end() && it->second.version == k.version;
+  }
+  const TcOperand& tc_operand(const MatView& X, int64_t rows, int64_t K, const OperandKey* key,
+                              TcOperand& tmp) {
+    if (!key) {
+      tc->prepare_operand_view(X, rows, K, tmp);
+      return tmp;
+    }
+    CacheEntry& e = opcache[std::make_tuple(key->graph, key->id, key->layout)];
+    if (e.op.data && e.version == key->version && e.op.rows == rows && e.op.k == K) return e.op;
+    if (!X.p) throw std::runtime_error("tensor-core operand cache miss without data");
+    tc->prepare_operand_view(X, rows, K, e.op);
+    e.version = key->version;
+    return e.op;
+  }
+  void gemm_tc_keyed(int64_t M, int64_t N, int64_t K, double alpha, const MatView& A,
+                     const OperandKey* ka, const MatView& B, const OperandKey* kb,
+                     double* C) override {
+    const TcOperand& a = tc_operand(A, M, K, ka, tmpA);
+    const TcOperand& b = tc_operand(B, N, K, kb, tmpB);
+    tc->gemm_ops(M, N, alpha, a, b, C);
   }
 
   double* scratch(int slot, int64_t n) override {
@@ -669,6 +546,17 @@ class CudaBackend : public Backend {
     return ms;
   }
 
+  double* pool_get(int64_t n) override {
+    auto it = pool.find(n);
+    if (it != pool.end() && !it->second.empty()) {
+      double* p = it->second.back();
+      it->second.pop_back();
+      return p;
+    }
+    return alloc(n);
+  }
+  void pool_put(double* p, int64_t n) override { pool[n].push_back(p); }
+
   void profile(bool enable) override {
     sync();
     for (auto& e : ev) {
@@ -678,10 +566,11 @@ class CudaBackend : public Backend {
     ev.clear();
     prof = enable;
     prof_ms = 0.0;
+    prof_flops = 0.0;
     prof_calls = 0;
     launches0 = g_launches;
   }
-  void profile_read(double* ms, long long* calls, long long* launches) override {
+  void profile_read(double* ms, long long* calls, double* flops, long long* launches) override {
     sync();
     for (auto& e : ev) {
       float t = 0.f;
@@ -693,10 +582,12 @@ class CudaBackend : public Backend {
     ev.clear();
     if (ms) *ms = prof_ms;
     if (calls) *calls = prof_calls;
+    if (flops) *flops = prof_flops;
     if (launches) *launches = g_launches - launches0;
   }
 
-  void ladder(const Graph& g, const double* L, int64_t ver, const double* X, double* Y) override {
+  void ladder(const Graph& g, const double* L, int64_t ver, const double* X, double* Y,
+              int64_t rows) override {
     if (!G || ver != G_version || L != G_src) {
       build_ladder_integrals(g, L);
       G_version = ver;
@@ -709,15 +600,17 @@ class CudaBackend : public Backend {
       CK(cudaEventCreate(&e1));
       CK(cudaEventRecord(e0, st));
     }
-    // Y[(ij)][(ab)] = sum_(cd) X[(ij)][(cd)] G[(ab)][(cd)]
+    (void)o;
+    // Y[(z ij)][(ab)] = sum_(cd) X[(z ij)][(cd)] G[(ab)][(cd)]
     if (tc && precision != 0)
-      tc->gemm_prepared_b(o * o, vv, vv, 1.0, X, G_tc, Y, !prof);
+      tc->gemm_prepared_b(rows, vv, vv, 1.0, X, G_tc, Y, !prof);
     else
-      dgemm(1, o * o, vv, vv, 1.0, X, G, Y);
+      dgemm(1, rows, vv, vv, 1.0, X, G, Y);
     if (prof) {
       CK(cudaEventRecord(e1, st));
       ev.push_back({e0, e1});
       ++prof_calls;
+      prof_flops += 2.0 * (double)rows * (double)vv * (double)vv;
     }
   }
 

@@ -150,9 +150,10 @@ int Graph::embed(int X, const std::vector<int64_t>& off, const std::vector<int64
 }
 
 int Graph::ladder(int X, int L) {
-  const auto& d = t[X].dims;
-  if (d.size() != 4 || d[0] != o || d[1] != o || d[2] != v || d[3] != v)
-    throw std::runtime_error("ladder operand must be [o][o][v][v]");
+  const auto d = t[X].dims;
+  const size_t r = d.size();
+  if ((r != 4 && r != 5) || d[r - 4] != o || d[r - 3] != o || d[r - 2] != v || d[r - 1] != v)
+    throw std::runtime_error("ladder operand must be [(nb)][o][o][v][v]");
   if (is_zero(X)) return zero(d);
   int out = new_tensor(d, Kind::Node);
   Op op;
@@ -179,7 +180,21 @@ int Graph::ladder_adj_l(int Ybar, int X, int L) {
 
 // ---------------------------------------------------------------- tangents
 
-std::map<int, int> Graph::tangent(const std::map<int, int>& seeds, const Ranges& ranges) {
+std::map<int, int> Graph::tangent(const std::map<int, int>& seeds, const Ranges& ranges,
+                                  int64_t nb) {
+  const std::string Zs = nb > 0 ? "Z" : "";
+  auto bdims = [&](const std::vector<int64_t>& d) {
+    std::vector<int64_t> r;
+    if (nb > 0) r.push_back(nb);
+    r.insert(r.end(), d.begin(), d.end());
+    return r;
+  };
+  auto boff = [&](const std::vector<int64_t>& d) {
+    std::vector<int64_t> r;
+    if (nb > 0) r.push_back(0);
+    r.insert(r.end(), d.begin(), d.end());
+    return r;
+  };
   std::map<int, int> tan;
   for (auto& kv : seeds)
     if (!is_zero(kv.second)) tan[kv.first] = kv.second;
@@ -197,12 +212,12 @@ std::map<int, int> Graph::tangent(const std::map<int, int>& seeds, const Ranges&
       case OpKind::Contract: {
         int A = op.in[0], B = op.in[1];
         int dA = T(A), dB = T(B);
-        int c1 = dA >= 0 ? contract(dA, op.la, B, op.lb, op.lc, op.alpha, op.tc) : -1;
-        int c2 = dB >= 0 ? contract(A, op.la, dB, op.lb, op.lc, op.alpha, op.tc) : -1;
+        int c1 = dA >= 0 ? contract(dA, Zs + op.la, B, op.lb, Zs + op.lc, op.alpha, op.tc) : -1;
+        int c2 = dB >= 0 ? contract(A, op.la, dB, Zs + op.lb, Zs + op.lc, op.alpha, op.tc) : -1;
         if (c1 >= 0 && is_zero(c1)) c1 = -1;
         if (c2 >= 0 && is_zero(c2)) c2 = -1;
         if (c1 >= 0 && c2 >= 0)
-          d = add(op.lc, {{c1, op.lc, 1.0}, {c2, op.lc, 1.0}});
+          d = add(Zs + op.lc, {{c1, Zs + op.lc, 1.0}, {c2, Zs + op.lc, 1.0}});
         else
           d = c1 >= 0 ? c1 : c2;
         break;
@@ -211,19 +226,19 @@ std::map<int, int> Graph::tangent(const std::map<int, int>& seeds, const Ranges&
         std::vector<Term> terms;
         for (size_t k = 0; k < op.in.size(); ++k) {
           int dk = T(op.in[k]);
-          if (dk >= 0) terms.push_back({dk, op.perm[k], op.coef[k]});
+          if (dk >= 0) terms.push_back({dk, Zs + op.perm[k], op.coef[k]});
         }
-        if (!terms.empty()) d = add(op.lc, terms);
+        if (!terms.empty()) d = add(Zs + op.lc, terms);
         break;
       }
       case OpKind::Slice: {
         int dx = T(op.in[0]);
-        if (dx >= 0) d = slice(dx, op.off, t[op.out].dims);
+        if (dx >= 0) d = slice(dx, boff(op.off), bdims(t[op.out].dims));
         break;
       }
       case OpKind::Embed: {
         int dx = T(op.in[0]);
-        if (dx >= 0) d = embed(dx, op.off, t[op.out].dims);
+        if (dx >= 0) d = embed(dx, boff(op.off), bdims(t[op.out].dims));
         break;
       }
       case OpKind::Ladder: {
@@ -245,7 +260,20 @@ std::map<int, int> Graph::tangent(const std::map<int, int>& seeds, const Ranges&
 // ---------------------------------------------------------------- adjoints
 
 std::map<int, int> Graph::adjoint(const std::map<int, int>& seeds, const std::vector<int>& wrt,
-                                  const Ranges& ranges) {
+                                  const Ranges& ranges, int64_t nb) {
+  const std::string Zs = nb > 0 ? "Z" : "";
+  auto bdims = [&](const std::vector<int64_t>& d) {
+    std::vector<int64_t> r;
+    if (nb > 0) r.push_back(nb);
+    r.insert(r.end(), d.begin(), d.end());
+    return r;
+  };
+  auto boff = [&](const std::vector<int64_t>& d) {
+    std::vector<int64_t> r;
+    if (nb > 0) r.push_back(0);
+    r.insert(r.end(), d.begin(), d.end());
+    return r;
+  };
   std::vector<size_t> order;
   for (auto& r : ranges)
     for (size_t i = r.first; i < r.second; ++i) order.push_back(i);
@@ -265,7 +293,7 @@ std::map<int, int> Graph::adjoint(const std::map<int, int>& seeds, const std::ve
     auto& v = it->second;
     if (v.size() == 1) return v[0];
     std::string l;
-    for (size_t k = 0; k < t[id].dims.size(); ++k) l.push_back(char('A' + k));
+    for (size_t k = 0; k < t[v[0]].dims.size(); ++k) l.push_back(char('A' + k));
     std::vector<Term> terms;
     for (int c : v) terms.push_back({c, l, 1.0});
     int s = add(l, terms);
@@ -284,24 +312,26 @@ std::map<int, int> Graph::adjoint(const std::map<int, int>& seeds, const std::ve
     switch (op.kind) {
       case OpKind::Contract: {
         int A = op.in[0], B = op.in[1];
-        if (dep[A]) push(A, contract(g, op.lc, B, op.lb, op.la, op.alpha, op.tc));
-        if (dep[B]) push(B, contract(A, op.la, g, op.lc, op.lb, op.alpha, op.tc));
+        if (dep[A]) push(A, contract(g, Zs + op.lc, B, op.lb, Zs + op.la, op.alpha, op.tc));
+        if (dep[B]) push(B, contract(A, op.la, g, Zs + op.lc, Zs + op.lb, op.alpha, op.tc));
         break;
       }
       case OpKind::Add:
         for (size_t k = 0; k < op.in.size(); ++k)
-          if (dep[op.in[k]]) push(op.in[k], add(op.perm[k], {{g, op.lc, op.coef[k]}}));
+          if (dep[op.in[k]])
+            push(op.in[k], add(Zs + op.perm[k], {{g, Zs + op.lc, op.coef[k]}}));
         break;
       case OpKind::Slice:
-        if (dep[op.in[0]]) push(op.in[0], embed(g, op.off, t[op.in[0]].dims));
+        if (dep[op.in[0]]) push(op.in[0], embed(g, boff(op.off), bdims(t[op.in[0]].dims)));
         break;
       case OpKind::Embed:
-        if (dep[op.in[0]]) push(op.in[0], slice(g, op.off, t[op.in[0]].dims));
+        if (dep[op.in[0]]) push(op.in[0], slice(g, boff(op.off), bdims(t[op.in[0]].dims)));
         break;
       case OpKind::Ladder: {
         int X = op.in[0], L = op.in[1];
         if (dep[X]) push(X, ladder(g, L));
         if (dep[L]) {
+          if (nb > 0) throw std::runtime_error("batched adjoint w.r.t. L not supported");
           int a = ladder_adj_l(g, X, L);
           push(L, embed(a, {0, (int64_t)o, (int64_t)o}, t[L].dims));
         }
@@ -314,7 +344,7 @@ std::map<int, int> Graph::adjoint(const std::map<int, int>& seeds, const std::ve
   std::map<int, int> res;
   for (int w : wrt) {
     int s = total(w);
-    res[w] = s >= 0 ? s : zero(t[w].dims);
+    res[w] = s >= 0 ? s : zero(bdims(t[w].dims));
   }
   return res;
 }
@@ -329,7 +359,24 @@ void Graph::set_input(int id, const double* src, bool src_on_device) {
   touch(id);
 }
 
+void Graph::set_volatile_inputs(const std::vector<int>& inputs) {
+  vol_.assign(t.size(), 0);
+  for (int x : inputs) vol_[x] = 1;
+  for (auto& op : ops)
+    for (int x : op.in)
+      if (vol_[x]) vol_[op.out] = 1;
+}
+
 void Graph::run(const std::vector<int>& targets) {
+  if (vol_.size() < t.size()) vol_.resize(t.size(), 0);
+  // buffers of volatile results handed to the caller by the previous run
+  for (int x : held_) {
+    if (t[x].data && t[x].kind == Kind::Node) {
+      be->pool_put(t[x].data, std::max<int64_t>(1, t[x].numel()));
+      t[x].data = nullptr;
+    }
+  }
+  held_.clear();
   // producer of each node
   std::vector<int> prod(t.size(), -1);
   for (size_t i = 0; i < ops.size(); ++i) prod[ops[i].out] = (int)i;
@@ -352,10 +399,23 @@ void Graph::run(const std::vector<int>& targets) {
         stack.push_back(y);
       }
   }
+  // last use of each volatile node among the ops of this run
+  std::vector<char> is_target(t.size(), 0);
+  for (int x : targets) is_target[x] = 1;
+  std::vector<size_t> last_use(t.size(), 0);
+  for (size_t i = 0; i < ops.size(); ++i)
+    if (need_op[i])
+      for (int x : ops[i].in) last_use[x] = i;
+  std::vector<std::vector<int>> free_after(ops.size());
+  for (size_t i = 0; i < ops.size(); ++i) {
+    if (!need_op[i]) continue;
+    int x = ops[i].out;
+    if (vol_[x] && !is_target[x]) free_after[std::max(last_use[x], i)].push_back(x);
+  }
   for (size_t i = 0; i < ops.size(); ++i) {
     if (!need_op[i]) continue;
     Op& op = ops[i];
-    bool need = !op.ran;
+    bool need = !op.ran || vol_[op.out];
     if (!need)
       for (size_t k = 0; k < op.in.size(); ++k)
         if (t[op.in[k]].version != op.seen[k]) {
@@ -367,6 +427,8 @@ void Graph::run(const std::vector<int>& targets) {
       if (t[x].kind == Kind::Input && !t[x].data)
         throw std::runtime_error("graph input '" + t[x].name + "' was never set");
     void* e0 = trace ? be->record_event() : nullptr;
+    if (vol_[op.out] && !t[op.out].data)
+      t[op.out].data = be->pool_get(std::max<int64_t>(1, t[op.out].numel()));
     exec(op);
     if (trace) {
       void* e1 = be->record_event();
@@ -377,7 +439,15 @@ void Graph::run(const std::vector<int>& targets) {
     for (size_t k = 0; k < op.in.size(); ++k) op.seen[k] = t[op.in[k]].version;
     op.ran = true;
     touch(op.out);
+    for (int x : free_after[i]) {
+      if (t[x].data) {
+        be->pool_put(t[x].data, std::max<int64_t>(1, t[x].numel()));
+        t[x].data = nullptr;
+      }
+    }
   }
+  for (int x : targets)
+    if (x < (int)vol_.size() && vol_[x] && t[x].kind == Kind::Node) held_.push_back(x);
 }
 
 std::string Graph::trace_report(int top) {
@@ -445,7 +515,8 @@ void Graph::exec(Op& op) {
       break;
     }
     case OpKind::Ladder:
-      be->ladder(*this, t[op.in[1]].data, t[op.in[1]].version, t[op.in[0]].data, out.data);
+      be->ladder(*this, t[op.in[1]].data, t[op.in[1]].version, t[op.in[0]].data, out.data,
+                 t[op.in[0]].numel() / ((int64_t)v * v));
       break;
     case OpKind::LadderAdjL:
       be->ladder_adj_l(*this, t[op.in[2]].data, t[op.in[0]].data, t[op.in[1]].data, out.data);
@@ -469,28 +540,82 @@ void Graph::exec(Op& op) {
         if (lb.find(c) != std::string::npos && lc.find(c) == std::string::npos) ka.push_back(c);
       for (char c : lb)
         if (la.find(c) != std::string::npos && lc.find(c) == std::string::npos) kb.push_back(c);
-      // choose the contracted-label order that needs fewer operand copies
-      auto cost = [&](const std::string& k) {
-        int64_t c = 0;
-        if (la != bat + ml + k) c += A.numel();
-        if (lb != bat + nl + k) c += B.numel();
-        return c;
-      };
-      std::string kl = cost(ka) <= cost(kb) ? ka : kb;
       auto dim_of = [&](char c) -> int64_t {
         size_t p = la.find(c);
         if (p != std::string::npos) return A.dims[p];
         return B.dims[lb.find(c)];
       };
+      // a label group of X collapsed to at most two strided levels
+      struct Grp {
+        bool ok = true;
+        int64_t n2 = 0, s1 = 0, s2 = 0;
+      };
+      auto collapse = [&](const Tensor& X, const std::string& lx, const std::string& grp) {
+        auto xs = row_strides(X.dims);
+        std::vector<std::pair<int64_t, int64_t>> runs;  // (extent, innermost stride)
+        for (char c : grp) {
+          size_t p = lx.find(c);
+          int64_t d = X.dims[p], st = xs[p];
+          if (d == 1) continue;
+          if (!runs.empty() && runs.back().second == st * d) {
+            runs.back().first *= d;
+            runs.back().second = st;
+          } else {
+            runs.push_back({d, st});
+          }
+        }
+        Grp g;
+        if (runs.size() == 1) {
+          g.s2 = runs[0].second;
+        } else if (runs.size() == 2) {
+          g.n2 = runs[1].first;
+          g.s1 = runs[0].second;
+          g.s2 = runs[1].second;
+        } else if (runs.size() > 2) {
+          g.ok = false;
+        }
+        return g;
+      };
+      auto view_of = [&](const Tensor& X, const std::string& lx, const std::string& rows,
+                         const std::string& kls, MatView& v) {
+        Grp gb = collapse(X, lx, bat), gr = collapse(X, lx, rows), gk = collapse(X, lx, kls);
+        if (!gb.ok || gb.n2 || !gr.ok || !gk.ok) return false;
+        v.p = X.data;
+        v.sb = gb.s2;
+        v.n2r = gr.n2;
+        v.sr1 = gr.s1;
+        v.sr2 = gr.s2;
+        v.n2k = gk.n2;
+        v.sk1 = gk.s1;
+        v.sk2 = gk.s2;
+        // a K group of extent 1 has no stride of its own
+        if (!gk.n2 && gk.s2 == 0) v.sk2 = 1;
+        return true;
+      };
+      // contracted-label order: the one for which both operands are views
+      MatView Av, Bv;
+      std::string kl = ka;
+      bool okA = view_of(A, la, ml, kl, Av), okB = view_of(B, lb, nl, kl, Bv);
+      if (!(okA && okB)) {
+        MatView A2, B2;
+        bool a2 = view_of(A, la, ml, kb, A2), b2 = view_of(B, lb, nl, kb, B2);
+        if ((int)a2 + (int)b2 > (int)okA + (int)okB) {
+          kl = kb;
+          okA = a2;
+          okB = b2;
+          Av = A2;
+          Bv = B2;
+        }
+      }
       int64_t nb = 1, M = 1, N = 1, K = 1;
       for (char c : bat) nb *= dim_of(c);
       for (char c : ml) M *= dim_of(c);
       for (char c : nl) N *= dim_of(c);
       for (char c : kl) K *= dim_of(c);
-      // bring an operand into [batch][rows][K] order
+      // dense [batch][rows][K] copy for operands that are not a two-level view
       auto arrange = [&](const Tensor& X, const std::string& lx, const std::string& want,
-                         int slot) -> const double* {
-        if (lx == want) return X.data;
+                         int slot, int64_t rows) -> MatView {
+        if (lx == want) return MatView::dense(X.data, rows, K);
         double* dst = be->scratch(slot, std::max<int64_t>(1, X.numel()));
         std::vector<int64_t> wd;
         for (char c : want) wd.push_back(X.dims[lx.find(c)]);
@@ -499,17 +624,9 @@ void Graph::exec(Op& op) {
         int64_t istr[kMaxRank];
         for (size_t q = 0; q < want.size(); ++q) istr[q] = xs[lx.find(want[q])];
         be->copy_view((int)want.size(), wd.data(), dst, ws.data(), X.data, istr, 1.0, false);
-        return dst;
+        return MatView::dense(dst, rows, K);
       };
-      const double* Ap = arrange(A, la, bat + ml + kl, 0);
-      const double* Bp = arrange(B, lb, bat + nl + kl, 1);
-      if (lc == bat + ml + nl) {
-        be->gemm_tn(nb, M, N, K, op.alpha, Ap, Bp, out.data, op.tc);
-      } else if (lc == bat + nl + ml) {
-        be->gemm_tn(nb, N, M, K, op.alpha, Bp, Ap, out.data, op.tc);
-      } else {
-        double* Cp = be->scratch(2, std::max<int64_t>(1, nb * M * N));
-        be->gemm_tn(nb, M, N, K, op.alpha, Ap, Bp, Cp, op.tc);
+      auto finish = [&](double* Cp) {
         std::string cl = bat + ml + nl;
         std::vector<int64_t> cd;
         for (char c : cl) cd.push_back(dim_of(c));
@@ -518,6 +635,50 @@ void Graph::exec(Op& op) {
         int64_t istr[kMaxRank];
         for (int q = 0; q < rc; ++q) istr[q] = cs[cl.find(lc[q])];
         be->copy_view(rc, out.dims.data(), out.data, os.data(), Cp, istr, 1.0, false);
+      };
+      // tensor-core route: operands that do not change between calls keep
+      // their converted form in the backend (keyed by node, layout, version)
+      const bool use_tc = op.tc && be->tc_will_use(nb, M, N, K);
+      if (use_tc) {
+        auto hash = [](const std::string& a, const std::string& b) {
+          uint64_t h = 1469598103934665603ull;
+          for (char c : a + "|" + b) h = (h ^ (uint64_t)(unsigned char)c) * 1099511628211ull;
+          return h;
+        };
+        Backend::OperandKey kA{this, op.in[0], A.version, hash(la, bat + ml + kl)};
+        Backend::OperandKey kB{this, op.in[1], B.version, hash(lb, bat + nl + kl)};
+        const bool cA = !vol_[op.in[0]], cB = !vol_[op.in[1]];
+        if (cA && be->tc_cached(kA))
+          Av.p = nullptr;
+        else if (!okA)
+          Av = arrange(A, la, bat + ml + kl, 0, M);
+        if (cB && be->tc_cached(kB))
+          Bv.p = nullptr;
+        else if (!okB)
+          Bv = arrange(B, lb, bat + nl + kl, 1, N);
+        const Backend::OperandKey* pA = cA ? &kA : nullptr;
+        const Backend::OperandKey* pB = cB ? &kB : nullptr;
+        if (lc == bat + ml + nl) {
+          be->gemm_tc_keyed(M, N, K, op.alpha, Av, pA, Bv, pB, out.data);
+        } else if (lc == bat + nl + ml) {
+          be->gemm_tc_keyed(N, M, K, op.alpha, Bv, pB, Av, pA, out.data);
+        } else {
+          double* Cp = be->scratch(2, std::max<int64_t>(1, nb * M * N));
+          be->gemm_tc_keyed(M, N, K, op.alpha, Av, pA, Bv, pB, Cp);
+          finish(Cp);
+        }
+        break;
+      }
+      if (!okA) Av = arrange(A, la, bat + ml + kl, 0, M);
+      if (!okB) Bv = arrange(B, lb, bat + nl + kl, 1, N);
+      if (lc == bat + ml + nl) {
+        be->gemm_view(nb, M, N, K, op.alpha, Av, Bv, out.data, false);
+      } else if (lc == bat + nl + ml) {
+        be->gemm_view(nb, N, M, K, op.alpha, Bv, Av, out.data, false);
+      } else {
+        double* Cp = be->scratch(2, std::max<int64_t>(1, nb * M * N));
+        be->gemm_view(nb, M, N, K, op.alpha, Av, Bv, Cp, false);
+        finish(Cp);
       }
       break;
     }

@@ -94,12 +94,18 @@ class Graph {
   // Tangents of every node produced by ops [begin, end) given tangents of some
   // nodes (seeds). Returns node -> tangent node for all nodes with a non-zero
   // tangent (seeds included).
+  // With nb > 0 every tangent carries an extra leading dimension of size nb
+  // (label 'Z'): nb directions are propagated at once, and contractions with
+  // a primal operand fold the batch into their row dimension.
   using Ranges = std::vector<std::pair<size_t, size_t>>;
-  std::map<int, int> tangent(const std::map<int, int>& seeds, const Ranges& ranges);
+  std::map<int, int> tangent(const std::map<int, int>& seeds, const Ranges& ranges,
+                             int64_t nb = 0);
   // Adjoints: seeds map output node -> adjoint node; returns adjoint nodes of
   // the requested wrt nodes (Zero node if it does not depend on the seeds).
+  // With nb > 0 the seeds (and all adjoints) carry a leading batch dimension;
+  // the ops in ranges must then be unbatched.
   std::map<int, int> adjoint(const std::map<int, int>& seeds, const std::vector<int>& wrt,
-                             const Ranges& ranges);
+                             const Ranges& ranges, int64_t nb = 0);
 
   // --- execution ------------------------------------------------------------
   void set_input(int id, const double* src, bool src_on_device);
@@ -107,6 +113,10 @@ class Graph {
   // Run the ops among [begin, end) that the target nodes need, skipping ops
   // whose inputs did not change since their last execution.
   void run(const std::vector<int>& targets);
+  // Nodes that depend on the given inputs are recomputed on every run and
+  // their buffers are recycled after their last use (inputs that change on
+  // every call: trial vectors, bras, seeds). Call after the graph is built.
+  void set_volatile_inputs(const std::vector<int>& inputs);
   double* data(int id) { return t[id].data; }
   // Tracing: when enabled, every executed op is bracketed by events and its
   // time accumulated per op; trace_report() lists the most expensive ops.
@@ -116,6 +126,8 @@ class Graph {
  private:
   int new_tensor(const std::vector<int64_t>& dims, Kind k);
   void exec(Op& op);
+  std::vector<char> vol_;
+  std::vector<int> held_;  // volatile buffers kept alive for the caller
 };
 
 }  // namespace sccsd

@@ -101,7 +101,9 @@ __global__ void __launch_bounds__(192, 1)
   float* epi = (float*)(smem + STAGES * STAGE_BYTES + 256);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+  // M tiles run fastest so that the CTAs resident at one time share a B tile
+  // (read once from HBM, then served from L2)
+  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -236,21 +238,43 @@ __global__ void __launch_bounds__(192, 1)
   }
 }
 
-// x = sum_s slice_s with slice_s = bf16(x - sum_{r<s} slice_r); padded with zeros
-__global__ void k_split_bf16(const double* __restrict__ X, int64_t rows, int64_t K,
-                             int64_t rows_pad, int64_t k_pad, int slices,
-                             __nv_bfloat16* __restrict__ out) {
-  const int64_t total = rows_pad * k_pad;
+// x = sum_s slice_s with slice_s = bf16(x - sum_{r<s} slice_r); padded with
+// zeros. The source is a strided view; a 32 x 64 tile goes through shared
+// memory so that reads walk the source's unit-stride index and writes walk k.
+__device__ __forceinline__ int64_t vrow(const MatView& v, int64_t r) {
+  return v.n2r ? (r / v.n2r) * v.sr1 + (r % v.n2r) * v.sr2 : r * v.sr2;
+}
+__device__ __forceinline__ int64_t vk(const MatView& v, int64_t k) {
+  return v.n2k ? (k / v.n2k) * v.sk1 + (k % v.n2k) * v.sk2 : k * v.sk2;
+}
+
+__global__ void k_split_bf16_view(MatView X, int64_t rows, int64_t K, int64_t rows_pad,
+                                  int64_t k_pad, int slices, __nv_bfloat16* __restrict__ out) {
+  __shared__ double tile[32][65];
+  const int64_t ktiles = k_pad / 64;
+  const int64_t tiles = (rows_pad / 32) * ktiles;
+  const bool kfast = X.sk2 == 1;
   const int64_t sstride = rows_pad * k_pad;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e / k_pad, k = e % k_pad;
-    double x = (r < rows && k < K) ? X[r * K + k] : 0.0;
-    for (int s = 0; s < slices; ++s) {
-      __nv_bfloat16 b = __double2bfloat16(x);
-      out[s * sstride + e] = b;
-      x -= (double)__bfloat162float(b);
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int64_t r0 = (t / ktiles) * 32, k0 = (t % ktiles) * 64;
+    for (int e = threadIdx.x; e < 32 * 64; e += blockDim.x) {
+      const int rr = kfast ? e / 64 : e % 32;
+      const int kk = kfast ? e % 64 : e / 32;
+      const int64_t r = r0 + rr, k = k0 + kk;
+      tile[rr][kk] = (r < rows && k < K) ? X.p[vrow(X, r) + vk(X, k)] : 0.0;
     }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 32 * 64; e += blockDim.x) {
+      const int rr = e / 64, kk = e % 64;
+      double x = tile[rr][kk];
+      const int64_t o = (r0 + rr) * k_pad + k0 + kk;
+      for (int s = 0; s < slices; ++s) {
+        __nv_bfloat16 b = __double2bfloat16(x);
+        out[s * sstride + o] = b;
+        x -= (double)__bfloat162float(b);
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -287,7 +311,7 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 }  // namespace
 
 TcGemm::TcGemm(cudaStream_t st, int precision) : st_(st) {
-  nslices_ = precision == 1 ? 3 : 1;
+  nslices_ = precision == 1 ? 2 : 1;
   if (cudaMalloc(&d_err_, sizeof(int)) != cudaSuccess) throw OomError("tc error flag");
   cudaMemsetAsync(d_err_, 0, sizeof(int), st_);
   cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -310,7 +334,7 @@ bool TcGemm::worthwhile(int64_t nb, int64_t M, int64_t N, int64_t K) const {
   return nb == 1 && M >= 64 && N >= 64 && K >= 64 && (double)M * N * K >= 6.7e7;
 }
 
-void TcGemm::convert(const double* X, int64_t rows, int64_t K, TcOperand& out) {
+void TcGemm::convert(const MatView& X, int64_t rows, int64_t K, TcOperand& out) {
   const int64_t rp = round_up(rows, BN), kp = round_up(K, BK);
   const size_t need = (size_t)rp * kp * 2 * nslices_;
   if (out.bytes < need) {
@@ -330,15 +354,19 @@ void TcGemm::convert(const double* X, int64_t rows, int64_t K, TcOperand& out) {
   out.rows_pad = rp;
   out.k_pad = kp;
   out.slices = nslices_;
-  const int64_t total = rp * kp;
-  int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
-  k_split_bf16<<<grid, 256, 0, st_>>>(X, rows, K, rp, kp, nslices_, (__nv_bfloat16*)out.data);
+  const int64_t tiles = (rp / 32) * (kp / 64);
+  int grid = (int)std::min<int64_t>(tiles, 152 * 16);
+  k_split_bf16_view<<<grid, 256, 0, st_>>>(X, rows, K, rp, kp, nslices_, (__nv_bfloat16*)out.data);
   count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw CudaError(std::string("split_bf16: ") + cudaGetErrorString(e));
 }
 
 void TcGemm::prepare_operand(const double* X, int64_t rows, int64_t K, TcOperand& out) {
+  convert(MatView::dense(X, rows, K), rows, K, out);
+}
+
+void TcGemm::prepare_operand_view(const MatView& X, int64_t rows, int64_t K, TcOperand& out) {
   convert(X, rows, K, out);
 }
 
@@ -359,7 +387,8 @@ void TcGemm::run(const TcOperand& A, int sa, const TcOperand& B, int sb, int64_t
   const __nv_bfloat16* b = (const __nv_bfloat16*)B.data + (size_t)sb * B.rows_pad * B.k_pad;
   CUtensorMap ma = make_map(a, A.rows_pad, A.k_pad, BM);
   CUtensorMap mb = make_map(b, B.rows_pad, B.k_pad, BN);
-  dim3 grid((unsigned)(B.rows_pad / BN), (unsigned)((M + BM - 1) / BM));
+  if (B.rows_pad / BN > 65535) throw std::runtime_error("tc: N too large for the grid");
+  dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)(B.rows_pad / BN));
   const int nk = (int)(A.k_pad / BK);
   k_tc_gemm<<<grid, 192, SMEM_BYTES, st_>>>(ma, mb, M, N, nk, alpha, C, N, accumulate ? 1 : 0,
                                            d_err_);
@@ -377,7 +406,7 @@ static void slice_pairs(int s, std::vector<std::pair<int, int>>& out) {
 
 void TcGemm::gemm_prepared_b(int64_t M, int64_t N, int64_t K, double alpha, const double* A,
                              const TcOperand& B, double* C, bool check) {
-  convert(A, M, K, a_tmp_);
+  convert(MatView::dense(A, M, K), M, K, a_tmp_);
   std::vector<std::pair<int, int>> pairs;
   slice_pairs(nslices_, pairs);
   // accumulate the small products first, the leading one last
@@ -386,10 +415,18 @@ void TcGemm::gemm_prepared_b(int64_t M, int64_t N, int64_t K, double alpha, cons
   (void)check;  // the error flag is read by the backend at each synchronisation
 }
 
+void TcGemm::gemm_ops(int64_t M, int64_t N, double alpha, const TcOperand& A, const TcOperand& B,
+                      double* C) {
+  std::vector<std::pair<int, int>> pairs;
+  slice_pairs(nslices_, pairs);
+  for (size_t p = pairs.size(); p-- > 0;)
+    run(A, pairs[p].first, B, pairs[p].second, M, N, alpha, C, p + 1 != pairs.size());
+}
+
 void TcGemm::gemm(int64_t nb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
                   const double* B, double* C) {
   if (nb != 1) throw std::runtime_error("tc: batched GEMM not supported");
-  convert(B, N, K, b_tmp_);
+  convert(MatView::dense(B, N, K), N, K, b_tmp_);
   gemm_prepared_b(M, N, K, alpha, A, b_tmp_, C);
 }
 

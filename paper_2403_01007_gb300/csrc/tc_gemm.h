@@ -3,14 +3,18 @@
 // FP64 operands are split into BF16 slices x = x_0 + x_1 + ... (each slice the
 // BF16 rounding of what the previous ones left over); slice products run as
 // BF16 x BF16 -> FP32 GEMMs on the tensor cores and are summed into the FP64
-// result. One slice (SCCSD_BF16) keeps about 8 significant bits per operand,
-// three slices with the six leading products (SCCSD_BF16X3) about 24.
+// result. One slice (SCCSD_BF16) keeps about 8 significant bits per operand;
+// two slices with the three leading products x0 y0 + x0 y1 + x1 y0
+// (SCCSD_BF16X3) about 16, at which point the FP32 accumulation over long
+// contractions is the limiting error.
 #pragma once
 
 #include <cuda_runtime.h>
 
 #include <cstdint>
 #include <vector>
+
+#include "backend.h"
 
 namespace sccsd {
 
@@ -31,15 +35,20 @@ class TcGemm {
   void gemm(int64_t nb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
             const double* B, double* C);
   void prepare_operand(const double* X, int64_t rows, int64_t K, TcOperand& out);
+  // same from a strided view (the permutation is folded into the conversion)
+  void prepare_operand_view(const MatView& X, int64_t rows, int64_t K, TcOperand& out);
   // check: read back the pipeline error flag (synchronises the stream)
   void gemm_prepared_b(int64_t M, int64_t N, int64_t K, double alpha, const double* A,
                        const TcOperand& B, double* C, bool check = true);
   void check_error();
+  // C = alpha * A B^T for operands already in slice form
+  void gemm_ops(int64_t M, int64_t N, double alpha, const TcOperand& A, const TcOperand& B,
+                double* C);
   void release(TcOperand& op);
   int slices() const { return nslices_; }
 
  private:
-  void convert(const double* X, int64_t rows, int64_t K, TcOperand& out);
+  void convert(const MatView& X, int64_t rows, int64_t K, TcOperand& out);
   void run(const TcOperand& A, int sa, const TcOperand& B, int sb, int64_t M, int64_t N,
            double alpha, double* C, bool accumulate);
   cudaStream_t st_;

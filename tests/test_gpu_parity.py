@@ -58,10 +58,12 @@ def test_tc_gemm_split_accuracy(B):
     assert err3 < 1e-5
 
 
-def test_fp64_gemm_split_k(B):
-    """Few output tiles and a long contraction take the split-K path."""
+def test_fp64_gemm_shapes(B):
+    """Every FP64 route: dot products, matrix-vector, skinny tiles, split K."""
     rng = np.random.default_rng(7)
-    for (M, N, K) in [(100, 30, 50000), (200, 21, 132600), (1, 1, 9000)]:
+    for (M, N, K) in [(100, 30, 50000), (200, 21, 132600), (1, 1, 9000), (21, 42, 840000),
+                      (40000, 1, 663), (1, 5000, 700), (5000, 70, 3000), (20, 3000, 5000),
+                      (3000, 20, 5000), (33, 33, 100000)]:
         A = rng.normal(size=(M, K))
         Bm = rng.normal(size=(N, K))
         C = torch.empty((M, N), dtype=torch.float64, device="cuda:0")
@@ -142,4 +144,50 @@ def test_error_codes(B):
     with pytest.raises(B.SccsdError) as ei:
         ctx.jacobian_right(R)
     assert ei.value.code == -4
+    ctx.close()
+
+
+@pytest.mark.parametrize("nvec", [1, 3, 8, 11])
+def test_batched_transforms(B, nvec):
+    """Batches of trial vectors (chunked by 8 inside the library) give the
+    same A R, eta.R and A^T L as the oracle vector by vector."""
+    o, v, J = 3, 6, 10
+    eps, L = syn.system(o, v, J, 0.2, 4242)
+    prob = cc.Problem(eps, L, o)
+    t = syn.random_vectors(o, v, 1, 4243, scale=0.05)[0]
+    R = syn.random_vectors(o, v, nvec, 4244 + nvec, normalise=True)
+    ctx = B.Context(o, v, J, eps, L)
+    ctx.residual(t)
+    s, eta = ctx.jacobian_right(dev(R), with_eta=True)
+    s = s.cpu().numpy()
+    sl = ctx.jacobian_left(dev(R)).cpu().numpy()
+    for k in range(nvec):
+        assert maxrel(s[k], rp.jacobian_right(prob, t, R[k]).numpy()) < 1e-12
+        assert abs(eta[k] - float(rp.eta(prob, t) @ torch.tensor(R[k]))) < 1e-12
+        assert maxrel(sl[k], rp.jacobian_left(prob, t, R[k]).numpy()) < 1e-12
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("bf16x3", 2e-4), ("bf16", 3e-2)])
+def test_mixed_precision_medium(B, precision, tol):
+    """o=10, v=90, J=300: the contractions run on tcgen05 tensor cores. Errors
+    against the FP64 oracle stay at the level the operand split allows
+    (BF16x3: about 16 significant bits per product, FP32 accumulation;
+    BF16: 8 bits)."""
+    w = syn.MEDIUM
+    eps, L = syn.workload_system(w)
+    prob = cc.Problem(eps, L, w.o)
+    t = syn.random_vectors(w.o, w.v, 1, 91, scale=1e-3)[0]
+    R = syn.random_vectors(w.o, w.v, 2, 92, normalise=True)
+    ctx = B.Context(w.o, w.v, w.J, eps, L, precision=precision)
+    e, om = ctx.residual(t)
+    E0, Om = rp.residual(prob, t)
+    Ehf = float(rp.residual(prob, np.zeros(prob.dim))[0])
+    assert maxrel(om, Om.numpy()) < tol
+    assert abs(e - (float(E0) - Ehf)) < tol * max(1.0, abs(float(E0) - Ehf))
+    s = ctx.jacobian_right(dev(R)).cpu().numpy()
+    sl = ctx.jacobian_left(dev(R)).cpu().numpy()
+    for k in range(2):
+        assert maxrel(s[k], rp.jacobian_right(prob, t, R[k]).numpy()) < tol
+        assert maxrel(sl[k], rp.jacobian_left(prob, t, R[k]).numpy()) < tol
     ctx.close()
