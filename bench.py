@@ -171,6 +171,32 @@ def time_batches(ctx, R, sig, steps, stream, torch):
     return s0.elapsed_time(s1)
 
 
+def kernel_case(args):
+    """The particle-particle ladder as a bare contraction C = X G^T with
+    X [nvec*o^2][V^2] and G [V^2][V^2] (random data), on the tensor cores."""
+    import torch
+    from paper_2403_01007_gb300 import binding as B
+    o, V = syn.LARGE.o, args.kernel_case
+    M, N = args.nvec * o * o, V * V
+    g = torch.Generator(device="cuda").manual_seed(1)
+    X = torch.randn(M, N, dtype=torch.float64, device="cuda", generator=g)
+    G = torch.randn(N, N, dtype=torch.float64, device="cuda", generator=g)
+    C = torch.empty(M, N, dtype=torch.float64, device="cuda")
+    prec = "bf16" if args.precision == "fp64" else args.precision
+    for _ in range(args.warmup):
+        B.gemm_tn(X, G, C, precision=prec)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        B.gemm_tn(X, G, C, precision=prec)
+    torch.cuda.synchronize()
+    sec = (time.perf_counter() - t0) / max(1, args.steps)
+    print(json.dumps({"kernel_case": "ladder", "M": M, "N": N, "K": N, "precision": prec,
+                      "ms_per_call_incl_conversion": sec * 1e3,
+                      "tflops_incl_conversion": 2.0 * M * N * N / sec / 1e12}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -184,9 +210,14 @@ def main():
     ap.add_argument("--no-fp64-arm", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--kernel-case", type=int, default=0, metavar="V",
+                    help="time only the ladder-shaped contraction (rows = nvec*21^2, "
+                         "N = K = V^2) through sccsd_gemm_tn; a small case for profilers")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.kernel_case:
+        return kernel_case(args)
 
     import torch
     import torch.distributed as dist

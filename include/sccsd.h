@@ -42,7 +42,9 @@ enum {
   SCCSD_ENOMEM = -2,   /* device allocation failed */
   SCCSD_ECUDA = -3,    /* a CUDA call or kernel failed */
   SCCSD_ESTATE = -4,   /* call order: e.g. a Jacobian before any residual */
-  SCCSD_EINTERNAL = -5
+  SCCSD_EINTERNAL = -5,
+  SCCSD_ENOTCONV = -6, /* an iterative solver hit its iteration limit */
+  SCCSD_ECOMPLEX = -7  /* a complex-conjugate pair among the wanted EOM roots */
 };
 
 /* Precision of the tensor-core-eligible contractions (ladder, rings,
@@ -132,6 +134,39 @@ int sccsd_profile_read(sccsd_ctx* ctx, double* ladder_ms, long long* ladder_call
 int sccsd_gemm_tn_noalloc(long long M, long long N, long long K, double alpha, const double* A,
                           const double* B, double* C, void* stream);
 long long sccsd_gemm_tn_noalloc_capacity(void);
+
+/* Switch the precision of the tensor-core-eligible contractions for later
+ * calls (SCCSD_FP64 / SCCSD_BF16X3 / SCCSD_BF16). */
+int sccsd_set_precision(sccsd_ctx* ctx, int precision);
+
+/* Ground state: converge Omega(t) = 0 (Sec. 2.1; with Ra/Rb non-NULL the SCC
+ * residual of sccsd_residual at fixed zeta) by the orbital-energy
+ * preconditioned update t <- t - Omega/D, D_ai = e_a - e_i,
+ * D_aibj = D_ai + D_bj, with DIIS (8 vectors). Starts from t0 (packed ket) or
+ * from zero (whose first step is the MP2 guess). With a mixed precision and
+ * refine_tol > 0 the iterations run in that precision until |Omega| <
+ * refine_tol and finish in FP64 (iterative refinement); the FP64 residual
+ * then decides convergence (|Omega|_2 < tol). Outputs (each may be NULL):
+ * t_out (packed), e_corr, iterations. The converged state is fixed for the
+ * Jacobian and density calls. SCCSD_ENOTCONV when maxit is reached (outputs
+ * hold the last iterate). */
+int sccsd_solve_ground(sccsd_ctx* ctx, const double* t0, double zeta, const double* Ra,
+                       const double* Rb, double tol, int maxit, double refine_tol,
+                       double* t_out, double* e_corr, int* iterations);
+
+/* The nroots (<= 12) EOM roots omega of lowest real part (Sec. 2.1:
+ * A R = omega R for side 0, L^T A = omega L^T for side 1) at the fixed state,
+ * by the Davidson method with a subspace of at most 48 vectors and the
+ * diagonal preconditioner (omega - D')^-1, D' built from the diagonals of the
+ * dressed one-body intermediates (f_a - f_i for singles, f_a + f_b - f_i - f_j
+ * for doubles); restarts keep the current and previous Ritz vectors. The
+ * subspace eigenproblem and all vector work run on the device. Convergence: |A x - omega x| / |x| < tol for every
+ * root. Mixed precisions refine in FP64 once every residual is below
+ * refine_tol (refine_tol <= 0: no refinement). Outputs: omega[nroots],
+ * vecs[nroots][dim] (unit-norm packed vectors, may be NULL), iterations.
+ * SCCSD_ECOMPLEX if a complex pair appears among the wanted roots. */
+int sccsd_solve_states(sccsd_ctx* ctx, int nroots, int side, double tol, int maxit,
+                       double refine_tol, double* omega, double* vecs, int* iterations);
 
 /* Size of a packed vector. */
 long long sccsd_dim(int o, int v);

@@ -84,8 +84,8 @@ def eom(prob, x, nroots, side="right", tol=1e-8, maxit=200, scc=None,
     V = V.T
     AV = np.array([op(v) for v in V])
     for it in range(maxit):
-        Hs = V @ AV.T                      # Hs[p,q] = v_p . A v_q  (A^T for left)
-        w, Y = np.linalg.eig(Hs.T)
+        Hs = V @ AV.T                      # Hs[p,q] = v_p . (A v_q)
+        w, Y = np.linalg.eig(Hs)
         order = np.argsort(w.real)[:nroots]
         w, Y = w[order], Y[:, order]
         if np.max(np.abs(w.imag)) > 1e-8:
@@ -105,11 +105,10 @@ def eom(prob, x, nroots, side="right", tol=1e-8, maxit=200, scc=None,
                 den[np.abs(den) < 1e-6] = 1e-6
                 new.append(Rres[k] / den)
         if V.shape[0] + len(new) > max_space:
-            V, AV = X, AX
-            Qx, _ = np.linalg.qr(V.T)
-            # re-orthonormalise the collapsed space and its images
-            C = np.linalg.lstsq(V.T, Qx, rcond=None)[0]
-            V, AV = (V.T @ C).T, (AV.T @ C).T
+            # restart from the Ritz vectors
+            Q, _ = np.linalg.qr(X.T)
+            V = Q.T
+            AV = np.array([op(v) for v in V])
         for nv in new:
             for _ in range(2):
                 nv = nv - V.T @ (V @ nv)

@@ -40,6 +40,14 @@ def _declare(lib):
     lib.sccsd_gemm_tn_noalloc.restype = ctypes.c_int
     lib.sccsd_gemm_tn_noalloc_capacity.argtypes = []
     lib.sccsd_gemm_tn_noalloc_capacity.restype = ctypes.c_longlong
+    lib.sccsd_set_precision.argtypes = [_dp, ctypes.c_int]
+    lib.sccsd_set_precision.restype = ctypes.c_int
+    lib.sccsd_solve_ground.argtypes = [_dp, _dp, ctypes.c_double, _dp, _dp, ctypes.c_double,
+                                       ctypes.c_int, ctypes.c_double, _dp, _dp, _dp]
+    lib.sccsd_solve_ground.restype = ctypes.c_int
+    lib.sccsd_solve_states.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_int, ctypes.c_double, _dp, _dp, _dp]
+    lib.sccsd_solve_states.restype = ctypes.c_int
     lib.sccsd_dim.argtypes = [ctypes.c_int, ctypes.c_int]
     lib.sccsd_dim.restype = ctypes.c_longlong
     lib.sccsd_last_error.argtypes = [_dp]
@@ -177,6 +185,34 @@ class Context:
             sigma = np.empty_like(L) if isinstance(L, np.ndarray) else L.new_empty(L.shape)
         self._check(self.lib.sccsd_jacobian_left(self.h, nvec, _ptr(L), _ptr(sigma)))
         return sigma
+
+    def set_precision(self, precision):
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self._check(self.lib.sccsd_set_precision(self.h, prec))
+
+    def solve_ground(self, t0=None, tol=1e-10, maxit=200, refine_tol=1e-4, scc=None, t_out=None):
+        """Converge the ground state; returns (e_corr, t, iterations)."""
+        if t_out is None:
+            t_out = np.empty(self.dim)
+        e = ctypes.c_double()
+        it = ctypes.c_int()
+        zeta, Ra, Rb = (0.0, None, None) if scc is None else scc
+        self._check(self.lib.sccsd_solve_ground(self.h, _ptr(t0), float(zeta), _ptr(Ra), _ptr(Rb),
+                                                float(tol), int(maxit), float(refine_tol),
+                                                _ptr(t_out), ctypes.addressof(e),
+                                                ctypes.addressof(it)))
+        return e.value, t_out, it.value
+
+    def solve_states(self, nroots, side="right", tol=1e-8, maxit=200, refine_tol=1e-4, vecs=True):
+        """Lowest EOM roots; returns (omega[nroots], vecs[nroots][dim] or None, iterations)."""
+        w = np.empty(nroots)
+        V = np.empty((nroots, self.dim)) if vecs else None
+        it = ctypes.c_int()
+        sd = 0 if side in ("right", 0) else 1
+        self._check(self.lib.sccsd_solve_states(self.h, int(nroots), sd, float(tol), int(maxit),
+                                                float(refine_tol), w.ctypes.data, _ptr(V),
+                                                ctypes.addressof(it)))
+        return w, V, it.value
 
     def profile(self, enable=True):
         self._check(self.lib.sccsd_profile(self.h, 1 if enable else 0))

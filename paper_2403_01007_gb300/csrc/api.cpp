@@ -13,6 +13,7 @@
 #include "../../include/sccsd.h"
 #include "backend.h"
 #include "ccsd_graph.h"
+#include "small_la.h"
 
 namespace sccsd {
 
@@ -190,6 +191,12 @@ struct sccsd_ctx {
   double* stage2 = nullptr;
   double e_hf = 0.0;
   int max_batch = 8;  // trial vectors per batched pass
+  std::vector<double> eps_host;
+  double* eps_dev = nullptr;  // orbital energies on the device
+  double* D = nullptr;        // packed orbital-energy denominators
+  std::vector<double*> sv;    // solver work buffers
+  double* sv_small = nullptr; // small matrices and vectors
+  int* sv_info = nullptr;
   std::string err;
   ~sccsd_ctx() {
     if (getenv("SCCSD_TRACE")) {
@@ -199,8 +206,11 @@ struct sccsd_ctx {
     plain.reset();
     scc.reset();
     if (be) {
-      for (double* p : {L, h, delta, stage, stage2})
+      for (double* p : {L, h, delta, stage, stage2, eps_dev, D, sv_small})
         if (p) be->release(p);
+      for (double* p : sv)
+        if (p) be->release(p);
+      if (sv_info) be->release((double*)sv_info);
     }
   }
 };
@@ -223,6 +233,8 @@ int guarded(sccsd_ctx* c, F&& f) {
     return fail(c, SCCSD_ECUDA, e.what());
   } catch (const std::invalid_argument& e) {
     return fail(c, SCCSD_EINVAL, e.what());
+  } catch (const std::domain_error& e) {
+    return fail(c, SCCSD_ECOMPLEX, e.what());
   } catch (const std::logic_error& e) {
     return fail(c, SCCSD_ESTATE, e.what());
   } catch (const std::bad_alloc&) {
@@ -335,6 +347,8 @@ const char* sccsd_strerror(int code) {
     case SCCSD_ECUDA: return "CUDA error";
     case SCCSD_ESTATE: return "invalid call order";
     case SCCSD_EINTERNAL: return "internal error";
+    case SCCSD_ENOTCONV: return "not converged";
+    case SCCSD_ECOMPLEX: return "complex roots";
     default: return "unknown error";
   }
 }
@@ -373,6 +387,11 @@ int sccsd_init(sccsd_ctx** out, int o, int v, int J, const double* eps, const do
     for (int k = o + 1; k < n; ++k)
       if (e[k] < e[k - 1]) throw std::invalid_argument("virtual eps not ascending");
     if (e[o] <= e[o - 1]) throw std::invalid_argument("no gap between occupied and virtual eps");
+    c->eps_host = e;
+    c->eps_dev = c->be->alloc(n);
+    c->be->upload(c->eps_dev, e.data(), n, false);
+    c->D = c->be->alloc(c->dim);
+    launch_denoms((cudaStream_t)c->be->stream(), o, v, c->eps_dev, c->D);
     std::vector<double> I(o * o, 0.0), E(n * n, 0.0);
     for (int k = 0; k < o; ++k) I[k * o + k] = 1.0;
     for (int k = 0; k < n; ++k) E[k * n + k] = e[k];
@@ -558,6 +577,412 @@ int sccsd_gemm_tn(int precision, long long M, long long N, long long K, double a
     be->gemm_tn(1, M, N, K, alpha, A, B, C, precision != SCCSD_FP64);
     be->sync();
   });
+}
+
+}  // extern "C"
+
+
+// ======================================================================
+// Solvers: ground state (Jacobi + DIIS) and EOM roots (Davidson), driven from
+// the host with every vector on the device.
+// ======================================================================
+namespace {
+
+constexpr int kDiis = 8;
+constexpr int kMaxSpace = 48;
+
+struct Dev {
+  sccsd_ctx* c;
+  cudaStream_t st() const { return (cudaStream_t)c->be->stream(); }
+  double dot(const double* x, const double* y, int64_t n) {
+    double* r = c->sv_small + 4 * kMaxSpace * kMaxSpace;
+    c->be->gemm_tn(1, 1, 1, n, 1.0, x, y, r, false);
+    double h = 0.0;
+    c->be->download(&h, r, 1, false);
+    return h;
+  }
+  void copy(double* dst, const double* src, int64_t n) { c->be->upload(dst, src, n, true); }
+  // y = a x + b y
+  void axpby(int64_t n, double a, const double* x, double b, double* y) {
+    launch_axpby(st(), n, a, x, b, y);
+  }
+  // out[k][:] = sum_p coef[p][k] V[p][:], coef [m][nk] row-major on the device
+  void combine(int nk, int m, const double* coef, const double* V, double* out) {
+    MatView A;  // element (k, p) = coef[p * nk + k]
+    A.p = coef;
+    A.sr2 = 1;
+    A.sk2 = nk;
+    MatView B;  // element (j, p) = V[p * dim + j]
+    B.p = V;
+    B.sr2 = 1;
+    B.sk2 = c->dim;
+    c->be->gemm_view(1, nk, c->dim, m, 1.0, A, B, out, false);
+  }
+};
+
+double* solver_buf(sccsd_ctx* c, size_t i, int64_t n) {
+  if (c->sv.size() <= i) c->sv.resize(i + 1, nullptr);
+  if (!c->sv[i]) c->sv[i] = c->be->alloc(n);
+  return c->sv[i];
+}
+
+void ensure_small(sccsd_ctx* c) {
+  if (!c->sv_small) c->sv_small = c->be->alloc(6 * kMaxSpace * kMaxSpace + 16);
+  if (!c->sv_info) c->sv_info = (int*)c->be->alloc(kMaxSpace + 4);
+}
+
+void switch_precision(sccsd_ctx* c, int p) {
+  if (c->be->get_precision() == p) return;
+  c->be->set_precision(p);
+  for (Model* m : {c->plain.get(), c->scc.get()})
+    if (m) m->g.invalidate();
+}
+
+// E0 and packed omega (device) at packed amplitudes t (device)
+double eval_residual(sccsd_ctx* c, const double* t, double zeta, const double* Ra,
+                     const double* Rb, double* om) {
+  const bool scc = Ra != nullptr;
+  Model& m = model(c, scc);
+  load_packed(c, m.g, t, m.t1, m.t2, false);
+  if (scc) {
+    load_packed(c, m.g, Ra, m.Ra1, m.Ra2, false);
+    load_packed(c, m.g, Rb, m.Rb1, m.Rb2, false);
+    set_scalar(c, m.g, m.zeta, zeta);
+  }
+  c->cur = &m;
+  m.g.run({m.er.E0, m.er.O1, m.er.O2});
+  store_packed(c, m.g, m.er.O1, m.er.O2, om, false);
+  return get_scalar(c, m.g, m.er.E0);
+}
+
+// sigma[k] = A V[k] (side 0) or A^T V[k] (side 1), all on the device
+void transform(sccsd_ctx* c, int side, int nvec, const double* V, double* W) {
+  Model& m = *c->cur;
+  for (int k0 = 0; k0 < nvec; k0 += c->max_batch) {
+    const int nb = std::min(c->max_batch, nvec - k0);
+    if (side == 0) {
+      RightSec& S = right_section(m, nb);
+      load_packed_batch(c, m.g, V + (int64_t)k0 * c->dim, nb, S.R1, S.R2, false);
+      m.g.run({S.sig1, S.sig2});
+      store_packed_batch(c, m.g, nb, S.sig1, S.sig2, W + (int64_t)k0 * c->dim, false);
+    } else {
+      LeftSec& S = left_section(m, nb);
+      load_packed_batch(c, m.g, V + (int64_t)k0 * c->dim, nb, S.Lb1, S.Lb2, true);
+      m.g.run({S.lt1, S.lt2});
+      store_packed_batch(c, m.g, nb, S.lt1, S.lt2, W + (int64_t)k0 * c->dim, true);
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int sccsd_set_precision(sccsd_ctx* c, int precision) {
+  if (!c) return SCCSD_EINVAL;
+  if (precision < SCCSD_FP64 || precision > SCCSD_BF16) return fail(c, SCCSD_EINVAL, "bad precision");
+  return guarded(c, [&] {
+    switch_precision(c, precision);
+    c->precision = precision;
+  });
+}
+
+int sccsd_solve_ground(sccsd_ctx* c, const double* t0, double zeta, const double* Ra,
+                       const double* Rb, double tol, int maxit, double refine_tol, double* t_out,
+                       double* e_corr, int* iterations) {
+  if (!c) return SCCSD_EINVAL;
+  if (!(tol > 0.0) || maxit < 1) return fail(c, SCCSD_EINVAL, "bad tolerance or iteration limit");
+  if ((Ra == nullptr) != (Rb == nullptr)) return fail(c, SCCSD_EINVAL, "give both Ra and Rb or neither");
+  int status = SCCSD_OK;
+  int rc = guarded(c, [&] {
+    Dev d{c};
+    ensure_small(c);
+    const int64_t dim = c->dim;
+    double* t = solver_buf(c, 0, dim);
+    double* om = solver_buf(c, 1, dim);
+    double* tn = solver_buf(c, 2, dim);
+    double* X = solver_buf(c, 3, kDiis * dim);
+    double* Rr = solver_buf(c, 4, kDiis * dim);
+    double* Bm = c->sv_small;
+    double* cf = c->sv_small + kMaxSpace * kMaxSpace;
+    // device copies of the SCC vectors (they may be host arrays)
+    const double *ra = Ra, *rb = Rb;
+    if (Ra) {
+      double* a = solver_buf(c, 5, dim);
+      double* b = solver_buf(c, 6, dim);
+      c->be->upload(a, Ra, dim, c->be->is_device(Ra));
+      c->be->upload(b, Rb, dim, c->be->is_device(Rb));
+      ra = a;
+      rb = b;
+    }
+    if (t0)
+      c->be->upload(t, t0, dim, c->be->is_device(t0));
+    else
+      c->be->fill(t, dim, 0.0);
+    const int p0 = c->be->get_precision();
+    const bool refine = p0 != SCCSD_FP64 && refine_tol > 0.0;
+    bool fp64_phase = !refine;
+    int nh = 0, head = 0, it = 0;
+    double E = 0.0, nrm = 0.0;
+    for (it = 1; it <= maxit; ++it) {
+      E = eval_residual(c, t, zeta, ra, rb, om);
+      nrm = std::sqrt(d.dot(om, om, dim));
+      if (getenv("SCCSD_LOG"))
+        fprintf(stderr, "{\"solver\": \"ground\", \"iter\": %d, \"fp64\": %d, \"residual\": %.3e, \"e_corr\": %.12f}\n", it,
+                (int)fp64_phase, nrm, E - c->e_hf);
+      if (!std::isfinite(nrm)) throw std::runtime_error("ground state diverged (non-finite residual)");
+      if (!fp64_phase && nrm < refine_tol) {
+        // mixed-precision phase done: refine in FP64 from the current amplitudes
+        switch_precision(c, SCCSD_FP64);
+        fp64_phase = true;
+        nh = 0;
+        head = 0;
+        --it;
+        continue;
+      }
+      if (fp64_phase && nrm < tol) break;
+      launch_jacobi(d.st(), dim, t, om, c->D, tn);
+      const int slot = head;
+      head = (head + 1) % kDiis;
+      nh = std::min(nh + 1, kDiis);
+      d.copy(X + (int64_t)slot * dim, tn, dim);
+      d.copy(Rr + (int64_t)slot * dim, tn, dim);
+      d.axpby(dim, -1.0, t, 1.0, Rr + (int64_t)slot * dim);
+      if (nh >= 2) {
+        c->be->gemm_tn(1, nh, nh, dim, 1.0, Rr, Rr, Bm, false);
+        launch_diis(d.st(), nh, Bm, cf, c->sv_info);
+        int info = 0;
+        cudaMemcpyAsync(&info, c->sv_info, sizeof(int), cudaMemcpyDeviceToHost, d.st());
+        c->be->sync();
+        if (info == 0)
+          d.combine(1, nh, cf, X, t);
+        else
+          d.copy(t, tn, dim);
+      } else {
+        d.copy(t, tn, dim);
+      }
+    }
+    if (it > maxit) status = SCCSD_ENOTCONV;
+    if (refine) switch_precision(c, p0);
+    if (refine) eval_residual(c, t, zeta, ra, rb, om);  // fix the state for later transforms
+    if (t_out) c->be->download(t_out, t, dim, c->be->is_device(t_out));
+    if (e_corr) *e_corr = E - c->e_hf;
+    if (iterations) *iterations = std::min(it, maxit);
+    c->be->sync();
+  });
+  if (rc != SCCSD_OK) return rc;
+  if (status != SCCSD_OK) return fail(c, status, "ground state not converged within maxit");
+  return SCCSD_OK;
+}
+
+int sccsd_solve_states(sccsd_ctx* c, int nroots, int side, double tol, int maxit,
+                       double refine_tol, double* omega, double* vecs, int* iterations) {
+  if (!c) return SCCSD_EINVAL;
+  if (nroots < 1 || nroots > 12 || (side != 0 && side != 1) || !(tol > 0.0) || maxit < 1 || !omega)
+    return fail(c, SCCSD_EINVAL, "bad arguments");
+  if (!c->cur) return fail(c, SCCSD_ESTATE, "call sccsd_residual or sccsd_solve_ground first");
+  int status = SCCSD_OK;
+  int rc = guarded(c, [&] {
+    Dev d{c};
+    ensure_small(c);
+    const int64_t dim = c->dim;
+    const int mmax = kMaxSpace;
+    if (dim < mmax) throw std::invalid_argument("problem too small for the requested roots");
+    double* V = solver_buf(c, 10, (int64_t)kMaxSpace * dim);
+    double* W = solver_buf(c, 11, (int64_t)kMaxSpace * dim);
+    double* Xr = solver_buf(c, 12, 12 * dim);
+    double* AX = solver_buf(c, 13, 12 * dim);
+    double* Rz = solver_buf(c, 14, 13 * dim);
+    double* Xp = solver_buf(c, 15, 12 * dim);   // Ritz vectors of the previous iteration
+    double* AXp = solver_buf(c, 16, 12 * dim);
+    bool have_prev = false;
+    double* S = c->sv_small;
+    double* Y = c->sv_small + kMaxSpace * kMaxSpace;
+    double* wr = c->sv_small + 2 * kMaxSpace * kMaxSpace;
+    double* wi = wr + kMaxSpace;
+    double* cf = wi + kMaxSpace;
+    double* G = c->sv_small + 3 * kMaxSpace * kMaxSpace;
+    int* order = c->sv_info;
+    int* info_d = c->sv_info + kMaxSpace;
+    cudaStream_t st = d.st();
+    auto get_info = [&]() {
+      int h = 0;
+      cudaMemcpyAsync(&h, info_d, sizeof(int), cudaMemcpyDeviceToHost, st);
+      c->be->sync();
+      return h;
+    };
+    // Gram-Schmidt of vec (and the same combination of its image) against V[0:m)
+    auto orthogonalize = [&](double* vec, double* img, int m) {
+      for (int pass = 0; pass < 2 && m > 0; ++pass) {
+        c->be->gemm_tn(1, m, 1, dim, 1.0, V, vec, cf, false);     // cf[p] = v_p . vec
+        double* tmp = Rz + 12 * dim;
+        d.combine(1, m, cf, V, tmp);
+        d.axpby(dim, -1.0, tmp, 1.0, vec);
+        if (img) {
+          d.combine(1, m, cf, W, tmp);
+          d.axpby(dim, -1.0, tmp, 1.0, img);
+        }
+      }
+    };
+    // Preconditioner: dressed denominators D'_ai = f_a - f_i, D'_aibj = f_a + f_b
+    // - f_i - f_j from the diagonals f of the Fock-like intermediates at the
+    // fixed state (they carry most of the correlation shift of diag(A));
+    // initial guesses: unit vectors on the lowest singles D'.
+    const int o = c->o, v = c->v;
+    Model& mdl = *c->cur;
+    mdl.g.run({mdl.er.Fooi, mdl.er.Fvvi});
+    double* fdiag = solver_buf(c, 17, o + v);
+    double* Dp = solver_buf(c, 18, dim);
+    {
+      int64_t d1[1] = {o}, os1[1] = {1}, is1[1] = {o + 1};
+      c->be->copy_view(1, d1, fdiag, os1, mdl.g.data(mdl.er.Fooi), is1, 1.0, false);
+      int64_t d2[1] = {v}, os2[1] = {1}, is2[1] = {v + 1};
+      c->be->copy_view(1, d2, fdiag + o, os2, mdl.g.data(mdl.er.Fvvi), is2, 1.0, false);
+    }
+    launch_denoms(st, o, v, fdiag, Dp);
+    std::vector<double> fh(o + v);
+    c->be->download(fh.data(), fdiag, o + v, false);
+    std::vector<std::pair<double, int>> dd;
+    for (int a = 0; a < v; ++a)
+      for (int i = 0; i < o; ++i) dd.push_back({fh[o + a] - fh[i], a * o + i});
+    std::sort(dd.begin(), dd.end());
+    int m = std::min<int>(std::min<int>((int)dd.size(), 2 * nroots + 2), mmax);
+    c->be->fill(V, (int64_t)m * dim, 0.0);
+    for (int k = 0; k < m; ++k) {
+      double one = 1.0;
+      c->be->upload(V + (int64_t)k * dim + dd[k].second, &one, 1, false);
+    }
+    transform(c, side, m, V, W);
+    const int p0 = c->be->get_precision();
+    const bool refine = p0 != SCCSD_FP64 && refine_tol > 0.0;
+    bool fp64_phase = !refine;
+    std::vector<double> lam(nroots), res(nroots);
+    int it = 0;
+    bool converged = false;
+    for (it = 1; it <= maxit; ++it) {
+      // subspace matrix and its lowest roots
+      c->be->gemm_tn(1, m, m, dim, 1.0, V, W, S, false);
+      launch_small_eig(st, m, S, wr, wi, Y, nroots, order, info_d);
+      int info = get_info();
+      if (info == 3) throw std::domain_error("complex pair among the lowest roots");
+      if (info != 0) throw std::runtime_error("subspace eigensolver failed");
+      std::vector<int> ord(nroots);
+      cudaMemcpyAsync(ord.data(), order, sizeof(int) * nroots, cudaMemcpyDeviceToHost, st);
+      std::vector<double> w(m);
+      cudaMemcpyAsync(w.data(), wr, sizeof(double) * m, cudaMemcpyDeviceToHost, st);
+      c->be->sync();
+      for (int k = 0; k < nroots; ++k) lam[k] = w[ord[k]];
+      // Ritz vectors, their images and residuals
+      d.combine(nroots, m, Y, V, Xr);
+      d.combine(nroots, m, Y, W, AX);
+      launch_ritz_residual(st, nroots, dim, AX, Xr, wr, order, Rz);
+      c->be->gemm_tn(1, nroots, nroots, dim, 1.0, Rz, Rz, G, false);
+      c->be->gemm_tn(1, nroots, nroots, dim, 1.0, Xr, Xr, G + 144, false);
+      std::vector<double> g1(nroots * nroots), g2(nroots * nroots);
+      c->be->download(g1.data(), G, nroots * nroots, false);
+      c->be->download(g2.data(), G + 144, nroots * nroots, false);
+      double worst = 0.0;
+      for (int k = 0; k < nroots; ++k) {
+        res[k] = std::sqrt(g1[k * nroots + k] / g2[k * nroots + k]);
+        worst = std::max(worst, res[k]);
+      }
+      if (getenv("SCCSD_LOG")) {
+        fprintf(stderr, "{\"solver\": \"davidson\", \"iter\": %d, \"space\": %d, \"fp64\": %d, \"max_res\": %.3e, \"omega\": [", it, m,
+                (int)fp64_phase, worst);
+        for (int k = 0; k < nroots; ++k) fprintf(stderr, "%s%.12f", k ? ", " : "", lam[k]);
+        fprintf(stderr, "]}\n");
+      }
+      if (!fp64_phase && worst < refine_tol) {
+        // restart in FP64 from the current Ritz vectors
+        switch_precision(c, SCCSD_FP64);
+        fp64_phase = true;
+        have_prev = false;
+        d.copy(V, Xr, (int64_t)nroots * dim);
+        m = 0;
+        for (int k = 0; k < nroots; ++k) {
+          double* vk = V + (int64_t)m * dim;
+          if (k != m) d.copy(vk, Xr + (int64_t)k * dim, dim);
+          orthogonalize(vk, nullptr, m);
+          double nn = std::sqrt(d.dot(vk, vk, dim));
+          if (nn < 1e-10) continue;
+          d.axpby(dim, 0.0, vk, 1.0 / nn, vk);
+          ++m;
+        }
+        transform(c, side, m, V, W);
+        continue;
+      }
+      if (fp64_phase && worst < tol) {
+        converged = true;
+        break;
+      }
+      // preconditioned residuals of the unconverged roots
+      std::vector<int> want;
+      for (int k = 0; k < nroots; ++k)
+        if (res[k] >= tol) want.push_back(k);
+      if (m + (int)want.size() > mmax) {
+        // thick restart: current and previous Ritz vectors, orthonormalised
+        // (their images follow the same combinations)
+        d.copy(V, Xr, (int64_t)nroots * dim);
+        d.copy(W, AX, (int64_t)nroots * dim);
+        int nk = nroots;
+        if (have_prev) {
+          d.copy(V + (int64_t)nroots * dim, Xp, (int64_t)nroots * dim);
+          d.copy(W + (int64_t)nroots * dim, AXp, (int64_t)nroots * dim);
+          nk = 2 * nroots;
+        }
+        int mm = 0;
+        for (int k = 0; k < nk; ++k) {
+          double* vk = V + (int64_t)mm * dim;
+          double* wk = W + (int64_t)mm * dim;
+          if (k != mm) {
+            d.copy(vk, V + (int64_t)k * dim, dim);
+            d.copy(wk, W + (int64_t)k * dim, dim);
+          }
+          orthogonalize(vk, wk, mm);
+          double nn = std::sqrt(d.dot(vk, vk, dim));
+          if (!(nn > 1e-10)) continue;
+          d.axpby(dim, 0.0, vk, 1.0 / nn, vk);
+          d.axpby(dim, 0.0, wk, 1.0 / nn, wk);
+          ++mm;
+        }
+        m = mm;
+      }
+      d.copy(Xp, Xr, (int64_t)nroots * dim);
+      d.copy(AXp, AX, (int64_t)nroots * dim);
+      have_prev = true;
+      int added = 0;
+      for (int k : want) {
+        double* nv = V + (int64_t)(m + added) * dim;
+        launch_precond(st, dim, Rz + (int64_t)k * dim, Dp, lam[k], nv);
+        double n0 = std::sqrt(d.dot(nv, nv, dim));
+        orthogonalize(nv, nullptr, m + added);
+        double nn = std::sqrt(d.dot(nv, nv, dim));
+        if (!(nn > 1e-8 * n0) || nn == 0.0) continue;
+        d.axpby(dim, 0.0, nv, 1.0 / nn, nv);
+        ++added;
+      }
+      if (added == 0) throw std::runtime_error("Davidson subspace stagnated");
+      transform(c, side, added, V + (int64_t)m * dim, W + (int64_t)m * dim);
+      m += added;
+    }
+    if (!converged) status = SCCSD_ENOTCONV;
+    if (refine) switch_precision(c, p0);
+    for (int k = 0; k < nroots; ++k) omega[k] = lam[k];
+    if (vecs) {
+      // unit-norm Ritz vectors
+      for (int k = 0; k < nroots; ++k) {
+        double* xk = Xr + (int64_t)k * dim;
+        double nn = std::sqrt(d.dot(xk, xk, dim));
+        d.axpby(dim, 0.0, xk, 1.0 / nn, xk);
+      }
+      c->be->download(vecs, Xr, (int64_t)nroots * dim, c->be->is_device(vecs));
+    }
+    if (iterations) *iterations = std::min(it, maxit);
+    c->be->sync();
+  });
+  if (rc != SCCSD_OK) return rc;
+  if (status != SCCSD_OK) return fail(c, status, "roots not converged within maxit");
+  return SCCSD_OK;
 }
 
 }  // extern "C"

@@ -118,6 +118,8 @@ EnergyResidual build_energy_residual(Graph& g, int t1, int t2, int L, int h, int
                           {g.contract(u, "ljcd", Govov, "kldc", "kj", 1.0, true), "kj", 1.0}});
   int E2 = g.add("ijab", {{g.contract(t2, "ijac", Fvvi, "bc", "ijab", 1.0, true), "ijab", 1.0},
                           {g.contract(t2, "ikab", Fooi, "kj", "ijab", 1.0, true), "ijab", -1.0}});
+  r.Fvvi = Fvvi;
+  r.Fooi = Fooi;
   int Pp = g.add("ijab", {{C2, "ijab", 1.0}, {D2, "ijab", 1.0}, {E2, "ijab", 1.0}});
   r.O2 = g.add("ijab", {{A2, "ijab", 1.0},
                         {lad, "ijab", 1.0},

@@ -7,6 +7,9 @@ namespace sccsd {
 
 struct EnergyResidual {
   int E0 = -1, O1 = -1, O2 = -1;
+  // dressed one-body intermediates whose diagonals approximate the diagonal of
+  // the Jacobian (the Davidson preconditioner): Fvv'[b][c], Foo'[k][j]
+  int Fvvi = -1, Fooi = -1;
 };
 
 // Builds E0 = <HF|Hbar|HF> and Omega_mu = <mu~|Hbar|HF> (Sec. 2.1) in the

@@ -211,6 +211,9 @@ class CudaBackend : public Backend {
   double* G = nullptr;
   int64_t G_version = -1;
   const double* G_src = nullptr;
+  int64_t Gtc_version = -1;
+  const double* Gtc_src = nullptr;
+  int Gtc_slices = 0;
   std::unique_ptr<TcGemm> tc;
   TcOperand G_tc;
   bool prof = false;
@@ -283,6 +286,22 @@ class CudaBackend : public Backend {
   void sync() override {
     CK(cudaStreamSynchronize(st));
     if (tc) tc->check_error();
+  }
+  void* stream() override { return (void*)st; }
+  int get_precision() const override { return precision; }
+  void set_precision(int p) override {
+    if (p == precision) return;
+    sync();
+    precision = p;
+    if (p != 0) {
+      if (!tc)
+        tc = std::make_unique<TcGemm>(st, p);
+      else
+        tc->set_precision(p);
+    }
+    if (tc)
+      for (auto& kv : opcache) tc->release(kv.second.op);
+    opcache.clear();
   }
   void fill(double* p, int64_t n, double v) override {
     if (n <= 0) return;
@@ -461,7 +480,7 @@ class CudaBackend : public Backend {
 
   void gemm_view(int64_t nb, int64_t M, int64_t N, int64_t K, double alpha, const MatView& A,
                  const MatView& B, double* C, bool use_tc) override {
-    if (use_tc && tc && tc->worthwhile(nb, M, N, K)) {
+    if (use_tc && tc && precision != 0 && tc->worthwhile(nb, M, N, K)) {
       gemm_tc_keyed(M, N, K, alpha, A, nullptr, B, nullptr, C);
       return;
     }
@@ -469,7 +488,7 @@ class CudaBackend : public Backend {
   }
 
   bool tc_will_use(int64_t nb, int64_t M, int64_t N, int64_t K) override {
-    return tc && tc->worthwhile(nb, M, N, K);
+    return tc && precision != 0 && tc->worthwhile(nb, M, N, K);
   }
   bool tc_cached(const OperandKey& k) override {
     auto it = opcache.find(std::make_tuple(k.graph, k.id, k.layout));
@@ -509,8 +528,10 @@ class CudaBackend : public Backend {
     return slots[slot];
   }
 
-  // G[(ab)][(cd)] = sum_J L^J_ac L^J_bd over the virtual block of L
-  void build_ladder_integrals(const Graph& g, const double* L) {
+  // G[(ab)][(cd)] = sum_J L^J_ac L^J_bd over the virtual block of L, built on
+  // the device from the Cholesky vectors: exactly in FP64 for the FP64 mode,
+  // on the tensor cores for the mixed modes (then split into BF16 slices)
+  void build_ladder_integrals(const Graph& g, const double* L, bool exact, double* dst) {
     const int64_t o = g.o, v = g.v, J = g.J, n = o + v, vv = v * v;
     // Lt[(ac)][J] = L[J][o+a][o+c]
     double* Lt = scratch(3, vv * J);
@@ -520,15 +541,13 @@ class CudaBackend : public Backend {
       int64_t istr[3] = {n, 1, n * n};
       copy_view(3, dims, Lt, ostr, L + o * n + o, istr, 1.0, false);
     }
-    if (!G) G = alloc(vv * vv);
     double* Gp = scratch(4, vv * vv);  // Gp[(ac)][(bd)]
-    gemm_tn(1, vv, vv, J, 1.0, Lt, Lt, Gp, true);
+    gemm_tn(1, vv, vv, J, 1.0, Lt, Lt, Gp, !exact);
     // G[a][b][c][d] = Gp[a][c][b][d]
     int64_t dims[4] = {v, v, v, v};
     int64_t ostr[4] = {v * vv, vv, v, 1};
     int64_t istr[4] = {v * vv, v, vv, 1};
-    copy_view(4, dims, G, ostr, Gp, istr, 1.0, false);
-    if (tc) tc->prepare_operand(G, vv, vv, G_tc);
+    copy_view(4, dims, dst, ostr, Gp, istr, 1.0, false);
   }
 
   void* record_event() override {
@@ -588,21 +607,36 @@ class CudaBackend : public Backend {
 
   void ladder(const Graph& g, const double* L, int64_t ver, const double* X, double* Y,
               int64_t rows) override {
-    if (!G || ver != G_version || L != G_src) {
-      build_ladder_integrals(g, L);
-      G_version = ver;
-      G_src = L;
+    const int64_t v = g.v, vv = v * v;
+    const bool mixed = tc && precision != 0;
+    if (!mixed) {
+      if (!G || G_version != ver || G_src != L) {
+        if (!G) G = alloc(vv * vv);
+        build_ladder_integrals(g, L, true, G);
+        G_version = ver;
+        G_src = L;
+      }
+    } else if (Gtc_version != ver || Gtc_src != L || Gtc_slices != tc->slices()) {
+      // reuse the exact integrals when they are current, else build on tensor cores
+      const double* src = G;
+      if (!G || G_version != ver || G_src != L) {
+        double* tmp = scratch(6, vv * vv);
+        build_ladder_integrals(g, L, false, tmp);
+        src = tmp;
+      }
+      tc->prepare_operand(src, vv, vv, G_tc);
+      Gtc_version = ver;
+      Gtc_src = L;
+      Gtc_slices = tc->slices();
     }
-    const int64_t o = g.o, v = g.v, vv = v * v;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (prof) {
       CK(cudaEventCreate(&e0));
       CK(cudaEventCreate(&e1));
       CK(cudaEventRecord(e0, st));
     }
-    (void)o;
     // Y[(z ij)][(ab)] = sum_(cd) X[(z ij)][(cd)] G[(ab)][(cd)]
-    if (tc && precision != 0)
+    if (mixed)
       tc->gemm_prepared_b(rows, vv, vv, 1.0, X, G_tc, Y, !prof);
     else
       dgemm(1, rows, vv, vv, 1.0, X, G, Y);

@@ -117,6 +117,10 @@ class Graph {
   // their buffers are recycled after their last use (inputs that change on
   // every call: trial vectors, bras, seeds). Call after the graph is built.
   void set_volatile_inputs(const std::vector<int>& inputs);
+  // Forget all memoised results (e.g. after a change of arithmetic precision).
+  void invalidate() {
+    for (auto& op : ops) op.ran = false;
+  }
   double* data(int id) { return t[id].data; }
   // Tracing: when enabled, every executed op is bracketed by events and its
   // time accumulated per op; trace_report() lists the most expensive ops.

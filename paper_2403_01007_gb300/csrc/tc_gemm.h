@@ -46,6 +46,7 @@ class TcGemm {
                 double* C);
   void release(TcOperand& op);
   int slices() const { return nslices_; }
+  void set_precision(int precision) { nslices_ = precision == 1 ? 2 : 1; }
 
  private:
   void convert(const MatView& X, int64_t rows, int64_t K, TcOperand& out);

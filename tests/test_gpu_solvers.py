@@ -1,0 +1,70 @@
+"""Ground-state and EOM solvers on the GPU against the FP64 CPU oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import ccsd as cc
+from oracle import response as rp
+from oracle import solvers as sv
+from paper_2403_01007_gb300 import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def small():
+    from paper_2403_01007_gb300 import binding as B
+    w = syn.SMALL
+    eps, L = syn.workload_system(w)
+    prob = cc.Problem(eps, L, w.o)
+    x, E0, _ = sv.ground_state(prob, tol=1e-11)
+    Ehf = float(rp.residual(prob, np.zeros(prob.dim))[0])
+    return B, w, eps, L, prob, x, E0 - Ehf
+
+
+def test_ground_state_small(small):
+    """o=5 v=19: converged correlation energy and amplitudes equal the oracle's."""
+    B, w, eps, L, prob, x, ecorr = small
+    ctx = B.Context(w.o, w.v, w.J, eps, L)
+    e, t, it = ctx.solve_ground(tol=1e-10, maxit=100)
+    assert abs(e - ecorr) < 1e-9
+    assert np.abs(t - x).max() < 1e-9
+    ctx.close()
+
+
+def test_eom_states_small(small):
+    """Lowest 3 right and left roots equal the oracle's Davidson roots; the
+    right vectors satisfy the oracle's A R = omega R."""
+    B, w, eps, L, prob, x, ecorr = small
+    ctx = B.Context(w.o, w.v, w.J, eps, L)
+    ctx.solve_ground(tol=1e-11, maxit=100)
+    wR, VR, _ = ctx.solve_states(3, "right", tol=1e-8)
+    wL, VL, _ = ctx.solve_states(3, "left", tol=1e-8)
+    wo, Xo = sv.eom(prob, x, 3, side="right", tol=1e-9)
+    assert np.abs(wR - wo).max() < 1e-8
+    assert np.abs(wL - wo).max() < 1e-8
+    for k in range(3):
+        r = rp.jacobian_right(prob, x, VR[k]).numpy() - wR[k] * VR[k]
+        assert np.linalg.norm(r) < 1e-7
+        l = rp.jacobian_left(prob, x, VL[k]).numpy() - wL[k] * VL[k]
+        assert np.linalg.norm(l) < 1e-7
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", ["bf16x3"])
+def test_mixed_precision_refinement_medium(precision):
+    """o=10 v=90 J=300: the mixed-precision solvers, refined in FP64 at the
+    end, reproduce the FP64 GPU results to 1e-8 Eh (energy and roots)."""
+    from paper_2403_01007_gb300 import binding as B
+    w = syn.MEDIUM
+    eps, L = syn.workload_system(w)
+    ref = B.Context(w.o, w.v, w.J, eps, L, precision="fp64")
+    e64, t64, _ = ref.solve_ground(tol=1e-9, maxit=400)
+    w64, _, _ = ref.solve_states(1, "right", tol=1e-7, maxit=400, vecs=False)
+    ref.close()
+    ctx = B.Context(w.o, w.v, w.J, eps, L, precision=precision)
+    e, t, _ = ctx.solve_ground(tol=1e-9, maxit=400, refine_tol=1e-5)
+    assert abs(e - e64) < 1e-8
+    wm, _, _ = ctx.solve_states(1, "right", tol=1e-7, maxit=400, refine_tol=1e-4, vecs=False)
+    assert np.abs(wm - w64).max() < 1e-8
+    ctx.close()
