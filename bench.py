@@ -314,8 +314,11 @@ def main():
                 "frac": achieved / 1.2 if achieved else None, "traffic": None,
                 "kernel": "k_dgemm_tn (ladder)", "peak_source": "FP64 rate derived in DESIGN.md"}
     else:
+        # DRAM bytes of one full-size ladder launch (6 x o^2 rows, N = K = v^2) from a 1-pass
+        # ncu capture (profiles/k_tc_gemm_ladder.md)
+        traffic = 9.23e9 if (w.o, w.v) == (21, 200) and args.nvec == 6 else None
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if achieved else None, "traffic": None,
+                "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "kernel": "k_tc_gemm (ladder)", "peak_source": f"bf16 sustained, {peak_src}",
                 "executed_tflops": achieved * slices if achieved else None,
                 "ladder_share_of_step": lad_ms / ms if ms > 0 else None}
