@@ -135,6 +135,31 @@ int sccsd_gemm_tn_noalloc(long long M, long long N, long long K, double alpha, c
                           const double* B, double* C, void* stream);
 long long sccsd_gemm_tn_noalloc_capacity(void);
 
+/* SCC orthogonality of the natural projection (Sec. 2.4.1, 2.4.2):
+ *   O_ab = <psi_a|P|psi_b>,  psi = exp(T) (R0 |HF> + sum_mu R_mu |mu>),
+ * P the projector onto HF, singles and doubles, T the cluster operator of the
+ * fixed state without X3 (the triples part does not reach the projected
+ * space). States a, b are given by (ra0, Ra) and (rb0, Rb), Ra/Rb packed kets.
+ * The inner product is that of the Hilbert space (the metric of the singlet
+ * singles and doubles kets included). Result in *O. */
+int sccsd_overlap(sccsd_ctx* ctx, double ra0, const double* Ra, double rb0, const double* Rb,
+                  double* O);
+
+/* Self-consistent SCCSD for the two lowest states, K = {a, b} (Sec. 2.4.2):
+ * find zeta with O_ab = 0 (Sec. 2.2). For each zeta the ground state is
+ * converged with zeta X3 built from the current R_a, R_b (ground_tol), the two
+ * lowest right EOM roots of the SCC Jacobian follow (eom_tol), with
+ * R0 = eta.R / omega (block form of the EOM matrix, Sec. 2.1) and state vectors
+ * of unit norm with their largest component positive; zeta is updated by the
+ * secant method on O_ab, starting from zeta = 0 (plain CCSD), which selects
+ * the root connected to CCSD (the paper notes the equation may have several,
+ * Sec. 3.1.1). Converged when |O_ab| < tol and the zeta step is below 1e-8.
+ * Outputs (may be NULL): zeta, e_corr, omega2[2], r0_2[2], Ra/Rb (packed),
+ * iterations. Afterwards the fixed state is the SCC state of the last zeta. */
+int sccsd_solve_scc(sccsd_ctx* ctx, double tol, int maxit, double ground_tol, double eom_tol,
+                    double* zeta, double* e_corr, double* omega2, double* r0_2, double* Ra,
+                    double* Rb, int* iterations);
+
 /* Switch the precision of the tensor-core-eligible contractions for later
  * calls (SCCSD_FP64 / SCCSD_BF16X3 / SCCSD_BF16). */
 int sccsd_set_precision(sccsd_ctx* ctx, int precision);

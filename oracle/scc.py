@@ -30,6 +30,7 @@ operator does not reach the projected space).
 """
 from __future__ import annotations
 
+import numpy as np
 import torch
 from torch.func import jvp
 
@@ -103,3 +104,41 @@ def overlap(x_t, Ra0, Ra, Rb0, Rb, o, v):
     """O_ab of the natural projection (Sec. 2.4.2)."""
     return metric_product(projected_state(x_t, Ra0, Ra, o, v),
                           projected_state(x_t, Rb0, Rb, o, v))
+
+
+def fix_sign(x):
+    """Sign convention for state vectors: largest |component| positive."""
+    return -x if x[np.argmax(np.abs(x))] < 0 else x
+
+
+def solve_scc(prob, tol=1e-10, maxit=40, ground_tol=1e-11, eom_tol=1e-9):
+    """Self-consistent SCCSD for the two lowest states a, b (K = {a, b},
+    Sec. 2.4.2): find zeta with O_ab(zeta) = 0, where at each zeta the ground
+    state T(zeta) is converged with X3 built from the current R_a, R_b and the
+    states are the two lowest right EOM roots of the SCC Jacobian; R0 = eta.R/omega
+    (block form of the EOM matrix, Sec. 2.1). The root is followed from zeta = 0
+    (plain CCSD) by the secant method on O_ab. Returns a dict."""
+    from . import solvers as sv
+    from . import response as rp
+    o, v = prob.o, prob.v
+    zeta, Ra, Rb, x = 0.0, None, None, None
+    hist = []
+    for it in range(1, maxit + 1):
+        scc = None if Ra is None else (zeta, torch.tensor(Ra), torch.tensor(Rb))
+        x, E0, _ = sv.ground_state(prob, tol=ground_tol, scc=scc, x0=x)
+        w, X = sv.eom(prob, x, 2, side="right", tol=eom_tol, scc=scc)
+        Xa, Xb = fix_sign(X[0]), fix_sign(X[1])
+        eta = rp.eta(prob, x, scc=scc).numpy()
+        r0a, r0b = float(eta @ Xa / w[0]), float(eta @ Xb / w[1])
+        O = float(overlap(torch.tensor(x), r0a, torch.tensor(Xa), r0b, torch.tensor(Xb), o, v))
+        hist.append((zeta, O))
+        Ra, Rb = Xa, Xb
+        if abs(O) < tol and len(hist) > 1 and abs(hist[-1][0] - hist[-2][0]) < 1e-8:
+            return {"zeta": zeta, "O": O, "E0": E0, "omega": w, "t": x, "Ra": Xa, "Rb": Xb,
+                    "r0": (r0a, r0b), "iterations": it}
+        if len(hist) == 1:
+            zeta = zeta - O
+        else:
+            (z1, o1), (z2, o2) = hist[-2], hist[-1]
+            zeta = z2 - o2 * (z2 - z1) / (o2 - o1) if o2 != o1 else z2
+    raise RuntimeError("SCC zeta iteration did not converge")

@@ -48,6 +48,11 @@ def _declare(lib):
     lib.sccsd_solve_states.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                        ctypes.c_int, ctypes.c_double, _dp, _dp, _dp]
     lib.sccsd_solve_states.restype = ctypes.c_int
+    lib.sccsd_overlap.argtypes = [_dp, ctypes.c_double, _dp, ctypes.c_double, _dp, _dp]
+    lib.sccsd_overlap.restype = ctypes.c_int
+    lib.sccsd_solve_scc.argtypes = [_dp, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                    ctypes.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+    lib.sccsd_solve_scc.restype = ctypes.c_int
     lib.sccsd_dim.argtypes = [ctypes.c_int, ctypes.c_int]
     lib.sccsd_dim.restype = ctypes.c_longlong
     lib.sccsd_last_error.argtypes = [_dp]
@@ -213,6 +218,27 @@ class Context:
                                                 float(refine_tol), w.ctypes.data, _ptr(V),
                                                 ctypes.addressof(it)))
         return w, V, it.value
+
+    def overlap(self, ra0, Ra, rb0, Rb):
+        """SCC orthogonality O_ab at the fixed state."""
+        out = ctypes.c_double()
+        self._check(self.lib.sccsd_overlap(self.h, float(ra0), _ptr(Ra), float(rb0), _ptr(Rb),
+                                           ctypes.addressof(out)))
+        return out.value
+
+    def solve_scc(self, tol=1e-10, maxit=40, ground_tol=1e-11, eom_tol=1e-9):
+        """Self-consistent SCCSD for the two lowest states; returns a dict."""
+        z, e = ctypes.c_double(), ctypes.c_double()
+        w, r0 = np.empty(2), np.empty(2)
+        Ra, Rb = np.empty(self.dim), np.empty(self.dim)
+        it = ctypes.c_int()
+        self._check(self.lib.sccsd_solve_scc(self.h, float(tol), int(maxit), float(ground_tol),
+                                             float(eom_tol), ctypes.addressof(z),
+                                             ctypes.addressof(e), w.ctypes.data, r0.ctypes.data,
+                                             Ra.ctypes.data, Rb.ctypes.data,
+                                             ctypes.addressof(it)))
+        return {"zeta": z.value, "e_corr": e.value, "omega": w, "r0": r0, "Ra": Ra, "Rb": Rb,
+                "iterations": it.value}
 
     def profile(self, enable=True):
         self._check(self.lib.sccsd_profile(self.h, 1 if enable else 0))

@@ -29,9 +29,16 @@ struct LeftSec {
   int Lb1, Lb2, lt1, lt2;
 };
 
+// O_ab of the natural projection for two states given as (R0, R1, R2)
+struct OverlapSec {
+  int ra0, ra1, ra2, rb0, rb1, rb2;
+  int O;
+};
+
 struct Model {
   Graph g;
   bool scc = false;
+  std::unique_ptr<OverlapSec> ovl;
   Graph::Ranges fwd;
   std::vector<int> vol_inputs;
   std::map<int64_t, RightSec> right;  // batched right transformations by batch size
@@ -129,6 +136,44 @@ static std::unique_ptr<Model> build_model(Backend* be, int o, int v, int J, bool
   M->vol_inputs = {M->R1, M->R2, M->Lb1, M->Lb2, M->s_l0r0, M->s_l0, M->s_r0};
   g.set_volatile_inputs(M->vol_inputs);
   return M;
+}
+
+// O_ab = <psi_a|P|psi_b>, P onto HF + singles + doubles, psi = exp(T)(R0 + R)|HF>
+// with T without X3 (Sec. 2.4.2): the Hilbert-space inner product of
+//   c0 = R0, c1 = r1 + R0 t1, c2 = r2 + (t1 x r1 + transpose) + R0 (t2 + t1 x t1)
+// with <S|S'> = 2 sum c1 c1' and <D|D'> = sum c2 (2 c2' - c2' with i <-> j).
+static OverlapSec& overlap_section(Model& M) {
+  if (M.ovl) return *M.ovl;
+  Graph& g = M.g;
+  const int64_t o = g.o, v = g.v;
+  auto S = std::make_unique<OverlapSec>();
+  S->ra0 = g.input({}, "Oa0");
+  S->ra1 = g.input({v, o}, "Oa1");
+  S->ra2 = g.input({o, o, v, v}, "Oa2");
+  S->rb0 = g.input({}, "Ob0");
+  S->rb1 = g.input({v, o}, "Ob1");
+  S->rb2 = g.input({o, o, v, v}, "Ob2");
+  int tt = g.contract(M.t1, "ai", M.t1, "bj", "ijab");
+  auto state = [&](int r0, int r1, int r2, int& c1, int& c2) {
+    c1 = g.add("ai", {{r1, "ai", 1.0}, {g.contract(r0, "", M.t1, "ai", "ai"), "ai", 1.0}});
+    int tr = g.contract(M.t1, "ai", r1, "bj", "ijab");
+    int tp = g.add("ijab", {{M.t2, "ijab", 1.0}, {tt, "ijab", 1.0}});
+    c2 = g.add("ijab", {{r2, "ijab", 1.0},
+                        {tr, "ijab", 1.0},
+                        {tr, "jiba", 1.0},
+                        {g.contract(r0, "", tp, "ijab", "ijab"), "ijab", 1.0}});
+  };
+  int ca1, ca2, cb1, cb2;
+  state(S->ra0, S->ra1, S->ra2, ca1, ca2);
+  state(S->rb0, S->rb1, S->rb2, cb1, cb2);
+  int q = g.add("ijab", {{cb2, "ijab", 2.0}, {cb2, "jiab", -1.0}});
+  S->O = g.add("", {{g.contract(S->ra0, "", S->rb0, "", ""), "", 1.0},
+                    {g.contract(ca1, "ai", cb1, "ai", ""), "", 2.0},
+                    {g.contract(ca2, "ijab", q, "ijab", ""), "", 1.0}});
+  for (int x : {S->ra0, S->ra1, S->ra2, S->rb0, S->rb1, S->rb2}) M.vol_inputs.push_back(x);
+  g.set_volatile_inputs(M.vol_inputs);
+  M.ovl = std::move(S);
+  return *M.ovl;
 }
 
 // sigma = A R for nb trial vectors at once (forward mode with a batch label)
@@ -678,6 +723,24 @@ void transform(sccsd_ctx* c, int side, int nvec, const double* V, double* W) {
 
 extern "C" {
 
+int sccsd_overlap(sccsd_ctx* c, double ra0, const double* Ra, double rb0, const double* Rb,
+                  double* O) {
+  if (!c) return SCCSD_EINVAL;
+  if (!Ra || !Rb || !O) return fail(c, SCCSD_EINVAL, "NULL argument");
+  if (!c->cur) return fail(c, SCCSD_ESTATE, "call sccsd_residual or a solver first");
+  return guarded(c, [&] {
+    Model& m = *c->cur;
+    OverlapSec& S = overlap_section(m);
+    set_scalar(c, m.g, S.ra0, ra0);
+    set_scalar(c, m.g, S.rb0, rb0);
+    load_packed(c, m.g, Ra, S.ra1, S.ra2, false);
+    load_packed(c, m.g, Rb, S.rb1, S.rb2, false);
+    m.g.run({S.O});
+    *O = get_scalar(c, m.g, S.O);
+    c->be->sync();
+  });
+}
+
 int sccsd_set_precision(sccsd_ctx* c, int precision) {
   if (!c) return SCCSD_EINVAL;
   if (precision < SCCSD_FP64 || precision > SCCSD_BF16) return fail(c, SCCSD_EINVAL, "bad precision");
@@ -982,6 +1045,97 @@ int sccsd_solve_states(sccsd_ctx* c, int nroots, int side, double tol, int maxit
   });
   if (rc != SCCSD_OK) return rc;
   if (status != SCCSD_OK) return fail(c, status, "roots not converged within maxit");
+  return SCCSD_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+// Self-consistent SCCSD for the two lowest states (K = {a, b}, Sec. 2.4.2).
+int sccsd_solve_scc(sccsd_ctx* c, double tol, int maxit, double ground_tol, double eom_tol,
+                    double* zeta_out, double* e_corr, double* omega2, double* r0_2, double* Ra_out,
+                    double* Rb_out, int* iterations) {
+  if (!c) return SCCSD_EINVAL;
+  if (!(tol > 0.0) || maxit < 1 || !(ground_tol > 0.0) || !(eom_tol > 0.0))
+    return fail(c, SCCSD_EINVAL, "bad tolerances or iteration limit");
+  int status = SCCSD_OK;
+  int rc = guarded(c, [&] {
+    const int64_t dim = c->dim;
+    std::vector<double> t(dim), vecs(2 * dim), sig(2 * dim), Ra(dim), Rb(dim);
+    double zeta = 0.0, E = 0.0, O = 0.0;
+    double w[2] = {0.0, 0.0}, r0[2] = {0.0, 0.0};
+    bool have_states = false, have_t = false;
+    std::vector<std::pair<double, double>> hist;
+    auto check = [&](int r) {
+      if (r != SCCSD_OK) throw std::runtime_error("inner solver failed: " + c->err);
+    };
+    int it = 0;
+    for (it = 1; it <= maxit; ++it) {
+      int gi = 0;
+      if (have_states)
+        check(sccsd_solve_ground(c, have_t ? t.data() : nullptr, zeta, Ra.data(), Rb.data(),
+                                 ground_tol, 1000, 1e-5, t.data(), &E, &gi));
+      else
+        check(sccsd_solve_ground(c, nullptr, 0.0, nullptr, nullptr, ground_tol, 1000, 1e-5,
+                                 t.data(), &E, &gi));
+      have_t = true;
+      int si = 0;
+      check(sccsd_solve_states(c, 2, 0, eom_tol, 1000, 1e-4, w, vecs.data(), &si));
+      // sign convention: largest |component| positive
+      for (int k = 0; k < 2; ++k) {
+        double* x = vecs.data() + k * dim;
+        int64_t im = 0;
+        for (int64_t q = 1; q < dim; ++q)
+          if (std::fabs(x[q]) > std::fabs(x[im])) im = q;
+        if (x[im] < 0)
+          for (int64_t q = 0; q < dim; ++q) x[q] = -x[q];
+      }
+      double etaR[2];
+      check(sccsd_jacobian_right(c, 2, vecs.data(), sig.data(), etaR));
+      r0[0] = etaR[0] / w[0];
+      r0[1] = etaR[1] / w[1];
+      check(sccsd_overlap(c, r0[0], vecs.data(), r0[1], vecs.data() + dim, &O));
+      if (getenv("SCCSD_LOG"))
+        fprintf(stderr, "{\"solver\": \"scc\", \"iter\": %d, \"zeta\": %.12f, \"O_ab\": %.3e, \"omega\": [%.12f, %.12f]}\n",
+                it, zeta, O, w[0], w[1]);
+      hist.push_back({zeta, O});
+      std::copy(vecs.begin(), vecs.begin() + dim, Ra.begin());
+      std::copy(vecs.begin() + dim, vecs.end(), Rb.begin());
+      have_states = true;
+      if (std::fabs(O) < tol && hist.size() > 1 &&
+          std::fabs(hist[hist.size() - 1].first - hist[hist.size() - 2].first) < 1e-8)
+        break;
+      if (hist.size() == 1) {
+        zeta = zeta - O;
+      } else {
+        auto [z1, o1] = hist[hist.size() - 2];
+        auto [z2, o2] = hist[hist.size() - 1];
+        zeta = (o2 != o1) ? z2 - o2 * (z2 - z1) / (o2 - o1) : z2;
+      }
+    }
+    if (it > maxit) status = SCCSD_ENOTCONV;
+    if (zeta_out) *zeta_out = hist.back().first;
+    if (e_corr) *e_corr = E;
+    if (omega2) {
+      omega2[0] = w[0];
+      omega2[1] = w[1];
+    }
+    if (r0_2) {
+      r0_2[0] = r0[0];
+      r0_2[1] = r0[1];
+    }
+    for (auto pr : {std::make_pair(Ra_out, &Ra), std::make_pair(Rb_out, &Rb)}) {
+      if (!pr.first) continue;
+      if (c->be->is_device(pr.first))
+        c->be->upload(pr.first, pr.second->data(), dim, false);
+      else
+        std::memcpy(pr.first, pr.second->data(), sizeof(double) * dim);
+    }
+    if (iterations) *iterations = std::min(it, maxit);
+  });
+  if (rc != SCCSD_OK) return rc;
+  if (status != SCCSD_OK) return fail(c, status, "zeta iteration not converged within maxit");
   return SCCSD_OK;
 }
 

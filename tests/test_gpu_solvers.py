@@ -68,3 +68,27 @@ def test_mixed_precision_refinement_medium(precision):
     wm, _, _ = ctx.solve_states(1, "right", tol=1e-7, maxit=400, refine_tol=1e-4, vecs=False)
     assert np.abs(wm - w64).max() < 1e-8
     ctx.close()
+
+
+def test_scc_self_consistent_small():
+    """SCCSD for the two lowest states of an o=3, v=8 system: zeta, the energies
+    and the constrained overlap agree with the oracle's self-consistent loop,
+    and O_ab vanishes at the solution."""
+    from oracle import scc as sc
+    from paper_2403_01007_gb300 import binding as B
+    o, v, J = 3, 8, 14
+    eps, L = syn.system(o, v, J, 0.1, 123)
+    prob = cc.Problem(eps, L, o)
+    ref = sc.solve_scc(prob, tol=1e-10)
+    Ehf = float(rp.residual(prob, np.zeros(prob.dim))[0])
+    ctx = B.Context(o, v, J, eps, L)
+    r = ctx.solve_scc(tol=1e-10)
+    assert abs(r["zeta"] - ref["zeta"]) < 1e-7
+    assert np.abs(r["omega"] - ref["omega"]).max() < 1e-8
+    assert abs(r["e_corr"] - (ref["E0"] - Ehf)) < 1e-9
+    # the constraint holds for the returned states (checked by the oracle)
+    Oo = float(sc.overlap(torch.tensor(ref["t"]), r["r0"][0], torch.tensor(r["Ra"]),
+                          r["r0"][1], torch.tensor(r["Rb"]), o, v))
+    assert abs(Oo) < 1e-8
+    assert abs(r["zeta"]) > 0.1        # the constraint is active on this system
+    ctx.close()
