@@ -170,8 +170,9 @@ int sccsd_set_precision(sccsd_ctx* ctx, int precision);
  * D_aibj = D_ai + D_bj, with DIIS (8 vectors). Starts from t0 (packed ket) or
  * from zero (whose first step is the MP2 guess). With a mixed precision and
  * refine_tol > 0 the iterations run in that precision until |Omega| <
- * refine_tol and finish in FP64 (iterative refinement); the FP64 residual
- * then decides convergence (|Omega|_2 < tol). Outputs (each may be NULL):
+ * refine_tol, or until they stall (no 10% improvement in 6 iterations: the
+ * noise floor of the mixed arithmetic), and finish in FP64 (iterative
+ * refinement); the FP64 residual then decides convergence (|Omega|_2 < tol). Outputs (each may be NULL):
  * t_out (packed), e_corr, iterations. The converged state is fixed for the
  * Jacobian and density calls. SCCSD_ENOTCONV when maxit is reached (outputs
  * hold the last iterate). */
@@ -187,11 +188,55 @@ int sccsd_solve_ground(sccsd_ctx* ctx, const double* t0, double zeta, const doub
  * for doubles); restarts keep the current and previous Ritz vectors. The
  * subspace eigenproblem and all vector work run on the device. Convergence: |A x - omega x| / |x| < tol for every
  * root. Mixed precisions refine in FP64 once every residual is below
- * refine_tol (refine_tol <= 0: no refinement). Outputs: omega[nroots],
+ * refine_tol or the residuals stall for 8 iterations (refine_tol <= 0: no
+ * refinement). Outputs: omega[nroots],
  * vecs[nroots][dim] (unit-norm packed vectors, may be NULL), iterations.
  * SCCSD_ECOMPLEX if a complex pair appears among the wanted roots. */
 int sccsd_solve_states(sccsd_ctx* ctx, int nroots, int side, double tol, int maxit,
                        double refine_tol, double* omega, double* vecs, int* iterations);
+
+/* ---- Learned initial guess and preconditioner ----------------------------
+ * A per-amplitude MLP (BF16 weights and activations, FP32 accumulation) maps
+ * MP2-level features of each doubles amplitude to (t_ij^ab / s_t,
+ * log(D'_ij^ab / D_ij^ab)): a guess for the converged amplitude and for the
+ * dressed denominator D' (the diagonal of the Jacobian estimated from the
+ * intermediates) used as the ground-state preconditioner. The plain solver
+ * judges the result: the guess only sets the starting point and the update
+ * preconditioner, and callers fall back to t0 = 0 (MP2 first step) and D.
+ * (An extension of the method, not in the paper.) */
+typedef struct sccsd_mlp sccsd_mlp;
+
+/* Network with n_in inputs, n_hidden_layers hidden layers of width hidden
+ * (ReLU), n_out outputs; He-uniform initialisation from a splitmix64 stream. */
+int sccsd_mlp_create(sccsd_mlp** net, int n_in, int hidden, int n_hidden_layers, int n_out,
+                     unsigned long long seed, void* stream);
+void sccsd_mlp_destroy(sccsd_mlp* net);
+const char* sccsd_mlp_last_error(sccsd_mlp* net);
+long long sccsd_mlp_num_params(sccsd_mlp* net);
+/* parameters as one host FP32 array, per layer W[in][out] then b[out] */
+int sccsd_mlp_get_params(sccsd_mlp* net, float* params);
+int sccsd_mlp_set_params(sccsd_mlp* net, const float* params);
+/* Y[N][n_out] = net(X[N][n_in]); device FP32 arrays */
+int sccsd_mlp_forward(sccsd_mlp* net, const float* X, long long N, float* Y);
+/* gradient of the mean-squared error against T[N][n_out] (host FP32 array
+ * laid out like the parameters) and the loss */
+int sccsd_mlp_gradient(sccsd_mlp* net, const float* X, const float* T, long long N, float* grad,
+                       float* loss);
+/* one Adam step (beta 0.9/0.999) on the minibatch; loss before the step */
+int sccsd_mlp_train_step(sccsd_mlp* net, const float* X, const float* T, long long N, float lr,
+                         float* loss);
+
+/* Features X[o^2 v^2][10] (device FP32) of every full doubles element
+ * (i,j,a,b), evaluated at the MP2 amplitudes; scales[3] = (s_t, s_g, s_D).
+ * Leaves the fixed state at the MP2 amplitudes. */
+int sccsd_learned_features(sccsd_ctx* ctx, float* X, double* scales);
+/* Training targets Y[o^2 v^2][2] (device FP32) from converged amplitudes t. */
+int sccsd_learned_targets(sccsd_ctx* ctx, const double* t, double s_t, float* Y);
+/* Packed initial amplitudes t0 and packed preconditioner Dprec proposed by net. */
+int sccsd_learned_guess(sccsd_ctx* ctx, sccsd_mlp* net, double* t0, double* Dprec);
+/* Preconditioner of sccsd_solve_ground's update (packed, positive), or NULL
+ * for the orbital-energy denominators D. */
+int sccsd_set_preconditioner(sccsd_ctx* ctx, const double* Dprec);
 
 /* Size of a packed vector. */
 long long sccsd_dim(int o, int v);

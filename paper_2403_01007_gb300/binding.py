@@ -53,6 +53,28 @@ def _declare(lib):
     lib.sccsd_solve_scc.argtypes = [_dp, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
     lib.sccsd_solve_scc.restype = ctypes.c_int
+    lib.sccsd_mlp_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, _dp]
+    lib.sccsd_mlp_destroy.argtypes = [_dp]
+    lib.sccsd_mlp_destroy.restype = None
+    lib.sccsd_mlp_last_error.argtypes = [_dp]
+    lib.sccsd_mlp_last_error.restype = ctypes.c_char_p
+    lib.sccsd_mlp_num_params.argtypes = [_dp]
+    lib.sccsd_mlp_num_params.restype = ctypes.c_longlong
+    lib.sccsd_mlp_get_params.argtypes = [_dp, _dp]
+    lib.sccsd_mlp_set_params.argtypes = [_dp, _dp]
+    lib.sccsd_mlp_forward.argtypes = [_dp, _dp, ctypes.c_longlong, _dp]
+    lib.sccsd_mlp_gradient.argtypes = [_dp, _dp, _dp, ctypes.c_longlong, _dp, _dp]
+    lib.sccsd_mlp_train_step.argtypes = [_dp, _dp, _dp, ctypes.c_longlong, ctypes.c_float, _dp]
+    lib.sccsd_learned_features.argtypes = [_dp, _dp, _dp]
+    lib.sccsd_learned_targets.argtypes = [_dp, _dp, ctypes.c_double, _dp]
+    lib.sccsd_learned_guess.argtypes = [_dp, _dp, _dp, _dp]
+    lib.sccsd_set_preconditioner.argtypes = [_dp, _dp]
+    for f in ("sccsd_mlp_create", "sccsd_mlp_get_params", "sccsd_mlp_set_params",
+              "sccsd_mlp_forward", "sccsd_mlp_gradient", "sccsd_mlp_train_step",
+              "sccsd_learned_features", "sccsd_learned_targets", "sccsd_learned_guess",
+              "sccsd_set_preconditioner"):
+        getattr(lib, f).restype = ctypes.c_int
     lib.sccsd_dim.argtypes = [ctypes.c_int, ctypes.c_int]
     lib.sccsd_dim.restype = ctypes.c_longlong
     lib.sccsd_last_error.argtypes = [_dp]
@@ -132,6 +154,75 @@ def gemm_tn_noalloc(A, B, C, alpha=1.0, lib=None):
     if rc != 0:
         raise SccsdError(rc, lib.sccsd_strerror(rc).decode())
     return C
+
+
+def _fptr(x):
+    """Pointer of a float32 array (NumPy or torch)."""
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float32 or not x.flags.c_contiguous:
+            raise TypeError("arrays must be C-contiguous float32")
+        return x.ctypes.data
+    import torch
+    if x.dtype != torch.float32 or not x.is_contiguous():
+        raise TypeError("tensors must be contiguous float32")
+    return x.data_ptr()
+
+
+class Mlp:
+    """Per-amplitude network of the learned guess (BF16 weights, FP32 accumulation)."""
+
+    def __init__(self, n_in=10, hidden=256, layers=3, n_out=2, seed=1, lib=None):
+        self.lib = lib or load()
+        h = ctypes.c_void_p()
+        rc = self.lib.sccsd_mlp_create(ctypes.byref(h), n_in, hidden, layers, n_out, seed, None)
+        if rc != 0:
+            raise SccsdError(rc, "mlp create failed")
+        self.h = h
+        self.n_in, self.n_out = n_in, n_out
+
+    def _check(self, rc):
+        if rc != 0:
+            raise SccsdError(rc, self.lib.sccsd_mlp_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sccsd_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def num_params(self):
+        return self.lib.sccsd_mlp_num_params(self.h)
+
+    def get_params(self):
+        p = np.empty(self.num_params(), dtype=np.float32)
+        self._check(self.lib.sccsd_mlp_get_params(self.h, p.ctypes.data))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._check(self.lib.sccsd_mlp_set_params(self.h, p.ctypes.data))
+
+    def forward(self, X, Y):
+        self._check(self.lib.sccsd_mlp_forward(self.h, _fptr(X), X.shape[0], _fptr(Y)))
+        return Y
+
+    def gradient(self, X, T):
+        g = np.empty(self.num_params(), dtype=np.float32)
+        loss = ctypes.c_float()
+        self._check(self.lib.sccsd_mlp_gradient(self.h, _fptr(X), _fptr(T), X.shape[0],
+                                                g.ctypes.data, ctypes.addressof(loss)))
+        return g, loss.value
+
+    def train_step(self, X, T, lr):
+        loss = ctypes.c_float()
+        self._check(self.lib.sccsd_mlp_train_step(self.h, _fptr(X), _fptr(T), X.shape[0],
+                                                  float(lr), ctypes.addressof(loss)))
+        return loss.value
 
 
 class Context:
@@ -239,6 +330,24 @@ class Context:
                                              ctypes.addressof(it)))
         return {"zeta": z.value, "e_corr": e.value, "omega": w, "r0": r0, "Ra": Ra, "Rb": Rb,
                 "iterations": it.value}
+
+    def learned_features(self, X):
+        """Features [o^2 v^2][10] (device float32) at the MP2 amplitudes; returns scales."""
+        sc = np.empty(3)
+        self._check(self.lib.sccsd_learned_features(self.h, _fptr(X), sc.ctypes.data))
+        return sc
+
+    def learned_targets(self, t, s_t, Y):
+        self._check(self.lib.sccsd_learned_targets(self.h, _ptr(t), float(s_t), _fptr(Y)))
+        return Y
+
+    def learned_guess(self, net):
+        t0, D = np.empty(self.dim), np.empty(self.dim)
+        self._check(self.lib.sccsd_learned_guess(self.h, net.h, t0.ctypes.data, D.ctypes.data))
+        return t0, D
+
+    def set_preconditioner(self, D=None):
+        self._check(self.lib.sccsd_set_preconditioner(self.h, _ptr(D)))
 
     def profile(self, enable=True):
         self._check(self.lib.sccsd_profile(self.h, 1 if enable else 0))

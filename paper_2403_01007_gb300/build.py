@@ -14,7 +14,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "lib")
 OBJ = os.path.join(HERE, "lib", "obj")
 SOURCES = ["graph.cpp", "ccsd_graph.cpp", "api.cpp", "cuda_backend.cu", "tc_gemm.cu",
-           "noalloc.cu", "small_la.cu"]
+           "noalloc.cu", "small_la.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

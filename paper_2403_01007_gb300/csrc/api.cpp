@@ -239,6 +239,8 @@ struct sccsd_ctx {
   std::vector<double> eps_host;
   double* eps_dev = nullptr;  // orbital energies on the device
   double* D = nullptr;        // packed orbital-energy denominators
+  double* Dprec = nullptr;    // user/learned preconditioner of the ground-state update
+  bool use_dprec = false;
   std::vector<double*> sv;    // solver work buffers
   double* sv_small = nullptr; // small matrices and vectors
   int* sv_info = nullptr;
@@ -251,7 +253,7 @@ struct sccsd_ctx {
     plain.reset();
     scc.reset();
     if (be) {
-      for (double* p : {L, h, delta, stage, stage2, eps_dev, D, sv_small})
+      for (double* p : {L, h, delta, stage, stage2, eps_dev, D, Dprec, sv_small})
         if (p) be->release(p);
       for (double* p : sv)
         if (p) be->release(p);
@@ -787,6 +789,8 @@ int sccsd_solve_ground(sccsd_ctx* c, const double* t0, double zeta, const double
     bool fp64_phase = !refine;
     int nh = 0, head = 0, it = 0;
     double E = 0.0, nrm = 0.0;
+    double best = 1e300;
+    int since_best = 0;
     for (it = 1; it <= maxit; ++it) {
       E = eval_residual(c, t, zeta, ra, rb, om);
       nrm = std::sqrt(d.dot(om, om, dim));
@@ -794,7 +798,14 @@ int sccsd_solve_ground(sccsd_ctx* c, const double* t0, double zeta, const double
         fprintf(stderr, "{\"solver\": \"ground\", \"iter\": %d, \"fp64\": %d, \"residual\": %.3e, \"e_corr\": %.12f}\n", it,
                 (int)fp64_phase, nrm, E - c->e_hf);
       if (!std::isfinite(nrm)) throw std::runtime_error("ground state diverged (non-finite residual)");
-      if (!fp64_phase && nrm < refine_tol) {
+      if (nrm < 0.9 * best) {
+        best = nrm;
+        since_best = 0;
+      } else {
+        ++since_best;
+      }
+      // the mixed phase ends below refine_tol, or when it stalls at its noise floor
+      if (!fp64_phase && (nrm < refine_tol || since_best >= 6)) {
         // mixed-precision phase done: refine in FP64 from the current amplitudes
         switch_precision(c, SCCSD_FP64);
         fp64_phase = true;
@@ -804,7 +815,7 @@ int sccsd_solve_ground(sccsd_ctx* c, const double* t0, double zeta, const double
         continue;
       }
       if (fp64_phase && nrm < tol) break;
-      launch_jacobi(d.st(), dim, t, om, c->D, tn);
+      launch_jacobi(d.st(), dim, t, om, c->use_dprec ? c->Dprec : c->D, tn);
       const int slot = head;
       head = (head + 1) % kDiis;
       nh = std::min(nh + 1, kDiis);
@@ -922,6 +933,8 @@ int sccsd_solve_states(sccsd_ctx* c, int nroots, int side, double tol, int maxit
     std::vector<double> lam(nroots), res(nroots);
     int it = 0;
     bool converged = false;
+    double best = 1e300;
+    int since_best = 0;
     for (it = 1; it <= maxit; ++it) {
       // subspace matrix and its lowest roots
       c->be->gemm_tn(1, m, m, dim, 1.0, V, W, S, false);
@@ -955,7 +968,13 @@ int sccsd_solve_states(sccsd_ctx* c, int nroots, int side, double tol, int maxit
         for (int k = 0; k < nroots; ++k) fprintf(stderr, "%s%.12f", k ? ", " : "", lam[k]);
         fprintf(stderr, "]}\n");
       }
-      if (!fp64_phase && worst < refine_tol) {
+      if (worst < 0.9 * best) {
+        best = worst;
+        since_best = 0;
+      } else {
+        ++since_best;
+      }
+      if (!fp64_phase && (worst < refine_tol || since_best >= 8)) {
         // restart in FP64 from the current Ritz vectors
         switch_precision(c, SCCSD_FP64);
         fp64_phase = true;
@@ -1137,6 +1156,143 @@ int sccsd_solve_scc(sccsd_ctx* c, double tol, int maxit, double ground_tol, doub
   if (rc != SCCSD_OK) return rc;
   if (status != SCCSD_OK) return fail(c, status, "zeta iteration not converged within maxit");
   return SCCSD_OK;
+}
+
+}  // extern "C"
+
+// ======================================================================
+// Learned initial guess and preconditioner (per-amplitude MLP)
+// ======================================================================
+namespace {
+
+// diagonals f of the dressed one-body intermediates at the fixed state
+void dressed_diagonals(sccsd_ctx* c, double* f) {
+  Model& m = *c->cur;
+  m.g.run({m.er.Fooi, m.er.Fvvi});
+  const int64_t o = c->o, v = c->v;
+  int64_t d1[1] = {o}, os1[1] = {1}, is1[1] = {o + 1};
+  c->be->copy_view(1, d1, f, os1, m.g.data(m.er.Fooi), is1, 1.0, false);
+  int64_t d2[1] = {v}, os2[1] = {1}, is2[1] = {v + 1};
+  c->be->copy_view(1, d2, f + o, os2, m.g.data(m.er.Fvvi), is2, 1.0, false);
+}
+
+struct Scales {
+  double st, sg, sD;
+};
+
+// features at the MP2 amplitudes into X [o^2 v^2][10]; returns the scales
+Scales learned_features(sccsd_ctx* c, float* X) {
+  Dev d{c};
+  ensure_small(c);
+  const int64_t dim = c->dim, o = c->o, v = c->v, nf = o * o * v * v;
+  double* tz = solver_buf(c, 30, dim);
+  double* om = solver_buf(c, 31, dim);
+  double* tm = solver_buf(c, 32, dim);
+  double* t1 = solver_buf(c, 33, o * v);
+  double* t2 = solver_buf(c, 34, nf);
+  double* f = solver_buf(c, 35, o + v);
+  c->be->fill(tz, dim, 0.0);
+  eval_residual(c, tz, 0.0, nullptr, nullptr, om);
+  launch_jacobi(d.st(), dim, tz, om, c->D, tm);          // MP2 first iterate
+  eval_residual(c, tm, 0.0, nullptr, nullptr, om);
+  dressed_diagonals(c, f);
+  Model& m = *c->cur;
+  m.g.run({m.er.Govov});
+  const double* g = m.g.data(m.er.Govov);
+  c->be->unpack(tm, c->o, c->v, t1, t2, false);
+  Scales s;
+  s.st = std::sqrt(d.dot(t2, t2, nf) / nf);
+  s.sg = std::sqrt(d.dot(g, g, nf) / nf);
+  double eo = 0, ev = 0;
+  for (int i = 0; i < c->o; ++i) eo += c->eps_host[i];
+  for (int a = 0; a < c->v; ++a) ev += c->eps_host[c->o + a];
+  s.sD = 2.0 * (ev / c->v - eo / c->o);
+  if (!(s.st > 0)) s.st = 1.0;
+  if (!(s.sg > 0)) s.sg = 1.0;
+  launch_learned_features(d.st(), c->o, c->v, t2, g, c->eps_dev, f, s.st, s.sg, s.sD, X);
+  return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sccsd_learned_features(sccsd_ctx* c, float* X, double* scales) {
+  if (!c || !X) return SCCSD_EINVAL;
+  if (!c->be->is_device(X)) return fail(c, SCCSD_EINVAL, "X must be device memory");
+  return guarded(c, [&] {
+    Scales s = learned_features(c, X);
+    if (scales) {
+      scales[0] = s.st;
+      scales[1] = s.sg;
+      scales[2] = s.sD;
+    }
+    c->be->sync();
+  });
+}
+
+int sccsd_learned_targets(sccsd_ctx* c, const double* t, double st, float* Y) {
+  if (!c || !t || !Y || !(st > 0)) return SCCSD_EINVAL;
+  if (!c->be->is_device(Y)) return fail(c, SCCSD_EINVAL, "Y must be device memory");
+  return guarded(c, [&] {
+    const int64_t dim = c->dim, o = c->o, v = c->v, nf = o * o * v * v;
+    double* tt = solver_buf(c, 30, dim);
+    double* om = solver_buf(c, 31, dim);
+    double* t1 = solver_buf(c, 33, o * v);
+    double* t2 = solver_buf(c, 34, nf);
+    double* f = solver_buf(c, 35, o + v);
+    c->be->upload(tt, t, dim, c->be->is_device(t));
+    eval_residual(c, tt, 0.0, nullptr, nullptr, om);
+    dressed_diagonals(c, f);
+    c->be->unpack(tt, c->o, c->v, t1, t2, false);
+    launch_learned_targets((cudaStream_t)c->be->stream(), c->o, c->v, t2, c->eps_dev, f, st, Y);
+    c->be->sync();
+  });
+}
+
+int sccsd_mlp_forward(sccsd_mlp* net, const float* X, long long N, float* Y);
+
+int sccsd_learned_guess(sccsd_ctx* c, sccsd_mlp* net, double* t0, double* Dprec) {
+  if (!c || !net || !t0 || !Dprec) return SCCSD_EINVAL;
+  return guarded(c, [&] {
+    const int64_t dim = c->dim, o = c->o, v = c->v, nf = o * o * v * v;
+    float* X = (float*)solver_buf(c, 36, nf * 5);   // nf x 10 floats
+    float* Y = (float*)solver_buf(c, 37, nf);       // nf x 2 floats
+    Scales s = learned_features(c, X);
+    if (sccsd_mlp_forward(net, X, nf, Y) != SCCSD_OK) throw std::runtime_error("network forward failed");
+    double* t2 = solver_buf(c, 34, nf);
+    double* d2 = solver_buf(c, 38, nf);
+    double* z1 = solver_buf(c, 39, o * v);
+    double* f = solver_buf(c, 35, o + v);
+    double* outt = solver_buf(c, 40, dim);
+    double* outd = solver_buf(c, 41, dim);
+    cudaStream_t st = (cudaStream_t)c->be->stream();
+    launch_learned_apply(st, c->o, c->v, Y, c->eps_dev, s.st, t2, d2);
+    c->be->fill(z1, o * v, 0.0);
+    c->be->pack(z1, t2, c->o, c->v, outt, false);
+    // singles of the preconditioner: dressed denominators at the MP2 amplitudes
+    double* fd = solver_buf(c, 42, dim);
+    launch_denoms(st, c->o, c->v, f, fd);
+    c->be->pack(z1, d2, c->o, c->v, outd, false);
+    c->be->upload(outd, fd, o * v, true);
+    c->be->download(t0, outt, dim, c->be->is_device(t0));
+    c->be->download(Dprec, outd, dim, c->be->is_device(Dprec));
+    c->be->sync();
+  });
+}
+
+int sccsd_set_preconditioner(sccsd_ctx* c, const double* Dprec) {
+  if (!c) return SCCSD_EINVAL;
+  return guarded(c, [&] {
+    if (!Dprec) {
+      c->use_dprec = false;
+      return;
+    }
+    if (!c->Dprec) c->Dprec = c->be->alloc(c->dim);
+    c->be->upload(c->Dprec, Dprec, c->dim, c->be->is_device(Dprec));
+    c->use_dprec = true;
+    c->be->sync();
+  });
 }
 
 }  // extern "C"

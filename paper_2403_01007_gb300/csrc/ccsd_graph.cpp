@@ -120,6 +120,7 @@ EnergyResidual build_energy_residual(Graph& g, int t1, int t2, int L, int h, int
                           {g.contract(t2, "ikab", Fooi, "kj", "ijab", 1.0, true), "ijab", -1.0}});
   r.Fvvi = Fvvi;
   r.Fooi = Fooi;
+  r.Govov = Govov;
   int Pp = g.add("ijab", {{C2, "ijab", 1.0}, {D2, "ijab", 1.0}, {E2, "ijab", 1.0}});
   r.O2 = g.add("ijab", {{A2, "ijab", 1.0},
                         {lad, "ijab", 1.0},

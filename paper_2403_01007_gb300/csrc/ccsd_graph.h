@@ -10,6 +10,7 @@ struct EnergyResidual {
   // dressed one-body intermediates whose diagonals approximate the diagonal of
   // the Jacobian (the Davidson preconditioner): Fvv'[b][c], Foo'[k][j]
   int Fvvi = -1, Fooi = -1;
+  int Govov = -1;  // g_iajb as [i][j][a][b] (undressed)
 };
 
 // Builds E0 = <HF|Hbar|HF> and Omega_mu = <mu~|Hbar|HF> (Sec. 2.1) in the

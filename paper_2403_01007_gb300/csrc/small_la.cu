@@ -436,3 +436,86 @@ void launch_ritz_residual(cudaStream_t st, int nr, int64_t n, const double* ax, 
 }
 
 }  // namespace sccsd
+
+namespace sccsd {
+
+// Per-amplitude features of the learned guess, for every full doubles element
+// (i, j, a, b) (row index ((i*o + j)*v + a)*v + b), all symmetric under
+// (ia) <-> (jb):
+//   0 t_MP2 / st   1 g_iajb / sg   2 g_ibja / sg   3 D / sD   4 log D
+//   5 log(D'_MP2 / D)   6 (e_a + e_b)/2   7 (e_i + e_j)/2   8 |e_a - e_b|   9 |e_i - e_j|
+// with D = e_a + e_b - e_i - e_j and D' the same from the diagonals f of the
+// dressed intermediates at the MP2 amplitudes.
+__global__ void k_learned_features(int o, int v, const double* __restrict__ tmp2,
+                                   const double* __restrict__ govov, const double* __restrict__ eps,
+                                   const double* __restrict__ f, double st, double sg, double sD,
+                                   float* __restrict__ X) {
+  const int64_t total = (int64_t)o * o * v * v;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = e % v, r1 = e / v, a = r1 % v, r2 = r1 / v, j = r2 % o, i = r2 / o;
+    const double ea = eps[o + a], eb = eps[o + b], ei = eps[i], ej = eps[j];
+    const double D = ea + eb - ei - ej;
+    const double Dp = f[o + a] + f[o + b] - f[i] - f[j];
+    const double exch = govov[((i * o + j) * v + b) * v + a];
+    float* x = X + e * 10;
+    x[0] = (float)(tmp2[e] / st);
+    x[1] = (float)(govov[e] / sg);
+    x[2] = (float)(exch / sg);
+    x[3] = (float)(D / sD);
+    x[4] = (float)log(D);
+    x[5] = (float)log(fmax(Dp, 1e-3) / D);
+    x[6] = (float)(0.5 * (ea + eb));
+    x[7] = (float)(0.5 * (ei + ej));
+    x[8] = (float)fabs(ea - eb);
+    x[9] = (float)fabs(ei - ej);
+  }
+}
+
+// targets: y0 = t / st, y1 = log(D'/D) for every full doubles element
+__global__ void k_learned_targets(int o, int v, const double* __restrict__ t,
+                                  const double* __restrict__ eps, const double* __restrict__ f,
+                                  double st, float* __restrict__ Y) {
+  const int64_t total = (int64_t)o * o * v * v;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = e % v, r1 = e / v, a = r1 % v, r2 = r1 / v, j = r2 % o, i = r2 / o;
+    const double D = eps[o + a] + eps[o + b] - eps[i] - eps[j];
+    const double Dp = f[o + a] + f[o + b] - f[i] - f[j];
+    Y[e * 2] = (float)(t[e] / st);
+    Y[e * 2 + 1] = (float)log(fmax(Dp, 1e-3) / D);
+  }
+}
+
+// network outputs -> full doubles guess t = y0 * st and preconditioner
+// D_prec = D * exp(y1) (clamped to [D/4, 8 D])
+__global__ void k_learned_apply(int o, int v, const float* __restrict__ Y,
+                                const double* __restrict__ eps, double st, double* __restrict__ t2,
+                                double* __restrict__ d2) {
+  const int64_t total = (int64_t)o * o * v * v;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = e % v, r1 = e / v, a = r1 % v, r2 = r1 / v, j = r2 % o, i = r2 / o;
+    const double D = eps[o + a] + eps[o + b] - eps[i] - eps[j];
+    t2[e] = (double)Y[e * 2] * st;
+    double s = exp((double)Y[e * 2 + 1]);
+    d2[e] = D * fmin(8.0, fmax(0.25, s));
+  }
+}
+
+void launch_learned_features(cudaStream_t st, int o, int v, const double* tmp2, const double* govov,
+                             const double* eps, const double* f, double s_t, double s_g, double s_D,
+                             float* X) {
+  k_learned_features<<<vgrid((int64_t)o * o * v * v), 256, 0, st>>>(o, v, tmp2, govov, eps, f, s_t,
+                                                                    s_g, s_D, X);
+}
+void launch_learned_targets(cudaStream_t st, int o, int v, const double* t, const double* eps,
+                            const double* f, double s_t, float* Y) {
+  k_learned_targets<<<vgrid((int64_t)o * o * v * v), 256, 0, st>>>(o, v, t, eps, f, s_t, Y);
+}
+void launch_learned_apply(cudaStream_t st, int o, int v, const float* Y, const double* eps, double s_t,
+                          double* t2, double* d2) {
+  k_learned_apply<<<vgrid((int64_t)o * o * v * v), 256, 0, st>>>(o, v, Y, eps, s_t, t2, d2);
+}
+
+}  // namespace sccsd

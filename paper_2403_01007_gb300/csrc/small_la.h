@@ -22,3 +22,13 @@ void launch_ritz_residual(cudaStream_t st, int nr, int64_t n, const double* ax, 
                           const double* wr, const int* order, double* r);
 
 }  // namespace sccsd
+
+namespace sccsd {
+void launch_learned_features(cudaStream_t st, int o, int v, const double* tmp2, const double* govov,
+                             const double* eps, const double* f, double s_t, double s_g, double s_D,
+                             float* X);
+void launch_learned_targets(cudaStream_t st, int o, int v, const double* t, const double* eps,
+                            const double* f, double s_t, float* Y);
+void launch_learned_apply(cudaStream_t st, int o, int v, const float* Y, const double* eps, double s_t,
+                          double* t2, double* d2);
+}  // namespace sccsd

@@ -122,3 +122,9 @@ void launch_ritz_residual(cudaStream_t, int, int64_t, const double*, const doubl
 }
 extern "C" long long sccsd_gemm_tn_noalloc_capacity(void) { return 0; }
 extern "C" int sccsd_gemm_tn_noalloc(long long, long long, long long, double, const double*, const double*, double*, void*) { return -1; }
+namespace sccsd {
+void launch_learned_features(cudaStream_t, int, int, const double*, const double*, const double*, const double*, double, double, double, float*) { no_device(); }
+void launch_learned_targets(cudaStream_t, int, int, const double*, const double*, const double*, double, float*) { no_device(); }
+void launch_learned_apply(cudaStream_t, int, int, const float*, const double*, double, double*, double*) { no_device(); }
+}
+extern "C" int sccsd_mlp_forward(struct sccsd_mlp*, const float*, long long, float*) { return -5; }

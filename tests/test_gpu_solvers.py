@@ -51,7 +51,7 @@ def test_eom_states_small(small):
     ctx.close()
 
 
-@pytest.mark.parametrize("precision", ["bf16x3"])
+@pytest.mark.parametrize("precision", ["bf16", "bf16x3"])
 def test_mixed_precision_refinement_medium(precision):
     """o=10 v=90 J=300: the mixed-precision solvers, refined in FP64 at the
     end, reproduce the FP64 GPU results to 1e-8 Eh (energy and roots)."""
