@@ -199,6 +199,77 @@ def kernel_case(args):
     return 0
 
 
+def batched_case(args):
+    """64 uneven instances (o in [4,12], v in [30,110], J = 3(o+v), 2-5 states
+    each): one batch of right transformations per instance and step, either as
+    per-instance calls or as one launch of the joined CUDA graph."""
+    import torch
+    from paper_2403_01007_gb300 import binding as B
+    inst = syn.batch_instances()
+    torch.cuda.set_device(0)
+    items = []
+    t_setup = time.perf_counter()
+    for k, x in enumerate(inst):
+        eps, L = syn.system(x.o, x.v, x.J, x.sd, x.seed)
+        st = torch.cuda.Stream()
+        ctx = B.Context(x.o, x.v, x.J, eps, L, precision=args.precision, stream=st.cuda_stream)
+        t = syn.random_vectors(x.o, x.v, 1, x.seed + 1000, scale=1e-2)[0]
+        ctx.residual(t)
+        R = torch.tensor(syn.random_vectors(x.o, x.v, x.nstates, x.seed + 2000, normalise=True),
+                         device="cuda")
+        items.append((ctx, R, torch.empty_like(R), torch.empty_like(R)))
+    setup_s = time.perf_counter() - t_setup
+    ntr = sum(x.nstates for x in inst)
+    flops = sum(x.nstates * transform_flops(x.o, x.v) for x in inst)
+
+    def per_instance():
+        for ctx, R, W, _ in items:
+            ctx.jacobian_right(R, sigma=W)
+
+    for _ in range(args.warmup):
+        per_instance()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        per_instance()
+    torch.cuda.synchronize()
+    per_s = (time.perf_counter() - t0) / args.steps
+
+    graphs = [ctx.capture_transform(R, Wg) for ctx, R, _, Wg in items]
+    batch = B.GraphBatch(graphs)
+    st = torch.cuda.Stream()
+    for _ in range(args.warmup):
+        batch.launch(st.cuda_stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(0) as clk:
+        e0.record(st)
+        for _ in range(args.steps):
+            batch.launch(st.cuda_stream)
+        e1.record(st)
+        torch.cuda.synchronize()
+    g_s = e0.elapsed_time(e1) / 1e3 / args.steps
+    rel = max(float((Wg - W).abs().max() / W.abs().max()) for _, _, W, Wg in items)
+    batch.close()
+    for ctx, *_ in items:
+        ctx.close()
+    print(json.dumps({
+        "metric": "Jacobian transforms/s, 64 uneven instances (o 4-12, v 30-110, 2-5 states)",
+        "value": ntr / g_s, "unit": "transforms/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": g_s * 1e3, "higher_is_better": True,
+        "dtype": {"bf16x3": "bf16x3->f32->f64", "bf16": "bf16->f32->f64", "fp64": "f64"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": "batch64_o4-12_v30-110", "instances": len(inst), "transforms": ntr,
+                   "precision": args.precision, "form": "one launch of the joined CUDA graph"},
+        "per_instance_calls": {"transforms_per_s": ntr / per_s, "ms_per_step": per_s * 1e3},
+        "graph_speedup": per_s / g_s,
+        "tflops_dense": flops / g_s / 1e12,
+        "max_rel_diff_graph_vs_calls": rel,
+        "setup_s": setup_s, "clocks": clk.summary()}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -216,7 +287,11 @@ def main():
     ap.add_argument("--kernel-case", type=int, default=0, metavar="V",
                     help="time only the ladder-shaped contraction (rows = nvec*21^2, "
                          "N = K = V^2) through sccsd_gemm_tn; a small case for profilers")
+    ap.add_argument("--batched", action="store_true",
+                    help="64 uneven instances: joined CUDA graph vs per-instance calls")
     args = ap.parse_args()
+    if args.batched and args.impl == "ours":
+        return batched_case(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.kernel_case:

@@ -238,6 +238,27 @@ int sccsd_learned_guess(sccsd_ctx* ctx, sccsd_mlp* net, double* t0, double* Dpre
  * for the orbital-energy denominators D. */
 int sccsd_set_preconditioner(sccsd_ctx* ctx, const double* Dprec);
 
+/* ---- CUDA graphs: many instances in one launch --------------------------
+ * sccsd_capture_transform records W = A V (side 0, V packed kets, as
+ * sccsd_jacobian_right) or W = A^T V (side 1, V packed bras, as
+ * sccsd_jacobian_left) for nvec vectors at the fixed state of ctx into a CUDA
+ * graph (cudaGraph_t, returned as void*), after one ordinary call with the same
+ * arguments that sizes every buffer. V and W must be device memory and stay
+ * valid while the graph is used; a launch reads V as it is then. The
+ * context needs its own (non-default) stream. The graph reuses the context's
+ * internal buffers: do not run other calls on the same context while a launch
+ * of its graph is in flight.
+ * sccsd_graph_join instantiates one executable graph with the n graphs as
+ * independent child graphs (e.g. one per instance of a batch of uneven
+ * systems), so that a single sccsd_graph_launch runs them all concurrently.
+ * sccsd_graph_launch enqueues on the given stream and returns immediately. */
+int sccsd_capture_transform(sccsd_ctx* ctx, int side, int nvec, const double* V, double* W,
+                            void** graph);
+int sccsd_graph_join(void** graphs, int n, void** exec);
+int sccsd_graph_launch(void* exec, void* stream);
+void sccsd_graph_destroy(void* graph);
+void sccsd_graph_exec_destroy(void* exec);
+
 /* Size of a packed vector. */
 long long sccsd_dim(int o, int v);
 const char* sccsd_last_error(sccsd_ctx* ctx);

@@ -53,28 +53,44 @@ def _declare(lib):
     lib.sccsd_solve_scc.argtypes = [_dp, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
     lib.sccsd_solve_scc.restype = ctypes.c_int
-    lib.sccsd_mlp_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int,
-                                     ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, _dp]
-    lib.sccsd_mlp_destroy.argtypes = [_dp]
-    lib.sccsd_mlp_destroy.restype = None
-    lib.sccsd_mlp_last_error.argtypes = [_dp]
-    lib.sccsd_mlp_last_error.restype = ctypes.c_char_p
-    lib.sccsd_mlp_num_params.argtypes = [_dp]
-    lib.sccsd_mlp_num_params.restype = ctypes.c_longlong
-    lib.sccsd_mlp_get_params.argtypes = [_dp, _dp]
-    lib.sccsd_mlp_set_params.argtypes = [_dp, _dp]
-    lib.sccsd_mlp_forward.argtypes = [_dp, _dp, ctypes.c_longlong, _dp]
-    lib.sccsd_mlp_gradient.argtypes = [_dp, _dp, _dp, ctypes.c_longlong, _dp, _dp]
-    lib.sccsd_mlp_train_step.argtypes = [_dp, _dp, _dp, ctypes.c_longlong, ctypes.c_float, _dp]
-    lib.sccsd_learned_features.argtypes = [_dp, _dp, _dp]
-    lib.sccsd_learned_targets.argtypes = [_dp, _dp, ctypes.c_double, _dp]
-    lib.sccsd_learned_guess.argtypes = [_dp, _dp, _dp, _dp]
-    lib.sccsd_set_preconditioner.argtypes = [_dp, _dp]
-    for f in ("sccsd_mlp_create", "sccsd_mlp_get_params", "sccsd_mlp_set_params",
-              "sccsd_mlp_forward", "sccsd_mlp_gradient", "sccsd_mlp_train_step",
-              "sccsd_learned_features", "sccsd_learned_targets", "sccsd_learned_guess",
-              "sccsd_set_preconditioner"):
-        getattr(lib, f).restype = ctypes.c_int
+    # The MLP entry points live in their own translation unit; the host test
+    # double of the executor links without it (the export test checks that
+    # the product library has every declared symbol).
+    if hasattr(lib, "sccsd_mlp_create"):
+        lib.sccsd_mlp_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, _dp]
+        lib.sccsd_mlp_destroy.argtypes = [_dp]
+        lib.sccsd_mlp_destroy.restype = None
+        lib.sccsd_mlp_last_error.argtypes = [_dp]
+        lib.sccsd_mlp_last_error.restype = ctypes.c_char_p
+        lib.sccsd_mlp_num_params.argtypes = [_dp]
+        lib.sccsd_mlp_num_params.restype = ctypes.c_longlong
+        lib.sccsd_mlp_get_params.argtypes = [_dp, _dp]
+        lib.sccsd_mlp_set_params.argtypes = [_dp, _dp]
+        lib.sccsd_mlp_forward.argtypes = [_dp, _dp, ctypes.c_longlong, _dp]
+        lib.sccsd_mlp_gradient.argtypes = [_dp, _dp, _dp, ctypes.c_longlong, _dp, _dp]
+        lib.sccsd_mlp_train_step.argtypes = [_dp, _dp, _dp, ctypes.c_longlong, ctypes.c_float, _dp]
+        lib.sccsd_learned_features.argtypes = [_dp, _dp, _dp]
+        lib.sccsd_learned_targets.argtypes = [_dp, _dp, ctypes.c_double, _dp]
+        lib.sccsd_learned_guess.argtypes = [_dp, _dp, _dp, _dp]
+        lib.sccsd_set_preconditioner.argtypes = [_dp, _dp]
+        for f in ("sccsd_mlp_create", "sccsd_mlp_get_params", "sccsd_mlp_set_params",
+                  "sccsd_mlp_forward", "sccsd_mlp_gradient", "sccsd_mlp_train_step",
+                  "sccsd_learned_features", "sccsd_learned_targets", "sccsd_learned_guess",
+                  "sccsd_set_preconditioner"):
+            getattr(lib, f).restype = ctypes.c_int
+    lib.sccsd_capture_transform.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp, _dp,
+                                            ctypes.POINTER(ctypes.c_void_p)]
+    lib.sccsd_capture_transform.restype = ctypes.c_int
+    lib.sccsd_graph_join.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_void_p)]
+    lib.sccsd_graph_join.restype = ctypes.c_int
+    lib.sccsd_graph_launch.argtypes = [_dp, _dp]
+    lib.sccsd_graph_launch.restype = ctypes.c_int
+    lib.sccsd_graph_destroy.argtypes = [_dp]
+    lib.sccsd_graph_destroy.restype = None
+    lib.sccsd_graph_exec_destroy.argtypes = [_dp]
+    lib.sccsd_graph_exec_destroy.restype = None
     lib.sccsd_dim.argtypes = [ctypes.c_int, ctypes.c_int]
     lib.sccsd_dim.restype = ctypes.c_longlong
     lib.sccsd_last_error.argtypes = [_dp]
@@ -166,6 +182,32 @@ def _fptr(x):
     if x.dtype != torch.float32 or not x.is_contiguous():
         raise TypeError("tensors must be contiguous float32")
     return x.data_ptr()
+
+
+class GraphBatch:
+    """One executable CUDA graph joining captured per-instance graphs."""
+
+    def __init__(self, graphs, lib=None):
+        self.lib = lib or load()
+        arr = (ctypes.c_void_p * len(graphs))(*[g.value for g in graphs])
+        e = ctypes.c_void_p()
+        rc = self.lib.sccsd_graph_join(arr, len(graphs), ctypes.byref(e))
+        if rc != 0:
+            raise SccsdError(rc, "graph join failed")
+        self.exec = e
+        self.graphs = graphs
+
+    def launch(self, stream=None):
+        rc = self.lib.sccsd_graph_launch(self.exec, None if stream is None else ctypes.c_void_p(stream))
+        if rc != 0:
+            raise SccsdError(rc, "graph launch failed")
+
+    def close(self):
+        if getattr(self, "exec", None):
+            self.lib.sccsd_graph_exec_destroy(self.exec)
+            for g in self.graphs:
+                self.lib.sccsd_graph_destroy(g)
+            self.exec = None
 
 
 class Mlp:
@@ -348,6 +390,15 @@ class Context:
 
     def set_preconditioner(self, D=None):
         self._check(self.lib.sccsd_set_preconditioner(self.h, _ptr(D)))
+
+    def capture_transform(self, V, W, side="right"):
+        """CUDA graph (handle) of W = A V (right) or A^T V (left), device tensors."""
+        g = ctypes.c_void_p()
+        nvec = 1 if V.ndim == 1 else V.shape[0]
+        sd = {"right": 0, "left": 1}[side]
+        self._check(self.lib.sccsd_capture_transform(self.h, sd, nvec, _ptr(V), _ptr(W),
+                                                     ctypes.byref(g)))
+        return g
 
     def profile(self, enable=True):
         self._check(self.lib.sccsd_profile(self.h, 1 if enable else 0))

@@ -52,6 +52,8 @@ class Backend {
   // (SCCSD_FP64 / SCCSD_BF16X3 / SCCSD_BF16); cached operands are dropped.
   virtual void set_precision(int p) = 0;
   virtual int get_precision() const = 0;
+  // While capturing a CUDA graph: no synchronisation, no allocation.
+  virtual void set_capturing(bool on) = 0;
   // packed singles+doubles vector <-> t1[a][i], full t2[i][j][a][b].
   // ket: t2 = t_mu on both (P,Q) and (Q,P);  bra: off-diagonal pairs halved
   // on unpack and summed on pack, so that sum_packed L X = sum_full L~ X.

@@ -251,7 +251,16 @@ class CudaBackend : public Backend {
     tc.reset();
   }
 
+  bool capturing = false, prof_saved = false;
+  // profiling events stay out of captured graphs
+  void set_capturing(bool on) override {
+    if (on && !capturing) { prof_saved = prof; prof = false; }
+    if (!on && capturing) prof = prof_saved;
+    capturing = on;
+  }
+
   double* alloc(int64_t n) override {
+    if (capturing) throw std::runtime_error("device allocation during graph capture (warm-up missing)");
     void* p = nullptr;
     cudaError_t e = cudaMalloc(&p, sizeof(double) * std::max<int64_t>(1, n));
     if (e != cudaSuccess) {
@@ -284,6 +293,7 @@ class CudaBackend : public Backend {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
   }
   void sync() override {
+    if (capturing) return;
     CK(cudaStreamSynchronize(st));
     if (tc) tc->check_error();
   }
@@ -459,10 +469,10 @@ class CudaBackend : public Backend {
       }
       check_launch("dgemm_view");
     };
-    if (nb == 1 && tiles < 2 * 152 && K >= 2048) {
+    if (nb == 1 && tiles < 2 * 152 && K >= 256) {
       // split K so that the grid fills the GPU; the partial tiles are summed
       // in a fixed order afterwards (deterministic)
-      int64_t splits = std::min<int64_t>((4 * 152 + tiles - 1) / tiles, K / 512);
+      int64_t splits = std::min<int64_t>((4 * 152 + tiles - 1) / tiles, K / 128);
       splits = std::max<int64_t>(2, std::min<int64_t>(splits, 1024));
       int64_t kc = (K + splits - 1) / splits;
       kc = (kc + bk - 1) / bk * bk;

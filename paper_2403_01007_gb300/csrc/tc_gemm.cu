@@ -331,13 +331,19 @@ void TcGemm::release(TcOperand& op) {
 }
 
 bool TcGemm::worthwhile(int64_t nb, int64_t M, int64_t N, int64_t K) const {
-  return nb == 1 && M >= 64 && N >= 64 && K >= 64 && (double)M * N * K >= 6.7e7;
+  // FP64 FMAs run at about 1/1000 of the BF16 tensor rate here, so even small
+  // contractions are cheaper as a conversion plus one tensor-core launch
+  return nb == 1 && M >= 64 && N >= 64 && K >= 64 && (double)M * N * K >= 4.0e6;
 }
 
 void TcGemm::convert(const MatView& X, int64_t rows, int64_t K, TcOperand& out) {
   const int64_t rp = round_up(rows, BN), kp = round_up(K, BK);
   const size_t need = (size_t)rp * kp * 2 * nslices_;
   if (out.bytes < need) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st_, &cs);
+    if (cs != cudaStreamCaptureStatusNone)
+      throw std::runtime_error("tensor-core buffer growth during graph capture (warm-up missing)");
     if (out.data) {
       cudaStreamSynchronize(st_);
       cudaFree(out.data);

@@ -102,6 +102,32 @@ def random_vectors(o: int, v: int, count: int, seed: int, scale: float = 1.0,
     return x
 
 
+@dataclass(frozen=True)
+class Instance:
+    """One member of a batch of uneven systems."""
+    o: int
+    v: int
+    J: int
+    nstates: int
+    sd: float
+    seed: int
+
+
+def batch_instances(count: int = 64, config: int = 4, o_range=(4, 12), v_range=(30, 110),
+                    states=(2, 5), sd: float = 0.03) -> list:
+    """Sizes of a batch of uneven systems: o ~ U{o_range}, v ~ U{v_range},
+    J = 3(o + v), nstates ~ U{states} (all bounds inclusive); instance k's
+    integrals are system(o, v, J, sd, seed_of(config, 10 + k))."""
+    rng = np.random.Generator(np.random.PCG64(seed_of(config, 0)))
+    out = []
+    for k in range(count):
+        o = int(rng.integers(o_range[0], o_range[1] + 1))
+        v = int(rng.integers(v_range[0], v_range[1] + 1))
+        ns = int(rng.integers(states[0], states[1] + 1))
+        out.append(Instance(o, v, 3 * (o + v), ns, sd, seed_of(config, 10 + k)))
+    return out
+
+
 def random_scalars(count: int, seed: int) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.normal(0.0, 1.0, size=count)

@@ -66,6 +66,7 @@ class HostBackend : public Backend {
   void* stream() override { return nullptr; }
   void set_precision(int) override {}
   int get_precision() const override { return 0; }
+  void set_capturing(bool) override {}
   bool tc_will_use(int64_t, int64_t, int64_t, int64_t) override { return false; }
   bool tc_cached(const OperandKey&) override { return false; }
   void gemm_tc_keyed(int64_t, int64_t, int64_t, double, const MatView&, const OperandKey*, const MatView&, const OperandKey*, double*) override {}
