@@ -34,6 +34,25 @@ struct MatView {
   }
 };
 
+// Output of a contraction as a strided multi-level view: the row index m of
+// the M x N result is split into levels (outermost first) of extents re[] and
+// strides rs[], i.e. row(m) = sum_l digit_l(m) * rs[l] with the digits of m
+// in the mixed radix re[] (the outermost extent is not needed); the same for
+// the column index n. Element (m, n) lives at C + row(m) + col(n), so that
+// any permuted output layout is written directly by the GEMM epilogue.
+constexpr int kOutLevels = 6;
+struct OutView {
+  int nr = 1, nc = 1;
+  int64_t re[kOutLevels] = {0}, rs[kOutLevels] = {0};
+  int64_t ce[kOutLevels] = {0}, cs[kOutLevels] = {0};
+  static OutView dense(int64_t ldc) {
+    OutView v;
+    v.rs[0] = ldc;
+    v.cs[0] = 1;
+    return v;
+  }
+};
+
 class Backend {
  public:
   virtual ~Backend() {}
@@ -85,9 +104,10 @@ class Backend {
   virtual bool tc_will_use(int64_t nb, int64_t M, int64_t N, int64_t K) = 0;
   virtual bool tc_cached(const OperandKey& k) = 0;
   // A.p or B.p may be NULL when its key is cached.
+  // ov == NULL: C dense [M][N]. accumulate: C += alpha A B^T.
   virtual void gemm_tc_keyed(int64_t M, int64_t N, int64_t K, double alpha, const MatView& A,
                              const OperandKey* ka, const MatView& B, const OperandKey* kb,
-                             double* C) = 0;
+                             double* C, const OutView* ov = nullptr, bool accumulate = false) = 0;
   // Reusable temporary device buffers (slot 0..7), grown on demand.
   virtual double* scratch(int slot, int64_t n) = 0;
   // Particle-particle ladder with the vv block of L (see Graph::ladder).

@@ -38,11 +38,11 @@ EnergyResidual build_energy_residual(Graph& g, int t1, int t2, int L, int h, int
   int hvv = g.slice(h, {o, o}, {v, v});
 
   // T1-transformed Cholesky vectors and one-electron integrals
-  int Lhoo = g.add("Jkl", {{Loo, "Jkl", 1.0}, {g.contract(Lov, "Jka", t1, "al", "Jkl"), "Jkl", 1.0}});
+  int Lhoo = g.add("Jkl", {{Loo, "Jkl", 1.0}, {g.contract(Lov, "Jka", t1, "al", "Jkl", 1.0, true), "Jkl", 1.0}});
   int Lhvv = g.add("Jab", {{Lvv, "Jab", 1.0}, {g.contract(t1, "ak", Lov, "Jkb", "Jab", 1.0, true), "Jab", -1.0}});
   int Lhvo = g.add("Jai", {{Lvo, "Jai", 1.0},
                            {g.contract(Lvv, "Jac", t1, "ci", "Jai", 1.0, true), "Jai", 1.0},
-                           {g.contract(t1, "ak", Lhoo, "Jki", "Jai"), "Jai", -1.0}});
+                           {g.contract(t1, "ak", Lhoo, "Jki", "Jai", 1.0, true), "Jai", -1.0}});
   int hhoo = g.add("kl", {{hoo, "kl", 1.0}, {g.contract(hov, "ka", t1, "al", "kl"), "kl", 1.0}});
   int hhvo = g.add("ai", {{hvo, "ai", 1.0},
                           {g.contract(hvv, "ac", t1, "ci", "ai"), "ai", 1.0},
@@ -52,14 +52,14 @@ EnergyResidual build_energy_residual(Graph& g, int t1, int t2, int L, int h, int
   // dressed Fock matrix F_pq = h_pq + sum_k (2 g_pqkk - g_pkkq)
   int s = g.contract(Lhoo, "Jkl", delta, "kl", "J");
   int Foo = g.add("kl", {{hhoo, "kl", 1.0},
-                         {g.contract(Lhoo, "Jkl", s, "J", "kl"), "kl", 2.0},
-                         {g.contract(Lhoo, "Jkm", Lhoo, "Jml", "kl"), "kl", -1.0}});
+                         {g.contract(Lhoo, "Jkl", s, "J", "kl", 1.0, true), "kl", 2.0},
+                         {g.contract(Lhoo, "Jkm", Lhoo, "Jml", "kl", 1.0, true), "kl", -1.0}});
   int Fov = g.add("kc", {{hov, "kc", 1.0},
-                         {g.contract(Lov, "Jkc", s, "J", "kc"), "kc", 2.0},
-                         {g.contract(Lhoo, "Jkm", Lov, "Jmc", "kc"), "kc", -1.0}});
+                         {g.contract(Lov, "Jkc", s, "J", "kc", 1.0, true), "kc", 2.0},
+                         {g.contract(Lhoo, "Jkm", Lov, "Jmc", "kc", 1.0, true), "kc", -1.0}});
   int Fvo = g.add("ai", {{hhvo, "ai", 1.0},
-                         {g.contract(Lhvo, "Jai", s, "J", "ai"), "ai", 2.0},
-                         {g.contract(Lhvo, "Jam", Lhoo, "Jmi", "ai"), "ai", -1.0}});
+                         {g.contract(Lhvo, "Jai", s, "J", "ai", 1.0, true), "ai", 2.0},
+                         {g.contract(Lhvo, "Jam", Lhoo, "Jmi", "ai", 1.0, true), "ai", -1.0}});
   int Fvv = g.add("ab", {{hhvv, "ab", 1.0},
                          {g.contract(Lhvv, "Jab", s, "J", "ab", 1.0, true), "ab", 2.0},
                          {g.contract(Lhvo, "Jam", Lov, "Jmb", "ab", 1.0, true), "ab", -1.0}});
@@ -96,7 +96,7 @@ EnergyResidual build_energy_residual(Graph& g, int t1, int t2, int L, int h, int
   int Zl = g.contract(t2, "ijcd", Govov, "klcd", "ijkl", 1.0, true);
   int l4 = g.contract(g.contract(t1, "ak", Zl, "ijkl", "ijal", 1.0, true), "ijal", t1, "bl", "ijab", 1.0, true);
   // hole-hole ladder
-  int Goooo = g.contract(Lhoo, "Jki", Lhoo, "Jlj", "kilj");
+  int Goooo = g.contract(Lhoo, "Jki", Lhoo, "Jlj", "kilj", 1.0, true);
   int Bint = g.add("ijkl", {{Goooo, "kilj", 1.0}, {Zl, "ijkl", 1.0}});
   int B2 = g.contract(Bint, "ijkl", t2, "klab", "ijab", 1.0, true);
   // C-type (exchange ring) terms

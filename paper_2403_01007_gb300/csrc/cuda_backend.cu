@@ -491,7 +491,7 @@ class CudaBackend : public Backend {
   void gemm_view(int64_t nb, int64_t M, int64_t N, int64_t K, double alpha, const MatView& A,
                  const MatView& B, double* C, bool use_tc) override {
     if (use_tc && tc && precision != 0 && tc->worthwhile(nb, M, N, K)) {
-      gemm_tc_keyed(M, N, K, alpha, A, nullptr, B, nullptr, C);
+      gemm_tc_keyed(M, N, K, alpha, A, nullptr, B, nullptr, C, nullptr, false);
       return;
     }
     dgemm_v(nb, M, N, K, alpha, A, B, C);
@@ -519,10 +519,10 @@ class CudaBackend : public Backend {
   }
   void gemm_tc_keyed(int64_t M, int64_t N, int64_t K, double alpha, const MatView& A,
                      const OperandKey* ka, const MatView& B, const OperandKey* kb,
-                     double* C) override {
+                     double* C, const OutView* ov, bool accumulate) override {
     const TcOperand& a = tc_operand(A, M, K, ka, tmpA);
     const TcOperand& b = tc_operand(B, N, K, kb, tmpB);
-    tc->gemm_ops(M, N, alpha, a, b, C);
+    tc->gemm_ops(M, N, alpha, a, b, C, ov ? *ov : OutView::dense(N), accumulate);
   }
 
   double* scratch(int slot, int64_t n) override {

@@ -406,6 +406,32 @@ void Graph::run(const std::vector<int>& targets) {
   for (size_t i = 0; i < ops.size(); ++i)
     if (need_op[i])
       for (int x : ops[i].in) last_use[x] = i;
+  // Contractions whose result only feeds one volatile permuted sum are
+  // evaluated inside that sum, straight into its output: the intermediate
+  // is never stored and the sum does not re-read it.
+  std::vector<int> uses(t.size(), 0);
+  for (size_t i = 0; i < ops.size(); ++i)
+    if (need_op[i])
+      for (int x : ops[i].in) uses[x]++;
+  std::vector<char> fused_op(ops.size(), 0);
+  std::map<size_t, std::vector<int>> add_fused;
+  for (size_t i = 0; i < ops.size(); ++i) {
+    const Op& a = ops[i];
+    if (!need_op[i] || a.kind != OpKind::Add || !vol_[a.out] || t[a.out].dims.empty()) continue;
+    std::vector<int> f(a.in.size(), -1);
+    bool any = false;
+    for (size_t k = 0; k < a.in.size(); ++k) {
+      const int x = a.in[k], p = prod[x];
+      if (p < 0 || !need_op[p] || ops[p].kind != OpKind::Contract || !vol_[x] || is_target[x] ||
+          uses[x] != 1 || t[x].kind != Kind::Node)
+        continue;
+      f[k] = p;
+      fused_op[p] = 1;
+      any = true;
+      for (int y : ops[p].in) last_use[y] = std::max(last_use[y], i);
+    }
+    if (any) add_fused[i] = f;
+  }
   std::vector<std::vector<int>> free_after(ops.size());
   for (size_t i = 0; i < ops.size(); ++i) {
     if (!need_op[i]) continue;
@@ -413,7 +439,7 @@ void Graph::run(const std::vector<int>& targets) {
     if (vol_[x] && !is_target[x]) free_after[std::max(last_use[x], i)].push_back(x);
   }
   for (size_t i = 0; i < ops.size(); ++i) {
-    if (!need_op[i]) continue;
+    if (!need_op[i] || fused_op[i]) continue;
     Op& op = ops[i];
     bool need = !op.ran || vol_[op.out];
     if (!need)
@@ -429,7 +455,11 @@ void Graph::run(const std::vector<int>& targets) {
     void* e0 = trace ? be->record_event() : nullptr;
     if (vol_[op.out] && !t[op.out].data)
       t[op.out].data = be->pool_get(std::max<int64_t>(1, t[op.out].numel()));
-    exec(op);
+    auto fz = add_fused.find(i);
+    if (fz != add_fused.end())
+      exec_add(op, fz->second);
+    else
+      exec(op);
     if (trace) {
       void* e1 = be->record_event();
       op.trace_ms += be->elapsed_ms(e0, e1);
@@ -483,18 +513,9 @@ void Graph::exec(Op& op) {
   if (!out.data) out.data = be->alloc(std::max<int64_t>(1, out.numel()));
   const int rc = (int)out.dims.size();
   switch (op.kind) {
-    case OpKind::Add: {
-      auto ostr = row_strides(out.dims);
-      for (size_t k = 0; k < op.in.size(); ++k) {
-        const Tensor& x = t[op.in[k]];
-        auto xs = row_strides(x.dims);
-        int64_t istr[kMaxRank];
-        for (int q = 0; q < rc; ++q) istr[q] = xs[op.perm[k].find(op.lc[q])];
-        be->copy_view(rc, out.dims.data(), out.data, ostr.data(), x.data, istr, op.coef[k], k > 0);
-      }
-      if (rc == 0 && op.in.empty()) be->fill(out.data, 1, 0.0);
+    case OpKind::Add:
+      exec_add(op, {});
       break;
-    }
     case OpKind::Slice: {
       const Tensor& x = t[op.in[0]];
       auto xs = row_strides(x.dims);
@@ -522,166 +543,232 @@ void Graph::exec(Op& op) {
       be->ladder_adj_l(*this, t[op.in[2]].data, t[op.in[0]].data, t[op.in[1]].data, out.data);
       break;
     case OpKind::Contract: {
-      const Tensor& A = t[op.in[0]];
-      const Tensor& B = t[op.in[1]];
-      const std::string &la = op.la, &lb = op.lb, &lc = op.lc;
-      std::string bat, ml, nl;
-      for (char c : lc) {
-        bool ia = la.find(c) != std::string::npos, ib = lb.find(c) != std::string::npos;
-        if (ia && ib)
-          bat.push_back(c);
-        else if (ia)
-          ml.push_back(c);
-        else
-          nl.push_back(c);
-      }
-      std::string ka, kb;  // contracted labels in A's order / in B's order
-      for (char c : la)
-        if (lb.find(c) != std::string::npos && lc.find(c) == std::string::npos) ka.push_back(c);
-      for (char c : lb)
-        if (la.find(c) != std::string::npos && lc.find(c) == std::string::npos) kb.push_back(c);
-      auto dim_of = [&](char c) -> int64_t {
-        size_t p = la.find(c);
-        if (p != std::string::npos) return A.dims[p];
-        return B.dims[lb.find(c)];
-      };
-      // a label group of X collapsed to at most two strided levels
-      struct Grp {
-        bool ok = true;
-        int64_t n2 = 0, s1 = 0, s2 = 0;
-      };
-      auto collapse = [&](const Tensor& X, const std::string& lx, const std::string& grp) {
-        auto xs = row_strides(X.dims);
-        std::vector<std::pair<int64_t, int64_t>> runs;  // (extent, innermost stride)
-        for (char c : grp) {
-          size_t p = lx.find(c);
-          int64_t d = X.dims[p], st = xs[p];
-          if (d == 1) continue;
-          if (!runs.empty() && runs.back().second == st * d) {
-            runs.back().first *= d;
-            runs.back().second = st;
-          } else {
-            runs.push_back({d, st});
-          }
-        }
-        Grp g;
-        if (runs.size() == 1) {
-          g.s2 = runs[0].second;
-        } else if (runs.size() == 2) {
-          g.n2 = runs[1].first;
-          g.s1 = runs[0].second;
-          g.s2 = runs[1].second;
-        } else if (runs.size() > 2) {
-          g.ok = false;
-        }
-        return g;
-      };
-      auto view_of = [&](const Tensor& X, const std::string& lx, const std::string& rows,
-                         const std::string& kls, MatView& v) {
-        Grp gb = collapse(X, lx, bat), gr = collapse(X, lx, rows), gk = collapse(X, lx, kls);
-        if (!gb.ok || gb.n2 || !gr.ok || !gk.ok) return false;
-        v.p = X.data;
-        v.sb = gb.s2;
-        v.n2r = gr.n2;
-        v.sr1 = gr.s1;
-        v.sr2 = gr.s2;
-        v.n2k = gk.n2;
-        v.sk1 = gk.s1;
-        v.sk2 = gk.s2;
-        // a K group of extent 1 has no stride of its own
-        if (!gk.n2 && gk.s2 == 0) v.sk2 = 1;
-        return true;
-      };
-      // contracted-label order: the one for which both operands are views
-      MatView Av, Bv;
-      std::string kl = ka;
-      bool okA = view_of(A, la, ml, kl, Av), okB = view_of(B, lb, nl, kl, Bv);
-      if (!(okA && okB)) {
-        MatView A2, B2;
-        bool a2 = view_of(A, la, ml, kb, A2), b2 = view_of(B, lb, nl, kb, B2);
-        if ((int)a2 + (int)b2 > (int)okA + (int)okB) {
-          kl = kb;
-          okA = a2;
-          okB = b2;
-          Av = A2;
-          Bv = B2;
-        }
-      }
-      int64_t nb = 1, M = 1, N = 1, K = 1;
-      for (char c : bat) nb *= dim_of(c);
-      for (char c : ml) M *= dim_of(c);
-      for (char c : nl) N *= dim_of(c);
-      for (char c : kl) K *= dim_of(c);
-      // dense [batch][rows][K] copy for operands that are not a two-level view
-      auto arrange = [&](const Tensor& X, const std::string& lx, const std::string& want,
-                         int slot, int64_t rows) -> MatView {
-        if (lx == want) return MatView::dense(X.data, rows, K);
-        double* dst = be->scratch(slot, std::max<int64_t>(1, X.numel()));
-        std::vector<int64_t> wd;
-        for (char c : want) wd.push_back(X.dims[lx.find(c)]);
-        auto ws = row_strides(wd);
-        auto xs = row_strides(X.dims);
-        int64_t istr[kMaxRank];
-        for (size_t q = 0; q < want.size(); ++q) istr[q] = xs[lx.find(want[q])];
-        be->copy_view((int)want.size(), wd.data(), dst, ws.data(), X.data, istr, 1.0, false);
-        return MatView::dense(dst, rows, K);
-      };
-      auto finish = [&](double* Cp) {
-        std::string cl = bat + ml + nl;
-        std::vector<int64_t> cd;
-        for (char c : cl) cd.push_back(dim_of(c));
-        auto cs = row_strides(cd);
-        auto os = row_strides(out.dims);
-        int64_t istr[kMaxRank];
-        for (int q = 0; q < rc; ++q) istr[q] = cs[cl.find(lc[q])];
-        be->copy_view(rc, out.dims.data(), out.data, os.data(), Cp, istr, 1.0, false);
-      };
-      // tensor-core route: operands that do not change between calls keep
-      // their converted form in the backend (keyed by node, layout, version)
-      const bool use_tc = op.tc && be->tc_will_use(nb, M, N, K);
-      if (use_tc) {
-        auto hash = [](const std::string& a, const std::string& b) {
-          uint64_t h = 1469598103934665603ull;
-          for (char c : a + "|" + b) h = (h ^ (uint64_t)(unsigned char)c) * 1099511628211ull;
-          return h;
-        };
-        Backend::OperandKey kA{this, op.in[0], A.version, hash(la, bat + ml + kl)};
-        Backend::OperandKey kB{this, op.in[1], B.version, hash(lb, bat + nl + kl)};
-        const bool cA = !vol_[op.in[0]], cB = !vol_[op.in[1]];
-        if (cA && be->tc_cached(kA))
-          Av.p = nullptr;
-        else if (!okA)
-          Av = arrange(A, la, bat + ml + kl, 0, M);
-        if (cB && be->tc_cached(kB))
-          Bv.p = nullptr;
-        else if (!okB)
-          Bv = arrange(B, lb, bat + nl + kl, 1, N);
-        const Backend::OperandKey* pA = cA ? &kA : nullptr;
-        const Backend::OperandKey* pB = cB ? &kB : nullptr;
-        if (lc == bat + ml + nl) {
-          be->gemm_tc_keyed(M, N, K, op.alpha, Av, pA, Bv, pB, out.data);
-        } else if (lc == bat + nl + ml) {
-          be->gemm_tc_keyed(N, M, K, op.alpha, Bv, pB, Av, pA, out.data);
-        } else {
-          double* Cp = be->scratch(2, std::max<int64_t>(1, nb * M * N));
-          be->gemm_tc_keyed(M, N, K, op.alpha, Av, pA, Bv, pB, Cp);
-          finish(Cp);
-        }
-        break;
-      }
-      if (!okA) Av = arrange(A, la, bat + ml + kl, 0, M);
-      if (!okB) Bv = arrange(B, lb, bat + nl + kl, 1, N);
-      if (lc == bat + ml + nl) {
-        be->gemm_view(nb, M, N, K, op.alpha, Av, Bv, out.data, false);
-      } else if (lc == bat + nl + ml) {
-        be->gemm_view(nb, N, M, K, op.alpha, Bv, Av, out.data, false);
-      } else {
-        double* Cp = be->scratch(2, std::max<int64_t>(1, nb * M * N));
-        be->gemm_view(nb, M, N, K, op.alpha, Av, Bv, Cp, false);
-        finish(Cp);
-      }
+      auto os = row_strides(out.dims);
+      exec_contract(op, out.data, os.data(), 1.0, false);
       break;
     }
+  }
+}
+
+// Permuted sum. fused[k] >= 0: term k is the output of contraction op
+// fused[k], which is evaluated here straight into the sum (scaled, and
+// accumulated after the first term) instead of through its own buffer.
+void Graph::exec_add(Op& op, const std::vector<int>& fused) {
+  Tensor& out = t[op.out];
+  const int rc = (int)out.dims.size();
+  auto ostr = row_strides(out.dims);
+  for (size_t k = 0; k < op.in.size(); ++k) {
+    const Tensor& x = t[op.in[k]];
+    if (!fused.empty() && fused[k] >= 0) {
+      int64_t cs[kMaxRank];
+      for (size_t q = 0; q < x.dims.size(); ++q) cs[q] = ostr[op.lc.find(op.perm[k][q])];
+      void* e0 = trace ? be->record_event() : nullptr;
+      exec_contract(ops[fused[k]], out.data, cs, op.coef[k], k > 0);
+      if (trace) {
+        // the sum's own time includes this; the contraction is listed too
+        ops[fused[k]].trace_ms += be->elapsed_ms(e0, be->record_event());
+        ops[fused[k]].trace_calls += 1;
+      }
+      continue;
+    }
+    auto xs = row_strides(x.dims);
+    int64_t istr[kMaxRank];
+    for (int q = 0; q < rc; ++q) istr[q] = xs[op.perm[k].find(op.lc[q])];
+    be->copy_view(rc, out.dims.data(), out.data, ostr.data(), x.data, istr, op.coef[k], k > 0);
+  }
+  if (rc == 0 && op.in.empty()) be->fill(out.data, 1, 0.0);
+}
+
+// Contraction into out_data, whose dims are those of op's output and whose
+// strides are ostr (per output label): out (= or +=) coef * result.
+void Graph::exec_contract(Op& op, double* out_data, const int64_t* ostr, double coef, bool acc) {
+  Tensor& out = t[op.out];
+  const int rc = (int)out.dims.size();
+  const std::vector<int64_t> ostrides(ostr, ostr + rc);
+  const bool plain = !acc && coef == 1.0 && ostrides == row_strides(out.dims);
+  const Tensor& A = t[op.in[0]];
+  const Tensor& B = t[op.in[1]];
+  const std::string &la = op.la, &lb = op.lb, &lc = op.lc;
+  std::string bat, ml, nl;
+  for (char c : lc) {
+    bool ia = la.find(c) != std::string::npos, ib = lb.find(c) != std::string::npos;
+    if (ia && ib)
+      bat.push_back(c);
+    else if (ia)
+      ml.push_back(c);
+    else
+      nl.push_back(c);
+  }
+  std::string ka, kb;  // contracted labels in A's order / in B's order
+  for (char c : la)
+    if (lb.find(c) != std::string::npos && lc.find(c) == std::string::npos) ka.push_back(c);
+  for (char c : lb)
+    if (la.find(c) != std::string::npos && lc.find(c) == std::string::npos) kb.push_back(c);
+  auto dim_of = [&](char c) -> int64_t {
+    size_t p = la.find(c);
+    if (p != std::string::npos) return A.dims[p];
+    return B.dims[lb.find(c)];
+  };
+  // a label group of X collapsed to at most two strided levels
+  struct Grp {
+    bool ok = true;
+    int64_t n2 = 0, s1 = 0, s2 = 0;
+  };
+  // maximal runs (extent, innermost stride) of a label group, outermost first
+  auto runs_of = [&](const std::vector<int64_t>& dims, const std::vector<int64_t>& xs,
+                     const std::string& lx, const std::string& grp) {
+    std::vector<std::pair<int64_t, int64_t>> runs;
+    for (char c : grp) {
+      size_t p = lx.find(c);
+      int64_t d = dims[p], st = xs[p];
+      if (d == 1) continue;
+      if (!runs.empty() && runs.back().second == st * d) {
+        runs.back().first *= d;
+        runs.back().second = st;
+      } else {
+        runs.push_back({d, st});
+      }
+    }
+    return runs;
+  };
+  auto collapse_s = [&](const std::vector<int64_t>& dims, const std::vector<int64_t>& xs,
+                        const std::string& lx, const std::string& grp) {
+    auto runs = runs_of(dims, xs, lx, grp);
+    Grp g;
+    if (runs.size() == 1) {
+      g.s2 = runs[0].second;
+    } else if (runs.size() == 2) {
+      g.n2 = runs[1].first;
+      g.s1 = runs[0].second;
+      g.s2 = runs[1].second;
+    } else if (runs.size() > 2) {
+      g.ok = false;
+    }
+    return g;
+  };
+  auto collapse = [&](const Tensor& X, const std::string& lx, const std::string& grp) {
+    return collapse_s(X.dims, row_strides(X.dims), lx, grp);
+  };
+  auto view_of = [&](const Tensor& X, const std::string& lx, const std::string& rows,
+                     const std::string& kls, MatView& v) {
+    Grp gb = collapse(X, lx, bat), gr = collapse(X, lx, rows), gk = collapse(X, lx, kls);
+    if (!gb.ok || gb.n2 || !gr.ok || !gk.ok) return false;
+    v.p = X.data;
+    v.sb = gb.s2;
+    v.n2r = gr.n2;
+    v.sr1 = gr.s1;
+    v.sr2 = gr.s2;
+    v.n2k = gk.n2;
+    v.sk1 = gk.s1;
+    v.sk2 = gk.s2;
+    // a K group of extent 1 has no stride of its own
+    if (!gk.n2 && gk.s2 == 0) v.sk2 = 1;
+    return true;
+  };
+  // contracted-label order: the one for which both operands are views
+  MatView Av, Bv;
+  std::string kl = ka;
+  bool okA = view_of(A, la, ml, kl, Av), okB = view_of(B, lb, nl, kl, Bv);
+  if (!(okA && okB)) {
+    MatView A2, B2;
+    bool a2 = view_of(A, la, ml, kb, A2), b2 = view_of(B, lb, nl, kb, B2);
+    if ((int)a2 + (int)b2 > (int)okA + (int)okB) {
+      kl = kb;
+      okA = a2;
+      okB = b2;
+      Av = A2;
+      Bv = B2;
+    }
+  }
+  int64_t nb = 1, M = 1, N = 1, K = 1;
+  for (char c : bat) nb *= dim_of(c);
+  for (char c : ml) M *= dim_of(c);
+  for (char c : nl) N *= dim_of(c);
+  for (char c : kl) K *= dim_of(c);
+  // dense [batch][rows][K] copy for operands that are not a two-level view
+  auto arrange = [&](const Tensor& X, const std::string& lx, const std::string& want,
+                     int slot, int64_t rows) -> MatView {
+    if (lx == want) return MatView::dense(X.data, rows, K);
+    double* dst = be->scratch(slot, std::max<int64_t>(1, X.numel()));
+    std::vector<int64_t> wd;
+    for (char c : want) wd.push_back(X.dims[lx.find(c)]);
+    auto ws = row_strides(wd);
+    auto xs = row_strides(X.dims);
+    int64_t istr[kMaxRank];
+    for (size_t q = 0; q < want.size(); ++q) istr[q] = xs[lx.find(want[q])];
+    be->copy_view((int)want.size(), wd.data(), dst, ws.data(), X.data, istr, 1.0, false);
+    return MatView::dense(dst, rows, K);
+  };
+  auto finish = [&](double* Cp) {
+    std::string cl = bat + ml + nl;
+    std::vector<int64_t> cd;
+    for (char c : cl) cd.push_back(dim_of(c));
+    auto cs = row_strides(cd);
+    int64_t istr[kMaxRank];
+    for (int q = 0; q < rc; ++q) istr[q] = cs[cl.find(lc[q])];
+    be->copy_view(rc, out.dims.data(), out_data, ostrides.data(), Cp, istr, coef, acc);
+  };
+  // tensor-core route: operands that do not change between calls keep
+  // their converted form in the backend (keyed by node, layout, version)
+  const bool use_tc = op.tc && be->tc_will_use(nb, M, N, K);
+  if (use_tc) {
+    auto hash = [](const std::string& a, const std::string& b) {
+      uint64_t h = 1469598103934665603ull;
+      for (char c : a + "|" + b) h = (h ^ (uint64_t)(unsigned char)c) * 1099511628211ull;
+      return h;
+    };
+    Backend::OperandKey kA{this, op.in[0], A.version, hash(la, bat + ml + kl)};
+    Backend::OperandKey kB{this, op.in[1], B.version, hash(lb, bat + nl + kl)};
+    const bool cA = !vol_[op.in[0]], cB = !vol_[op.in[1]];
+    if (cA && be->tc_cached(kA))
+      Av.p = nullptr;
+    else if (!okA)
+      Av = arrange(A, la, bat + ml + kl, 0, M);
+    if (cB && be->tc_cached(kB))
+      Bv.p = nullptr;
+    else if (!okB)
+      Bv = arrange(B, lb, bat + nl + kl, 1, N);
+    const Backend::OperandKey* pA = cA ? &kA : nullptr;
+    const Backend::OperandKey* pB = cB ? &kB : nullptr;
+    if (plain && lc == bat + ml + nl) {
+      be->gemm_tc_keyed(M, N, K, op.alpha, Av, pA, Bv, pB, out_data);
+    } else if (plain && lc == bat + nl + ml) {
+      be->gemm_tc_keyed(N, M, K, op.alpha, Bv, pB, Av, pA, out_data);
+    } else {
+      // a permuted (or accumulated) output is written by the GEMM epilogue
+      // through a multi-level view of the M and N label groups
+      auto rm = runs_of(out.dims, ostrides, lc, ml), rn = runs_of(out.dims, ostrides, lc, nl);
+      if ((int)rm.size() <= kOutLevels && (int)rn.size() <= kOutLevels) {
+        OutView ov;
+        ov.nr = std::max<int>(1, (int)rm.size());
+        ov.nc = std::max<int>(1, (int)rn.size());
+        for (size_t l = 0; l < rm.size(); ++l) {
+          ov.re[l] = rm[l].first;
+          ov.rs[l] = rm[l].second;
+        }
+        for (size_t l = 0; l < rn.size(); ++l) {
+          ov.ce[l] = rn[l].first;
+          ov.cs[l] = rn[l].second;
+        }
+        be->gemm_tc_keyed(M, N, K, op.alpha * coef, Av, pA, Bv, pB, out_data, &ov, acc);
+      } else {
+        double* Cp = be->scratch(2, std::max<int64_t>(1, nb * M * N));
+        be->gemm_tc_keyed(M, N, K, op.alpha, Av, pA, Bv, pB, Cp);
+        finish(Cp);
+      }
+    }
+    return;
+  }
+  if (!okA) Av = arrange(A, la, bat + ml + kl, 0, M);
+  if (!okB) Bv = arrange(B, lb, bat + nl + kl, 1, N);
+  if (plain && lc == bat + ml + nl) {
+    be->gemm_view(nb, M, N, K, op.alpha, Av, Bv, out_data, false);
+  } else if (plain && lc == bat + nl + ml) {
+    be->gemm_view(nb, N, M, K, op.alpha, Bv, Av, out_data, false);
+  } else {
+    double* Cp = be->scratch(2, std::max<int64_t>(1, nb * M * N));
+    be->gemm_view(nb, M, N, K, op.alpha, Av, Bv, Cp, false);
+    finish(Cp);
   }
 }
 

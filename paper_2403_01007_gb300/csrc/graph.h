@@ -130,6 +130,8 @@ class Graph {
  private:
   int new_tensor(const std::vector<int64_t>& dims, Kind k);
   void exec(Op& op);
+  void exec_contract(Op& op, double* out_data, const int64_t* ostr, double coef, bool acc);
+  void exec_add(Op& op, const std::vector<int>& fused);
   std::vector<char> vol_;
   std::vector<int> held_;  // volatile buffers kept alive for the caller
 };

@@ -1,15 +1,20 @@
 // tcgen05 BF16 GEMM with TMA loads and TMEM accumulators (sm_103a).
 //
 // One CTA computes a 128 x 256 FP32 tile of A * B^T (both operands K-major
-// BF16 in global memory, padded to whole tiles) and writes alpha * tile into
-// an FP64 output (overwrite or accumulate). Warp roles:
+// BF16 in global memory, padded to whole tiles) over a range of K blocks
+// (blockIdx.z selects the range when K is split) and writes alpha * tile into
+// an FP64 output through a two-level strided view (overwrite or accumulate),
+// so that permuted tensor layouts need no separate copy. Warp roles:
 //   warp 4    : TMA producer, 4-stage ring of (A 128x64, B 256x64) tiles,
 //               128-byte swizzle, completion on mbarriers (expect_tx)
 //   warp 5    : one elected thread issues tcgen05.mma.kind::f16 (M=128,
 //               N=256, K=16 per instruction, 4 per stage), commits each stage
 //               back to the producer and finally the accumulator
-//   warps 0-3 : epilogue, tcgen05.ld 32 lanes x 32 columns at a time, staged
-//               through shared memory for coalesced FP64 stores
+//   warps 0-3 : epilogue, tcgen05.ld 32 lanes x 32 columns at a time; when
+//               the output's row index is the unit-stride one each thread
+//               stores its own row (consecutive lanes, consecutive
+//               addresses), otherwise the block is transposed through shared
+//               memory so that lanes walk the columns
 // Every mbarrier wait is bounded; on expiry the kernel records an error code
 // and the remaining roles skip their work, so a fault in the pipeline shows
 // up as an error status instead of a hang. TMEM is always freed.
@@ -37,7 +42,7 @@ constexpr int B_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int EPI_FLOATS = 4 * 32 * 33;
 constexpr int SMEM_BYTES = 1024 /*align slack*/ + STAGES * STAGE_BYTES + 256 /*barriers*/ +
-                           EPI_FLOATS * 4;
+                           EPI_FLOATS * 4 + 2 * 4 * 32 * 8 /*row and column offsets*/;
 constexpr int TMEM_COLS = 256;
 constexpr uint32_t WAIT_LIMIT = 1u << 24;  // polls before a wait is declared failed
 
@@ -85,10 +90,26 @@ __host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
          | ((uint32_t)(M >> 4) << 24);  // M / 16
 }
 
+__device__ __forceinline__ int64_t level_offset(int n, const int64_t* e, const int64_t* s,
+                                                int64_t i) {
+  int64_t off = 0;
+  for (int l = n - 1; l > 0; --l) {
+    off += (i % e[l]) * s[l];
+    i /= e[l];
+  }
+  return off + i * s[0];
+}
+__device__ __forceinline__ int64_t out_row(const OutView& v, int64_t r) {
+  return level_offset(v.nr, v.re, v.rs, r);
+}
+__device__ __forceinline__ int64_t out_col(const OutView& v, int64_t c) {
+  return level_offset(v.nc, v.ce, v.cs, c);
+}
+
 __global__ void __launch_bounds__(192, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-              int64_t M, int64_t N, int nk, double alpha, double* __restrict__ C, int64_t ldc,
-              int accumulate, int* err) {
+              int64_t M, int64_t N, int nk_total, int kbs, double alpha, double* __restrict__ C,
+              int64_t split_stride, const OutView ov, int accumulate, int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
@@ -99,11 +120,15 @@ __global__ void __launch_bounds__(192, 1)
   uint32_t* tmem_slot = (uint32_t*)(accf + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   float* epi = (float*)(smem + STAGES * STAGE_BYTES + 256);
+  int64_t* row_off = (int64_t*)(epi + EPI_FLOATS);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // M tiles run fastest so that the CTAs resident at one time share a B tile
   // (read once from HBM, then served from L2)
   const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  // this CTA's K blocks: [kb0, kb0 + nk)
+  const int kb0 = (int)blockIdx.z * kbs;
+  const int nk = (nk_total - kb0 < kbs) ? nk_total - kb0 : kbs;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -142,7 +167,7 @@ __global__ void __launch_bounds__(192, 1)
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
                      "r"(STAGE_BYTES)
                      : "memory");
-        const int x = kb * BK;
+        const int x = (kb0 + kb) * BK;
         asm volatile(
             "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
             " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(sA + s * A_BYTES)),
@@ -198,7 +223,17 @@ __global__ void __launch_bounds__(192, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok && !*abort_flag) {
       float* buf = epi + warp * 32 * 33;
+      int64_t* roff = row_off + warp * 32;
+      int64_t* coff = row_off + 4 * 32 + warp * 32;
+      {
+        const int64_t row = m0 + warp * 32 + lane;
+        roff[lane] = row < M ? out_row(ov, row) : -1;
+      }
+      __syncwarp();
+      double* Cz = C + (int64_t)blockIdx.z * split_stride;
+      const bool rows_fast = ov.rs[ov.nr - 1] == 1 && ov.cs[ov.nc - 1] != 1;
       for (int c0 = 0; c0 < BN; c0 += 32) {
+        if (n0 + c0 >= N) break;  // warp-uniform: no valid column left
         uint32_t r[32];
         const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
         asm volatile(
@@ -213,19 +248,46 @@ __global__ void __launch_bounds__(192, 1)
               "=r"(r[30]), "=r"(r[31])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int j = 0; j < 32; ++j) buf[lane * 33 + j] = __uint_as_float(r[j]);
-        __syncwarp();
-        const int64_t col = n0 + c0 + lane;
-        for (int rr = 0; rr < 32; ++rr) {
-          const int64_t row = m0 + warp * 32 + rr;
-          if (row < M && col < N) {
-            double v = alpha * (double)buf[rr * 33 + lane];
-            double* p = C + row * ldc + col;
-            *p = accumulate ? *p + v : v;
-          }
+        {
+          // output offsets of this chunk's 32 columns, one per lane
+          const int64_t col = n0 + c0 + lane;
+          coff[lane] = col < N ? out_col(ov, col) : -1;
         }
         __syncwarp();
+        // Accumulation reads all 32 old values of a thread before the first
+        // store, so that the loads overlap instead of each waiting on HBM.
+        if (rows_fast) {
+          // lane = row: for each column the warp stores 32 consecutive rows
+          const int64_t ro = roff[lane];
+          double old[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int64_t co = coff[j];
+            old[j] = (accumulate && ro >= 0 && co >= 0) ? Cz[ro + co] : 0.0;
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int64_t co = coff[j];
+            if (ro >= 0 && co >= 0) Cz[ro + co] = old[j] + alpha * (double)__uint_as_float(r[j]);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) buf[lane * 33 + j] = __uint_as_float(r[j]);
+          __syncwarp();
+          const int64_t co = coff[lane];
+          double old[32];
+#pragma unroll
+          for (int rr = 0; rr < 32; ++rr) {
+            const int64_t ro = roff[rr];
+            old[rr] = (accumulate && ro >= 0 && co >= 0) ? Cz[ro + co] : 0.0;
+          }
+#pragma unroll
+          for (int rr = 0; rr < 32; ++rr) {
+            const int64_t ro = roff[rr];
+            if (ro >= 0 && co >= 0) Cz[ro + co] = old[rr] + alpha * (double)buf[rr * 33 + lane];
+          }
+        }
+        __syncwarp();  // buf and coff are rewritten by the next chunk
       }
     }
   }
@@ -278,6 +340,20 @@ __global__ void k_split_bf16_view(MatView X, int64_t rows, int64_t K, int64_t ro
   }
 }
 
+// C (= or +=) sum_z part[z] through the output view (split-K reduction; the
+// partials already carry alpha)
+__global__ void k_sum_splits(int64_t M, int64_t N, int splits, const double* __restrict__ part,
+                             double* __restrict__ C, const OutView ov, int accumulate) {
+  const int64_t n = M * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int z = 0; z < splits; ++z) s += part[(int64_t)z * n + e];
+    double* p = C + out_row(ov, e / N) + out_col(ov, e % N);
+    *p = accumulate ? *p + s : s;
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -322,6 +398,7 @@ TcGemm::TcGemm(cudaStream_t st, int precision) : st_(st) {
 TcGemm::~TcGemm() {
   release(a_tmp_);
   release(b_tmp_);
+  if (part_) cudaFree(part_);
   if (d_err_) cudaFree(d_err_);
 }
 
@@ -332,8 +409,9 @@ void TcGemm::release(TcOperand& op) {
 
 bool TcGemm::worthwhile(int64_t nb, int64_t M, int64_t N, int64_t K) const {
   // FP64 FMAs run at about 1/1000 of the BF16 tensor rate here, so even small
-  // contractions are cheaper as a conversion plus one tensor-core launch
-  return nb == 1 && M >= 64 && N >= 64 && K >= 64 && (double)M * N * K >= 4.0e6;
+  // or skinny contractions (padded to 128 x 256 x 64 tiles) are cheaper as a
+  // conversion plus one tensor-core launch; matrix-vector shapes are not
+  return nb == 1 && M >= 16 && N >= 16 && (double)M * N * K >= 1.0e6;
 }
 
 void TcGemm::convert(const MatView& X, int64_t rows, int64_t K, TcOperand& out) {
@@ -387,17 +465,18 @@ void TcGemm::check_error() {
 }
 
 void TcGemm::run(const TcOperand& A, int sa, const TcOperand& B, int sb, int64_t M, int64_t N,
-                 double alpha, double* C, bool accumulate) {
+                 double alpha, double* C, int64_t split_stride, const OutView& ov,
+                 bool accumulate, int splits, int kbs) {
   if (A.k_pad != B.k_pad) throw std::runtime_error("tc: K mismatch");
   const __nv_bfloat16* a = (const __nv_bfloat16*)A.data + (size_t)sa * A.rows_pad * A.k_pad;
   const __nv_bfloat16* b = (const __nv_bfloat16*)B.data + (size_t)sb * B.rows_pad * B.k_pad;
   CUtensorMap ma = make_map(a, A.rows_pad, A.k_pad, BM);
   CUtensorMap mb = make_map(b, B.rows_pad, B.k_pad, BN);
   if (B.rows_pad / BN > 65535) throw std::runtime_error("tc: N too large for the grid");
-  dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)(B.rows_pad / BN));
+  dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)(B.rows_pad / BN), (unsigned)splits);
   const int nk = (int)(A.k_pad / BK);
-  k_tc_gemm<<<grid, 192, SMEM_BYTES, st_>>>(ma, mb, M, N, nk, alpha, C, N, accumulate ? 1 : 0,
-                                           d_err_);
+  k_tc_gemm<<<grid, 192, SMEM_BYTES, st_>>>(ma, mb, M, N, nk, kbs, alpha, C, split_stride, ov,
+                                           accumulate ? 1 : 0, d_err_);
   count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw CudaError(std::string("tc_gemm launch: ") + cudaGetErrorString(e));
@@ -413,20 +492,59 @@ static void slice_pairs(int s, std::vector<std::pair<int, int>>& out) {
 void TcGemm::gemm_prepared_b(int64_t M, int64_t N, int64_t K, double alpha, const double* A,
                              const TcOperand& B, double* C, bool check) {
   convert(MatView::dense(A, M, K), M, K, a_tmp_);
-  std::vector<std::pair<int, int>> pairs;
-  slice_pairs(nslices_, pairs);
-  // accumulate the small products first, the leading one last
-  for (size_t p = pairs.size(); p-- > 0;)
-    run(a_tmp_, pairs[p].first, B, pairs[p].second, M, N, alpha, C, p + 1 != pairs.size());
+  gemm_ops(M, N, alpha, a_tmp_, B, C, OutView::dense(N), false);
   (void)check;  // the error flag is read by the backend at each synchronisation
 }
 
 void TcGemm::gemm_ops(int64_t M, int64_t N, double alpha, const TcOperand& A, const TcOperand& B,
-                      double* C) {
+                      double* C, const OutView& ov, bool accumulate) {
   std::vector<std::pair<int, int>> pairs;
   slice_pairs(nslices_, pairs);
+  const int64_t tiles = ((M + BM - 1) / BM) * (B.rows_pad / BN);
+  const int nk = (int)(A.k_pad / BK);
+  int splits = 1, kbs = nk;
+  if (tiles < 152 && nk >= 8) {
+    // too few output tiles to fill the GPU: split K, at least 4 blocks each
+    int64_t want = std::min<int64_t>((2 * 152 + tiles - 1) / tiles, nk / 4);
+    if (want > 1) {
+      kbs = (int)((nk + want - 1) / want);
+      splits = (nk + kbs - 1) / kbs;
+    }
+  }
+  // accumulate the small slice products first, the leading one last
+  if (splits == 1) {
+    for (size_t p = pairs.size(); p-- > 0;)
+      run(A, pairs[p].first, B, pairs[p].second, M, N, alpha, C, 0, ov,
+          accumulate || p + 1 != pairs.size(), 1, nk);
+    return;
+  }
+  const size_t need = (size_t)splits * M * N * sizeof(double);
+  if (part_bytes_ < need) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st_, &cs);
+    if (cs != cudaStreamCaptureStatusNone)
+      throw std::runtime_error("tensor-core buffer growth during graph capture (warm-up missing)");
+    if (part_) {
+      cudaStreamSynchronize(st_);
+      cudaFree(part_);
+      part_ = nullptr;
+      part_bytes_ = 0;
+    }
+    if (cudaMalloc(&part_, need) != cudaSuccess) {
+      cudaGetLastError();
+      throw OomError("split-K buffer of " + std::to_string(need) + " bytes");
+    }
+    part_bytes_ = need;
+  }
   for (size_t p = pairs.size(); p-- > 0;)
-    run(A, pairs[p].first, B, pairs[p].second, M, N, alpha, C, p + 1 != pairs.size());
+    run(A, pairs[p].first, B, pairs[p].second, M, N, alpha, part_, M * N, OutView::dense(N),
+        p + 1 != pairs.size(), splits, kbs);
+  const int64_t n = M * N;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16));
+  k_sum_splits<<<grid, 256, 0, st_>>>(M, N, splits, part_, C, ov, accumulate ? 1 : 0);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw CudaError(std::string("sum_splits: ") + cudaGetErrorString(e));
 }
 
 void TcGemm::gemm(int64_t nb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,

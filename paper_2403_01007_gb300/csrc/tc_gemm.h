@@ -41,9 +41,10 @@ class TcGemm {
   void gemm_prepared_b(int64_t M, int64_t N, int64_t K, double alpha, const double* A,
                        const TcOperand& B, double* C, bool check = true);
   void check_error();
-  // C = alpha * A B^T for operands already in slice form
+  // C (= or +=) alpha * A B^T for operands already in slice form; C through
+  // the output view ov. Small output grids split K over extra CTAs.
   void gemm_ops(int64_t M, int64_t N, double alpha, const TcOperand& A, const TcOperand& B,
-                double* C);
+                double* C, const OutView& ov, bool accumulate);
   void release(TcOperand& op);
   int slices() const { return nslices_; }
   void set_precision(int precision) { nslices_ = precision == 1 ? 2 : 1; }
@@ -51,10 +52,13 @@ class TcGemm {
  private:
   void convert(const MatView& X, int64_t rows, int64_t K, TcOperand& out);
   void run(const TcOperand& A, int sa, const TcOperand& B, int sb, int64_t M, int64_t N,
-           double alpha, double* C, bool accumulate);
+           double alpha, double* C, int64_t split_stride, const OutView& ov, bool accumulate,
+           int splits, int kbs);
   cudaStream_t st_;
   int nslices_;
   TcOperand a_tmp_, b_tmp_;
+  double* part_ = nullptr;   // split-K partial results
+  size_t part_bytes_ = 0;
   int* d_err_ = nullptr;
 };
 

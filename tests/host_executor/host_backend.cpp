@@ -69,7 +69,7 @@ class HostBackend : public Backend {
   void set_capturing(bool) override {}
   bool tc_will_use(int64_t, int64_t, int64_t, int64_t) override { return false; }
   bool tc_cached(const OperandKey&) override { return false; }
-  void gemm_tc_keyed(int64_t, int64_t, int64_t, double, const MatView&, const OperandKey*, const MatView&, const OperandKey*, double*) override {}
+  void gemm_tc_keyed(int64_t, int64_t, int64_t, double, const MatView&, const OperandKey*, const MatView&, const OperandKey*, double*, const OutView*, bool) override {}
   double* scratch(int slot, int64_t n) override {
     if (slot_n[slot] < n) { delete[] slots[slot]; slots[slot]=new double[n]; slot_n[slot]=n; }
     return slots[slot];
