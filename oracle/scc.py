@@ -111,22 +111,28 @@ def fix_sign(x):
     return -x if x[np.argmax(np.abs(x))] < 0 else x
 
 
-def solve_scc(prob, tol=1e-10, maxit=40, ground_tol=1e-11, eom_tol=1e-9):
+def solve_scc(prob, tol=1e-10, maxit=40, ground_tol=1e-11, eom_tol=1e-9, dense=False,
+              start=None):
     """Self-consistent SCCSD for the two lowest states a, b (K = {a, b},
     Sec. 2.4.2): find zeta with O_ab(zeta) = 0, where at each zeta the ground
     state T(zeta) is converged with X3 built from the current R_a, R_b and the
     states are the two lowest right EOM roots of the SCC Jacobian; R0 = eta.R/omega
     (block form of the EOM matrix, Sec. 2.1). The root is followed from zeta = 0
-    (plain CCSD) by the secant method on O_ab. Returns a dict."""
+    (plain CCSD) by the secant method on O_ab. dense=True takes the roots from
+    the explicit Jacobian (small systems); start = (zeta, t, Ra, Rb) of a
+    nearby solution replaces the zeta = 0 start. Returns a dict."""
     from . import solvers as sv
     from . import response as rp
     o, v = prob.o, prob.v
-    zeta, Ra, Rb, x = 0.0, None, None, None
+    zeta, Ra, Rb, x = (0.0, None, None, None) if start is None else start
     hist = []
     for it in range(1, maxit + 1):
         scc = None if Ra is None else (zeta, torch.tensor(Ra), torch.tensor(Rb))
         x, E0, _ = sv.ground_state(prob, tol=ground_tol, scc=scc, x0=x)
-        w, X = sv.eom(prob, x, 2, side="right", tol=eom_tol, scc=scc)
+        if dense:
+            w, X = sv.eom_dense(prob, x, 2, side="right", scc=scc)
+        else:
+            w, X = sv.eom(prob, x, 2, side="right", tol=eom_tol, scc=scc)
         Xa, Xb = fix_sign(X[0]), fix_sign(X[1])
         eta = rp.eta(prob, x, scc=scc).numpy()
         r0a, r0b = float(eta @ Xa / w[0]), float(eta @ Xb / w[1])

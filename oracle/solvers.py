@@ -65,6 +65,26 @@ def ground_state(prob, tol=1e-10, maxit=200, scc=None, x0=None, diis=8):
     raise RuntimeError(f"ground state did not converge: |Omega| = {nrm:.3e}")
 
 
+def jacobian_matrix(prob, x, scc=None):
+    """Explicit A (columns A e_nu) for small systems."""
+    f = lambda y: rp.jacobian_right(prob, x, y, scc=scc)
+    return torch.func.vmap(f)(torch.eye(prob.dim, dtype=torch.float64)).T.numpy()
+
+
+def eom_dense(prob, x, nroots, side="right", scc=None):
+    """Lowest-Re roots from a dense eigendecomposition of the explicit
+    Jacobian (small systems; same conventions as eom)."""
+    A = jacobian_matrix(prob, x, scc=scc)
+    w, V = np.linalg.eig(A if side == "right" else A.T)
+    order = np.argsort(w.real)[:nroots]
+    w, V = w[order], V[:, order]
+    if np.max(np.abs(w.imag)) > 1e-10:
+        raise RuntimeError("complex EOM roots")
+    X = V.real.T
+    X /= np.linalg.norm(X, axis=1, keepdims=True)
+    return w.real, X
+
+
 def eom(prob, x, nroots, side="right", tol=1e-8, maxit=200, scc=None,
         max_space=None, seed_vectors=None):
     """Lowest-Re roots of the EOM Jacobian; returns (omega[nroots], V[nroots][dim])."""
