@@ -238,6 +238,49 @@ int sccsd_learned_guess(sccsd_ctx* ctx, sccsd_mlp* net, double* t0, double* Dpre
  * for the orbital-energy denominators D. */
 int sccsd_set_preconditioner(sccsd_ctx* ctx, const double* Dprec);
 
+/* ---- Lagrangian multipliers (gradients and couplings) ---------------------
+ * sccsd_solve_multipliers solves the stationarity equations of the SCCSD
+ * Lagrangian (Sec. 2.3.1 and 2.3.3 of the paper) for K = {a, b} with the
+ * natural projection, at fixed orbitals (no orbital multipliers), for
+ *   kind 0: the gradient of state n_state (0 = a, 1 = b), or
+ *   kind 1: the derivative coupling <psi_m|d psi_n> from the bra-frozen
+ *           overlap O_mn (Sec. 2.3.4), m_state != n_state.
+ * Inputs describe the converged SCCSD solution:
+ *   vecs [5][dim] packed: t, R_a, R_b (right EOM vectors, kets), L_a, L_b
+ *        (left EOM vectors normalised so that L_k . R_k = 1, bras);
+ *   scal [5]: zeta, r0_a, r0_b, omega_a, omega_b  (r0 = eta . R / omega).
+ * Outputs (any may be NULL; host or device memory):
+ *   zbar [dim]   ground-state multipliers (a bra);
+ *   K [2][dim]   the gauge-free excited-state bras
+ *                K_k = (delta_kn - <Lbar_k|R_k>) L_k + Lbar_k (no delta_kn for
+ *                a coupling; Sec. 2.3.2); Lbar_k itself is fixed only up to
+ *                multiples of L_k, which do not enter any result;
+ *   out_scal [5] gbar, Lbar0_a, Lbar0_b, Ebar_a, Ebar_b (Ebar in the gauge
+ *                Lbar_k . R_k = 0, i.e. Lbar_k = K_k - (delta_kn -
+ *                Lbar0_k r0_k) L_k);
+ *   D1 [n][n], Gamma [J][n][n]  derivatives of the Lagrangian with respect to
+ *                h_pq and L^J_pq: the effective densities of the gradient or
+ *                coupling (Gamma needs D1).
+ * Solver: right-preconditioned restarted GMRES on the affine stationarity map,
+ * with an FP64 residual driving correction solves in the context's precision
+ * when that is mixed and refine_tol > 0; maxit bounds the number of
+ * applications of the map. Returns SCCSD_ENOTCONV (outputs hold the last
+ * iterate) when the FP64 residual norm does not reach tol. */
+int sccsd_solve_multipliers(sccsd_ctx* ctx, const double* vecs, const double* scal, int kind,
+                            int m_state, int n_state, double tol, int maxit, double refine_tol,
+                            double* zbar, double* K, double* out_scal, double* D1,
+                            double* Gamma, int* iterations);
+/* The packed amplitudes t of the context's current state (the last
+ * sccsd_residual, or the result of a solver), e.g. the SCCSD ground state
+ * after sccsd_solve_scc. */
+int sccsd_state_amplitudes(sccsd_ctx* ctx, double* t);
+/* The stationarity residual r [3 dim + 1] = (d/dt, d/dR_a, d/dR_b, d/dzeta)
+ * of the Lagrangian at the unknowns u [3 dim + 1] = (zbar, Lbar_a, Lbar_b,
+ * gbar), with the closed forms for Lbar0_k and Ebar_k substituted (the map
+ * the solver drives to zero; same inputs as sccsd_solve_multipliers). */
+int sccsd_multiplier_residual(sccsd_ctx* ctx, const double* vecs, const double* scal, int kind,
+                              int m_state, int n_state, const double* u, double* r);
+
 /* ---- CUDA graphs: many instances in one launch --------------------------
  * sccsd_capture_transform records W = A V (side 0, V packed kets, as
  * sccsd_jacobian_right) or W = A^T V (side 1, V packed bras, as

@@ -79,6 +79,15 @@ def _declare(lib):
                   "sccsd_learned_features", "sccsd_learned_targets", "sccsd_learned_guess",
                   "sccsd_set_preconditioner"):
             getattr(lib, f).restype = ctypes.c_int
+    lib.sccsd_solve_multipliers.argtypes = [_dp, _dp, _dp, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                            ctypes.c_double, _dp, _dp, _dp, _dp, _dp, _dp]
+    lib.sccsd_solve_multipliers.restype = ctypes.c_int
+    lib.sccsd_multiplier_residual.argtypes = [_dp, _dp, _dp, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_int, _dp, _dp]
+    lib.sccsd_multiplier_residual.restype = ctypes.c_int
+    lib.sccsd_state_amplitudes.argtypes = [_dp, _dp]
+    lib.sccsd_state_amplitudes.restype = ctypes.c_int
     lib.sccsd_capture_transform.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp, _dp,
                                             ctypes.POINTER(ctypes.c_void_p)]
     lib.sccsd_capture_transform.restype = ctypes.c_int
@@ -390,6 +399,61 @@ class Context:
 
     def set_preconditioner(self, D=None):
         self._check(self.lib.sccsd_set_preconditioner(self.h, _ptr(D)))
+
+    def state_amplitudes(self):
+        t = np.empty(self.dim)
+        self._check(self.lib.sccsd_state_amplitudes(self.h, _ptr(t)))
+        return t
+
+    def scc_state(self, tol=1e-10, maxit=40, ground_tol=1e-11, eom_tol=1e-9, left_tol=1e-9):
+        """Converged SCCSD for the two lowest states plus their left vectors
+        (L_k . R_k = 1): the state dict taken by solve_multipliers."""
+        r = self.solve_scc(tol=tol, maxit=maxit, ground_tol=ground_tol, eom_tol=eom_tol)
+        t = self.state_amplitudes()
+        wl, VL, _ = self.solve_states(2, side="left", tol=left_tol)
+        La = VL[0] / (VL[0] @ r["Ra"])
+        Lb = VL[1] / (VL[1] @ r["Rb"])
+        return {"t": t, "Ra": r["Ra"], "Rb": r["Rb"], "La": La, "Lb": Lb, "zeta": r["zeta"],
+                "r0a": float(r["r0"][0]), "r0b": float(r["r0"][1]),
+                "omega_a": float(r["omega"][0]), "omega_b": float(r["omega"][1]),
+                "omega_left": wl, "e_corr": r["e_corr"]}
+
+    @staticmethod
+    def _mult_args(state, target):
+        vecs = np.ascontiguousarray(np.concatenate(
+            [np.asarray(state[k], dtype=np.float64).reshape(-1) for k in ("t", "Ra", "Rb", "La", "Lb")]))
+        scal = np.array([state["zeta"], state["r0a"], state["r0b"], state["omega_a"],
+                         state["omega_b"]], dtype=np.float64)
+        if target[0] == "gradient":
+            return vecs, scal, 0, 0, int(target[1])
+        return vecs, scal, 1, int(target[1]), int(target[2])
+
+    def multiplier_residual(self, state, target, u):
+        vecs, scal, kind, m, n = self._mult_args(state, target)
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        r = np.empty(3 * self.dim + 1)
+        self._check(self.lib.sccsd_multiplier_residual(self.h, _ptr(vecs), _ptr(scal), kind, m, n,
+                                                       _ptr(u), _ptr(r)))
+        return r
+
+    def solve_multipliers(self, state, target, tol=1e-9, maxit=400, refine_tol=1e-6,
+                          densities=True):
+        """Multipliers of the SCCSD Lagrangian for target ("gradient", n) or
+        ("coupling", m, n) at the converged state (dict with t, Ra, Rb, La, Lb
+        packed vectors and zeta, r0a, r0b, omega_a, omega_b)."""
+        dim = self.dim
+        vecs, scal, kind, m, n = self._mult_args(state, target)
+        zbar = np.empty(dim)
+        K = np.empty((2, dim))
+        sc = np.empty(5)
+        D1 = np.empty((self.n, self.n)) if densities else None
+        G = np.empty((self.J, self.n, self.n)) if densities else None
+        it = ctypes.c_int()
+        self._check(self.lib.sccsd_solve_multipliers(
+            self.h, _ptr(vecs), _ptr(scal), kind, m, n, float(tol), int(maxit), float(refine_tol),
+            _ptr(zbar), _ptr(K), _ptr(sc), _ptr(D1), _ptr(G), ctypes.addressof(it)))
+        return {"zbar": zbar, "K": K, "gbar": sc[0], "lb0": sc[1:3], "Ebar": sc[3:5],
+                "D1": D1, "Gamma": G, "iterations": it.value}
 
     def capture_transform(self, V, W, side="right"):
         """CUDA graph (handle) of W = A V (right) or A^T V (left), device tensors."""

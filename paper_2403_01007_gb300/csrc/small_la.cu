@@ -399,6 +399,14 @@ __global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, doubl
     y[k] = a * x[k] + b * y[k];
 }
 
+// y = d * x elementwise
+__global__ void k_scale(int64_t n, const double* __restrict__ d, const double* __restrict__ x,
+                        double* __restrict__ y) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    y[k] = d[k] * x[k];
+}
+
 // y_k = x_k - lam_k-weighted: r[k][:] = ax[k][:] - lam[order[k]] * x[k][:]
 __global__ void k_ritz_residual(int nr, int64_t n, const double* __restrict__ ax,
                                 const double* __restrict__ x, const double* __restrict__ wr,
@@ -429,6 +437,9 @@ void launch_precond(cudaStream_t st, int64_t n, const double* r, const double* D
 }
 void launch_axpby(cudaStream_t st, int64_t n, double a, const double* x, double b, double* y) {
   k_axpby<<<vgrid(n), 256, 0, st>>>(n, a, x, b, y);
+}
+void launch_scale(cudaStream_t st, int64_t n, const double* d, const double* x, double* y) {
+  k_scale<<<vgrid(n), 256, 0, st>>>(n, d, x, y);
 }
 void launch_ritz_residual(cudaStream_t st, int nr, int64_t n, const double* ax, const double* x,
                           const double* wr, const int* order, double* r) {

@@ -115,10 +115,27 @@ static void no_device() { throw std::runtime_error("solver kernels need the devi
 void launch_small_solve(cudaStream_t, int, const double*, const double*, double*, int*) { no_device(); }
 void launch_small_eig(cudaStream_t, int, const double*, double*, double*, double*, int, int*, int*) { no_device(); }
 void launch_diis(cudaStream_t, int, const double*, double*, int*) { no_device(); }
-void launch_denoms(cudaStream_t, int, int, const double*, double*) {}
+void launch_denoms(cudaStream_t, int o, int v, const double* eps, double* D) {
+  const int64_t ov = (int64_t)o * v;
+  for (int64_t k = 0; k < ov; ++k) D[k] = eps[o + k / o] - eps[k % o];
+  int64_t q = ov;
+  for (int64_t Q = 0; Q < ov; ++Q)
+    for (int64_t P = 0; P <= Q; ++P) D[q++] = D[P] + D[Q];
+}
 void launch_jacobi(cudaStream_t, int64_t, const double*, const double*, const double*, double*) { no_device(); }
-void launch_precond(cudaStream_t, int64_t, const double*, const double*, double, double*) { no_device(); }
-void launch_axpby(cudaStream_t, int64_t, double, const double*, double, double*) { no_device(); }
+void launch_precond(cudaStream_t, int64_t n, const double* r, const double* D, double lam, double* out) {
+  for (int64_t k = 0; k < n; ++k) {
+    double d = lam - D[k];
+    if (d > -1e-4 && d < 1e-4) d = d < 0 ? -1e-4 : 1e-4;
+    out[k] = r[k] / d;
+  }
+}
+void launch_axpby(cudaStream_t, int64_t n, double a, const double* x, double b, double* y) {
+  for (int64_t k = 0; k < n; ++k) y[k] = a * x[k] + b * y[k];
+}
+void launch_scale(cudaStream_t, int64_t n, const double* d, const double* x, double* y) {
+  for (int64_t k = 0; k < n; ++k) y[k] = d[k] * x[k];
+}
 void launch_ritz_residual(cudaStream_t, int, int64_t, const double*, const double*, const double*, const int*, double*) { no_device(); }
 }
 extern "C" long long sccsd_gemm_tn_noalloc_capacity(void) { return 0; }

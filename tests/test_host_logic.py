@@ -51,7 +51,11 @@ def host_lib():
     so = os.path.join(tmp, "libsccsd_hostexec.so")
     srcs = [os.path.join(CSRC, f) for f in ("graph.cpp", "ccsd_graph.cpp", "api.cpp")]
     srcs.append(os.path.join(ROOT, "tests", "host_executor", "host_backend.cpp"))
-    cmd = ["g++", "-O1", "-std=c++17", "-fPIC", "-shared", "-I/usr/local/cuda/include",
+    # SCCSD_HOST_SANITIZE=1 builds the executor with AddressSanitizer (run the
+    # tests with the sanitizer runtime preloaded) to catch out-of-range buffer use
+    san = ["-g", "-fsanitize=address", "-fno-omit-frame-pointer"] \
+        if os.environ.get("SCCSD_HOST_SANITIZE") else []
+    cmd = ["g++", "-O1", "-std=c++17", "-fPIC", "-shared", *san, "-I/usr/local/cuda/include",
            *srcs, "-L/usr/local/cuda/lib64", "-lcudart", "-o", so]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -106,4 +110,65 @@ def test_abi_argument_checks(host_lib):
     with pytest.raises(B.SccsdError) as ei:
         ctx.residual(np.zeros(B.dim(2, 2)), scc=(float("nan"), np.zeros(B.dim(2, 2)), np.zeros(B.dim(2, 2))))
     assert ei.value.code == -1
+    ctx.close()
+
+
+@pytest.fixture(scope="module")
+def mult_system():
+    from oracle import multipliers as mu
+    o, v, J = 2, 4, 10
+    eps, L = syn.system(o, v, J, 0.1, 1)
+    prob = cc.Problem(eps, L, o)
+    st = mu.scc_state(prob)
+    state = {"t": st["t"].numpy(), "Ra": st["Ra"].numpy(), "Rb": st["Rb"].numpy(),
+             "La": st["La"].numpy(), "Lb": st["Lb"].numpy(), "zeta": st["zeta"],
+             "r0a": st["r0a"], "r0b": st["r0b"], "omega_a": st["omega"][0],
+             "omega_b": st["omega"][1]}
+    return (o, v, J, eps, L), prob, st, state
+
+
+@pytest.mark.parametrize("target", [("gradient", 0), ("coupling", 1, 0)], ids=str)
+def test_multiplier_solve_matches_oracle(host_lib, mult_system, target):
+    """The C-ABI multiplier solver (GMRES over the graph's reverse-over-forward
+    Lagrangian gradient), run by the host test double of the device backend,
+    against the oracle's dense solve: every gauge-free quantity and the
+    Lagrangian densities."""
+    from oracle import multipliers as mu
+    B, lib = host_lib
+    (o, v, J, eps, L), prob, st, state = mult_system
+    ctx = B.Context(o, v, J, eps, L, lib=lib)
+    res = ctx.solve_multipliers(state, target, tol=1e-11, maxit=600)
+    M = mu.solve_multipliers(prob, st, target)
+    D1, G = mu.lagrangian_densities(prob, st, target, M)
+    assert abs(res["gbar"] - float(M["gbar"])) < 1e-9
+    assert np.abs(res["lb0"] - np.array([float(M["lb0a"]), float(M["lb0b"])])).max() < 1e-9
+    # Ebar in the gauge Lbar_k . R_k = 0
+    E = np.array([st["E0"] + st["omega"][0], st["E0"] + st["omega"][1]])
+    d = np.array([1.0 if (target[0] == "gradient" and k == target[1]) else 0.0 for k in range(2)])
+    lb0 = np.array([float(M["lb0a"]), float(M["lb0b"])])
+    Eb = E * (d - lb0 * np.array([st["r0a"], st["r0b"]]))
+    assert np.abs(res["Ebar"] - Eb).max() < 1e-8
+    assert np.abs(res["zbar"] - M["zbar"].numpy()).max() < 1e-9
+    for k in range(2):
+        assert np.abs(res["K"][k] - M["K"][k].numpy()).max() < 1e-9
+    assert np.abs(res["D1"] - D1.numpy()).max() < 1e-9
+    assert np.abs(res["Gamma"] - G.numpy()).max() < 1e-9
+    ctx.close()
+
+
+def test_multiplier_residual_map_matches_oracle(host_lib, mult_system):
+    """The stationarity map through the C ABI equals the oracle's at random
+    unknowns (both the affine constant and the linear part)."""
+    from oracle import multipliers as mu
+    B, lib = host_lib
+    (o, v, J, eps, L), prob, st, state = mult_system
+    ctx = B.Context(o, v, J, eps, L, lib=lib)
+    for target in [("gradient", 1), ("coupling", 0, 1)]:
+        f = mu.residual_map(prob, st, target)
+        for seed in (0, 1):
+            u = np.zeros(3 * prob.dim + 1) if seed == 0 else \
+                np.random.default_rng(seed).normal(size=3 * prob.dim + 1)
+            r = ctx.multiplier_residual(state, target, u)
+            ro = f(torch.tensor(u)).numpy()
+            assert np.abs(r - ro).max() < 1e-11 * max(1.0, np.abs(ro).max()), target
     ctx.close()
