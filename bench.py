@@ -270,6 +270,62 @@ def batched_case(args):
     return 0
 
 
+def row_timings(B, w, eps, L, t, Rh, prec, dev, torch, reps=2):
+    """Device time of the other hot-path rows at the same workload and
+    precision, on one SCCSD state (zeta = 0.1, X3 from two of the trial
+    vectors): the residual (ladder, rings, X3 terms), a 6-vector left
+    transformation, the transition densities d_pq and Gamma^J_pq of one
+    bra/ket pair, and one application of the multiplier stationarity map
+    (three reverse-over-forward state gradients plus the overlap gradient).
+    Inputs are synthetic and not converged: the cost does not depend on it."""
+    st = torch.cuda.Stream(device=dev)
+    ctx = B.Context(w.o, w.v, w.J, torch.tensor(eps, device=dev), torch.tensor(L, device=dev),
+                    precision=prec, stream=st.cuda_stream)
+    td = torch.tensor(t, device=dev)
+    Rd = torch.tensor(Rh, device=dev)
+    Ra, Rb = Rd[0].clone(), Rd[1].clone()
+    scc = (0.1, Ra, Rb)
+    sig = torch.empty_like(Rd)
+    n = w.o + w.v
+    D1 = torch.empty(n, n, dtype=torch.float64, device=dev)
+    G = torch.empty(w.J, n, n, dtype=torch.float64, device=dev)
+    vecs = torch.cat([td, Rd[0], Rd[1], Rd[2], Rd[3]]).contiguous()
+    scal = np.array([0.1, 0.05, -0.03, 0.4, 0.5])
+    u = torch.cat([Rd[4], Rd[5], Rd[0] * 0.1, torch.tensor([0.2], dtype=torch.float64,
+                                                           device=dev)]).contiguous()
+    r = torch.empty_like(u)
+    rows = {
+        "residual": lambda: ctx.residual(td, omega=sig[0], scc=scc),
+        "left_6": lambda: ctx.jacobian_left(Rd, sigma=sig),
+        "densities": lambda: ctx.lib.sccsd_densities(ctx.h, 0.3, Rd[2].data_ptr(), 0.05,
+                                                     Rd[0].data_ptr(), D1.data_ptr(),
+                                                     G.data_ptr()),
+        "multiplier_map": lambda: ctx.lib.sccsd_multiplier_residual(
+            ctx.h, vecs.data_ptr(), scal.ctypes.data, 0, 0, 0, u.data_ptr(), r.data_ptr()),
+    }
+    out = {}
+    ctx.residual(td, scc=scc)
+    for name, f in rows.items():
+        rc = f()
+        if isinstance(rc, int) and rc != 0:
+            raise RuntimeError(f"{name}: sccsd error {rc}")
+        if name != "residual":
+            ctx.residual(td, scc=scc)      # keep the SCC state current
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            f()
+        e1.record(st)
+        torch.cuda.synchronize()
+        out[name + "_ms"] = e0.elapsed_time(e1) / reps
+    ctx.close()
+    out["note"] = ("device time per call at this workload and precision; one SCCSD state; "
+                   "the multiplier map is one GMRES operator application")
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -284,6 +340,8 @@ def main():
     ap.add_argument("--no-x3-arm", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-rows", action="store_true",
+                    help="skip the timings of the other hot-path rows")
     ap.add_argument("--kernel-case", type=int, default=0, metavar="V",
                     help="time only the ladder-shaped contraction (rows = nvec*21^2, "
                          "N = K = V^2) through sccsd_gemm_tn; a small case for profilers")
@@ -392,6 +450,10 @@ def main():
         if fp64 is not None:
             x3["max_rel_diff_vs_fp64"] = float(np.abs(sx - s64).max() / np.abs(s64).max())
 
+    rows = None
+    if not args.no_rows and rank == 0 and args.nvec >= 6:
+        rows = row_timings(B, w, eps, L, t, Rh, args.precision, dev, torch)
+
     cpu = None
     if not args.no_cpu_baseline and rank == 0:
         val, sec, threads = cpu_oracle_sample(steps=1)
@@ -432,6 +494,7 @@ def main():
         "e2e": e2e,
         "fp64_arm": fp64,
         "bf16x3_arm": x3,
+        "rows": rows,
         "accuracy": "mixed transforms feed solvers that finish in FP64 (iterative refinement); "
                     "converged energies and roots equal the FP64 path to 1e-8 Eh "
                     "(tests/test_gpu_solvers.py)",
