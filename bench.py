@@ -450,6 +450,21 @@ def main():
         if fp64 is not None:
             x3["max_rel_diff_vs_fp64"] = float(np.abs(sx - s64).max() / np.abs(s64).max())
 
+    # the same batch through the SCCSD Jacobian (zeta = 0.1, X3 from two of the
+    # trial vectors): A R including the similarity-constraint terms
+    scc_arm = None
+    if not args.no_rows and args.nvec >= 2:
+        cs = make_ctx(args.precision)
+        scc = (0.1, R[0].clone(), R[1].clone())
+        with torch.cuda.stream(stream):
+            cs.residual(torch.tensor(t, device=dev), scc=scc)
+        for _ in range(2):
+            cs.jacobian_right(R, sigma=sig)
+        mss = time_batches(cs, R, sig, max(1, args.steps), stream, torch)
+        cs.close()
+        scc_arm = {"transforms_per_s": max(1, args.steps) * args.nvec / (mss / 1e3),
+                   "ms_per_step": mss / max(1, args.steps), "zeta": 0.1}
+
     rows = None
     if not args.no_rows and rank == 0 and args.nvec >= 6:
         rows = row_timings(B, w, eps, L, t, Rh, args.precision, dev, torch)
@@ -494,6 +509,7 @@ def main():
         "e2e": e2e,
         "fp64_arm": fp64,
         "bf16x3_arm": x3,
+        "sccsd_arm": scc_arm,
         "rows": rows,
         "accuracy": "mixed transforms feed solvers that finish in FP64 (iterative refinement); "
                     "converged energies and roots equal the FP64 path to 1e-8 Eh "

@@ -81,6 +81,11 @@ class Backend {
   // out[i] (+)= coef * in[i] over a rank-r index box; both sides strided.
   virtual void copy_view(int rank, const int64_t* dims, double* out, const int64_t* ostr,
                          const double* in, const int64_t* istr, double coef, bool accumulate) = 0;
+  // out[i] (+)= coef * a[i] * b[i] over a rank-r index box, all three strided
+  // (a stride 0 broadcasts): contractions with no contracted index.
+  virtual void mul_view(int rank, const int64_t* dims, double* out, const int64_t* ostr,
+                        const double* a, const int64_t* astr, const double* b,
+                        const int64_t* bstr, double coef, bool accumulate) = 0;
   // C[b][m][n] = alpha * sum_k A(b,m,k) B(b,n,k); C dense and overwritten.
   // tc: the contraction may use tensor cores when the precision mode allows.
   virtual void gemm_view(int64_t batch, int64_t M, int64_t N, int64_t K, double alpha,

@@ -91,6 +91,41 @@ __global__ void k_copy_view(ViewArgs a, int64_t total, double* __restrict__ out,
   }
 }
 
+// out (+)= coef * a * b elementwise over a strided index box (no contracted
+// index; a zero stride broadcasts)
+struct MulArgs32 {
+  int rank;
+  uint32_t dims[kMaxRank];
+  uint32_t ostr[kMaxRank];
+  uint32_t astr[kMaxRank];
+  uint32_t bstr[kMaxRank];
+};
+struct MulArgs {
+  int rank;
+  int64_t dims[kMaxRank];
+  int64_t ostr[kMaxRank];
+  int64_t astr[kMaxRank];
+  int64_t bstr[kMaxRank];
+};
+
+template <class Args, class I>
+__global__ void k_mul_view(Args m, I total, double* __restrict__ out, const double* __restrict__ a,
+                           const double* __restrict__ b, double coef, int acc) {
+  for (I lin = (I)blockIdx.x * blockDim.x + threadIdx.x; lin < total;
+       lin += (I)gridDim.x * blockDim.x) {
+    I r = lin, oo = 0, ia = 0, ib = 0;
+    for (int k = m.rank - 1; k >= 0; --k) {
+      const I c = r % (I)m.dims[k];
+      r /= (I)m.dims[k];
+      oo += c * (I)m.ostr[k];
+      ia += c * (I)m.astr[k];
+      ib += c * (I)m.bstr[k];
+    }
+    const double v = coef * a[ia] * b[ib];
+    out[oo] = acc ? out[oo] + v : v;
+  }
+}
+
 // 32x32 shared-memory tile transpose for copies whose fastest output index is
 // strided in the input while another output index is contiguous in the input.
 // Tile axes: x = output dim px (unit output stride), y = output dim py (unit
@@ -404,6 +439,64 @@ class CudaBackend : public Backend {
     }
     k_copy_view<<<grid_for(total, 256), 256, 0, st>>>(a, total, out, in, coef, acc ? 1 : 0);
     check_launch("copy_view");
+  }
+
+  void mul_view(int rank, const int64_t* dims, double* out, const int64_t* ostr, const double* a,
+                const int64_t* astr, const double* b, const int64_t* bstr, double coef,
+                bool acc) override {
+    // merge adjacent dims contiguous on all three sides; drop unit dims
+    int64_t d[kMaxRank], os[kMaxRank], as[kMaxRank], bs[kMaxRank];
+    int r = 0;
+    int64_t total = 1;
+    for (int k = 0; k < rank; ++k) {
+      total *= dims[k];
+      if (dims[k] == 1) continue;
+      if (r > 0 && os[r - 1] == ostr[k] * dims[k] && as[r - 1] == astr[k] * dims[k] &&
+          bs[r - 1] == bstr[k] * dims[k]) {
+        d[r - 1] *= dims[k];
+        os[r - 1] = ostr[k];
+        as[r - 1] = astr[k];
+        bs[r - 1] = bstr[k];
+        continue;
+      }
+      d[r] = dims[k];
+      os[r] = ostr[k];
+      as[r] = astr[k];
+      bs[r] = bstr[k];
+      ++r;
+    }
+    if (total == 0) return;
+    int64_t omax = 0, amax = 0, bmax = 0;
+    for (int k = 0; k < r; ++k) {
+      omax += (d[k] - 1) * os[k];
+      amax += (d[k] - 1) * as[k];
+      bmax += (d[k] - 1) * bs[k];
+    }
+    const int64_t lim = 1LL << 31;
+    if (total < lim && omax < lim && amax < lim && bmax < lim) {
+      MulArgs32 m;
+      m.rank = r;
+      for (int k = 0; k < r; ++k) {
+        m.dims[k] = (uint32_t)d[k];
+        m.ostr[k] = (uint32_t)os[k];
+        m.astr[k] = (uint32_t)as[k];
+        m.bstr[k] = (uint32_t)bs[k];
+      }
+      k_mul_view<MulArgs32, uint32_t><<<grid_for(total, 256), 256, 0, st>>>(
+          m, (uint32_t)total, out, a, b, coef, acc ? 1 : 0);
+    } else {
+      MulArgs m;
+      m.rank = r;
+      for (int k = 0; k < r; ++k) {
+        m.dims[k] = d[k];
+        m.ostr[k] = os[k];
+        m.astr[k] = as[k];
+        m.bstr[k] = bs[k];
+      }
+      k_mul_view<MulArgs, int64_t><<<grid_for(total, 256), 256, 0, st>>>(m, total, out, a, b,
+                                                                           coef, acc ? 1 : 0);
+    }
+    check_launch("mul_view");
   }
 
   void dgemm(int64_t nb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,

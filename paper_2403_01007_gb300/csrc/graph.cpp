@@ -504,6 +504,20 @@ std::string Graph::trace_report(int top) {
              (long long)op.trace_calls, idx[k], names[(int)op.kind], op.la.c_str(), op.lb.c_str(),
              op.lc.c_str(), (int)op.tc, dims.c_str());
     out += line;
+    if (op.kind == OpKind::Add) {
+      // the producer of every term: c contract, a add, s slice, e embed, l ladder, i input
+      std::string terms = "           terms:";
+      for (size_t q = 0; q < op.in.size(); ++q) {
+        char kc = 'i';
+        for (size_t p = 0; p < ops.size(); ++p)
+          if (ops[p].out == op.in[q]) {
+            kc = "caselL"[(int)ops[p].kind];
+            break;
+          }
+        terms += std::string(" ") + kc + ":" + op.perm[q];
+      }
+      out += terms + "\n";
+    }
   }
   return out;
 }
@@ -609,6 +623,25 @@ void Graph::exec_contract(Op& op, double* out_data, const int64_t* ostr, double 
     if (p != std::string::npos) return A.dims[p];
     return B.dims[lb.find(c)];
   };
+  // nothing contracted (scalings, outer and elementwise products): one
+  // elementwise pass over the output, no GEMM
+  {
+    bool all_out = true;
+    for (char c : la + lb)
+      if (lc.find(c) == std::string::npos) all_out = false;
+    if (all_out) {
+      auto as_ = row_strides(A.dims), bs_ = row_strides(B.dims);
+      int64_t astr[kMaxRank], bstr[kMaxRank];
+      for (int q = 0; q < rc; ++q) {
+        size_t pa = la.find(lc[q]), pb = lb.find(lc[q]);
+        astr[q] = pa == std::string::npos ? 0 : as_[pa];
+        bstr[q] = pb == std::string::npos ? 0 : bs_[pb];
+      }
+      be->mul_view(rc, out.dims.data(), out_data, ostrides.data(), A.data, astr, B.data, bstr,
+                   op.alpha * coef, acc);
+      return;
+    }
+  }
   // a label group of X collapsed to at most two strided levels
   struct Grp {
     bool ok = true;

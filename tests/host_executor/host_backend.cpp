@@ -54,6 +54,14 @@ class HostBackend : public Backend {
       out[oo] = (acc? out[oo]:0.0) + coef*in[ii];
     }
   }
+  void mul_view(int rank, const int64_t* dims, double* out, const int64_t* ostr, const double* a, const int64_t* astr, const double* b, const int64_t* bstr, double coef, bool acc) override {
+    int64_t total=1; for (int k=0;k<rank;++k) total*=dims[k];
+    for (int64_t lin=0; lin<total; ++lin) {
+      int64_t r=lin, oo=0, ia=0, ib=0;
+      for (int k=rank-1;k>=0;--k){ int64_t c=r%dims[k]; r/=dims[k]; oo+=c*ostr[k]; ia+=c*astr[k]; ib+=c*bstr[k]; }
+      out[oo] = (acc? out[oo]:0.0) + coef*a[ia]*b[ib];
+    }
+  }
   static int64_t vr(const MatView& v, int64_t r){ return v.n2r ? (r / v.n2r) * v.sr1 + (r % v.n2r) * v.sr2 : r * v.sr2; }
   static int64_t vk(const MatView& v, int64_t k){ return v.n2k ? (k / v.n2k) * v.sk1 + (k % v.n2k) * v.sk2 : k * v.sk2; }
   void gemm_view(int64_t nb, int64_t M, int64_t N, int64_t K, double alpha, const MatView& A, const MatView& B, double* C, bool) override {
