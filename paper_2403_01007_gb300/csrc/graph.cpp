@@ -406,31 +406,60 @@ void Graph::run(const std::vector<int>& targets) {
   for (size_t i = 0; i < ops.size(); ++i)
     if (need_op[i])
       for (int x : ops[i].in) last_use[x] = i;
-  // Contractions whose result only feeds one volatile permuted sum are
-  // evaluated inside that sum, straight into its output: the intermediate
-  // is never stored and the sum does not re-read it.
+  // Planning of the per-call permuted sums. A term produced by a contraction
+  // whose result feeds nothing else is evaluated inside the sum, straight into
+  // its output (the intermediate is never stored, the sum never re-reads it);
+  // a term produced by another such single-use sum is replaced by that sum's
+  // own terms (permutations composed, coefficients multiplied), recursively.
   std::vector<int> uses(t.size(), 0);
   for (size_t i = 0; i < ops.size(); ++i)
     if (need_op[i])
       for (int x : ops[i].in) uses[x]++;
   std::vector<char> fused_op(ops.size(), 0);
-  std::map<size_t, std::vector<int>> add_fused;
+  std::map<size_t, std::vector<SumTerm>> add_plan;
+  auto single_use = [&](int x) {
+    const int p = prod[x];
+    return p >= 0 && need_op[p] && vol_[x] && !is_target[x] && uses[x] == 1 &&
+           t[x].kind == Kind::Node;
+  };
   for (size_t i = 0; i < ops.size(); ++i) {
     const Op& a = ops[i];
     if (!need_op[i] || a.kind != OpKind::Add || !vol_[a.out] || t[a.out].dims.empty()) continue;
-    std::vector<int> f(a.in.size(), -1);
-    bool any = false;
-    for (size_t k = 0; k < a.in.size(); ++k) {
-      const int x = a.in[k], p = prod[x];
-      if (p < 0 || !need_op[p] || ops[p].kind != OpKind::Contract || !vol_[x] || is_target[x] ||
-          uses[x] != 1 || t[x].kind != Kind::Node)
-        continue;
-      f[k] = p;
-      fused_op[p] = 1;
-      any = true;
-      for (int y : ops[p].in) last_use[y] = std::max(last_use[y], i);
+    std::vector<SumTerm> plan;
+    bool changed = false;
+    std::vector<SumTerm> stack;
+    for (size_t k = a.in.size(); k-- > 0;) stack.push_back({a.in[k], a.perm[k], a.coef[k], -1});
+    while (!stack.empty()) {
+      SumTerm tm = stack.back();
+      stack.pop_back();
+      const int x = tm.node;
+      if (single_use(x)) {
+        const int p = prod[x];
+        const Op& q = ops[p];
+        if (q.kind == OpKind::Contract) {
+          tm.fused = p;
+          fused_op[p] = 1;
+          for (int y : q.in) last_use[y] = std::max(last_use[y], i);
+          plan.push_back(tm);
+          changed = true;
+          continue;
+        }
+        if (q.kind == OpKind::Add && !t[x].dims.empty()) {
+          // x's dim j has label q.lc[j] in q and label tm.perm[j] here
+          fused_op[p] = 1;
+          changed = true;
+          for (size_t r = q.in.size(); r-- > 0;) {
+            std::string pr;
+            for (char c : q.perm[r]) pr.push_back(tm.perm[q.lc.find(c)]);
+            stack.push_back({q.in[r], pr, tm.coef * q.coef[r], -1});
+          }
+          continue;
+        }
+      }
+      last_use[x] = std::max(last_use[x], i);
+      plan.push_back(tm);
     }
-    if (any) add_fused[i] = f;
+    if (changed) add_plan[i] = plan;
   }
   std::vector<std::vector<int>> free_after(ops.size());
   for (size_t i = 0; i < ops.size(); ++i) {
@@ -455,8 +484,8 @@ void Graph::run(const std::vector<int>& targets) {
     void* e0 = trace ? be->record_event() : nullptr;
     if (vol_[op.out] && !t[op.out].data)
       t[op.out].data = be->pool_get(std::max<int64_t>(1, t[op.out].numel()));
-    auto fz = add_fused.find(i);
-    if (fz != add_fused.end())
+    auto fz = add_plan.find(i);
+    if (fz != add_plan.end())
       exec_add(op, fz->second);
     else
       exec(op);
@@ -567,30 +596,35 @@ void Graph::exec(Op& op) {
 // Permuted sum. fused[k] >= 0: term k is the output of contraction op
 // fused[k], which is evaluated here straight into the sum (scaled, and
 // accumulated after the first term) instead of through its own buffer.
-void Graph::exec_add(Op& op, const std::vector<int>& fused) {
+void Graph::exec_add(Op& op, const std::vector<SumTerm>& terms_in) {
   Tensor& out = t[op.out];
   const int rc = (int)out.dims.size();
   auto ostr = row_strides(out.dims);
-  for (size_t k = 0; k < op.in.size(); ++k) {
-    const Tensor& x = t[op.in[k]];
-    if (!fused.empty() && fused[k] >= 0) {
+  std::vector<SumTerm> own;
+  if (terms_in.empty())
+    for (size_t k = 0; k < op.in.size(); ++k) own.push_back({op.in[k], op.perm[k], op.coef[k], -1});
+  const std::vector<SumTerm>& terms = terms_in.empty() ? own : terms_in;
+  for (size_t k = 0; k < terms.size(); ++k) {
+    const SumTerm& tm = terms[k];
+    const Tensor& x = t[tm.node];
+    if (tm.fused >= 0) {
       int64_t cs[kMaxRank];
-      for (size_t q = 0; q < x.dims.size(); ++q) cs[q] = ostr[op.lc.find(op.perm[k][q])];
+      for (size_t q = 0; q < x.dims.size(); ++q) cs[q] = ostr[op.lc.find(tm.perm[q])];
       void* e0 = trace ? be->record_event() : nullptr;
-      exec_contract(ops[fused[k]], out.data, cs, op.coef[k], k > 0);
+      exec_contract(ops[tm.fused], out.data, cs, tm.coef, k > 0);
       if (trace) {
         // the sum's own time includes this; the contraction is listed too
-        ops[fused[k]].trace_ms += be->elapsed_ms(e0, be->record_event());
-        ops[fused[k]].trace_calls += 1;
+        ops[tm.fused].trace_ms += be->elapsed_ms(e0, be->record_event());
+        ops[tm.fused].trace_calls += 1;
       }
       continue;
     }
     auto xs = row_strides(x.dims);
     int64_t istr[kMaxRank];
-    for (int q = 0; q < rc; ++q) istr[q] = xs[op.perm[k].find(op.lc[q])];
-    be->copy_view(rc, out.dims.data(), out.data, ostr.data(), x.data, istr, op.coef[k], k > 0);
+    for (int q = 0; q < rc; ++q) istr[q] = xs[tm.perm.find(op.lc[q])];
+    be->copy_view(rc, out.dims.data(), out.data, ostr.data(), x.data, istr, tm.coef, k > 0);
   }
-  if (rc == 0 && op.in.empty()) be->fill(out.data, 1, 0.0);
+  if (rc == 0 && terms.empty()) be->fill(out.data, 1, 0.0);
 }
 
 // Contraction into out_data, whose dims are those of op's output and whose
@@ -741,8 +775,8 @@ void Graph::exec_contract(Op& op, double* out_data, const int64_t* ostr, double 
     for (int q = 0; q < rc; ++q) istr[q] = cs[cl.find(lc[q])];
     be->copy_view(rc, out.dims.data(), out_data, ostrides.data(), Cp, istr, coef, acc);
   };
-  // tensor-core route: operands that do not change between calls keep
-  // their converted form in the backend (keyed by node, layout, version)
+  // tensor-core route: converted operands are kept in the backend, keyed by
+  // (node, layout, version)
   const bool use_tc = op.tc && be->tc_will_use(nb, M, N, K);
   if (use_tc) {
     auto hash = [](const std::string& a, const std::string& b) {
@@ -752,7 +786,10 @@ void Graph::exec_contract(Op& op, double* out_data, const int64_t* ostr, double 
     };
     Backend::OperandKey kA{this, op.in[0], A.version, hash(la, bat + ml + kl)};
     Backend::OperandKey kB{this, op.in[1], B.version, hash(lb, bat + nl + kl)};
-    const bool cA = !vol_[op.in[0]], cB = !vol_[op.in[1]];
+    // every operand is keyed: a per-call tensor changes version on every run,
+    // so its converted form is reused only by the other contractions of the
+    // same run that read it in the same layout
+    const bool cA = true, cB = true;
     if (cA && be->tc_cached(kA))
       Av.p = nullptr;
     else if (!okA)

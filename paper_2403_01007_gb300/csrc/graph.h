@@ -131,7 +131,16 @@ class Graph {
   int new_tensor(const std::vector<int64_t>& dims, Kind k);
   void exec(Op& op);
   void exec_contract(Op& op, double* out_data, const int64_t* ostr, double coef, bool acc);
-  void exec_add(Op& op, const std::vector<int>& fused);
+  // one term of a permuted sum after planning: node x labelled by perm (in
+  // the sum's labels), scaled by coef; fused >= 0: x is the output of that
+  // contraction op, which is evaluated straight into the sum
+  struct SumTerm {
+    int node;
+    std::string perm;
+    double coef;
+    int fused;
+  };
+  void exec_add(Op& op, const std::vector<SumTerm>& terms);
   std::vector<char> vol_;
   std::vector<int> held_;  // volatile buffers kept alive for the caller
 };
