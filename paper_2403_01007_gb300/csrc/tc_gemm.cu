@@ -1,15 +1,20 @@
 // tcgen05 BF16 GEMM with TMA loads and TMEM accumulators (sm_103a).
 //
-// One CTA computes a 128 x 256 FP32 tile of A * B^T (both operands K-major
-// BF16 in global memory, padded to whole tiles) over a range of K blocks
-// (blockIdx.z selects the range when K is split) and writes alpha * tile into
-// an FP64 output through a two-level strided view (overwrite or accumulate),
-// so that permuted tensor layouts need no separate copy. Warp roles:
+// A persistent CTA (one per SM) walks a list of work items, each a 128 x 256
+// FP32 tile of A * B^T (both operands K-major BF16 in global memory, padded to
+// whole tiles) over a range of K blocks (a split index selects the range when
+// K is split), and writes alpha * tile into an FP64 output through a strided
+// multi-level view (overwrite or accumulate), so that permuted tensor layouts
+// need no separate copy. TMEM holds two accumulators: the epilogue of one item
+// overlaps the MMAs of the next, and the set-up (TMEM allocation, barriers,
+// pipeline fill) is paid once per CTA instead of once per tile. Warp roles:
 //   warp 4    : TMA producer, 4-stage ring of (A 128x64, B 256x64) tiles,
 //               128-byte swizzle, completion on mbarriers (expect_tx)
 //   warp 5    : one elected thread issues tcgen05.mma.kind::f16 (M=128,
-//               N=256, K=16 per instruction, 4 per stage), commits each stage
-//               back to the producer and finally the accumulator
+//               N=256, K=16 per instruction, 4 per stage) into accumulator
+//               (item & 1), commits each stage back to the producer and the
+//               finished accumulator to the epilogue; before reusing an
+//               accumulator it waits until the epilogue has read it
 //   warps 0-3 : epilogue, tcgen05.ld 32 lanes x 32 columns at a time; when
 //               the output's row index is the unit-stride one each thread
 //               stores its own row (consecutive lanes, consecutive
@@ -43,7 +48,7 @@ constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int EPI_FLOATS = 4 * 32 * 33;
 constexpr int SMEM_BYTES = 1024 /*align slack*/ + STAGES * STAGE_BYTES + 256 /*barriers*/ +
                            EPI_FLOATS * 4 + 2 * 4 * 32 * 8 /*row and column offsets*/;
-constexpr int TMEM_COLS = 256;
+constexpr int TMEM_COLS = 512;  // two 128 x 256 FP32 accumulators
 constexpr uint32_t WAIT_LIMIT = 1u << 24;  // polls before a wait is declared failed
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -106,36 +111,53 @@ __device__ __forceinline__ int64_t out_col(const OutView& v, int64_t c) {
   return level_offset(v.nc, v.ce, v.cs, c);
 }
 
+// Work items are (split z, N tile, M tile), M fastest; a persistent CTA takes
+// items blockIdx.x, blockIdx.x + gridDim.x, ... so that the CTAs working at
+// one time share a B tile (read once from HBM, then served from L2).
+struct TcItem {
+  int64_t m0, n0;
+  int z;
+};
+__device__ __forceinline__ TcItem tc_item(int64_t w, int64_t mt, int64_t nt) {
+  TcItem r;
+  r.m0 = (w % mt) * BM;
+  const int64_t rest = w / mt;
+  r.n0 = (rest % nt) * BN;
+  r.z = (int)(rest / nt);
+  return r;
+}
+
 __global__ void __launch_bounds__(192, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-              int64_t M, int64_t N, int nk_total, int kbs, double alpha, double* __restrict__ C,
-              int64_t split_stride, const OutView ov, int accumulate, int* err) {
+              int64_t M, int64_t N, int64_t mt, int64_t nt, int64_t items, int nk_total, int kbs,
+              double alpha, double* __restrict__ C, int64_t split_stride, const OutView ov,
+              int accumulate, int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
   uint8_t* sB = smem + STAGES * A_BYTES;
   uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* accf = empty + STAGES;
-  uint32_t* tmem_slot = (uint32_t*)(accf + 1);
+  uint64_t* acc_full = empty + STAGES;   // [2]: accumulator buffer ready for the epilogue
+  uint64_t* acc_empty = acc_full + 2;    // [2]: epilogue done reading the buffer
+  uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   float* epi = (float*)(smem + STAGES * STAGE_BYTES + 256);
   int64_t* row_off = (int64_t*)(epi + EPI_FLOATS);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // M tiles run fastest so that the CTAs resident at one time share a B tile
-  // (read once from HBM, then served from L2)
-  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
-  // this CTA's K blocks: [kb0, kb0 + nk)
-  const int kb0 = (int)blockIdx.z * kbs;
-  const int nk = (nk_total - kb0 < kbs) ? nk_total - kb0 : kbs;
+  // K blocks of split z: [z * kbs, z * kbs + nk(z))
+  auto nk_of = [&](int z) { return (nk_total - z * kbs < kbs) ? nk_total - z * kbs : kbs; };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
     }
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(accf)));
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&acc_full[b])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&acc_empty[b])));
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -152,90 +174,125 @@ __global__ void __launch_bounds__(192, 1)
 
   if (warp == 4) {
     if (lane == 0) {
-      int issued_last[STAGES];
+      // TMA producer over all items of this CTA; g counts k-blocks globally
+      int64_t issued_last[STAGES];
       for (int s = 0; s < STAGES; ++s) issued_last[s] = -1;
-      for (int kb = 0; kb < nk; ++kb) {
-        const int s = kb % STAGES;
-        if (kb >= STAGES) {
-          if (!mbar_wait(smem_u32(&empty[s]), ((kb / STAGES) - 1) & 1, err, 1)) {
-            *abort_flag = 1;
-            break;
+      int64_t g = 0;
+      for (int64_t w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
+        const TcItem it = tc_item(w, mt, nt);
+        const int nk = nk_of(it.z), kb0 = it.z * kbs;
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = (int)(g % STAGES);
+          if (g >= STAGES) {
+            if (!mbar_wait(smem_u32(&empty[s]), (uint32_t)((g / STAGES) - 1) & 1, err, 1)) {
+              *abort_flag = 1;
+              break;
+            }
           }
+          if (*abort_flag) break;
+          const uint32_t fb = smem_u32(&full[s]);
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                       "r"(STAGE_BYTES)
+                       : "memory");
+          const int x = (kb0 + kb) * BK;
+          asm volatile(
+              "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+              " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(sA + s * A_BYTES)),
+              "l"((uint64_t)&tmA), "r"(fb), "r"(x), "r"((int)it.m0)
+              : "memory");
+          asm volatile(
+              "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+              " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(sB + s * B_BYTES)),
+              "l"((uint64_t)&tmB), "r"(fb), "r"(x), "r"((int)it.n0)
+              : "memory");
+          issued_last[s] = g;
         }
-        if (*abort_flag) break;
-        const uint32_t fb = smem_u32(&full[s]);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
-                     "r"(STAGE_BYTES)
-                     : "memory");
-        const int x = (kb0 + kb) * BK;
-        asm volatile(
-            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-            " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(sA + s * A_BYTES)),
-            "l"((uint64_t)&tmA), "r"(fb), "r"(x), "r"((int)m0)
-            : "memory");
-        asm volatile(
-            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-            " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(sB + s * B_BYTES)),
-            "l"((uint64_t)&tmB), "r"(fb), "r"(x), "r"((int)n0)
-            : "memory");
-        issued_last[s] = kb;
       }
       // make sure no copy issued by this CTA is still in flight at exit
       for (int s = 0; s < STAGES; ++s)
         if (issued_last[s] >= 0)
-          mbar_wait(smem_u32(&full[s]), (issued_last[s] / STAGES) & 1, err, 2);
+          mbar_wait(smem_u32(&full[s]), (uint32_t)(issued_last[s] / STAGES) & 1, err, 2);
     }
   } else if (warp == 5) {
     if (lane == 0) {
+      // MMA issuer: item number i of this CTA accumulates in TMEM buffer i & 1
       constexpr uint32_t idesc = make_idesc(BM, BN);
-      for (int kb = 0; kb < nk; ++kb) {
-        const int s = kb % STAGES;
-        if (!mbar_wait(smem_u32(&full[s]), (kb / STAGES) & 1, err, 3) || *abort_flag) {
-          *abort_flag = 1;
-          break;
+      int64_t g = 0;
+      int64_t i = 0;
+      for (int64_t w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x, ++i) {
+        const TcItem it = tc_item(w, mt, nt);
+        const int nk = nk_of(it.z);
+        const int b = (int)(i & 1);
+        if (i >= 2) {
+          // the epilogue has read this buffer's previous tile
+          if (!mbar_wait(smem_u32(&acc_empty[b]), (uint32_t)((i / 2) - 1) & 1, err, 5)) {
+            *abort_flag = 1;
+            break;
+          }
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
+        const uint32_t dst = tmem + (uint32_t)(b * BN);
+        bool ok = true;
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = (int)(g % STAGES);
+          if (!mbar_wait(smem_u32(&full[s]), (uint32_t)(g / STAGES) & 1, err, 3) || *abort_flag) {
+            *abort_flag = 1;
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
 #pragma unroll
-        for (int k = 0; k < BK / 16; ++k) {
-          const uint64_t ad = make_desc_sw128(a0 + k * 32);
-          const uint64_t bd = make_desc_sw128(b0 + k * 32);
-          const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+          for (int k = 0; k < BK / 16; ++k) {
+            const uint64_t ad = make_desc_sw128(a0 + k * 32);
+            const uint64_t bd = make_desc_sw128(b0 + k * 32);
+            const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dst),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+          }
           asm volatile(
-              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                  smem_u32(&empty[s]))
+              : "memory");
         }
+        // accumulator of this item ready (or the pipeline was abandoned)
         asm volatile(
             "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(&empty[s]))
+                smem_u32(&acc_full[b]))
             : "memory");
+        if (!ok) break;
       }
-      // accumulator ready (or the pipeline was abandoned)
-      asm volatile(
-          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              smem_u32(accf))
-          : "memory");
     }
   } else {
     // epilogue warps 0..3: TMEM lanes 32*warp .. 32*warp+31
-    bool ok = mbar_wait(smem_u32(accf), 0, err, 4);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok && !*abort_flag) {
-      float* buf = epi + warp * 32 * 33;
-      int64_t* roff = row_off + warp * 32;
-      int64_t* coff = row_off + 4 * 32 + warp * 32;
+    float* buf = epi + warp * 32 * 33;
+    int64_t* roff = row_off + warp * 32;
+    int64_t* coff = row_off + 4 * 32 + warp * 32;
+    int64_t i = 0;
+    const bool rows_fast = ov.rs[ov.nr - 1] == 1 && ov.cs[ov.nc - 1] != 1;
+    for (int64_t w = blockIdx.x; w < items; w += gridDim.x, ++i) {
+      if (*abort_flag) break;
+      const TcItem it = tc_item(w, mt, nt);
+      const int b = (int)(i & 1);
+      const bool ok = mbar_wait(smem_u32(&acc_full[b]), (uint32_t)(i / 2) & 1, err, 4);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (!ok || *abort_flag) {
+        *abort_flag = 1;
+        break;
+      }
       {
-        const int64_t row = m0 + warp * 32 + lane;
+        const int64_t row = it.m0 + warp * 32 + lane;
         roff[lane] = row < M ? out_row(ov, row) : -1;
       }
       __syncwarp();
-      double* Cz = C + (int64_t)blockIdx.z * split_stride;
-      const bool rows_fast = ov.rs[ov.nr - 1] == 1 && ov.cs[ov.nc - 1] != 1;
+      double* Cz = C + (int64_t)it.z * split_stride;
       for (int c0 = 0; c0 < BN; c0 += 32) {
-        if (n0 + c0 >= N) break;  // warp-uniform: no valid column left
+        if (it.n0 + c0 >= N) break;  // warp-uniform: no valid column left
         uint32_t r[32];
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+        const uint32_t taddr =
+            tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * BN) + (uint32_t)c0;
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
             "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, "
@@ -250,7 +307,7 @@ __global__ void __launch_bounds__(192, 1)
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         {
           // output offsets of this chunk's 32 columns, one per lane
-          const int64_t col = n0 + c0 + lane;
+          const int64_t col = it.n0 + c0 + lane;
           coff[lane] = col < N ? out_col(ov, col) : -1;
         }
         __syncwarp();
@@ -289,6 +346,12 @@ __global__ void __launch_bounds__(192, 1)
         }
         __syncwarp();  // buf and coff are rewritten by the next chunk
       }
+      // this warp has read its lanes of buffer b: hand it back to the MMA issuer
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[b]))
+                     : "memory");
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -390,6 +453,11 @@ TcGemm::TcGemm(cudaStream_t st, int precision) : st_(st) {
   nslices_ = precision == 1 ? 2 : 1;
   if (cudaMalloc(&d_err_, sizeof(int)) != cudaSuccess) throw OomError("tc error flag");
   cudaMemsetAsync(d_err_, 0, sizeof(int), st_);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sm_count_, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sm_count_ < 1)
+    throw CudaError("tc: cannot query the multiprocessor count");
   cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        SMEM_BYTES);
   if (e != cudaSuccess) throw CudaError(std::string("tc smem attribute: ") + cudaGetErrorString(e));
@@ -472,11 +540,12 @@ void TcGemm::run(const TcOperand& A, int sa, const TcOperand& B, int sb, int64_t
   const __nv_bfloat16* b = (const __nv_bfloat16*)B.data + (size_t)sb * B.rows_pad * B.k_pad;
   CUtensorMap ma = make_map(a, A.rows_pad, A.k_pad, BM);
   CUtensorMap mb = make_map(b, B.rows_pad, B.k_pad, BN);
-  if (B.rows_pad / BN > 65535) throw std::runtime_error("tc: N too large for the grid");
-  dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)(B.rows_pad / BN), (unsigned)splits);
+  const int64_t mt = (M + BM - 1) / BM, nt = B.rows_pad / BN;
+  const int64_t items = mt * nt * splits;
+  const int grid = (int)std::min<int64_t>(items, sm_count_);
   const int nk = (int)(A.k_pad / BK);
-  k_tc_gemm<<<grid, 192, SMEM_BYTES, st_>>>(ma, mb, M, N, nk, kbs, alpha, C, split_stride, ov,
-                                           accumulate ? 1 : 0, d_err_);
+  k_tc_gemm<<<grid, 192, SMEM_BYTES, st_>>>(ma, mb, M, N, mt, nt, items, nk, kbs, alpha, C,
+                                           split_stride, ov, accumulate ? 1 : 0, d_err_);
   count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw CudaError(std::string("tc_gemm launch: ") + cudaGetErrorString(e));
@@ -503,9 +572,9 @@ void TcGemm::gemm_ops(int64_t M, int64_t N, double alpha, const TcOperand& A, co
   const int64_t tiles = ((M + BM - 1) / BM) * (B.rows_pad / BN);
   const int nk = (int)(A.k_pad / BK);
   int splits = 1, kbs = nk;
-  if (tiles < 152 && nk >= 8) {
+  if (tiles < sm_count_ && nk >= 8) {
     // too few output tiles to fill the GPU: split K, at least 4 blocks each
-    int64_t want = std::min<int64_t>((2 * 152 + tiles - 1) / tiles, nk / 4);
+    int64_t want = std::min<int64_t>((2 * sm_count_ + tiles - 1) / tiles, nk / 4);
     if (want > 1) {
       kbs = (int)((nk + want - 1) / want);
       splits = (nk + kbs - 1) / kbs;

@@ -57,6 +57,7 @@ class TcGemm {
   cudaStream_t st_;
   int nslices_;
   TcOperand a_tmp_, b_tmp_;
+  int sm_count_ = 1;         // persistent grid size
   double* part_ = nullptr;   // split-K partial results
   size_t part_bytes_ = 0;
   int* d_err_ = nullptr;
