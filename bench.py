@@ -326,6 +326,56 @@ def row_timings(B, w, eps, L, t, Rh, prec, dev, torch, reps=2):
     return out
 
 
+def learned_case(args):
+    """Learned guess and preconditioner, reduced form of the C5 workload: train
+    on solver-generated amplitudes of n_train systems at o=8, v=60, then solve
+    n_eval fresh systems with o in [8,12], v in [60,110] to 1e-8 with the plain
+    MP2 start and with the network's proposal (the plain solver's result is
+    kept in both cases; the proposal is used only if it starts closer)."""
+    import torch
+    from paper_2403_01007_gb300 import binding as B
+    from paper_2403_01007_gb300 import learned as lrn
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    train_sys = [lrn.system(8, 60, k) for k in range(args.n_train)]
+    X, Y = lrn.generate(train_sys, samples_per_instance=20000)
+    gen_s = time.perf_counter() - t0
+    net = B.Mlp(seed=11)
+    t1 = time.perf_counter()
+    hist = lrn.train(net, X, Y, epochs=20, batch=4096, lr=2e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    rng = np.random.Generator(np.random.PCG64(syn.seed_of(lrn.LEARN_CONFIG, 999)))
+    evs = []
+    for k in range(args.n_eval):
+        o = int(rng.integers(8, 13))
+        v = int(rng.integers(60, 111))
+        evs.append(lrn.system(o, v, 1000 + k))
+    rows = lrn.evaluate(net, evs, tol=1e-8)
+    net.close()
+    it0 = [r["plain_iters"] for r in rows]
+    it1 = [r["learned_iters"] for r in rows]
+    s0 = [r["plain_s"] for r in rows]
+    s1 = [r["learned_s"] for r in rows]
+    print(json.dumps({
+        "metric": "ground-state iterations to 1e-8, learned proposal vs MP2 start",
+        "value": float(np.mean(it1)), "unit": "iterations", "higher_is_better": False,
+        "data": "synthetic", "dtype": "bf16 network, bf16->f32->f64 solver with FP64 refinement",
+        "config": {"workload": "learned_o8_v60_train_o8-12_v60-110_eval",
+                   "n_train": args.n_train, "n_eval": args.n_eval,
+                   "samples_per_train_system": 20000, "epochs": 20},
+        "plain_iterations_mean": float(np.mean(it0)),
+        "learned_iterations_mean": float(np.mean(it1)),
+        "iteration_ratio": float(np.mean(it1) / np.mean(it0)),
+        "plain_seconds_mean": float(np.mean(s0)), "learned_seconds_mean": float(np.mean(s1)),
+        "proposal_used": int(sum(r["used_net"] for r in rows)),
+        "max_abs_energy_difference": float(max(abs(r["de"]) for r in rows)),
+        "training": {"generate_s": gen_s, "train_s": train_s, "loss_first": hist[0],
+                     "loss_last": hist[-1]},
+        "rows": rows}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -345,11 +395,17 @@ def main():
     ap.add_argument("--kernel-case", type=int, default=0, metavar="V",
                     help="time only the ladder-shaped contraction (rows = nvec*21^2, "
                          "N = K = V^2) through sccsd_gemm_tn; a small case for profilers")
+    ap.add_argument("--learned", action="store_true",
+                    help="evaluate the learned guess/preconditioner on fresh systems")
+    ap.add_argument("--n-train", type=int, default=24)
+    ap.add_argument("--n-eval", type=int, default=12)
     ap.add_argument("--batched", action="store_true",
                     help="64 uneven instances: joined CUDA graph vs per-instance calls")
     args = ap.parse_args()
     if args.batched and args.impl == "ours":
         return batched_case(args)
+    if args.learned and args.impl == "ours":
+        return learned_case(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.kernel_case:
