@@ -878,6 +878,15 @@ int sccsd_solve_ground(sccsd_ctx* c, const double* t0, double zeta, const double
     double E = 0.0, nrm = 0.0;
     double best = 1e300;
     int since_best = 0;
+    // Update denominators: the caller's (or learned) preconditioner when set;
+    // otherwise the dressed denominators D' from the diagonals of the dressed
+    // Fock-like intermediates at the current amplitudes, refreshed at
+    // iterations 3, 6, 12, 24, ... (DIIS restarts with each refresh), floored
+    // at 0.2 D. At t = 0 they equal the orbital-energy denominators D.
+    double* Dp = solver_buf(c, 7, dim);
+    double* fdg = solver_buf(c, 8, c->o + c->v);
+    bool have_dp = false;
+    int next_refresh = 3;
     for (it = 1; it <= maxit; ++it) {
       E = eval_residual(c, t, zeta, ra, rb, om);
       nrm = std::sqrt(d.dot(om, om, dim));
@@ -902,7 +911,28 @@ int sccsd_solve_ground(sccsd_ctx* c, const double* t0, double zeta, const double
         continue;
       }
       if (fp64_phase && nrm < tol) break;
-      launch_jacobi(d.st(), dim, t, om, c->use_dprec ? c->Dprec : c->D, tn);
+      const double* Dstep = c->D;
+      if (c->use_dprec) {
+        Dstep = c->Dprec;
+      } else {
+        if (it >= next_refresh) {
+          Model& mdl = *c->cur;
+          mdl.g.run({mdl.er.Fooi, mdl.er.Fvvi});
+          const int o = c->o, v = c->v;
+          int64_t d1[1] = {o}, os1[1] = {1}, is1[1] = {o + 1};
+          c->be->copy_view(1, d1, fdg, os1, mdl.g.data(mdl.er.Fooi), is1, 1.0, false);
+          int64_t d2[1] = {v}, os2[1] = {1}, is2[1] = {v + 1};
+          c->be->copy_view(1, d2, fdg + o, os2, mdl.g.data(mdl.er.Fvvi), is2, 1.0, false);
+          launch_denoms(d.st(), o, v, fdg, Dp);
+          launch_floor(d.st(), dim, c->D, 0.2, Dp);
+          have_dp = true;
+          next_refresh *= 2;
+          nh = 0;
+          head = 0;
+        }
+        if (have_dp) Dstep = Dp;
+      }
+      launch_jacobi(d.st(), dim, t, om, Dstep, tn);
       const int slot = head;
       head = (head + 1) % kDiis;
       nh = std::min(nh + 1, kDiis);

@@ -399,6 +399,16 @@ __global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, doubl
     y[k] = a * x[k] + b * y[k];
 }
 
+// d = max(d, frac * ref) elementwise (a floor for refreshed denominators)
+__global__ void k_floor(int64_t n, const double* __restrict__ ref, double frac,
+                        double* __restrict__ d) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double f = frac * ref[k];
+    d[k] = d[k] > f ? d[k] : f;
+  }
+}
+
 // y = d * x elementwise
 __global__ void k_scale(int64_t n, const double* __restrict__ d, const double* __restrict__ x,
                         double* __restrict__ y) {
@@ -437,6 +447,9 @@ void launch_precond(cudaStream_t st, int64_t n, const double* r, const double* D
 }
 void launch_axpby(cudaStream_t st, int64_t n, double a, const double* x, double b, double* y) {
   k_axpby<<<vgrid(n), 256, 0, st>>>(n, a, x, b, y);
+}
+void launch_floor(cudaStream_t st, int64_t n, const double* ref, double frac, double* d) {
+  k_floor<<<vgrid(n), 256, 0, st>>>(n, ref, frac, d);
 }
 void launch_scale(cudaStream_t st, int64_t n, const double* d, const double* x, double* y) {
   k_scale<<<vgrid(n), 256, 0, st>>>(n, d, x, y);

@@ -18,6 +18,8 @@ void launch_jacobi(cudaStream_t st, int64_t n, const double* t, const double* om
 void launch_precond(cudaStream_t st, int64_t n, const double* r, const double* D, double lam,
                     double* out);
 void launch_axpby(cudaStream_t st, int64_t n, double a, const double* x, double b, double* y);
+// d = max(d, frac * ref) elementwise
+void launch_floor(cudaStream_t st, int64_t n, const double* ref, double frac, double* d);
 // y = d * x elementwise
 void launch_scale(cudaStream_t st, int64_t n, const double* d, const double* x, double* y);
 void launch_ritz_residual(cudaStream_t st, int nr, int64_t n, const double* ax, const double* x,

@@ -141,6 +141,9 @@ void launch_precond(cudaStream_t, int64_t n, const double* r, const double* D, d
 void launch_axpby(cudaStream_t, int64_t n, double a, const double* x, double b, double* y) {
   for (int64_t k = 0; k < n; ++k) y[k] = a * x[k] + b * y[k];
 }
+void launch_floor(cudaStream_t, int64_t n, const double* ref, double frac, double* d) {
+  for (int64_t k = 0; k < n; ++k) d[k] = d[k] > frac * ref[k] ? d[k] : frac * ref[k];
+}
 void launch_scale(cudaStream_t, int64_t n, const double* d, const double* x, double* y) {
   for (int64_t k = 0; k < n; ++k) y[k] = d[k] * x[k];
 }
