@@ -165,10 +165,14 @@ int sccsd_solve_scc(sccsd_ctx* ctx, double tol, int maxit, double ground_tol, do
 int sccsd_set_precision(sccsd_ctx* ctx, int precision);
 
 /* Ground state: converge Omega(t) = 0 (Sec. 2.1; with Ra/Rb non-NULL the SCC
- * residual of sccsd_residual at fixed zeta) by the orbital-energy
- * preconditioned update t <- t - Omega/D, D_ai = e_a - e_i,
- * D_aibj = D_ai + D_bj, with DIIS (8 vectors). Starts from t0 (packed ket) or
- * from zero (whose first step is the MP2 guess). With a mixed precision and
+ * residual of sccsd_residual at fixed zeta) by the preconditioned update
+ * t <- t - Omega/D with DIIS (8 vectors). D starts as the orbital-energy
+ * denominators D_ai = e_a - e_i, D_aibj = D_ai + D_bj (or the preconditioner
+ * of sccsd_set_preconditioner) and is replaced after two iterations, and then
+ * at doubling intervals, by the dressed denominators D' built the same way from
+ * the diagonals of the dressed Fock-like intermediates at the current
+ * amplitudes (floored at 0.2 D; DIIS restarts with each refresh). Starts from
+ * t0 (packed ket) or from zero (whose first step is the MP2 guess). With a mixed precision and
  * refine_tol > 0 the iterations run in that precision until |Omega| <
  * refine_tol, or until they stall (no 10% improvement in 6 iterations: the
  * noise floor of the mixed arithmetic), and finish in FP64 (iterative
@@ -234,8 +238,10 @@ int sccsd_learned_features(sccsd_ctx* ctx, float* X, double* scales);
 int sccsd_learned_targets(sccsd_ctx* ctx, const double* t, double s_t, float* Y);
 /* Packed initial amplitudes t0 and packed preconditioner Dprec proposed by net. */
 int sccsd_learned_guess(sccsd_ctx* ctx, sccsd_mlp* net, double* t0, double* Dprec);
-/* Preconditioner of sccsd_solve_ground's update (packed, positive), or NULL
- * for the orbital-energy denominators D. */
+/* Initial denominators of sccsd_solve_ground's update (packed, positive), or
+ * NULL for the orbital-energy denominators D. The solver replaces them by its
+ * own dressed denominators D' (from the dressed Fock diagonals at the current
+ * amplitudes) at its first refresh, after two iterations. */
 int sccsd_set_preconditioner(sccsd_ctx* ctx, const double* Dprec);
 
 /* ---- Lagrangian multipliers (gradients and couplings) ---------------------

@@ -878,11 +878,12 @@ int sccsd_solve_ground(sccsd_ctx* c, const double* t0, double zeta, const double
     double E = 0.0, nrm = 0.0;
     double best = 1e300;
     int since_best = 0;
-    // Update denominators: the caller's (or learned) preconditioner when set;
-    // otherwise the dressed denominators D' from the diagonals of the dressed
-    // Fock-like intermediates at the current amplitudes, refreshed at
-    // iterations 3, 6, 12, 24, ... (DIIS restarts with each refresh), floored
-    // at 0.2 D. At t = 0 they equal the orbital-energy denominators D.
+    // Update denominators: the dressed denominators D' from the diagonals of
+    // the dressed Fock-like intermediates at the current amplitudes, refreshed
+    // at iterations 3, 6, 12, 24, ... (DIIS restarts with each refresh) and
+    // floored at 0.2 D. Before the first refresh: the caller's (or learned)
+    // preconditioner when one is set, else the orbital-energy denominators D
+    // (which D' equals at t = 0).
     double* Dp = solver_buf(c, 7, dim);
     double* fdg = solver_buf(c, 8, c->o + c->v);
     bool have_dp = false;
@@ -911,10 +912,8 @@ int sccsd_solve_ground(sccsd_ctx* c, const double* t0, double zeta, const double
         continue;
       }
       if (fp64_phase && nrm < tol) break;
-      const double* Dstep = c->D;
-      if (c->use_dprec) {
-        Dstep = c->Dprec;
-      } else {
+      const double* Dstep = c->use_dprec ? c->Dprec : c->D;
+      {
         if (it >= next_refresh) {
           Model& mdl = *c->cur;
           mdl.g.run({mdl.er.Fooi, mdl.er.Fvvi});
