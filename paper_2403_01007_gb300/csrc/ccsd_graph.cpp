@@ -43,11 +43,11 @@ EnergyResidual build_energy_residual(Graph& g, int t1, int t2, int L, int h, int
   int Lhvo = g.add("Jai", {{Lvo, "Jai", 1.0},
                            {g.contract(Lvv, "Jac", t1, "ci", "Jai", 1.0, true), "Jai", 1.0},
                            {g.contract(t1, "ak", Lhoo, "Jki", "Jai", 1.0, true), "Jai", -1.0}});
-  int hhoo = g.add("kl", {{hoo, "kl", 1.0}, {g.contract(hov, "ka", t1, "al", "kl"), "kl", 1.0}});
+  int hhoo = g.add("kl", {{hoo, "kl", 1.0}, {g.contract(hov, "ka", t1, "al", "kl", 1.0, true), "kl", 1.0}});
   int hhvo = g.add("ai", {{hvo, "ai", 1.0},
-                          {g.contract(hvv, "ac", t1, "ci", "ai"), "ai", 1.0},
-                          {g.contract(t1, "ak", hhoo, "ki", "ai"), "ai", -1.0}});
-  int hhvv = g.add("ab", {{hvv, "ab", 1.0}, {g.contract(t1, "ak", hov, "kb", "ab"), "ab", -1.0}});
+                          {g.contract(hvv, "ac", t1, "ci", "ai", 1.0, true), "ai", 1.0},
+                          {g.contract(t1, "ak", hhoo, "ki", "ai", 1.0, true), "ai", -1.0}});
+  int hhvv = g.add("ab", {{hvv, "ab", 1.0}, {g.contract(t1, "ak", hov, "kb", "ab", 1.0, true), "ab", -1.0}});
 
   // dressed Fock matrix F_pq = h_pq + sum_k (2 g_pqkk - g_pkkq)
   int s = g.contract(Lhoo, "Jkl", delta, "kl", "J");

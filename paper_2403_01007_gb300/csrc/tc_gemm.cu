@@ -111,25 +111,29 @@ __device__ __forceinline__ int64_t out_col(const OutView& v, int64_t c) {
   return level_offset(v.nc, v.ce, v.cs, c);
 }
 
-// Work items are (split z, N tile, M tile), M fastest; a persistent CTA takes
-// items blockIdx.x, blockIdx.x + gridDim.x, ... so that the CTAs working at
-// one time share a B tile (read once from HBM, then served from L2).
+// Work items are (split z, N tile, M tile), M fastest (nfast = 0) or N fastest
+// (nfast = 1); a persistent CTA takes items blockIdx.x, blockIdx.x + gridDim.x,
+// ... so that the CTAs working at one time share the tile of the operand
+// that is expensive to re-read (read once from HBM, then served from L2).
 struct TcItem {
   int64_t m0, n0;
   int z;
 };
-__device__ __forceinline__ TcItem tc_item(int64_t w, int64_t mt, int64_t nt) {
+__device__ __forceinline__ TcItem tc_item(int64_t w, int64_t mt, int64_t nt, int nfast) {
   TcItem r;
-  r.m0 = (w % mt) * BM;
-  const int64_t rest = w / mt;
-  r.n0 = (rest % nt) * BN;
-  r.z = (int)(rest / nt);
+  const int64_t inner = nfast ? nt : mt, outer = nfast ? mt : nt;
+  const int64_t a = w % inner, rest = w / inner;
+  const int64_t b = rest % outer;
+  r.m0 = (nfast ? b : a) * BM;
+  r.n0 = (nfast ? a : b) * BN;
+  r.z = (int)(rest / outer);
   return r;
 }
 
 __global__ void __launch_bounds__(192, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-              int64_t M, int64_t N, int64_t mt, int64_t nt, int64_t items, int nk_total, int kbs,
+              int64_t M, int64_t N, int64_t mt, int64_t nt, int nfast, int64_t items, int nk_total,
+              int kbs,
               double alpha, double* __restrict__ C, int64_t split_stride, const OutView ov,
               int accumulate, int* err) {
   extern __shared__ uint8_t smem_raw[];
@@ -179,7 +183,7 @@ __global__ void __launch_bounds__(192, 1)
       for (int s = 0; s < STAGES; ++s) issued_last[s] = -1;
       int64_t g = 0;
       for (int64_t w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x) {
-        const TcItem it = tc_item(w, mt, nt);
+        const TcItem it = tc_item(w, mt, nt, nfast);
         const int nk = nk_of(it.z), kb0 = it.z * kbs;
         for (int kb = 0; kb < nk; ++kb, ++g) {
           const int s = (int)(g % STAGES);
@@ -220,7 +224,7 @@ __global__ void __launch_bounds__(192, 1)
       int64_t g = 0;
       int64_t i = 0;
       for (int64_t w = blockIdx.x; w < items && !*abort_flag; w += gridDim.x, ++i) {
-        const TcItem it = tc_item(w, mt, nt);
+        const TcItem it = tc_item(w, mt, nt, nfast);
         const int nk = nk_of(it.z);
         const int b = (int)(i & 1);
         if (i >= 2) {
@@ -274,7 +278,7 @@ __global__ void __launch_bounds__(192, 1)
     const bool rows_fast = ov.rs[ov.nr - 1] == 1 && ov.cs[ov.nc - 1] != 1;
     for (int64_t w = blockIdx.x; w < items; w += gridDim.x, ++i) {
       if (*abort_flag) break;
-      const TcItem it = tc_item(w, mt, nt);
+      const TcItem it = tc_item(w, mt, nt, nfast);
       const int b = (int)(i & 1);
       const bool ok = mbar_wait(smem_u32(&acc_full[b]), (uint32_t)(i / 2) & 1, err, 4);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -477,9 +481,10 @@ void TcGemm::release(TcOperand& op) {
 
 bool TcGemm::worthwhile(int64_t nb, int64_t M, int64_t N, int64_t K) const {
   // FP64 FMAs run at about 1/1000 of the BF16 tensor rate here, so even small
-  // or skinny contractions (padded to 128 x 256 x 64 tiles) are cheaper as a
-  // conversion plus one tensor-core launch; matrix-vector shapes are not
-  return nb == 1 && M >= 16 && N >= 16 && (double)M * N * K >= 1.0e6;
+  // or skinny contractions (padded to 128 x 256 x 64 tiles, e.g. N = 6 trial
+  // vectors) are cheaper as a conversion plus one tensor-core launch;
+  // matrix-vector shapes stay on the memory-bound FP64 kernels
+  return nb == 1 && M >= 2 && N >= 2 && (double)M * N * K >= 1.0e6;
 }
 
 void TcGemm::convert(const MatView& X, int64_t rows, int64_t K, TcOperand& out) {
@@ -544,8 +549,12 @@ void TcGemm::run(const TcOperand& A, int sa, const TcOperand& B, int sb, int64_t
   const int64_t items = mt * nt * splits;
   const int grid = (int)std::min<int64_t>(items, sm_count_);
   const int nk = (int)(A.k_pad / BK);
-  k_tc_gemm<<<grid, 192, SMEM_BYTES, st_>>>(ma, mb, M, N, mt, nt, items, nk, kbs, alpha, C,
-                                           split_stride, ov, accumulate ? 1 : 0, d_err_);
+  // share the A tile among concurrent CTAs when A is the operand that would
+  // otherwise be re-read from HBM for every N tile
+  const double abytes = (double)A.rows_pad * A.k_pad, bbytes = (double)B.rows_pad * B.k_pad;
+  const int nfast = (nt > 1 && abytes > 4.0 * bbytes) ? 1 : 0;
+  k_tc_gemm<<<grid, 192, SMEM_BYTES, st_>>>(ma, mb, M, N, mt, nt, nfast, items, nk, kbs, alpha,
+                                           C, split_stride, ov, accumulate ? 1 : 0, d_err_);
   count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw CudaError(std::string("tc_gemm launch: ") + cudaGetErrorString(e));
