@@ -323,7 +323,7 @@ struct sccsd_ctx {
   ~sccsd_ctx() {
     if (getenv("SCCSD_TRACE")) {
       for (Model* m : {plain.get(), scc.get()})
-        if (m) fprintf(stderr, "%s", m->g.trace_report(60).c_str());
+        if (m) fprintf(stderr, "%s", m->g.trace_report(std::max(60, atoi(getenv("SCCSD_TRACE")))).c_str());
     }
     plain.reset();
     scc.reset();

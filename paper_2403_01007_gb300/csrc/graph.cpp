@@ -533,6 +533,23 @@ std::string Graph::trace_report(int top) {
              (long long)op.trace_calls, idx[k], names[(int)op.kind], op.la.c_str(), op.lb.c_str(),
              op.lc.c_str(), (int)op.tc, dims.c_str());
     out += line;
+    if (op.kind == OpKind::Contract && op.trace_conv) {
+      // converted operands and their producers (c contract, a add, ... i input)
+      std::string conv = "           converted:";
+      for (int q = 0; q < 2; ++q) {
+        if (!(op.trace_conv & (1 << q))) continue;
+        char kc = 'i';
+        for (size_t p = 0; p < ops.size(); ++p)
+          if (ops[p].out == op.in[q]) {
+            kc = "caselL"[(int)ops[p].kind];
+            break;
+          }
+        const Tensor& x = t[op.in[q]];
+        conv += std::string(" ") + (q ? "B" : "A") + "(" + kc + ", " +
+                std::to_string(x.numel() * 8 / 1000000) + " MB)";
+      }
+      out += conv + "\n";
+    }
     if (op.kind == OpKind::Add) {
       // the producer of every term: c contract, a add, s slice, e embed, l ladder, i input
       std::string terms = "           terms:";
@@ -790,6 +807,7 @@ void Graph::exec_contract(Op& op, double* out_data, const int64_t* ostr, double 
     // so its converted form is reused only by the other contractions of the
     // same run that read it in the same layout
     const bool cA = true, cB = true;
+    if (trace) op.trace_conv = (be->tc_cached(kA) ? 0 : 1) | (be->tc_cached(kB) ? 0 : 2);
     if (cA && be->tc_cached(kA))
       Av.p = nullptr;
     else if (!okA)

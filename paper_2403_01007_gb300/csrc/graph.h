@@ -57,6 +57,8 @@ struct Op {
   bool ran = false;
   double trace_ms = 0.0;
   int64_t trace_calls = 0;
+  // tracing: operands converted for the tensor cores (bit 0 A, bit 1 B)
+  int trace_conv = 0;
 };
 
 class Backend;

@@ -367,9 +367,10 @@ __global__ void __launch_bounds__(192, 1)
   }
 }
 
-// x = sum_s slice_s with slice_s = bf16(x - sum_{r<s} slice_r); padded with
-// zeros. The source is a strided view; a 32 x 64 tile goes through shared
-// memory so that reads walk the source's unit-stride index and writes walk k.
+// x = sum_s slice_s with slice_s = bf16(x - sum_{r<s} slice_r); K padded with
+// zeros (padding rows are not written: their products are never stored). The
+// source is a strided view; a 32 x 64 tile goes through shared memory so that
+// reads walk the source's unit-stride index and writes walk k.
 __device__ __forceinline__ int64_t vrow(const MatView& v, int64_t r) {
   return v.n2r ? (r / v.n2r) * v.sr1 + (r % v.n2r) * v.sr2 : r * v.sr2;
 }
@@ -380,27 +381,44 @@ __device__ __forceinline__ int64_t vk(const MatView& v, int64_t k) {
 __global__ void k_split_bf16_view(MatView X, int64_t rows, int64_t K, int64_t rows_pad,
                                   int64_t k_pad, int slices, __nv_bfloat16* __restrict__ out) {
   __shared__ double tile[32][65];
+  __shared__ int64_t roff[32], koff[64];
   const int64_t ktiles = k_pad / 64;
   const int64_t tiles = (rows_pad / 32) * ktiles;
   const bool kfast = X.sk2 == 1;
   const int64_t sstride = rows_pad * k_pad;
   for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
     const int64_t r0 = (t / ktiles) * 32, k0 = (t % ktiles) * 64;
-    for (int e = threadIdx.x; e < 32 * 64; e += blockDim.x) {
-      const int rr = kfast ? e / 64 : e % 32;
-      const int kk = kfast ? e % 64 : e / 32;
-      const int64_t r = r0 + rr, k = k0 + kk;
-      tile[rr][kk] = (r < rows && k < K) ? X.p[vrow(X, r) + vk(X, k)] : 0.0;
+    // rows beyond `rows` only feed products that are never stored: left as is
+    if (r0 >= rows) continue;
+    // view offsets of the tile's rows and K indices, once per tile
+    if (threadIdx.x < 32) {
+      const int64_t r = r0 + threadIdx.x;
+      roff[threadIdx.x] = r < rows ? vrow(X, r) : -1;
+    } else if (threadIdx.x < 96) {
+      const int64_t k = k0 + threadIdx.x - 32;
+      koff[threadIdx.x - 32] = k < K ? vk(X, k) : -1;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < 32 * 64; e += blockDim.x) {
-      const int rr = e / 64, kk = e % 64;
-      double x = tile[rr][kk];
+      const int rr = kfast ? e / 64 : e % 32;
+      const int kk = kfast ? e % 64 : e / 32;
+      const int64_t ro = roff[rr], ko = koff[kk];
+      tile[rr][kk] = (ro >= 0 && ko >= 0) ? X.p[ro + ko] : 0.0;
+    }
+    __syncthreads();
+    // two consecutive K elements per thread, stored as one bf16x2
+    for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+      const int rr = e / 32, kk = 2 * (e % 32);
+      if (r0 + rr >= rows) continue;
+      double x0 = tile[rr][kk], x1 = tile[rr][kk + 1];
       const int64_t o = (r0 + rr) * k_pad + k0 + kk;
       for (int s = 0; s < slices; ++s) {
-        __nv_bfloat16 b = __double2bfloat16(x);
-        out[s * sstride + o] = b;
-        x -= (double)__bfloat162float(b);
+        __nv_bfloat162 b;
+        b.x = __double2bfloat16(x0);
+        b.y = __double2bfloat16(x1);
+        *reinterpret_cast<__nv_bfloat162*>(out + s * sstride + o) = b;
+        x0 -= (double)__bfloat162float(b.x);
+        x1 -= (double)__bfloat162float(b.y);
       }
     }
     __syncthreads();
