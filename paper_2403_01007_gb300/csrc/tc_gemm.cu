@@ -378,37 +378,55 @@ __device__ __forceinline__ int64_t vk(const MatView& v, int64_t k) {
   return v.n2k ? (k / v.n2k) * v.sk1 + (k % v.n2k) * v.sk2 : k * v.sk2;
 }
 
-__global__ void k_split_bf16_view(MatView X, int64_t rows, int64_t K, int64_t rows_pad,
-                                  int64_t k_pad, int slices, __nv_bfloat16* __restrict__ out) {
-  __shared__ double tile[32][65];
-  __shared__ int64_t roff[32], koff[64];
-  const int64_t ktiles = k_pad / 64;
-  const int64_t tiles = (rows_pad / 32) * ktiles;
+constexpr int CR = 64, CK = 64;  // conversion tile: rows x K
+
+__global__ void __launch_bounds__(256, 3)
+    k_split_bf16_view(MatView X, int64_t rows, int64_t K, int64_t rows_pad, int64_t k_pad,
+                      int slices, __nv_bfloat16* __restrict__ out) {
+  __shared__ double tile[CR][CK + 1];
+  __shared__ int64_t roff[CR], koff[CK];
+  const int64_t ktiles = k_pad / CK;
+  const int64_t tiles = (rows_pad / CR) * ktiles;
   const bool kfast = X.sk2 == 1;
   const int64_t sstride = rows_pad * k_pad;
+  const int tid = threadIdx.x;
   for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-    const int64_t r0 = (t / ktiles) * 32, k0 = (t % ktiles) * 64;
+    const int64_t r0 = (t / ktiles) * CR, k0 = (t % ktiles) * CK;
     // rows beyond `rows` only feed products that are never stored: left as is
     if (r0 >= rows) continue;
     // view offsets of the tile's rows and K indices, once per tile
-    if (threadIdx.x < 32) {
-      const int64_t r = r0 + threadIdx.x;
-      roff[threadIdx.x] = r < rows ? vrow(X, r) : -1;
-    } else if (threadIdx.x < 96) {
-      const int64_t k = k0 + threadIdx.x - 32;
-      koff[threadIdx.x - 32] = k < K ? vk(X, k) : -1;
+    if (tid < CR) {
+      const int64_t r = r0 + tid;
+      roff[tid] = r < rows ? vrow(X, r) : -1;
+    } else if (tid < CR + CK) {
+      const int64_t k = k0 + tid - CR;
+      koff[tid - CR] = k < K ? vk(X, k) : -1;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < 32 * 64; e += blockDim.x) {
-      const int rr = kfast ? e / 64 : e % 32;
-      const int kk = kfast ? e % 64 : e / 32;
+    // all 16 loads of a thread in flight before the first shared-memory store;
+    // consecutive lanes walk the source's unit-stride index
+    double val[CR * CK / 256];
+#pragma unroll
+    for (int q = 0; q < CR * CK / 256; ++q) {
+      const int e = tid + 256 * q;
+      const int rr = kfast ? e / CK : e % CR;
+      const int kk = kfast ? e % CK : e / CR;
       const int64_t ro = roff[rr], ko = koff[kk];
-      tile[rr][kk] = (ro >= 0 && ko >= 0) ? X.p[ro + ko] : 0.0;
+      val[q] = (ro >= 0 && ko >= 0) ? __ldg(X.p + ro + ko) : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < CR * CK / 256; ++q) {
+      const int e = tid + 256 * q;
+      const int rr = kfast ? e / CK : e % CR;
+      const int kk = kfast ? e % CK : e / CR;
+      tile[rr][kk] = val[q];
     }
     __syncthreads();
-    // two consecutive K elements per thread, stored as one bf16x2
-    for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
-      const int rr = e / 32, kk = 2 * (e % 32);
+    // a warp writes one row's 64 K values as 32 bf16x2 (128 bytes)
+#pragma unroll
+    for (int q = 0; q < CR * CK / 512; ++q) {
+      const int e = tid + 256 * q;
+      const int rr = e / (CK / 2), kk = 2 * (e % (CK / 2));
       if (r0 + rr >= rows) continue;
       double x0 = tile[rr][kk], x1 = tile[rr][kk + 1];
       const int64_t o = (r0 + rr) * k_pad + k0 + kk;
@@ -529,8 +547,8 @@ void TcGemm::convert(const MatView& X, int64_t rows, int64_t K, TcOperand& out) 
   out.rows_pad = rp;
   out.k_pad = kp;
   out.slices = nslices_;
-  const int64_t tiles = (rp / 32) * (kp / 64);
-  int grid = (int)std::min<int64_t>(tiles, 152 * 16);
+  const int64_t tiles = (rp / CR) * (kp / CK);
+  int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sm_count_ * 6));
   k_split_bf16_view<<<grid, 256, 0, st_>>>(X, rows, K, rp, kp, nslices_, (__nv_bfloat16*)out.data);
   count_launch();
   cudaError_t e = cudaGetLastError();
