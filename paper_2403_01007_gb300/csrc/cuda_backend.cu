@@ -126,7 +126,7 @@ __global__ void k_mul_view(Args m, I total, double* __restrict__ out, const doub
   }
 }
 
-// 32x32 shared-memory tile transpose for copies whose fastest output index is
+// 64x64 shared-memory tile transpose for copies whose fastest output index is
 // strided in the input while another output index is contiguous in the input.
 // Tile axes: x = output dim px (unit output stride), y = output dim py (unit
 // input stride); the remaining dims are walked by blockIdx.z.
@@ -138,10 +138,15 @@ struct TransArgs {
   int64_t rest_total;
 };
 
-__global__ void k_copy_transpose(TransArgs a, double* __restrict__ out,
-                                 const double* __restrict__ in, double coef, int acc) {
-  __shared__ double tile[32][33];
+constexpr int TT = 64;  // transpose tile edge
+
+__global__ void __launch_bounds__(256, 3) k_copy_transpose(TransArgs a, double* __restrict__ out,
+                                                        const double* __restrict__ in,
+                                                        double coef, int acc) {
+  __shared__ double tile[TT][TT + 1];
   const int64_t nx = a.dims[a.px], ny = a.dims[a.py];
+  const int64_t isx = a.istr[a.px], isy = a.istr[a.py], osx = a.ostr[a.px], osy = a.ostr[a.py];
+  const int tx = threadIdx.x, ty = threadIdx.y;  // blockDim = (32, 8)
   for (int64_t rest = blockIdx.z; rest < a.rest_total; rest += gridDim.z) {
     int64_t r = rest, ob = 0, ib = 0;
     for (int k = a.rank - 1; k >= 0; --k) {
@@ -151,19 +156,38 @@ __global__ void k_copy_transpose(TransArgs a, double* __restrict__ out,
       ob += c * a.ostr[k];
       ib += c * a.istr[k];
     }
-    const int64_t x0 = (int64_t)blockIdx.x * 32, y0 = (int64_t)blockIdx.y * 32;
-    // read: consecutive threads walk the input-contiguous dim (py)
-    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-      int64_t x = x0 + j, y = y0 + threadIdx.x;
-      if (x < nx && y < ny) tile[j][threadIdx.x] = in[ib + x * a.istr[a.px] + y * a.istr[a.py]];
+    const int64_t x0 = (int64_t)blockIdx.x * TT, y0 = (int64_t)blockIdx.y * TT;
+    // read: consecutive lanes walk the input-contiguous dim (y); the loads of
+    // a half tile are all issued before the shared-memory stores
+    const double* ip = in + ib + (x0 + ty) * isx + (y0 + tx) * isy;
+    const int64_t ix8 = 8 * isx, iy32 = 32 * isy;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      double v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int xi = ty + 8 * q, yj = tx + 32 * h;
+        v[q] = (x0 + xi < nx && y0 + yj < ny) ? __ldg(ip + q * ix8 + h * iy32) : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) tile[ty + 8 * q][tx + 32 * h] = v[q];
     }
     __syncthreads();
-    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-      int64_t y = y0 + j, x = x0 + threadIdx.x;
-      if (x < nx && y < ny) {
-        int64_t oo = ob + x * a.ostr[a.px] + y * a.ostr[a.py];
-        double v = coef * tile[threadIdx.x][j];
-        out[oo] = acc ? out[oo] + v : v;
+    // write: consecutive lanes walk the output-contiguous dim (x)
+    double* op = out + ob + (x0 + tx) * osx + (y0 + ty) * osy;
+    const int64_t oy8 = 8 * osy, ox32 = 32 * osx;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      double old[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int yj = ty + 8 * q, xi = tx + 32 * h;
+        old[q] = (acc && x0 + xi < nx && y0 + yj < ny) ? op[q * oy8 + h * ox32] : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int yj = ty + 8 * q, xi = tx + 32 * h;
+        if (x0 + xi < nx && y0 + yj < ny) op[q * oy8 + h * ox32] = old[q] + coef * tile[xi][yj];
       }
     }
     __syncthreads();
@@ -406,7 +430,7 @@ class CudaBackend : public Backend {
         a.istr[k] = is[k];
         if (k != px && k != py) a.rest_total *= d[k];
       }
-      dim3 grid((unsigned)((d[px] + 31) / 32), (unsigned)((d[py] + 31) / 32),
+      dim3 grid((unsigned)((d[px] + TT - 1) / TT), (unsigned)((d[py] + TT - 1) / TT),
                 (unsigned)std::min<int64_t>(a.rest_total, 65535));
       k_copy_transpose<<<grid, dim3(32, 8), 0, st>>>(a, out, in, coef, acc ? 1 : 0);
       check_launch("copy_transpose");
