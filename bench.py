@@ -179,10 +179,12 @@ def kernel_case(args):
     import torch
     from paper_2403_01007_gb300 import binding as B
     o, V = syn.LARGE.o, args.kernel_case
-    M, N = args.nvec * o * o, V * V
+    M, N, K = args.nvec * o * o, V * V, V * V
+    if args.gemm:
+        M, N, K = args.gemm
     g = torch.Generator(device="cuda").manual_seed(1)
-    X = torch.randn(M, N, dtype=torch.float64, device="cuda", generator=g)
-    G = torch.randn(N, N, dtype=torch.float64, device="cuda", generator=g)
+    X = torch.randn(M, K, dtype=torch.float64, device="cuda", generator=g)
+    G = torch.randn(N, K, dtype=torch.float64, device="cuda", generator=g)
     C = torch.empty(M, N, dtype=torch.float64, device="cuda")
     prec = "bf16" if args.precision == "fp64" else args.precision
     for _ in range(args.warmup):
@@ -193,9 +195,9 @@ def kernel_case(args):
         B.gemm_tn(X, G, C, precision=prec)
     torch.cuda.synchronize()
     sec = (time.perf_counter() - t0) / max(1, args.steps)
-    print(json.dumps({"kernel_case": "ladder", "M": M, "N": N, "K": N, "precision": prec,
-                      "ms_per_call_incl_conversion": sec * 1e3,
-                      "tflops_incl_conversion": 2.0 * M * N * N / sec / 1e12}))
+    print(json.dumps({"kernel_case": "gemm" if args.gemm else "ladder", "M": M, "N": N, "K": K,
+                      "precision": prec, "ms_per_call_incl_conversion": sec * 1e3,
+                      "tflops_incl_conversion": 2.0 * M * N * K / sec / 1e12}))
     return 0
 
 
@@ -392,6 +394,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-rows", action="store_true",
                     help="skip the timings of the other hot-path rows")
+    ap.add_argument("--gemm", type=int, nargs=3, metavar=("M", "N", "K"), default=None,
+                    help="with --kernel-case: time C[M][N] = X[M][K] G[N][K]^T instead")
     ap.add_argument("--kernel-case", type=int, default=0, metavar="V",
                     help="time only the ladder-shaped contraction (rows = nvec*21^2, "
                          "N = K = V^2) through sccsd_gemm_tn; a small case for profilers")
