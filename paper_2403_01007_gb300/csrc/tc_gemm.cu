@@ -41,13 +41,15 @@ void count_launch();
 
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int BM = 128, BN = 256, BK = 64;
 constexpr int A_BYTES = BM * BK * 2;
 constexpr int B_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int EPI_FLOATS = 4 * 32 * 33;
-constexpr int SMEM_BYTES = 1024 /*align slack*/ + STAGES * STAGE_BYTES + 256 /*barriers*/ +
-                           EPI_FLOATS * 4 + 2 * 4 * 32 * 8 /*row and column offsets*/;
+// dynamic shared memory of the kernel with NST pipeline stages and EW epilogue warps
+constexpr int smem_bytes(int NST, int EW) {
+  return 1024 /*align slack*/ + NST * STAGE_BYTES + 256 /*barriers*/ + EW * 32 * 33 * 4 +
+         2 * EW * 32 * 8 /*row and column offsets*/;
+}
 constexpr int TMEM_COLS = 512;  // two 128 x 256 FP32 accumulators
 constexpr uint32_t WAIT_LIMIT = 1u << 24;  // polls before a wait is declared failed
 
@@ -130,7 +132,11 @@ __device__ __forceinline__ TcItem tc_item(int64_t w, int64_t mt, int64_t nt, int
   return r;
 }
 
-__global__ void __launch_bounds__(192, 1)
+// NST pipeline stages; EW = 4 or 8 epilogue warps (with 8, two groups of four
+// each own one TMEM accumulator and take alternate items: more stores in
+// flight for the epilogue-bound short-K contractions)
+template <int NST, int EW>
+__global__ void __launch_bounds__((EW + 2) * 32, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               int64_t M, int64_t N, int64_t mt, int64_t nt, int nfast, int64_t items, int nk_total,
               int kbs,
@@ -139,6 +145,7 @@ __global__ void __launch_bounds__(192, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
+  constexpr int STAGES = NST;
   uint8_t* sB = smem + STAGES * A_BYTES;
   uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
@@ -147,7 +154,7 @@ __global__ void __launch_bounds__(192, 1)
   uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   float* epi = (float*)(smem + STAGES * STAGE_BYTES + 256);
-  int64_t* row_off = (int64_t*)(epi + EPI_FLOATS);
+  int64_t* row_off = (int64_t*)(epi + EW * 32 * 33);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // K blocks of split z: [z * kbs, z * kbs + nk(z))
@@ -176,7 +183,7 @@ __global__ void __launch_bounds__(192, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 4) {
+  if (warp == EW) {
     if (lane == 0) {
       // TMA producer over all items of this CTA; g counts k-blocks globally
       int64_t issued_last[STAGES];
@@ -217,7 +224,7 @@ __global__ void __launch_bounds__(192, 1)
         if (issued_last[s] >= 0)
           mbar_wait(smem_u32(&full[s]), (uint32_t)(issued_last[s] / STAGES) & 1, err, 2);
     }
-  } else if (warp == 5) {
+  } else if (warp == EW + 1) {
     if (lane == 0) {
       // MMA issuer: item number i of this CTA accumulates in TMEM buffer i & 1
       constexpr uint32_t idesc = make_idesc(BM, BN);
@@ -270,13 +277,19 @@ __global__ void __launch_bounds__(192, 1)
       }
     }
   } else {
-    // epilogue warps 0..3: TMEM lanes 32*warp .. 32*warp+31
+    // epilogue warp: TMEM lanes 32*q .. 32*q+31 of the items of its group
+    constexpr int G = EW / 4;            // groups of four warps
+    // old values of an accumulating store read ahead in batches of OLDN
+    // (fewer registers with eight epilogue warps)
+    constexpr int OLDN = EW == 8 ? 8 : 32;
+    const int q = warp % 4, grp = warp / 4;
     float* buf = epi + warp * 32 * 33;
     int64_t* roff = row_off + warp * 32;
-    int64_t* coff = row_off + 4 * 32 + warp * 32;
-    int64_t i = 0;
+    int64_t* coff = row_off + EW * 32 + warp * 32;
+    int64_t i = grp;
     const bool rows_fast = ov.rs[ov.nr - 1] == 1 && ov.cs[ov.nc - 1] != 1;
-    for (int64_t w = blockIdx.x; w < items; w += gridDim.x, ++i) {
+    for (int64_t w = blockIdx.x + (int64_t)grp * gridDim.x; w < items;
+         w += (int64_t)G * gridDim.x, i += G) {
       if (*abort_flag) break;
       const TcItem it = tc_item(w, mt, nt, nfast);
       const int b = (int)(i & 1);
@@ -287,7 +300,7 @@ __global__ void __launch_bounds__(192, 1)
         break;
       }
       {
-        const int64_t row = it.m0 + warp * 32 + lane;
+        const int64_t row = it.m0 + q * 32 + lane;
         roff[lane] = row < M ? out_row(ov, row) : -1;
       }
       __syncwarp();
@@ -296,7 +309,7 @@ __global__ void __launch_bounds__(192, 1)
         if (it.n0 + c0 >= N) break;  // warp-uniform: no valid column left
         uint32_t r[32];
         const uint32_t taddr =
-            tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * BN) + (uint32_t)c0;
+            tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN) + (uint32_t)c0;
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
             "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, "
@@ -320,32 +333,40 @@ __global__ void __launch_bounds__(192, 1)
         if (rows_fast) {
           // lane = row: for each column the warp stores 32 consecutive rows
           const int64_t ro = roff[lane];
-          double old[32];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int64_t co = coff[j];
-            old[j] = (accumulate && ro >= 0 && co >= 0) ? Cz[ro + co] : 0.0;
-          }
+          for (int h = 0; h < 32; h += OLDN) {
+            double old[OLDN];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int64_t co = coff[j];
-            if (ro >= 0 && co >= 0) Cz[ro + co] = old[j] + alpha * (double)__uint_as_float(r[j]);
+            for (int j = 0; j < OLDN; ++j) {
+              const int64_t co = coff[h + j];
+              old[j] = (accumulate && ro >= 0 && co >= 0) ? Cz[ro + co] : 0.0;
+            }
+#pragma unroll
+            for (int j = 0; j < OLDN; ++j) {
+              const int64_t co = coff[h + j];
+              if (ro >= 0 && co >= 0)
+                Cz[ro + co] = old[j] + alpha * (double)__uint_as_float(r[h + j]);
+            }
           }
         } else {
 #pragma unroll
           for (int j = 0; j < 32; ++j) buf[lane * 33 + j] = __uint_as_float(r[j]);
           __syncwarp();
           const int64_t co = coff[lane];
-          double old[32];
 #pragma unroll
-          for (int rr = 0; rr < 32; ++rr) {
-            const int64_t ro = roff[rr];
-            old[rr] = (accumulate && ro >= 0 && co >= 0) ? Cz[ro + co] : 0.0;
-          }
+          for (int h = 0; h < 32; h += OLDN) {
+            double old[OLDN];
 #pragma unroll
-          for (int rr = 0; rr < 32; ++rr) {
-            const int64_t ro = roff[rr];
-            if (ro >= 0 && co >= 0) Cz[ro + co] = old[rr] + alpha * (double)buf[rr * 33 + lane];
+            for (int j = 0; j < OLDN; ++j) {
+              const int64_t ro = roff[h + j];
+              old[j] = (accumulate && ro >= 0 && co >= 0) ? Cz[ro + co] : 0.0;
+            }
+#pragma unroll
+            for (int j = 0; j < OLDN; ++j) {
+              const int64_t ro = roff[h + j];
+              if (ro >= 0 && co >= 0)
+                Cz[ro + co] = old[j] + alpha * (double)buf[(h + j) * 33 + lane];
+            }
           }
         }
         __syncwarp();  // buf and coff are rewritten by the next chunk
@@ -498,8 +519,12 @@ TcGemm::TcGemm(cudaStream_t st, int precision) : st_(st) {
       cudaDeviceGetAttribute(&sm_count_, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       sm_count_ < 1)
     throw CudaError("tc: cannot query the multiprocessor count");
-  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       SMEM_BYTES);
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<4, 4>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       smem_bytes(4, 4));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tc_gemm<3, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem_bytes(3, 8));
   if (e != cudaSuccess) throw CudaError(std::string("tc smem attribute: ") + cudaGetErrorString(e));
 }
 
@@ -589,8 +614,16 @@ void TcGemm::run(const TcOperand& A, int sa, const TcOperand& B, int sb, int64_t
   // otherwise be re-read from HBM for every N tile
   const double abytes = (double)A.rows_pad * A.k_pad, bbytes = (double)B.rows_pad * B.k_pad;
   const int nfast = (nt > 1 && abytes > 4.0 * bbytes) ? 1 : 0;
-  k_tc_gemm<<<grid, 192, SMEM_BYTES, st_>>>(ma, mb, M, N, mt, nt, nfast, items, nk, kbs, alpha,
-                                           C, split_stride, ov, accumulate ? 1 : 0, d_err_);
+  // short K per item (skinny contractions): the epilogue bounds the time, so
+  // eight epilogue warps and three stages; otherwise four and four
+  if (kbs <= 4)
+    k_tc_gemm<3, 8><<<grid, 320, smem_bytes(3, 8), st_>>>(ma, mb, M, N, mt, nt, nfast, items, nk,
+                                                          kbs, alpha, C, split_stride, ov,
+                                                          accumulate ? 1 : 0, d_err_);
+  else
+    k_tc_gemm<4, 4><<<grid, 192, smem_bytes(4, 4), st_>>>(ma, mb, M, N, mt, nt, nfast, items, nk,
+                                                          kbs, alpha, C, split_stride, ov,
+                                                          accumulate ? 1 : 0, d_err_);
   count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw CudaError(std::string("tc_gemm launch: ") + cudaGetErrorString(e));
