@@ -364,7 +364,7 @@ __global__ void k_denoms(int o, int v, const double* __restrict__ eps, double* _
       continue;
     }
     int64_t q = k - ov;
-    int64_t Q = (int64_t)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+    int64_t Q = (int64_t)((sqrtf((float)(8 * q + 1)) - 1.0f) * 0.5f);
     while (Q * (Q + 1) / 2 > q) --Q;
     while ((Q + 1) * (Q + 2) / 2 <= q) ++Q;
     int64_t P = q - Q * (Q + 1) / 2;
