@@ -546,7 +546,7 @@ def main():
     else:
         # DRAM bytes of one full-size ladder launch (6 x o^2 rows, N = K = v^2) from a 1-pass
         # ncu capture (profiles/k_tc_gemm_ladder.md)
-        traffic = 9.28e9 if (w.o, w.v) == (21, 200) and args.nvec == 6 else None
+        traffic = 9.19e9 if (w.o, w.v) == (21, 200) and args.nvec == 6 else None
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "kernel": "k_tc_gemm (ladder)", "peak_source": f"bf16 sustained, {peak_src}",
