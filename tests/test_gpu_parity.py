@@ -39,6 +39,27 @@ def test_tc_gemm_exact_integers(B):
     assert np.array_equal(C.cpu().numpy(), A @ Bm.T)
 
 
+@pytest.mark.parametrize("shape", [(100000, 21, 21), (5000, 6, 663), (40000, 2, 90),
+                                   (25200, 300, 128), (300, 4200, 64), (126, 21, 84000),
+                                   (1, 300, 5000)], ids=str)
+def test_tc_gemm_exact_integer_shapes(B, shape):
+    """Every form of the persistent tensor-core kernel on exact integer data:
+    short K (the eight-warp form), N down to 2, an A operand that dominates
+    (N-fastest work order), few output tiles with split-K, and M = 1 (which
+    stays on the FP64 matrix-vector kernel)."""
+    M, N, K = shape
+    rng = np.random.default_rng(M + N + K)
+    amp = 3 if K > 3000 else 8
+    A = rng.integers(-amp, amp + 1, size=(M, K)).astype(np.float64)
+    Bm = rng.integers(-amp, amp + 1, size=(N, K)).astype(np.float64)
+    assert amp * amp * K < 2 ** 24      # every partial sum exact in FP32
+    C = torch.empty((M, N), dtype=torch.float64, device="cuda:0")
+    for rep in range(2):
+        C.fill_(float("nan"))
+        B.gemm_tn(dev(A), dev(Bm), C, precision="bf16")
+        assert np.array_equal(C.cpu().numpy(), A @ Bm.T), (shape, rep)
+
+
 def test_tc_gemm_split_accuracy(B):
     rng = np.random.default_rng(6)
     M, N, K = 1000, 777, 1300
