@@ -328,6 +328,42 @@ def row_timings(B, w, eps, L, t, Rh, prec, dev, torch, reps=2):
     return out
 
 
+def chain_case(args):
+    """The whole method on one system (default o=10, v=90, J=300) in the mixed
+    precision with FP64 refinement: the SCCSD state (ground state, the two
+    lowest states and zeta by the secant loop, then the left vectors), and the
+    multipliers plus effective densities of the gradient of state a and of the
+    coupling <psi_a|d psi_b>. Each stage is timed on the host around its
+    synchronous call (every call ends with a device synchronisation)."""
+    import torch
+    from paper_2403_01007_gb300 import binding as B
+    torch.cuda.set_device(0)
+    w = getattr(syn, args.workload if args.workload != "LARGE" else "MEDIUM")
+    eps, L = syn.workload_system(w)
+    ctx = B.Context(w.o, w.v, w.J, eps, L, precision=args.precision)
+    out = {"metric": "SCCSD gradient and coupling chain, seconds per stage", "unit": "s",
+           "higher_is_better": False, "data": "synthetic",
+           "config": {"workload": w.name, "o": w.o, "v": w.v, "J": w.J,
+                      "precision": args.precision, "refinement": "FP64"}}
+    t0 = time.perf_counter()
+    state = ctx.scc_state(tol=1e-9, ground_tol=1e-10, eom_tol=1e-8, left_tol=1e-8)
+    out["state_s"] = time.perf_counter() - t0
+    out["zeta"] = state["zeta"]
+    out["omega"] = [state["omega_a"], state["omega_b"]]
+    out["omega_left"] = [float(x) for x in state["omega_left"]]
+    out["e_corr"] = state["e_corr"]
+    for name, target in [("gradient_a", ("gradient", 0)), ("coupling_ab", ("coupling", 0, 1))]:
+        t1 = time.perf_counter()
+        r = ctx.solve_multipliers(state, target, tol=1e-9, maxit=1500, refine_tol=1e-6)
+        out[name] = {"seconds": time.perf_counter() - t1, "map_applications": r["iterations"],
+                     "gbar": float(r["gbar"]), "trace_D1": float(np.trace(r["D1"])),
+                     "norm_Gamma": float(np.linalg.norm(r["Gamma"]))}
+    out["value"] = time.perf_counter() - t0
+    ctx.close()
+    print(json.dumps(out))
+    return 0
+
+
 def learned_case(args):
     """Learned guess and preconditioner, reduced form of the C5 workload: train
     on solver-generated amplitudes of n_train systems at o=8, v=60, then solve
@@ -399,6 +435,8 @@ def main():
     ap.add_argument("--kernel-case", type=int, default=0, metavar="V",
                     help="time only the ladder-shaped contraction (rows = nvec*21^2, "
                          "N = K = V^2) through sccsd_gemm_tn; a small case for profilers")
+    ap.add_argument("--chain", action="store_true",
+                    help="time the whole method (state, multipliers, densities) at o=10 v=90")
     ap.add_argument("--learned", action="store_true",
                     help="evaluate the learned guess/preconditioner on fresh systems")
     ap.add_argument("--n-train", type=int, default=24)
@@ -410,6 +448,8 @@ def main():
         return batched_case(args)
     if args.learned and args.impl == "ours":
         return learned_case(args)
+    if args.chain and args.impl == "ours":
+        return chain_case(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.kernel_case:
