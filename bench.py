@@ -346,7 +346,8 @@ def chain_case(args):
            "config": {"workload": w.name, "o": w.o, "v": w.v, "J": w.J,
                       "precision": args.precision, "refinement": "FP64"}}
     t0 = time.perf_counter()
-    state = ctx.scc_state(tol=1e-9, ground_tol=1e-10, eom_tol=1e-8, left_tol=1e-8)
+    state = ctx.scc_state(tol=1e-9, ground_tol=1e-10, eom_tol=1e-8, left_tol=1e-7,
+                          left_maxit=600)
     out["state_s"] = time.perf_counter() - t0
     out["zeta"] = state["zeta"]
     out["omega"] = [state["omega_a"], state["omega_b"]]
@@ -354,7 +355,7 @@ def chain_case(args):
     out["e_corr"] = state["e_corr"]
     for name, target in [("gradient_a", ("gradient", 0)), ("coupling_ab", ("coupling", 0, 1))]:
         t1 = time.perf_counter()
-        r = ctx.solve_multipliers(state, target, tol=1e-9, maxit=1500, refine_tol=1e-6)
+        r = ctx.solve_multipliers(state, target, tol=1e-8, maxit=1500, refine_tol=1e-6)
         out[name] = {"seconds": time.perf_counter() - t1, "map_applications": r["iterations"],
                      "gbar": float(r["gbar"]), "trace_D1": float(np.trace(r["D1"])),
                      "norm_Gamma": float(np.linalg.norm(r["Gamma"]))}

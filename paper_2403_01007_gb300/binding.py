@@ -405,12 +405,13 @@ class Context:
         self._check(self.lib.sccsd_state_amplitudes(self.h, _ptr(t)))
         return t
 
-    def scc_state(self, tol=1e-10, maxit=40, ground_tol=1e-11, eom_tol=1e-9, left_tol=1e-9):
+    def scc_state(self, tol=1e-10, maxit=40, ground_tol=1e-11, eom_tol=1e-9, left_tol=1e-9,
+                  left_maxit=200):
         """Converged SCCSD for the two lowest states plus their left vectors
         (L_k . R_k = 1): the state dict taken by solve_multipliers."""
         r = self.solve_scc(tol=tol, maxit=maxit, ground_tol=ground_tol, eom_tol=eom_tol)
         t = self.state_amplitudes()
-        wl, VL, _ = self.solve_states(2, side="left", tol=left_tol)
+        wl, VL, _ = self.solve_states(2, side="left", tol=left_tol, maxit=left_maxit)
         La = VL[0] / (VL[0] @ r["Ra"])
         Lb = VL[1] / (VL[1] @ r["Rb"])
         return {"t": t, "Ra": r["Ra"], "Rb": r["Rb"], "La": La, "Lb": Lb, "zeta": r["zeta"],
