@@ -13,8 +13,21 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "lib")
 OBJ = os.path.join(HERE, "lib", "obj")
-SOURCES = ["graph.cpp", "ccsd_graph.cpp", "api.cpp", "cuda_backend.cu", "tc_gemm.cu",
-           "noalloc.cu", "small_la.cu", "mlp.cu"]
+SOURCES = [
+    "graph.cpp",
+    "ccsd_graph.cpp",
+    "api.cpp",
+    "model.cpp",
+    "solvers.cpp",
+    "multipliers.cpp",
+    "learned_api.cpp",
+    "capture.cpp",
+    "cuda_backend.cu",
+    "tc_gemm.cu",
+    "noalloc.cu",
+    "small_la.cu",
+    "mlp.cu",
+]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

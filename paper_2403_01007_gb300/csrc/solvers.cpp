@@ -1,0 +1,515 @@
+// Solvers: ground state (Jacobi + DIIS with dressed denominators), EOM roots
+// (Davidson) and the self-consistent SCC constraint, driven from the host
+// with every vector on the device.
+#include "context.h"
+
+using namespace sccsd;
+
+namespace sccsd {
+
+// solver work buffer i with room for at least n doubles (grown on demand)
+double* solver_buf(sccsd_ctx* c, size_t i, int64_t n) {
+  if (c->sv.size() <= i) {
+    c->sv.resize(i + 1, nullptr);
+    c->sv_n.resize(i + 1, 0);
+  }
+  if (c->sv[i] && c->sv_n[i] < n) {
+    c->be->sync();
+    c->be->release(c->sv[i]);
+    c->sv[i] = nullptr;
+  }
+  if (!c->sv[i]) {
+    c->sv[i] = c->be->alloc(n);
+    c->sv_n[i] = n;
+  }
+  return c->sv[i];
+}
+
+void ensure_small(sccsd_ctx* c) {
+  if (!c->sv_small) c->sv_small = c->be->alloc(6 * kMaxSpace * kMaxSpace + 16);
+  if (!c->sv_info) c->sv_info = (int*)c->be->alloc(kMaxSpace + 4);
+}
+
+void switch_precision(sccsd_ctx* c, int p) {
+  if (c->be->get_precision() == p) return;
+  c->be->set_precision(p);
+  for (Model* m : {c->plain.get(), c->scc.get()})
+    if (m) m->g.invalidate();
+}
+
+// E0 and packed omega (device) at packed amplitudes t (device)
+double eval_residual(sccsd_ctx* c, const double* t, double zeta, const double* Ra,
+                     const double* Rb, double* om) {
+  const bool scc = Ra != nullptr;
+  Model& m = model(c, scc);
+  load_packed(c, m.g, t, m.t1, m.t2, false);
+  if (scc) {
+    load_packed(c, m.g, Ra, m.Ra1, m.Ra2, false);
+    load_packed(c, m.g, Rb, m.Rb1, m.Rb2, false);
+    set_scalar(c, m.g, m.zeta, zeta);
+  }
+  c->cur = &m;
+  m.g.run({m.er.E0, m.er.O1, m.er.O2});
+  store_packed(c, m.g, m.er.O1, m.er.O2, om, false);
+  return get_scalar(c, m.g, m.er.E0);
+}
+
+// sigma[k] = A V[k] (side 0) or A^T V[k] (side 1), all on the device
+void transform(sccsd_ctx* c, int side, int nvec, const double* V, double* W) {
+  Model& m = *c->cur;
+  for (int k0 = 0; k0 < nvec; k0 += c->max_batch) {
+    const int nb = std::min(c->max_batch, nvec - k0);
+    if (side == 0) {
+      RightSec& S = right_section(m, nb);
+      load_packed_batch(c, m.g, V + (int64_t)k0 * c->dim, nb, S.R1, S.R2, false);
+      m.g.run({S.sig1, S.sig2});
+      store_packed_batch(c, m.g, nb, S.sig1, S.sig2, W + (int64_t)k0 * c->dim, false);
+    } else {
+      LeftSec& S = left_section(m, nb);
+      load_packed_batch(c, m.g, V + (int64_t)k0 * c->dim, nb, S.Lb1, S.Lb2, true);
+      m.g.run({S.lt1, S.lt2});
+      store_packed_batch(c, m.g, nb, S.lt1, S.lt2, W + (int64_t)k0 * c->dim, true);
+    }
+  }
+}
+
+}  // namespace sccsd
+
+extern "C" {
+
+int sccsd_solve_ground(sccsd_ctx* c, const double* t0, double zeta, const double* Ra,
+                       const double* Rb, double tol, int maxit, double refine_tol, double* t_out,
+                       double* e_corr, int* iterations) {
+  if (!c) return SCCSD_EINVAL;
+  if (!(tol > 0.0) || maxit < 1) return fail(c, SCCSD_EINVAL, "bad tolerance or iteration limit");
+  if ((Ra == nullptr) != (Rb == nullptr)) return fail(c, SCCSD_EINVAL, "give both Ra and Rb or neither");
+  int status = SCCSD_OK;
+  int rc = guarded(c, [&] {
+    Dev d{c};
+    ensure_small(c);
+    const int64_t dim = c->dim;
+    double* t = solver_buf(c, 0, dim);
+    double* om = solver_buf(c, 1, dim);
+    double* tn = solver_buf(c, 2, dim);
+    double* X = solver_buf(c, 3, kDiis * dim);
+    double* Rr = solver_buf(c, 4, kDiis * dim);
+    double* Bm = c->sv_small;
+    double* cf = c->sv_small + kMaxSpace * kMaxSpace;
+    // device copies of the SCC vectors (they may be host arrays)
+    const double *ra = Ra, *rb = Rb;
+    if (Ra) {
+      double* a = solver_buf(c, 5, dim);
+      double* b = solver_buf(c, 6, dim);
+      c->be->upload(a, Ra, dim, c->be->is_device(Ra));
+      c->be->upload(b, Rb, dim, c->be->is_device(Rb));
+      ra = a;
+      rb = b;
+    }
+    if (t0)
+      c->be->upload(t, t0, dim, c->be->is_device(t0));
+    else
+      c->be->fill(t, dim, 0.0);
+    const int p0 = c->be->get_precision();
+    const bool refine = p0 != SCCSD_FP64 && refine_tol > 0.0;
+    bool fp64_phase = !refine;
+    int nh = 0, head = 0, it = 0;
+    double E = 0.0, nrm = 0.0;
+    double best = 1e300;
+    int since_best = 0;
+    // Update denominators: the dressed denominators D' from the diagonals of
+    // the dressed Fock-like intermediates at the current amplitudes, refreshed
+    // at iterations 3, 6, 12, 24, ... (DIIS restarts with each refresh) and
+    // floored at 0.2 D. Before the first refresh: the caller's (or learned)
+    // preconditioner when one is set, else the orbital-energy denominators D
+    // (which D' equals at t = 0).
+    double* Dp = solver_buf(c, 7, dim);
+    double* fdg = solver_buf(c, 8, c->o + c->v);
+    bool have_dp = false;
+    int next_refresh = 3;
+    for (it = 1; it <= maxit; ++it) {
+      E = eval_residual(c, t, zeta, ra, rb, om);
+      nrm = std::sqrt(d.dot(om, om, dim));
+      if (getenv("SCCSD_LOG"))
+        fprintf(stderr, "{\"solver\": \"ground\", \"iter\": %d, \"fp64\": %d, \"residual\": %.3e, \"e_corr\": %.12f}\n", it,
+                (int)fp64_phase, nrm, E - c->e_hf);
+      if (!std::isfinite(nrm)) throw std::runtime_error("ground state diverged (non-finite residual)");
+      if (nrm < 0.9 * best) {
+        best = nrm;
+        since_best = 0;
+      } else {
+        ++since_best;
+      }
+      // the mixed phase ends below refine_tol, or when it stalls at its noise floor
+      if (!fp64_phase && (nrm < refine_tol || since_best >= 6)) {
+        // mixed-precision phase done: refine in FP64 from the current amplitudes
+        switch_precision(c, SCCSD_FP64);
+        fp64_phase = true;
+        nh = 0;
+        head = 0;
+        --it;
+        continue;
+      }
+      if (fp64_phase && nrm < tol) break;
+      const double* Dstep = c->use_dprec ? c->Dprec : c->D;
+      {
+        if (it >= next_refresh) {
+          Model& mdl = *c->cur;
+          mdl.g.run({mdl.er.Fooi, mdl.er.Fvvi});
+          const int o = c->o, v = c->v;
+          int64_t d1[1] = {o}, os1[1] = {1}, is1[1] = {o + 1};
+          c->be->copy_view(1, d1, fdg, os1, mdl.g.data(mdl.er.Fooi), is1, 1.0, false);
+          int64_t d2[1] = {v}, os2[1] = {1}, is2[1] = {v + 1};
+          c->be->copy_view(1, d2, fdg + o, os2, mdl.g.data(mdl.er.Fvvi), is2, 1.0, false);
+          launch_denoms(d.st(), o, v, fdg, Dp);
+          launch_floor(d.st(), dim, c->D, 0.2, Dp);
+          have_dp = true;
+          next_refresh *= 2;
+          nh = 0;
+          head = 0;
+        }
+        if (have_dp) Dstep = Dp;
+      }
+      launch_jacobi(d.st(), dim, t, om, Dstep, tn);
+      const int slot = head;
+      head = (head + 1) % kDiis;
+      nh = std::min(nh + 1, kDiis);
+      d.copy(X + (int64_t)slot * dim, tn, dim);
+      d.copy(Rr + (int64_t)slot * dim, tn, dim);
+      d.axpby(dim, -1.0, t, 1.0, Rr + (int64_t)slot * dim);
+      if (nh >= 2) {
+        c->be->gemm_tn(1, nh, nh, dim, 1.0, Rr, Rr, Bm, false);
+        launch_diis(d.st(), nh, Bm, cf, c->sv_info);
+        int info = 0;
+        cudaMemcpyAsync(&info, c->sv_info, sizeof(int), cudaMemcpyDeviceToHost, d.st());
+        c->be->sync();
+        if (info == 0)
+          d.combine(1, nh, cf, X, t);
+        else
+          d.copy(t, tn, dim);
+      } else {
+        d.copy(t, tn, dim);
+      }
+    }
+    if (it > maxit) status = SCCSD_ENOTCONV;
+    if (refine) switch_precision(c, p0);
+    if (refine) eval_residual(c, t, zeta, ra, rb, om);  // fix the state for later transforms
+    if (t_out) c->be->download(t_out, t, dim, c->be->is_device(t_out));
+    if (e_corr) *e_corr = E - c->e_hf;
+    if (iterations) *iterations = std::min(it, maxit);
+    c->be->sync();
+  });
+  if (rc != SCCSD_OK) return rc;
+  if (status != SCCSD_OK) return fail(c, status, "ground state not converged within maxit");
+  return SCCSD_OK;
+}
+
+int sccsd_solve_states(sccsd_ctx* c, int nroots, int side, double tol, int maxit,
+                       double refine_tol, double* omega, double* vecs, int* iterations) {
+  if (!c) return SCCSD_EINVAL;
+  if (nroots < 1 || nroots > 12 || (side != 0 && side != 1) || !(tol > 0.0) || maxit < 1 || !omega)
+    return fail(c, SCCSD_EINVAL, "bad arguments");
+  if (!c->cur) return fail(c, SCCSD_ESTATE, "call sccsd_residual or sccsd_solve_ground first");
+  int status = SCCSD_OK;
+  int rc = guarded(c, [&] {
+    Dev d{c};
+    ensure_small(c);
+    const int64_t dim = c->dim;
+    const int mmax = kMaxSpace;
+    if (dim < mmax) throw std::invalid_argument("problem too small for the requested roots");
+    double* V = solver_buf(c, 10, (int64_t)kMaxSpace * dim);
+    double* W = solver_buf(c, 11, (int64_t)kMaxSpace * dim);
+    double* Xr = solver_buf(c, 12, 12 * dim);
+    double* AX = solver_buf(c, 13, 12 * dim);
+    double* Rz = solver_buf(c, 14, 13 * dim);
+    double* Xp = solver_buf(c, 15, 12 * dim);   // Ritz vectors of the previous iteration
+    double* AXp = solver_buf(c, 16, 12 * dim);
+    bool have_prev = false;
+    double* S = c->sv_small;
+    double* Y = c->sv_small + kMaxSpace * kMaxSpace;
+    double* wr = c->sv_small + 2 * kMaxSpace * kMaxSpace;
+    double* wi = wr + kMaxSpace;
+    double* cf = wi + kMaxSpace;
+    double* G = c->sv_small + 3 * kMaxSpace * kMaxSpace;
+    int* order = c->sv_info;
+    int* info_d = c->sv_info + kMaxSpace;
+    cudaStream_t st = d.st();
+    auto get_info = [&]() {
+      int h = 0;
+      cudaMemcpyAsync(&h, info_d, sizeof(int), cudaMemcpyDeviceToHost, st);
+      c->be->sync();
+      return h;
+    };
+    // Gram-Schmidt of vec (and the same combination of its image) against V[0:m)
+    auto orthogonalize = [&](double* vec, double* img, int m) {
+      for (int pass = 0; pass < 2 && m > 0; ++pass) {
+        c->be->gemm_tn(1, m, 1, dim, 1.0, V, vec, cf, false);     // cf[p] = v_p . vec
+        double* tmp = Rz + 12 * dim;
+        d.combine(1, m, cf, V, tmp);
+        d.axpby(dim, -1.0, tmp, 1.0, vec);
+        if (img) {
+          d.combine(1, m, cf, W, tmp);
+          d.axpby(dim, -1.0, tmp, 1.0, img);
+        }
+      }
+    };
+    // Preconditioner: dressed denominators D'_ai = f_a - f_i, D'_aibj = f_a + f_b
+    // - f_i - f_j from the diagonals f of the Fock-like intermediates at the
+    // fixed state (they carry most of the correlation shift of diag(A));
+    // initial guesses: unit vectors on the lowest singles D'.
+    const int o = c->o, v = c->v;
+    Model& mdl = *c->cur;
+    mdl.g.run({mdl.er.Fooi, mdl.er.Fvvi});
+    double* fdiag = solver_buf(c, 17, o + v);
+    double* Dp = solver_buf(c, 18, dim);
+    {
+      int64_t d1[1] = {o}, os1[1] = {1}, is1[1] = {o + 1};
+      c->be->copy_view(1, d1, fdiag, os1, mdl.g.data(mdl.er.Fooi), is1, 1.0, false);
+      int64_t d2[1] = {v}, os2[1] = {1}, is2[1] = {v + 1};
+      c->be->copy_view(1, d2, fdiag + o, os2, mdl.g.data(mdl.er.Fvvi), is2, 1.0, false);
+    }
+    launch_denoms(st, o, v, fdiag, Dp);
+    std::vector<double> fh(o + v);
+    c->be->download(fh.data(), fdiag, o + v, false);
+    std::vector<std::pair<double, int>> dd;
+    for (int a = 0; a < v; ++a)
+      for (int i = 0; i < o; ++i) dd.push_back({fh[o + a] - fh[i], a * o + i});
+    std::sort(dd.begin(), dd.end());
+    int m = std::min<int>(std::min<int>((int)dd.size(), 2 * nroots + 2), mmax);
+    c->be->fill(V, (int64_t)m * dim, 0.0);
+    for (int k = 0; k < m; ++k) {
+      double one = 1.0;
+      c->be->upload(V + (int64_t)k * dim + dd[k].second, &one, 1, false);
+    }
+    transform(c, side, m, V, W);
+    const int p0 = c->be->get_precision();
+    const bool refine = p0 != SCCSD_FP64 && refine_tol > 0.0;
+    bool fp64_phase = !refine;
+    std::vector<double> lam(nroots), res(nroots);
+    int it = 0;
+    bool converged = false;
+    double best = 1e300;
+    int since_best = 0;
+    for (it = 1; it <= maxit; ++it) {
+      // subspace matrix and its lowest roots
+      c->be->gemm_tn(1, m, m, dim, 1.0, V, W, S, false);
+      launch_small_eig(st, m, S, wr, wi, Y, nroots, order, info_d);
+      int info = get_info();
+      if (info == 3) throw std::domain_error("complex pair among the lowest roots");
+      if (info != 0) throw std::runtime_error("subspace eigensolver failed");
+      std::vector<int> ord(nroots);
+      cudaMemcpyAsync(ord.data(), order, sizeof(int) * nroots, cudaMemcpyDeviceToHost, st);
+      std::vector<double> w(m);
+      cudaMemcpyAsync(w.data(), wr, sizeof(double) * m, cudaMemcpyDeviceToHost, st);
+      c->be->sync();
+      for (int k = 0; k < nroots; ++k) lam[k] = w[ord[k]];
+      // Ritz vectors, their images and residuals
+      d.combine(nroots, m, Y, V, Xr);
+      d.combine(nroots, m, Y, W, AX);
+      launch_ritz_residual(st, nroots, dim, AX, Xr, wr, order, Rz);
+      c->be->gemm_tn(1, nroots, nroots, dim, 1.0, Rz, Rz, G, false);
+      c->be->gemm_tn(1, nroots, nroots, dim, 1.0, Xr, Xr, G + 144, false);
+      std::vector<double> g1(nroots * nroots), g2(nroots * nroots);
+      c->be->download(g1.data(), G, nroots * nroots, false);
+      c->be->download(g2.data(), G + 144, nroots * nroots, false);
+      double worst = 0.0;
+      for (int k = 0; k < nroots; ++k) {
+        res[k] = std::sqrt(g1[k * nroots + k] / g2[k * nroots + k]);
+        worst = std::max(worst, res[k]);
+      }
+      if (getenv("SCCSD_LOG")) {
+        fprintf(stderr, "{\"solver\": \"davidson\", \"iter\": %d, \"space\": %d, \"fp64\": %d, \"max_res\": %.3e, \"omega\": [", it, m,
+                (int)fp64_phase, worst);
+        for (int k = 0; k < nroots; ++k) fprintf(stderr, "%s%.12f", k ? ", " : "", lam[k]);
+        fprintf(stderr, "]}\n");
+      }
+      if (worst < 0.9 * best) {
+        best = worst;
+        since_best = 0;
+      } else {
+        ++since_best;
+      }
+      if (!fp64_phase && (worst < refine_tol || since_best >= 8)) {
+        // restart in FP64 from the current Ritz vectors
+        switch_precision(c, SCCSD_FP64);
+        fp64_phase = true;
+        have_prev = false;
+        d.copy(V, Xr, (int64_t)nroots * dim);
+        m = 0;
+        for (int k = 0; k < nroots; ++k) {
+          double* vk = V + (int64_t)m * dim;
+          if (k != m) d.copy(vk, Xr + (int64_t)k * dim, dim);
+          orthogonalize(vk, nullptr, m);
+          double nn = std::sqrt(d.dot(vk, vk, dim));
+          if (nn < 1e-10) continue;
+          d.axpby(dim, 0.0, vk, 1.0 / nn, vk);
+          ++m;
+        }
+        transform(c, side, m, V, W);
+        continue;
+      }
+      if (fp64_phase && worst < tol) {
+        converged = true;
+        break;
+      }
+      // preconditioned residuals of the unconverged roots
+      std::vector<int> want;
+      for (int k = 0; k < nroots; ++k)
+        if (res[k] >= tol) want.push_back(k);
+      if (m + (int)want.size() > mmax) {
+        // thick restart: current and previous Ritz vectors, orthonormalised
+        // (their images follow the same combinations)
+        d.copy(V, Xr, (int64_t)nroots * dim);
+        d.copy(W, AX, (int64_t)nroots * dim);
+        int nk = nroots;
+        if (have_prev) {
+          d.copy(V + (int64_t)nroots * dim, Xp, (int64_t)nroots * dim);
+          d.copy(W + (int64_t)nroots * dim, AXp, (int64_t)nroots * dim);
+          nk = 2 * nroots;
+        }
+        int mm = 0;
+        for (int k = 0; k < nk; ++k) {
+          double* vk = V + (int64_t)mm * dim;
+          double* wk = W + (int64_t)mm * dim;
+          if (k != mm) {
+            d.copy(vk, V + (int64_t)k * dim, dim);
+            d.copy(wk, W + (int64_t)k * dim, dim);
+          }
+          orthogonalize(vk, wk, mm);
+          double nn = std::sqrt(d.dot(vk, vk, dim));
+          if (!(nn > 1e-10)) continue;
+          d.axpby(dim, 0.0, vk, 1.0 / nn, vk);
+          d.axpby(dim, 0.0, wk, 1.0 / nn, wk);
+          ++mm;
+        }
+        m = mm;
+      }
+      d.copy(Xp, Xr, (int64_t)nroots * dim);
+      d.copy(AXp, AX, (int64_t)nroots * dim);
+      have_prev = true;
+      int added = 0;
+      for (int k : want) {
+        double* nv = V + (int64_t)(m + added) * dim;
+        launch_precond(st, dim, Rz + (int64_t)k * dim, Dp, lam[k], nv);
+        double n0 = std::sqrt(d.dot(nv, nv, dim));
+        orthogonalize(nv, nullptr, m + added);
+        double nn = std::sqrt(d.dot(nv, nv, dim));
+        if (!(nn > 1e-8 * n0) || nn == 0.0) continue;
+        d.axpby(dim, 0.0, nv, 1.0 / nn, nv);
+        ++added;
+      }
+      if (added == 0) throw std::runtime_error("Davidson subspace stagnated");
+      transform(c, side, added, V + (int64_t)m * dim, W + (int64_t)m * dim);
+      m += added;
+    }
+    if (!converged) status = SCCSD_ENOTCONV;
+    if (refine) switch_precision(c, p0);
+    for (int k = 0; k < nroots; ++k) omega[k] = lam[k];
+    if (vecs) {
+      // unit-norm Ritz vectors
+      for (int k = 0; k < nroots; ++k) {
+        double* xk = Xr + (int64_t)k * dim;
+        double nn = std::sqrt(d.dot(xk, xk, dim));
+        d.axpby(dim, 0.0, xk, 1.0 / nn, xk);
+      }
+      c->be->download(vecs, Xr, (int64_t)nroots * dim, c->be->is_device(vecs));
+    }
+    if (iterations) *iterations = std::min(it, maxit);
+    c->be->sync();
+  });
+  if (rc != SCCSD_OK) return rc;
+  if (status != SCCSD_OK) return fail(c, status, "roots not converged within maxit");
+  return SCCSD_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+// Self-consistent SCCSD for the two lowest states (K = {a, b}, Sec. 2.4.2).
+int sccsd_solve_scc(sccsd_ctx* c, double tol, int maxit, double ground_tol, double eom_tol,
+                    double* zeta_out, double* e_corr, double* omega2, double* r0_2, double* Ra_out,
+                    double* Rb_out, int* iterations) {
+  if (!c) return SCCSD_EINVAL;
+  if (!(tol > 0.0) || maxit < 1 || !(ground_tol > 0.0) || !(eom_tol > 0.0))
+    return fail(c, SCCSD_EINVAL, "bad tolerances or iteration limit");
+  int status = SCCSD_OK;
+  int rc = guarded(c, [&] {
+    const int64_t dim = c->dim;
+    std::vector<double> t(dim), vecs(2 * dim), sig(2 * dim), Ra(dim), Rb(dim);
+    double zeta = 0.0, E = 0.0, O = 0.0;
+    double w[2] = {0.0, 0.0}, r0[2] = {0.0, 0.0};
+    bool have_states = false, have_t = false;
+    std::vector<std::pair<double, double>> hist;
+    auto check = [&](int r) {
+      if (r != SCCSD_OK) throw std::runtime_error("inner solver failed: " + c->err);
+    };
+    int it = 0;
+    for (it = 1; it <= maxit; ++it) {
+      int gi = 0;
+      if (have_states)
+        check(sccsd_solve_ground(c, have_t ? t.data() : nullptr, zeta, Ra.data(), Rb.data(),
+                                 ground_tol, 1000, 1e-5, t.data(), &E, &gi));
+      else
+        check(sccsd_solve_ground(c, nullptr, 0.0, nullptr, nullptr, ground_tol, 1000, 1e-5,
+                                 t.data(), &E, &gi));
+      have_t = true;
+      int si = 0;
+      check(sccsd_solve_states(c, 2, 0, eom_tol, 1000, 1e-4, w, vecs.data(), &si));
+      // sign convention: largest |component| positive
+      for (int k = 0; k < 2; ++k) {
+        double* x = vecs.data() + k * dim;
+        int64_t im = 0;
+        for (int64_t q = 1; q < dim; ++q)
+          if (std::fabs(x[q]) > std::fabs(x[im])) im = q;
+        if (x[im] < 0)
+          for (int64_t q = 0; q < dim; ++q) x[q] = -x[q];
+      }
+      double etaR[2];
+      check(sccsd_jacobian_right(c, 2, vecs.data(), sig.data(), etaR));
+      r0[0] = etaR[0] / w[0];
+      r0[1] = etaR[1] / w[1];
+      check(sccsd_overlap(c, r0[0], vecs.data(), r0[1], vecs.data() + dim, &O));
+      if (getenv("SCCSD_LOG"))
+        fprintf(stderr, "{\"solver\": \"scc\", \"iter\": %d, \"zeta\": %.12f, \"O_ab\": %.3e, \"omega\": [%.12f, %.12f]}\n",
+                it, zeta, O, w[0], w[1]);
+      hist.push_back({zeta, O});
+      std::copy(vecs.begin(), vecs.begin() + dim, Ra.begin());
+      std::copy(vecs.begin() + dim, vecs.end(), Rb.begin());
+      have_states = true;
+      if (std::fabs(O) < tol && hist.size() > 1 &&
+          std::fabs(hist[hist.size() - 1].first - hist[hist.size() - 2].first) < 1e-8)
+        break;
+      if (hist.size() == 1) {
+        zeta = zeta - O;
+      } else {
+        auto [z1, o1] = hist[hist.size() - 2];
+        auto [z2, o2] = hist[hist.size() - 1];
+        zeta = (o2 != o1) ? z2 - o2 * (z2 - z1) / (o2 - o1) : z2;
+      }
+    }
+    if (it > maxit) status = SCCSD_ENOTCONV;
+    if (zeta_out) *zeta_out = hist.back().first;
+    if (e_corr) *e_corr = E;
+    if (omega2) {
+      omega2[0] = w[0];
+      omega2[1] = w[1];
+    }
+    if (r0_2) {
+      r0_2[0] = r0[0];
+      r0_2[1] = r0[1];
+    }
+    for (auto pr : {std::make_pair(Ra_out, &Ra), std::make_pair(Rb_out, &Rb)}) {
+      if (!pr.first) continue;
+      if (c->be->is_device(pr.first))
+        c->be->upload(pr.first, pr.second->data(), dim, false);
+      else
+        std::memcpy(pr.first, pr.second->data(), sizeof(double) * dim);
+    }
+    if (iterations) *iterations = std::min(it, maxit);
+  });
+  if (rc != SCCSD_OK) return rc;
+  if (status != SCCSD_OK) return fail(c, status, "zeta iteration not converged within maxit");
+  return SCCSD_OK;
+}
+
+}  // extern "C"

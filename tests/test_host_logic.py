@@ -49,7 +49,9 @@ def host_lib():
     from paper_2403_01007_gb300 import binding
     tmp = tempfile.mkdtemp()
     so = os.path.join(tmp, "libsccsd_hostexec.so")
-    srcs = [os.path.join(CSRC, f) for f in ("graph.cpp", "ccsd_graph.cpp", "api.cpp")]
+    srcs = [os.path.join(CSRC, f) for f in ("graph.cpp", "ccsd_graph.cpp", "api.cpp", "model.cpp",
+                                            "solvers.cpp", "multipliers.cpp", "learned_api.cpp",
+                                            "capture.cpp")]
     srcs.append(os.path.join(ROOT, "tests", "host_executor", "host_backend.cpp"))
     # SCCSD_HOST_SANITIZE=1 builds the executor with AddressSanitizer (run the
     # tests with the sanitizer runtime preloaded) to catch out-of-range buffer use
