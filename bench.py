@@ -107,10 +107,8 @@ class Clocks:
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_2403_01007_gb300 import replicas
+    return replicas.rank_env()
 
 
 def cpu_oracle_sample(steps=1, warmup=0):
@@ -459,6 +457,7 @@ def main():
     import torch
     import torch.distributed as dist
     from paper_2403_01007_gb300 import binding as B
+    from paper_2403_01007_gb300 import replicas
 
     rank, world, local = dist_env()
     if world > 1:
@@ -466,10 +465,11 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = getattr(syn, args.workload)
-    eps, L = syn.workload_system(w, instance=rank)
+    inst = replicas.instance_of(rank)
+    eps, L = syn.workload_system(w, instance=inst)
     dim = B.dim(w.o, w.v)
-    t = syn.random_vectors(w.o, w.v, 1, syn.seed_of(w.config, 50 + rank), scale=1e-3)[0]
-    Rh = syn.random_vectors(w.o, w.v, args.nvec, syn.seed_of(w.config, 60 + rank), normalise=True)
+    t = syn.random_vectors(w.o, w.v, 1, syn.seed_of(w.config, 50 + inst), scale=1e-3)[0]
+    Rh = syn.random_vectors(w.o, w.v, args.nvec, syn.seed_of(w.config, 60 + inst), normalise=True)
 
     stream = torch.cuda.Stream(device=dev)
     peaks, peak_src = load_peaks()
@@ -487,8 +487,7 @@ def main():
     ctx = make_ctx(args.precision)
     for _ in range(args.warmup):
         ctx.jacobian_right(R, sigma=sig)
-    if world > 1:
-        dist.barrier()
+    replicas.barrier()
     torch.cuda.synchronize()
     ctx.profile(True)
     with Clocks(local) as clk:
@@ -496,11 +495,8 @@ def main():
     lad_ms, lad_calls, lad_flops, launches = ctx.profile_read()
     clocks = clk.summary()
     ctx.profile(False)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * args.steps * args.nvec / (ms / 1e3)
+    ms = replicas.max_over_ranks(ms, device=dev)
+    value = replicas.whole_job_rate(args.steps * args.nvec, world, ms)
     sig_mixed = sig.cpu().numpy().copy()
 
     # end to end: pinned host inputs and outputs through the same public call
@@ -510,12 +506,14 @@ def main():
         spin = torch.empty_like(Rpin).pin_memory()
         ctx.jacobian_right(Rpin, sigma=spin)
         torch.cuda.synchronize()
+        replicas.barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             ctx.jacobian_right(Rpin, sigma=spin)
         torch.cuda.synchronize()
-        es = time.perf_counter() - t0
-        e2e = {"value": world * args.steps * args.nvec / es, "unit": "transforms/s",
+        es = replicas.max_over_ranks(time.perf_counter() - t0, device=dev)
+        e2e = {"value": replicas.whole_job_rate(args.steps * args.nvec, world, es * 1e3),
+               "unit": "transforms/s",
                "h2d_bytes_per_step": int(Rpin.numel() * 8),
                "d2h_bytes_per_step": int(spin.numel() * 8)}
     ctx.close()
