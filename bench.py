@@ -72,6 +72,13 @@ class Clocks:
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (FileNotFoundError, OSError):
             self.proc = None
+        # the sampler takes a moment to start: wait (at most 5 s) for its
+        # first line so that the timed region is inside the sampled window
+        t0 = time.perf_counter()
+        while self.proc is not None and time.perf_counter() - t0 < 5.0:
+            if self.proc.poll() is not None or os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
         return self
 
     def __exit__(self, *a):
@@ -148,7 +155,10 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": syn.LARGE.name, "nvec": 1, "sample_workload": syn.MEDIUM.name},
+        "config": {"workload": syn.LARGE.name, "o": syn.LARGE.o, "v": syn.LARGE.v,
+                   "J": syn.LARGE.J, "nvec": args.nvec, "precision": args.precision,
+                   "parallelism": "replicas1",
+                   "l2": "inputs larger than L2 (ladder integrals alone exceed 129 MB)"},
         "cpu_baseline": {"value": val, "unit": "transforms/s", "cores": threads,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": "transforms/s", "h2d_bytes_per_step": 0,
@@ -416,7 +426,7 @@ def learned_case(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["bf16x3", "bf16", "fp64"])
@@ -570,10 +580,10 @@ def main():
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0:
-        val, sec, threads = cpu_oracle_sample(steps=1)
+        val, sec, threads = cpu_oracle_sample(steps=5)
         cpu = {"value": val, "unit": "transforms/s", "cores": threads, "kind": "oracle",
-               "sample": f"one A R of the FP64 CPU oracle at o=10 v=90 J=300 ({sec:.2f} s), "
-                         f"scaled by the dense-flop ratio to o=21 v=200 J=663"}
+               "sample": f"five A R of the FP64 CPU oracle at o=10 v=90 J=300 (median {sec:.2f} s "
+                         f"each), scaled by the dense-flop ratio to o=21 v=200 J=663"}
 
     peak = peaks.get("bf16_tflops_sustained", 1700.0)
     slices = {"bf16x3": 3, "bf16": 1, "fp64": 1}[args.precision]

@@ -212,3 +212,44 @@ def test_mixed_precision_medium(B, precision, tol):
         assert maxrel(s[k], rp.jacobian_right(prob, t, R[k]).numpy()) < tol
         assert maxrel(sl[k], rp.jacobian_left(prob, t, R[k]).numpy()) < tol
     ctx.close()
+
+
+def test_full_size_bench_configuration(B):
+    """o=21, v=200, J=663 with the benchmark's own inputs and batch of six
+    trial vectors. The oracle needs minutes per transform at this size, so the
+    checks are ones that hold at any size:
+      * A R in BF16 and BF16x3 against the FP64 GPU path (pinned to the
+        oracle element by element at the small and ragged sizes above);
+      * <L, A R> = <A^T L, R> for the FP64 right and left transforms, which
+        the exact Jacobian satisfies up to rounding."""
+    w = syn.LARGE
+    eps, L = syn.workload_system(w)
+    t = syn.random_vectors(w.o, w.v, 1, syn.seed_of(w.config, 50), scale=1e-3)[0]
+    R = syn.random_vectors(w.o, w.v, 6, syn.seed_of(w.config, 60), normalise=True)
+    Lv = syn.random_vectors(w.o, w.v, 1, syn.seed_of(w.config, 70), normalise=True)
+    Rd = dev(R)
+
+    out = {}
+    for prec in ("bf16", "bf16x3"):
+        ctx = B.Context(w.o, w.v, w.J, dev(eps), dev(L), precision=prec)
+        ctx.residual(t)
+        out[prec] = ctx.jacobian_right(Rd).cpu().numpy()
+        ctx.close()
+        del ctx
+        torch.cuda.empty_cache()
+
+    ctx = B.Context(w.o, w.v, w.J, dev(eps), dev(L), precision="fp64")
+    ctx.residual(t)
+    s64 = ctx.jacobian_right(dev(R[:2])).cpu().numpy()
+    l64 = ctx.jacobian_left(dev(Lv)).cpu().numpy()[0]
+    ctx.close()
+
+    for k in range(2):
+        assert maxrel(out["bf16"][k], s64[k]) < 2e-2
+        assert maxrel(out["bf16x3"][k], s64[k]) < 2e-4
+        a = float(np.dot(Lv[0], s64[k]))
+        b = float(np.dot(l64, R[k]))
+        scale = np.linalg.norm(s64[k]) + np.linalg.norm(l64)
+        assert abs(a - b) < 1e-11 * scale
+    # every row of the batch is a finite, non-trivial transform
+    assert np.all(np.isfinite(out["bf16"])) and np.all(np.linalg.norm(out["bf16"], axis=1) > 0)
