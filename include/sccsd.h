@@ -164,6 +164,33 @@ int sccsd_solve_scc(sccsd_ctx* ctx, double tol, int maxit, double ground_tol, do
  * calls (SCCSD_FP64 / SCCSD_BF16X3 / SCCSD_BF16). */
 int sccsd_set_precision(sccsd_ctx* ctx, int precision);
 
+/* Launch-shape tuning of the tensor-core contractions (an implementation
+ * choice, not part of the method: results are the same contraction up to the
+ * FP32 summation order of split K ranges).
+ * Each contraction has a fixed default launch shape: kernel variant (four or
+ * eight epilogue warps), order of the output tiles, number of K ranges. With
+ * tuning enabled on a context (enable = 1), the first contraction of each
+ * new shape (M, padded N, K blocks, slices, output view, accumulate mode, SM
+ * count) outside graph capture times every candidate shape on its operands,
+ * into a scratch buffer, so the caller's outputs are not touched. The fastest
+ * shape is recorded in a table shared by all contexts of the process and used
+ * by every later contraction of that shape, whether or not tuning is enabled.
+ * Tune before sccsd_capture_transform, which only reads the table. No effect
+ * in SCCSD_FP64 mode.
+ * sccsd_autotune_export writes the table as text, one line per shape, into
+ * buf[cap] (NUL-terminated). *len receives the bytes needed, NUL included.
+ * SCCSD_EINVAL if buf is NULL or cap is too small (*len is still set).
+ * sccsd_autotune_import merges a text written by export. On a malformed line,
+ * or a shape the library never launches, it merges nothing and returns
+ * SCCSD_EINVAL. sccsd_autotune_clear empties the table;
+ * sccsd_autotune_entries returns its size. These four take no context and
+ * run on the host. */
+int sccsd_set_autotune(sccsd_ctx* ctx, int enable);
+int sccsd_autotune_export(char* buf, long long cap, long long* len);
+int sccsd_autotune_import(const char* text);
+void sccsd_autotune_clear(void);
+long long sccsd_autotune_entries(void);
+
 /* Ground state: converge Omega(t) = 0 (Sec. 2.1; with Ra/Rb non-NULL the SCC
  * residual of sccsd_residual at fixed zeta) by the preconditioned update
  * t <- t - Omega/D with DIIS (8 vectors). D starts as the orbital-energy
@@ -205,7 +232,7 @@ int sccsd_solve_states(sccsd_ctx* ctx, int nroots, int side, double tol, int max
  * log(D'_ij^ab / D_ij^ab)): a guess for the converged amplitude and for the
  * dressed denominator D' (the diagonal of the Jacobian estimated from the
  * intermediates) used as the ground-state preconditioner. The plain solver
- * judges the result: the guess only sets the starting point and the update
+ * decides the result: the guess only sets the starting point and the update
  * preconditioner, and callers fall back to t0 = 0 (MP2 first step) and D.
  * (An extension of the method, not in the paper.) */
 typedef struct sccsd_mlp sccsd_mlp;

@@ -42,6 +42,17 @@ def _declare(lib):
     lib.sccsd_gemm_tn_noalloc_capacity.restype = ctypes.c_longlong
     lib.sccsd_set_precision.argtypes = [_dp, ctypes.c_int]
     lib.sccsd_set_precision.restype = ctypes.c_int
+    lib.sccsd_set_autotune.argtypes = [_dp, ctypes.c_int]
+    lib.sccsd_set_autotune.restype = ctypes.c_int
+    lib.sccsd_autotune_export.argtypes = [ctypes.c_char_p, ctypes.c_longlong,
+                                          ctypes.POINTER(ctypes.c_longlong)]
+    lib.sccsd_autotune_export.restype = ctypes.c_int
+    lib.sccsd_autotune_import.argtypes = [ctypes.c_char_p]
+    lib.sccsd_autotune_import.restype = ctypes.c_int
+    lib.sccsd_autotune_clear.argtypes = []
+    lib.sccsd_autotune_clear.restype = None
+    lib.sccsd_autotune_entries.argtypes = []
+    lib.sccsd_autotune_entries.restype = ctypes.c_longlong
     lib.sccsd_solve_ground.argtypes = [_dp, _dp, ctypes.c_double, _dp, _dp, ctypes.c_double,
                                        ctypes.c_int, ctypes.c_double, _dp, _dp, _dp]
     lib.sccsd_solve_ground.restype = ctypes.c_int
@@ -151,6 +162,34 @@ def _ptr(x):
             raise TypeError("tensors must be contiguous float64")
         return x.data_ptr()
     raise TypeError(f"unsupported array type {type(x)}")
+
+
+def autotune_export(lib=None) -> str:
+    """The process-wide table of tuned launch shapes as text."""
+    lib = lib or load()
+    n = ctypes.c_longlong()
+    lib.sccsd_autotune_export(None, 0, ctypes.byref(n))
+    buf = ctypes.create_string_buffer(n.value)
+    rc = lib.sccsd_autotune_export(buf, n.value, ctypes.byref(n))
+    if rc != 0:
+        raise SccsdError(rc, "autotune export")
+    return buf.value.decode()
+
+
+def autotune_import(text: str, lib=None):
+    """Merge a table written by autotune_export (all or nothing)."""
+    lib = lib or load()
+    rc = lib.sccsd_autotune_import(text.encode())
+    if rc != 0:
+        raise SccsdError(rc, "malformed or invalid autotune table")
+
+
+def autotune_clear(lib=None):
+    (lib or load()).sccsd_autotune_clear()
+
+
+def autotune_entries(lib=None) -> int:
+    return int((lib or load()).sccsd_autotune_entries())
 
 
 def dim(o: int, v: int) -> int:
@@ -336,6 +375,11 @@ class Context:
     def set_precision(self, precision):
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self._check(self.lib.sccsd_set_precision(self.h, prec))
+
+    def set_autotune(self, enable=True):
+        """Time the launch shapes of each new tensor-core contraction shape of
+        this context and record the fastest in the process-wide table."""
+        self._check(self.lib.sccsd_set_autotune(self.h, 1 if enable else 0))
 
     def solve_ground(self, t0=None, tol=1e-10, maxit=200, refine_tol=1e-4, scc=None, t_out=None):
         """Converge the ground state; returns (e_corr, t, iterations)."""

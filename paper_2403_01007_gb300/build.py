@@ -22,6 +22,7 @@ SOURCES = [
     "multipliers.cpp",
     "learned_api.cpp",
     "capture.cpp",
+    "tc_tune.cpp",
     "cuda_backend.cu",
     "tc_gemm.cu",
     "noalloc.cu",

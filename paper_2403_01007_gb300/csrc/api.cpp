@@ -2,6 +2,10 @@
 // densities and marshalling (solvers, multipliers, learned part and CUDA-graph
 // batching are in their own files).
 #include "context.h"
+#include "tc_tune.h"
+
+#include <cstring>
+#include <string>
 
 using namespace sccsd;
 
@@ -368,6 +372,30 @@ int sccsd_set_precision(sccsd_ctx* c, int precision) {
     c->precision = precision;
   });
 }
+
+int sccsd_set_autotune(sccsd_ctx* c, int enable) {
+  if (!c) return SCCSD_EINVAL;
+  if (enable != 0 && enable != 1) return fail(c, SCCSD_EINVAL, "enable must be 0 or 1");
+  return guarded(c, [&] { c->be->set_autotune(enable == 1); });
+}
+
+int sccsd_autotune_export(char* buf, long long cap, long long* len) {
+  const std::string text = TcTuneTable::global().dump();
+  const long long need = (long long)text.size() + 1;
+  if (len) *len = need;
+  if (!buf || cap < need) return SCCSD_EINVAL;
+  std::memcpy(buf, text.c_str(), (size_t)need);
+  return SCCSD_OK;
+}
+
+int sccsd_autotune_import(const char* text) {
+  if (!text) return SCCSD_EINVAL;
+  return TcTuneTable::global().load(std::string(text)) == 0 ? SCCSD_OK : SCCSD_EINVAL;
+}
+
+void sccsd_autotune_clear(void) { TcTuneTable::global().clear(); }
+
+long long sccsd_autotune_entries(void) { return (long long)TcTuneTable::global().size(); }
 
 int sccsd_state_amplitudes(sccsd_ctx* c, double* t) {
   if (!c) return SCCSD_EINVAL;

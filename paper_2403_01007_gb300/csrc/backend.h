@@ -73,6 +73,9 @@ class Backend {
   virtual int get_precision() const = 0;
   // While capturing a CUDA graph: no synchronisation, no allocation.
   virtual void set_capturing(bool on) = 0;
+  // time the launch-shape candidates of each new tensor-core contraction shape
+  // (no effect in FP64 mode)
+  virtual void set_autotune(bool on) { (void)on; }
   // packed singles+doubles vector <-> t1[a][i], full t2[i][j][a][b].
   // ket: t2 = t_mu on both (P,Q) and (Q,P);  bra: off-diagonal pairs halved
   // on unpack and summed on pack, so that sum_packed L X = sum_full L~ X.

@@ -310,6 +310,12 @@ class CudaBackend : public Backend {
     tc.reset();
   }
 
+  bool autotune = false;
+  void set_autotune(bool on) override {
+    autotune = on;
+    if (tc) tc->set_tune(on);
+  }
+
   bool capturing = false, prof_saved = false;
   // profiling events stay out of captured graphs
   void set_capturing(bool on) override {
@@ -363,10 +369,12 @@ class CudaBackend : public Backend {
     sync();
     precision = p;
     if (p != 0) {
-      if (!tc)
+      if (!tc) {
         tc = std::make_unique<TcGemm>(st, p);
-      else
+        tc->set_tune(autotune);
+      } else {
         tc->set_precision(p);
+      }
     }
     if (tc)
       for (auto& kv : opcache) tc->release(kv.second.op);

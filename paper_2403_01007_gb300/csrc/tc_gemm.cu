@@ -532,6 +532,7 @@ TcGemm::~TcGemm() {
   release(a_tmp_);
   release(b_tmp_);
   if (part_) cudaFree(part_);
+  if (tune_buf_) cudaFree(tune_buf_);
   if (d_err_) cudaFree(d_err_);
 }
 
@@ -600,7 +601,7 @@ void TcGemm::check_error() {
 
 void TcGemm::run(const TcOperand& A, int sa, const TcOperand& B, int sb, int64_t M, int64_t N,
                  double alpha, double* C, int64_t split_stride, const OutView& ov,
-                 bool accumulate, int splits, int kbs) {
+                 bool accumulate, int splits, int kbs, int variant, int nfast) {
   if (A.k_pad != B.k_pad) throw std::runtime_error("tc: K mismatch");
   const __nv_bfloat16* a = (const __nv_bfloat16*)A.data + (size_t)sa * A.rows_pad * A.k_pad;
   const __nv_bfloat16* b = (const __nv_bfloat16*)B.data + (size_t)sb * B.rows_pad * B.k_pad;
@@ -610,13 +611,8 @@ void TcGemm::run(const TcOperand& A, int sa, const TcOperand& B, int sb, int64_t
   const int64_t items = mt * nt * splits;
   const int grid = (int)std::min<int64_t>(items, sm_count_);
   const int nk = (int)(A.k_pad / BK);
-  // share the A tile among concurrent CTAs when A is the operand that would
-  // otherwise be re-read from HBM for every N tile
-  const double abytes = (double)A.rows_pad * A.k_pad, bbytes = (double)B.rows_pad * B.k_pad;
-  const int nfast = (nt > 1 && abytes > 4.0 * bbytes) ? 1 : 0;
-  // short K per item (skinny contractions): the epilogue bounds the time, so
-  // eight epilogue warps and three stages; otherwise four and four
-  if (kbs <= 4)
+  if (variant == 1 && kbs > 4) throw std::runtime_error("tc: eight-warp variant needs <= 4 K blocks");
+  if (variant == 1)
     k_tc_gemm<3, 8><<<grid, 320, smem_bytes(3, 8), st_>>>(ma, mb, M, N, mt, nt, nfast, items, nk,
                                                           kbs, alpha, C, split_stride, ov,
                                                           accumulate ? 1 : 0, d_err_);
@@ -643,26 +639,133 @@ void TcGemm::gemm_prepared_b(int64_t M, int64_t N, int64_t K, double alpha, cons
   (void)check;  // the error flag is read by the backend at each synchronisation
 }
 
+namespace {
+
+// FNV-1a over the levels and strides of an output view
+uint64_t view_hash(const OutView& ov) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](int64_t x) {
+    for (int b = 0; b < 8; ++b) {
+      h ^= (uint64_t)((x >> (8 * b)) & 0xff);
+      h *= 1099511628211ull;
+    }
+  };
+  mix(ov.nr);
+  mix(ov.nc);
+  for (int l = 0; l < ov.nr; ++l) { mix(ov.re[l]); mix(ov.rs[l]); }
+  for (int l = 0; l < ov.nc; ++l) { mix(ov.ce[l]); mix(ov.cs[l]); }
+  return h;
+}
+
+// 1 + the largest offset an M x N result can reach through the view (an upper
+// bound), or -1 for views with negative strides
+int64_t view_span(const OutView& ov, int64_t M, int64_t N) {
+  auto bound = [](int n, const int64_t* ext, const int64_t* str, int64_t count) -> int64_t {
+    int64_t inner = 1, b = 0;
+    for (int l = 1; l < n; ++l) {
+      if (ext[l] < 1 || str[l] < 0) return -1;
+      inner *= ext[l];
+      b += (ext[l] - 1) * str[l];
+    }
+    if (str[0] < 0) return -1;
+    return b + str[0] * ((count - 1) / inner);
+  };
+  const int64_t r = bound(ov.nr, ov.re, ov.rs, M), c = bound(ov.nc, ov.ce, ov.cs, N);
+  if (r < 0 || c < 0) return -1;
+  return r + c + 1;
+}
+
+}  // namespace
+
 void TcGemm::gemm_ops(int64_t M, int64_t N, double alpha, const TcOperand& A, const TcOperand& B,
                       double* C, const OutView& ov, bool accumulate) {
-  std::vector<std::pair<int, int>> pairs;
-  slice_pairs(nslices_, pairs);
-  const int64_t tiles = ((M + BM - 1) / BM) * (B.rows_pad / BN);
-  const int nk = (int)(A.k_pad / BK);
-  int splits = 1, kbs = nk;
-  if (tiles < sm_count_ && nk >= 8) {
-    // too few output tiles to fill the GPU: split K, at least 4 blocks each
-    int64_t want = std::min<int64_t>((2 * sm_count_ + tiles - 1) / tiles, nk / 4);
-    if (want > 1) {
-      kbs = (int)((nk + want - 1) / want);
-      splits = (nk + kbs - 1) / kbs;
+  TcShape s;
+  s.M = M;
+  s.n_pad = B.rows_pad;
+  s.nk = (int)(A.k_pad / BK);
+  s.slices = nslices_;
+  s.accumulate = accumulate ? 1 : 0;
+  s.sm_count = sm_count_;
+  s.view_hash = view_hash(ov);
+  const int64_t mt = (M + BM - 1) / BM, nt = B.rows_pad / BN;
+  const double abytes = (double)A.rows_pad * A.k_pad, bbytes = (double)B.rows_pad * B.k_pad;
+  TcConfig cfg;
+  if (!TcTuneTable::global().find(s, cfg)) {
+    cfg = tc_default_config(s, mt, nt, abytes, bbytes);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st_, &cs);
+    if (tune_ && cs == cudaStreamCaptureStatusNone) cfg = tune(s, M, N, alpha, A, B, ov, cfg);
+  }
+  execute(cfg, M, N, alpha, A, B, C, ov, accumulate);
+}
+
+TcConfig TcGemm::tune(const TcShape& s, int64_t M, int64_t N, double alpha, const TcOperand& A,
+                      const TcOperand& B, const OutView& ov, const TcConfig& fallback) {
+  const int64_t span = view_span(ov, M, N);
+  if (span < 1) return fallback;
+  if (tune_bytes_ < (size_t)span * sizeof(double)) {
+    cudaStreamSynchronize(st_);
+    if (tune_buf_) cudaFree(tune_buf_);
+    tune_buf_ = nullptr;
+    tune_bytes_ = 0;
+    if (cudaMalloc(&tune_buf_, (size_t)span * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return fallback;
+    }
+    tune_bytes_ = (size_t)span * sizeof(double);
+  }
+  const int64_t mt = (M + BM - 1) / BM, nt = B.rows_pad / BN;
+  const double abytes = (double)A.rows_pad * A.k_pad, bbytes = (double)B.rows_pad * B.k_pad;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return fallback;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fallback;
+  }
+  TcConfig best = fallback;
+  double best_us = 1e300;
+  const int reps = 3;
+  // candidates write the real view into a scratch buffer of its span (with the
+  // real accumulate mode), so the caller's output is untouched
+  for (const TcConfig& c : tc_candidates(s, mt, nt, abytes, bbytes)) {
+    try {
+      execute(c, M, N, alpha, A, B, tune_buf_, ov, s.accumulate != 0);
+      cudaEventRecord(e0, st_);
+      for (int r = 0; r < reps; ++r) execute(c, M, N, alpha, A, B, tune_buf_, ov, s.accumulate != 0);
+      cudaEventRecord(e1, st_);
+      cudaEventSynchronize(e1);
+    } catch (const OomError&) {
+      continue;
+    }
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    const double us = 1e3 * ms / reps;
+    if (us < best_us) {
+      best_us = us;
+      best = c;
     }
   }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  check_error();
+  TcTuneTable::global().put(s, best, best_us);
+  return best;
+}
+
+void TcGemm::execute(const TcConfig& cfg, int64_t M, int64_t N, double alpha, const TcOperand& A,
+                     const TcOperand& B, double* C, const OutView& ov, bool accumulate) {
+  std::vector<std::pair<int, int>> pairs;
+  slice_pairs(nslices_, pairs);
+  const int nk = (int)(A.k_pad / BK);
+  const int splits = cfg.splits, kbs = cfg.kbs;
   // accumulate the small slice products first, the leading one last
   if (splits == 1) {
     for (size_t p = pairs.size(); p-- > 0;)
       run(A, pairs[p].first, B, pairs[p].second, M, N, alpha, C, 0, ov,
-          accumulate || p + 1 != pairs.size(), 1, nk);
+          accumulate || p + 1 != pairs.size(), 1, nk, cfg.variant, cfg.nfast);
     return;
   }
   const size_t need = (size_t)splits * M * N * sizeof(double);
@@ -685,7 +788,7 @@ void TcGemm::gemm_ops(int64_t M, int64_t N, double alpha, const TcOperand& A, co
   }
   for (size_t p = pairs.size(); p-- > 0;)
     run(A, pairs[p].first, B, pairs[p].second, M, N, alpha, part_, M * N, OutView::dense(N),
-        p + 1 != pairs.size(), splits, kbs);
+        p + 1 != pairs.size(), splits, kbs, cfg.variant, cfg.nfast);
   const int64_t n = M * N;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16));
   k_sum_splits<<<grid, 256, 0, st_>>>(M, N, splits, part_, C, ov, accumulate ? 1 : 0);

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "backend.h"
+#include "tc_tune.h"
 
 namespace sccsd {
 
@@ -42,9 +43,15 @@ class TcGemm {
                        const TcOperand& B, double* C, bool check = true);
   void check_error();
   // C (= or +=) alpha * A B^T for operands already in slice form; C through
-  // the output view ov. Small output grids split K over extra CTAs.
+  // the output view ov. Small output grids split K over extra CTAs. The launch
+  // shape comes from the process-wide tuning table, else from the fixed rule
+  // (and is timed and recorded first when tuning is on).
   void gemm_ops(int64_t M, int64_t N, double alpha, const TcOperand& A, const TcOperand& B,
                 double* C, const OutView& ov, bool accumulate);
+  // the same with an explicit launch shape
+  void execute(const TcConfig& cfg, int64_t M, int64_t N, double alpha, const TcOperand& A,
+               const TcOperand& B, double* C, const OutView& ov, bool accumulate);
+  void set_tune(bool on) { tune_ = on; }
   void release(TcOperand& op);
   int slices() const { return nslices_; }
   void set_precision(int precision) { nslices_ = precision == 1 ? 2 : 1; }
@@ -53,7 +60,9 @@ class TcGemm {
   void convert(const MatView& X, int64_t rows, int64_t K, TcOperand& out);
   void run(const TcOperand& A, int sa, const TcOperand& B, int sb, int64_t M, int64_t N,
            double alpha, double* C, int64_t split_stride, const OutView& ov, bool accumulate,
-           int splits, int kbs);
+           int splits, int kbs, int variant, int nfast);
+  TcConfig tune(const TcShape& s, int64_t M, int64_t N, double alpha, const TcOperand& A,
+                const TcOperand& B, const OutView& ov, const TcConfig& fallback);
   cudaStream_t st_;
   int nslices_;
   TcOperand a_tmp_, b_tmp_;
@@ -61,6 +70,9 @@ class TcGemm {
   double* part_ = nullptr;   // split-K partial results
   size_t part_bytes_ = 0;
   int* d_err_ = nullptr;
+  bool tune_ = false;
+  double* tune_buf_ = nullptr;   // scratch output of the tuning runs
+  size_t tune_bytes_ = 0;
 };
 
 }  // namespace sccsd

@@ -1,0 +1,63 @@
+"""Launch-shape tuning of the tensor-core contractions: tuned shapes give the
+same Jacobian transforms as the fixed rule (up to the FP32 order of split K
+ranges), the tuning runs leave the caller's outputs alone, and an exported
+table reproduces the tuned results bit for bit in a fresh context."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2403_01007_gb300 import binding as B
+from paper_2403_01007_gb300 import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel(a, b):
+    return float((a - b).abs().max() / b.abs().max().clamp_min(1e-300))
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16x3"])
+def test_tuned_launch_shapes_give_the_same_transforms(prec):
+    w = syn.MEDIUM
+    eps, L = syn.workload_system(w)
+    t = syn.random_vectors(w.o, w.v, 1, 191, scale=1e-3)[0]
+    R = torch.tensor(syn.random_vectors(w.o, w.v, 3, 192, normalise=True), device="cuda")
+
+    def run(tune):
+        ctx = B.Context(w.o, w.v, w.J, eps, L, precision=prec)
+        if tune:
+            ctx.set_autotune(True)
+        e, om = ctx.residual(t)
+        s = ctx.jacobian_right(R).clone()
+        l = ctx.jacobian_left(R).clone()
+        return ctx, e, om, s, l
+
+    B.autotune_clear()
+    try:
+        c0, e0, om0, s0, l0 = run(False)
+        c0.close()
+        assert B.autotune_entries() == 0          # tuning off records nothing
+
+        c1, e1, om1, s1, l1 = run(True)
+        n = B.autotune_entries()
+        assert n > 0
+        s1b = c1.jacobian_right(R)
+        assert B.autotune_entries() == n          # known shapes are not tuned again
+        assert torch.equal(s1b, s1)
+        tol = 1e-4
+        assert _rel(s1, s0) < tol and _rel(l1, l0) < tol
+        assert np.abs(om1 - om0).max() < tol * np.abs(om0).max()
+        assert abs(e1 - e0) < tol * abs(e0)
+        text = B.autotune_export()
+        c1.close()
+        assert len(text.strip().splitlines()) == n
+
+        B.autotune_clear()
+        B.autotune_import(text)
+        c2, e2, om2, s2, l2 = run(False)
+        c2.close()
+        assert B.autotune_entries() == n
+        assert torch.equal(s2, s1) and torch.equal(l2, l1)
+        assert np.array_equal(om2, om1) and e2 == e1
+    finally:
+        B.autotune_clear()

@@ -51,7 +51,7 @@ def host_lib():
     so = os.path.join(tmp, "libsccsd_hostexec.so")
     srcs = [os.path.join(CSRC, f) for f in ("graph.cpp", "ccsd_graph.cpp", "api.cpp", "model.cpp",
                                             "solvers.cpp", "multipliers.cpp", "learned_api.cpp",
-                                            "capture.cpp")]
+                                            "capture.cpp", "tc_tune.cpp")]
     srcs.append(os.path.join(ROOT, "tests", "host_executor", "host_backend.cpp"))
     # SCCSD_HOST_SANITIZE=1 builds the executor with AddressSanitizer (run the
     # tests with the sanitizer runtime preloaded) to catch out-of-range buffer use
@@ -173,4 +173,115 @@ def test_multiplier_residual_map_matches_oracle(host_lib, mult_system):
             r = ctx.multiplier_residual(state, target, u)
             ro = f(torch.tensor(u)).numpy()
             assert np.abs(r - ro).max() < 1e-11 * max(1.0, np.abs(ro).max()), target
+    ctx.close()
+
+
+# ------------------------------------------- launch-shape tuning (host part)
+
+def _default_rule(M, n_pad, nk, sm, ab, bb):
+    """The fixed launch rule of the tensor-core contraction, written out: K is
+    split only when the output tiles (128 x 256) cannot fill the SMs and there
+    are at least 8 K blocks, into ranges of at least 4 blocks; N tiles are
+    walked fastest when A is more than four times larger than B; the
+    eight-warp variant serves items of at most 4 K blocks."""
+    mt, nt = -(-M // 128), n_pad // 256
+    tiles = mt * nt
+    want = min(-(-2 * sm // tiles), nk // 4) if (tiles < sm and nk >= 8) else 1
+    if want <= 1:
+        splits, kbs = 1, nk
+    else:
+        kbs = -(-nk // want)
+        splits = -(-nk // kbs)
+    return (1 if kbs <= 4 else 0, 1 if (nt > 1 and ab > 4 * bb) else 0, splits, kbs)
+
+
+TUNE_SHAPES = [
+    (2646, 40192, 625, 152, 2688 * 40000, 40192 * 40000),   # ladder, 6 vectors, o=21 v=200
+    (100000, 256, 1, 152, 100096 * 64, 256 * 64),           # skinny, K = o
+    (126, 256, 1313, 152, 128 * 84032, 256 * 84032),        # one output tile, long K
+    (5000, 768, 11, 152, 5120 * 704, 768 * 704),            # few tiles, short K
+    (40000, 512, 2, 152, 40064 * 128, 512 * 128),           # A much larger than B
+]
+
+
+def test_autotune_candidates_follow_the_launch_rules():
+    tmp = tempfile.mkdtemp()
+    exe = os.path.join(tmp, "tc_tune_main")
+    r = subprocess.run(["g++", "-O1", "-std=c++17", "-I", CSRC, os.path.join(CSRC, "tc_tune.cpp"),
+                        os.path.join(ROOT, "tests", "host_executor", "tc_tune_main.cpp"), "-o", exe],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        pytest.skip("host toolchain unavailable: " + r.stderr[-300:])
+    args = [str(x) for s in TUNE_SHAPES for x in s]
+    out = subprocess.run([exe, *args], capture_output=True, text=True, check=True).stdout
+    blocks = out.split("\n\n")
+    for shape, block in zip(TUNE_SHAPES, blocks):
+        M, n_pad, nk = shape[:3]
+        nt = n_pad // 256
+        cands = [tuple(int(x) for x in line.split()) for line in block.strip().splitlines()]
+        assert cands[0][:4] == _default_rule(*shape), shape
+        assert all(c[4] == 1 for c in cands), shape
+        assert len(set(c[:4] for c in cands)) == len(cands), shape
+        assert any(c[2] == 1 and c[3] == nk for c in cands), shape
+        for variant, nfast, splits, kbs, _ in cands:
+            assert variant == 0 or kbs <= 4
+            assert nfast == 0 or nt > 1
+            if splits > 1:
+                assert kbs >= 4 and splits == -(-nk // kbs) and nk >= 8
+            else:
+                assert kbs == nk
+    # one output tile over 1313 K blocks: no split, half the default number of
+    # ranges (120 ranges of 11 blocks) and the default (263 ranges of 5, which
+    # is also the finest split with at least 4 blocks per range)
+    cands = [tuple(int(x) for x in l.split()) for l in blocks[2].strip().splitlines()]
+    assert {(c[2], c[3]) for c in cands} == {(1, 1313), (120, 11), (263, 5)}
+
+
+def test_autotune_table_text(host_lib):
+    B, lib = host_lib
+    B.autotune_clear(lib)
+    assert B.autotune_entries(lib) == 0
+    good = ("2646 40192 625 1 0 152 12345 0 0 1 625 5100.000\n"
+            "126 256 1313 1 1 152 99 0 0 263 5 80.500\n")
+    B.autotune_import(good, lib)
+    assert B.autotune_entries(lib) == 2
+    text = B.autotune_export(lib)
+    rows = sorted(tuple(l.split()[:11]) for l in text.strip().splitlines())
+    assert rows == sorted(tuple(l.split()[:11]) for l in good.strip().splitlines())
+    B.autotune_import(text, lib)                      # re-import is idempotent
+    assert B.autotune_entries(lib) == 2
+    bad = [
+        "126 256 1313 1 1 152 99 1 0 263 5 1.0",      # eight-warp variant with 5 K blocks
+        "126 256 1313 1 1 152 99 0 0 200 5 1.0",      # split count does not cover K
+        "126 256 1313 1 1 152 99 0 1 263 5 1.0",      # N-fastest with one N tile
+        "2646 40192 625 1 0 152 1 0 0 1 600 1.0",     # unsplit but K range != K
+        "2646 40000 625 1 0 152 1 0 0 1 625 1.0",     # N not padded to 256
+        "2646 40192 625 3 0 152 1 0 0 1 625 1.0",     # three slices
+        "1 2 3",
+        "2646 40192 625 1 0 152 1 0 0 1 625 1.0 extra",
+        "9999 256 1 1 0 152 7 1 0 1 1 2.0\n126 256 1313 1 1 152 99 0 0 200 5 1.0",
+    ]
+    for b in bad:
+        with pytest.raises(B.SccsdError) as ei:
+            B.autotune_import(b, lib)
+        assert ei.value.code == -1, b
+        assert B.autotune_entries(lib) == 2, b        # all or nothing
+    assert lib.sccsd_autotune_import(None) == -1
+    n = ctypes.c_longlong()
+    small = ctypes.create_string_buffer(3)
+    assert lib.sccsd_autotune_export(small, 3, ctypes.byref(n)) == -1
+    assert n.value == len(text) + 1
+    B.autotune_clear(lib)
+    assert B.autotune_entries(lib) == 0
+
+
+def test_set_autotune_arguments(host_lib):
+    B, lib = host_lib
+    eps = np.linspace(-1, 1, 4)
+    L = np.zeros((2, 4, 4))
+    ctx = B.Context(2, 2, 2, eps, L, lib=lib)
+    ctx.set_autotune(True)
+    ctx.set_autotune(False)
+    assert lib.sccsd_set_autotune(ctx.h, 2) == -1
+    assert lib.sccsd_set_autotune(None, 1) == -1
     ctx.close()
