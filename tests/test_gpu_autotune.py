@@ -44,7 +44,11 @@ def test_tuned_launch_shapes_give_the_same_transforms(prec):
         s1b = c1.jacobian_right(R)
         assert B.autotune_entries() == n          # known shapes are not tuned again
         assert torch.equal(s1b, s1)
-        tol = 1e-4
+        # tuned and default shapes differ only where the split of K differs:
+        # one FP32 tensor-core accumulation over all K = v^2 = 8100 products
+        # against shorter FP32 ranges summed in FP64. Each order is within
+        # about K * 2^-24 = 5e-4 of the exact sum of the same BF16 products.
+        tol = 1e-3
         assert _rel(s1, s0) < tol and _rel(l1, l0) < tol
         assert np.abs(om1 - om0).max() < tol * np.abs(om0).max()
         assert abs(e1 - e0) < tol * abs(e0)
