@@ -477,7 +477,8 @@ def main():
     ap.add_argument("--n-train", type=int, default=24)
     ap.add_argument("--n-eval", type=int, default=12)
     ap.add_argument("--autotune", action="store_true",
-                    help="with --batched: also tune the launch shapes and time again")
+                    help="tune the launch shapes in the warm-up (with --batched: time the "
+                         "fixed rule, then tune and time again)")
     ap.add_argument("--batched", action="store_true",
                     help="64 uneven instances: joined CUDA graph vs per-instance calls")
     args = ap.parse_args()
@@ -516,6 +517,9 @@ def main():
         with torch.cuda.stream(stream):
             c = B.Context(w.o, w.v, w.J, torch.tensor(eps, device=dev), torch.tensor(L, device=dev),
                           precision=prec, stream=stream.cuda_stream)
+            # with --autotune, launch shapes are tuned by the first (untimed)
+            # call of each contraction shape
+            c.set_autotune(args.autotune)
             td = torch.tensor(t, device=dev)
             c.residual(td)
         return c
@@ -527,10 +531,14 @@ def main():
         ctx.jacobian_right(R, sigma=sig)
     replicas.barrier()
     torch.cuda.synchronize()
+    tuned_before = B.autotune_entries()
     ctx.profile(True)
     with Clocks(local) as clk:
         ms = time_batches(ctx, R, sig, args.steps, stream, torch)
     lad_ms, lad_calls, lad_flops, launches = ctx.profile_read()
+    tuning = {"launch_shapes": "tuned in warm-up" if args.autotune else "fixed rule",
+              "table_entries": tuned_before,
+              "tuned_in_timed_region": B.autotune_entries() - tuned_before}
     clocks = clk.summary()
     ctx.profile(False)
     ms = replicas.max_over_ranks(ms, device=dev)
@@ -639,6 +647,7 @@ def main():
                    "precision": args.precision, "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (ladder integrals alone exceed 129 MB)"},
         "roofline": roof,
+        "autotune": tuning,
         "ladder": {"ms_per_call": lad_ms / max(lad_calls, 1), "calls": lad_calls,
                    "tflops_algorithmic": achieved},
         "gpu_launches": launches,
