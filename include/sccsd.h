@@ -175,8 +175,11 @@ int sccsd_set_precision(sccsd_ctx* ctx, int precision);
  * into a scratch buffer, so the caller's outputs are not touched. The fastest
  * shape is recorded in a table shared by all contexts of the process and used
  * by every later contraction of that shape, whether or not tuning is enabled.
- * Tune before sccsd_capture_transform, which only reads the table. No effect
- * in SCCSD_FP64 mode.
+ * Tune before sccsd_capture_transform, which only reads the table. The
+ * scratch buffer of the tuning runs (as large as the largest output tuned)
+ * is held until tuning is switched off (enable = 0) or the context is
+ * destroyed; do not switch tuning while a captured graph of the context runs.
+ * No effect in SCCSD_FP64 mode.
  * sccsd_autotune_export writes the table as text, one line per shape, into
  * buf[cap] (NUL-terminated). *len receives the bytes needed, NUL included.
  * SCCSD_EINVAL if buf is NULL or cap is too small (*len is still set).

@@ -699,6 +699,16 @@ void TcGemm::gemm_ops(int64_t M, int64_t N, double alpha, const TcOperand& A, co
   execute(cfg, M, N, alpha, A, B, C, ov, accumulate);
 }
 
+void TcGemm::set_tune(bool on) {
+  tune_ = on;
+  if (!on && tune_buf_) {
+    cudaStreamSynchronize(st_);
+    cudaFree(tune_buf_);
+    tune_buf_ = nullptr;
+    tune_bytes_ = 0;
+  }
+}
+
 TcConfig TcGemm::tune(const TcShape& s, int64_t M, int64_t N, double alpha, const TcOperand& A,
                       const TcOperand& B, const OutView& ov, const TcConfig& fallback) {
   const int64_t span = view_span(ov, M, N);

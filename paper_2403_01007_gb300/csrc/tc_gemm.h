@@ -51,7 +51,8 @@ class TcGemm {
   // the same with an explicit launch shape
   void execute(const TcConfig& cfg, int64_t M, int64_t N, double alpha, const TcOperand& A,
                const TcOperand& B, double* C, const OutView& ov, bool accumulate);
-  void set_tune(bool on) { tune_ = on; }
+  // tuning off also frees the scratch output of the tuning runs
+  void set_tune(bool on);
   void release(TcOperand& op);
   int slices() const { return nslices_; }
   void set_precision(int precision) { nslices_ = precision == 1 ? 2 : 1; }
