@@ -131,3 +131,19 @@ def batch_instances(count: int = 64, config: int = 4, o_range=(4, 12), v_range=(
 def random_scalars(count: int, seed: int) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.normal(0.0, 1.0, size=count)
+
+
+def symmetric_system(o: int, v: int, J: int, sd: float, seed: int, irrep_occ, irrep_vir,
+                     irrep_chol=None):
+    """A system of system(o, v, J, sd, seed) with a two-irrep (C_s-like)
+    symmetry imposed: orbital p carries the label s_p in {0, 1}
+    (irrep_occ + irrep_vir), Cholesky vector J the label s_J (irrep_chol,
+    default alternating 0, 1, 0, ...), and L^J_pq is set to zero unless
+    s_p XOR s_q = s_J. Returns (eps, L, s_orb, s_chol)."""
+    eps, L = system(o, v, J, sd, seed)
+    s_orb = np.array(list(irrep_occ) + list(irrep_vir), dtype=np.int64)
+    if s_orb.size != o + v or not np.all((s_orb == 0) | (s_orb == 1)):
+        raise ValueError("one label 0 or 1 per orbital")
+    s_chol = np.arange(J) % 2 if irrep_chol is None else np.asarray(irrep_chol, dtype=np.int64)
+    keep = (s_orb[None, :, None] ^ s_orb[None, None, :]) == s_chol[:, None, None]
+    return eps, np.where(keep, L, 0.0), s_orb, s_chol

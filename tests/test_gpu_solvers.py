@@ -92,3 +92,45 @@ def test_scc_self_consistent_small():
     assert abs(Oo) < 1e-8
     assert abs(r["zeta"]) > 0.1        # the constraint is active on this system
     ctx.close()
+
+
+def _golden(name):
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)) as f:
+        return json.load(f)
+
+
+def test_two_electron_full_ci_golden():
+    """Two electrons: CCSD is exact, so the converged correlation energy and the
+    eigenvalues of the Jacobian assembled column by column through the C ABI
+    are the stored full-CI values (Sec. 2.1)."""
+    from paper_2403_01007_gb300 import binding as B
+    g = _golden("fci_two_electron_o1_v5.json")
+    p = g["inputs"]
+    eps, L = syn.system(p["o"], p["v"], p["J"], p["sd"], p["seed"])
+    ctx = B.Context(p["o"], p["v"], p["J"], eps, L)
+    e, t, it = ctx.solve_ground(tol=1e-12, maxit=200)
+    assert abs(e - g["values"]["e_corr"]) < 1e-10
+    E = np.eye(ctx.dim)
+    A = ctx.jacobian_right(E).T          # column k = A e_k
+    w = np.sort(np.linalg.eigvals(A).real)
+    ref = np.array(g["values"]["excitation_energies"])
+    assert np.abs(w - ref).max() < 1e-9
+    ctx.close()
+
+
+def test_scc_states_of_different_symmetry_golden():
+    """Two states of different symmetry: the GPU SCC loop stays at zeta = 0 and
+    gives the CCSD energies (Sec. 3.1.1; stored values)."""
+    from paper_2403_01007_gb300 import binding as B
+    g = _golden("scc_symmetric_o3_v6.json")
+    p = g["inputs"]
+    eps, L, _, _ = syn.symmetric_system(p["o"], p["v"], p["J"], p["sd"], p["seed"],
+                                        p["irrep_occ"], p["irrep_vir"])
+    ctx = B.Context(p["o"], p["v"], p["J"], eps, L)
+    r = ctx.solve_scc(tol=1e-10)
+    assert abs(r["zeta"]) < 1e-10
+    assert np.abs(r["omega"] - np.array(g["values"]["omega"])).max() < 1e-8
+    assert abs(r["e_corr"] - g["values"]["e_corr"]) < 1e-9
+    ctx.close()

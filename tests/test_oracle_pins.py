@@ -6,7 +6,9 @@
 * closed forms: the MP2 first iterate and energy, the HF energy, the
   commutation relations of the singlet excitation operators;
 * exact identities: a 7-point central stencil is exact for the quartic
-  polynomial Omega(t + e R); <L|A R> = <A^T L|R>; density sum rules.
+  polynomial Omega(t + e R); <L|A R> = <A^T L|R>; density sum rules;
+* symmetry: with two states of different symmetry the similarity constraint
+  holds at zeta = 0 and SCCSD is CCSD (Sec. 3.1.1).
 """
 import numpy as np
 import pytest
@@ -258,3 +260,58 @@ def test_zeta_zero_is_ccsd(small):
     _, O = rp.residual(prob, t)
     _, Oz = rp.residual(prob, t, scc=(0.0, torch.tensor(Ra), torch.tensor(Rb)))
     assert torch.abs(O - Oz).max() == 0.0
+
+
+# ------------------------------------------------------------------ symmetry
+
+SYM_OCC, SYM_VIR = [0, 1, 0], [0, 1, 0, 1, 0, 1]
+
+
+def irrep_weights(x, o, v):
+    """Fraction of |x|^2 on the components of each irrep (0, 1): a singles
+    component a<-i has irrep s_a XOR s_i, a doubles component the XOR of its
+    two pairs."""
+    t1, t2 = cc.unpack(x, o, v)
+    so, sv_ = np.array(SYM_OCC), np.array(SYM_VIR)
+    g1 = sv_[:, None] ^ so[None, :]
+    g2 = g1[:, :, None, None] ^ g1[None, None, :, :]
+    a1, a2 = t1.numpy(), t2.numpy()
+    w = np.array([(a1[g1 == k] ** 2).sum() + (a2[g2 == k] ** 2).sum() for k in (0, 1)])
+    return w / w.sum()
+
+
+def test_states_of_different_symmetry_need_no_constraint():
+    """Where the two intersecting states differ in symmetry, the SCC correction
+    vanishes and the method reduces to CCSD (Sec. 3.1.1, the planar
+    intersection of formaldimine). In a two-irrep system: the ground state is
+    totally symmetric, the two lowest roots lie in different irreps, O_ab
+    vanishes at zeta = 0, and the SCC loop returns zeta = 0 with the CCSD
+    energies. Contrast: in the same construction with a seed whose two lowest
+    roots share an irrep, O_ab(0) is far from zero, so the loop must move zeta."""
+    o, v, J = 3, 6, 18
+
+    def ccsd_pair(seed):
+        eps, L, _, _ = syn.symmetric_system(o, v, J, 0.2, seed, SYM_OCC, SYM_VIR)
+        prob = cc.Problem(eps, L, o)
+        x, E0, _ = sv.ground_state(prob, tol=1e-12)
+        w, X = sv.eom_dense(prob, x, 2, side="right")
+        Xa, Xb = sc.fix_sign(X[0]), sc.fix_sign(X[1])
+        eta = rp.eta(prob, x).numpy()
+        r0a, r0b = float(eta @ Xa / w[0]), float(eta @ Xb / w[1])
+        O = float(sc.overlap(torch.tensor(x), r0a, torch.tensor(Xa), r0b, torch.tensor(Xb), o, v))
+        return prob, x, E0, w, (Xa, Xb), O
+
+    prob, x, E0, w, (Xa, Xb), O = ccsd_pair(1007)
+    assert irrep_weights(x, o, v)[1] < 1e-24
+    wa, wb = irrep_weights(Xa, o, v), irrep_weights(Xb, o, v)
+    assert {int(np.argmax(wa)), int(np.argmax(wb))} == {0, 1}
+    assert max(wa.min(), wb.min()) < 1e-24
+    assert abs(O) < 1e-13
+    s = sc.solve_scc(prob, tol=1e-12, ground_tol=1e-12, dense=True)
+    assert abs(s["zeta"]) < 1e-12
+    assert np.allclose(s["omega"], w, rtol=0, atol=1e-11)
+    assert abs(s["E0"] - E0) < 1e-11
+
+    _, _, _, _, (Ya, Yb), O_same = ccsd_pair(1000)
+    assert np.argmax(irrep_weights(Ya, o, v)) == np.argmax(irrep_weights(Yb, o, v))
+    assert abs(O_same) > 1e-3
