@@ -14,7 +14,10 @@ Hartree-Fock reference):
 * Cholesky-factored two-electron integrals g_pqrs = sum_J L^J_pq L^J_rs with
   L^J symmetric in pq and the upper-triangle entries ~ N(0, sd^2);
 * amplitude-like vectors (t, R, L) drawn N(0, 1) in the packed layout and
-  scaled or normalised by the caller.
+  scaled or normalised by the caller;
+* symmetric variant: the same draws with entries L^J_pq set to zero where the
+  orbital labels s_p, s_q in {0, 1} and the vector's label s_J break
+  s_p XOR s_q = s_J (a two-irrep point group).
 
 Seeds follow  seed = 240301007 * 100 + config * 10 + instance,  drawn with
 NumPy's PCG64 in the order eps_occ, eps_vir, L (upper triangle, J-major).
