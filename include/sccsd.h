@@ -77,11 +77,14 @@ int sccsd_residual(sccsd_ctx* ctx, const double* t, double zeta, const double* R
 /* sigma_k = A R_k for nvec packed kets R[nvec][dim], with
  * A_mu,nu = <mu~|[Hbar, tau_nu]|HF> (Sec. 2.3.3), at the state fixed by the
  * last sccsd_residual call (SCC terms included when it had them).
- * Also returns eta.R_k in etaR[nvec] when etaR is non-NULL (eta of Sec. 2.3.3). */
+ * Also returns eta.R_k in etaR[nvec] when etaR is non-NULL (eta of Sec. 2.3.3).
+ * nvec = 0 does nothing and returns SCCSD_OK (R and sigma may then be NULL);
+ * nvec < 0 is SCCSD_EINVAL. */
 int sccsd_jacobian_right(sccsd_ctx* ctx, int nvec, const double* R, double* sigma,
                          double* etaR);
 
-/* sigma_k = A^T L_k (the left transformation) for nvec packed bras. */
+/* sigma_k = A^T L_k (the left transformation) for nvec packed bras; nvec = 0
+ * does nothing (L and sigma may be NULL). */
 int sccsd_jacobian_left(sccsd_ctx* ctx, int nvec, const double* L, double* sigma);
 
 /* One- and two-particle (transition) densities of Sec. 2.3.2 for the bra

@@ -253,3 +253,30 @@ def test_full_size_bench_configuration(B):
         assert abs(a - b) < 1e-11 * scale
     # every row of the batch is a finite, non-trivial transform
     assert np.all(np.isfinite(out["bf16"])) and np.all(np.linalg.norm(out["bf16"], axis=1) > 0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16"])
+def test_transform_edge_cases(B, precision):
+    """Empty batches are no-ops; zero vectors give exact zeros in both modes
+    (the BF16 split of zero is zero, and A R is linear in R, Sec. 2.1); in
+    FP64 the transforms are linear to rounding. Ragged o=7, v=37."""
+    o, v, J = 7, 37, 41
+    eps, L = syn.system(o, v, J, 0.05, 778)
+    ctx = B.Context(o, v, J, eps, L, precision=precision)
+    ctx.residual(syn.random_vectors(o, v, 1, 779, scale=0.02)[0])
+    lib = ctx.lib
+    assert lib.sccsd_jacobian_right(ctx.h, 0, None, None, None) == 0
+    assert lib.sccsd_jacobian_left(ctx.h, 0, None, None) == 0
+    Z = torch.zeros(3, ctx.dim, dtype=torch.float64, device="cuda:0")
+    s, eta = ctx.jacobian_right(Z, with_eta=True)
+    assert not s.any() and not np.any(eta)
+    assert not ctx.jacobian_left(Z).any()
+    if precision == "fp64":
+        R1, R2 = syn.random_vectors(o, v, 2, 780, normalise=True)
+        a, b = 0.7, -1.9
+        X = dev(np.stack([R1, R2, a * R1 + b * R2]))
+        s = ctx.jacobian_right(X).cpu().numpy()
+        sl = ctx.jacobian_left(X).cpu().numpy()
+        for y in (s, sl):
+            assert np.abs(y[2] - (a * y[0] + b * y[1])).max() < 1e-12 * np.abs(y).max()
+    ctx.close()

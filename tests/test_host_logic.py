@@ -285,3 +285,29 @@ def test_set_autotune_arguments(host_lib):
     assert lib.sccsd_set_autotune(ctx.h, 2) == -1
     assert lib.sccsd_set_autotune(None, 1) == -1
     ctx.close()
+
+
+def test_transform_edge_cases(host_lib):
+    """Empty batches, zero vectors and linearity of the Jacobian transforms
+    through the C ABI (A R is linear in R, Sec. 2.1)."""
+    B, lib = host_lib
+    o, v, J = 2, 3, 6
+    eps, L = syn.system(o, v, J, 0.3, 91)
+    ctx = B.Context(o, v, J, eps, L, lib=lib)
+    t = syn.random_vectors(o, v, 1, 92, scale=0.1)[0]
+    ctx.residual(t)
+    assert lib.sccsd_jacobian_right(ctx.h, 0, None, None, None) == 0
+    assert lib.sccsd_jacobian_left(ctx.h, 0, None, None) == 0
+    assert lib.sccsd_jacobian_right(ctx.h, -1, None, None, None) == -1
+    assert lib.sccsd_jacobian_left(ctx.h, -1, None, None) == -1
+    Z = np.zeros((2, ctx.dim))
+    s, eta = ctx.jacobian_right(Z, with_eta=True)
+    assert not s.any() and not np.any(eta)
+    assert not ctx.jacobian_left(Z).any()
+    R1, R2 = syn.random_vectors(o, v, 2, 93, normalise=True)
+    a, b = 0.7, -1.9
+    s = ctx.jacobian_right(np.stack([R1, R2, a * R1 + b * R2]))
+    assert np.abs(s[2] - (a * s[0] + b * s[1])).max() < 1e-13
+    sl = ctx.jacobian_left(np.stack([R1, R2, a * R1 + b * R2]))
+    assert np.abs(sl[2] - (a * sl[0] + b * sl[1])).max() < 1e-13
+    ctx.close()
