@@ -212,24 +212,33 @@ def kernel_case(args):
 def batched_case(args):
     """64 uneven instances (o in [4,12], v in [30,110], J = 3(o+v), 2-5 states
     each): one batch of right transformations per instance and step, either as
-    per-instance calls or as one launch of the joined CUDA graph."""
+    per-instance calls or as one launch of the joined CUDA graph. Under
+    torchrun the instances are dealt round-robin to the ranks (no data-path
+    collective); times are the slowest rank's and the rate counts all."""
     import torch
+    import torch.distributed as dist
     from paper_2403_01007_gb300 import binding as B
+    from paper_2403_01007_gb300 import replicas
+    rank, world, local = replicas.rank_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
     inst = syn.batch_instances()
-    torch.cuda.set_device(0)
+    mine = replicas.shard(inst, rank, world)
     items = []
     t_setup = time.perf_counter()
-    for k, x in enumerate(inst):
+    for x in mine:
         eps, L = syn.system(x.o, x.v, x.J, x.sd, x.seed)
-        st = torch.cuda.Stream()
+        st = torch.cuda.Stream(device=dev)
         ctx = B.Context(x.o, x.v, x.J, eps, L, precision=args.precision, stream=st.cuda_stream)
         t = syn.random_vectors(x.o, x.v, 1, x.seed + 1000, scale=1e-2)[0]
         ctx.residual(t)
         R = torch.tensor(syn.random_vectors(x.o, x.v, x.nstates, x.seed + 2000, normalise=True),
-                         device="cuda")
+                         device=dev)
         items.append((ctx, R, torch.empty_like(R), torch.empty_like(R)))
-    setup_s = time.perf_counter() - t_setup
-    ntr = sum(x.nstates for x in inst)
+    setup_s = replicas.max_over_ranks(time.perf_counter() - t_setup, device=dev)
+    ntr = sum(x.nstates for x in inst)            # all ranks together
     flops = sum(x.nstates * transform_flops(x.o, x.v) for x in inst)
 
     def per_instance():
@@ -241,27 +250,30 @@ def batched_case(args):
         for _ in range(args.warmup):
             per_instance()
         torch.cuda.synchronize()
+        replicas.barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             per_instance()
         torch.cuda.synchronize()
-        per_s = (time.perf_counter() - t0) / args.steps
+        per_s = replicas.max_over_ranks((time.perf_counter() - t0) / args.steps, device=dev)
         graphs = [ctx.capture_transform(R, Wg) for ctx, R, _, Wg in items]
         batch = B.GraphBatch(graphs)
-        st = torch.cuda.Stream()
+        st = torch.cuda.Stream(device=dev)
         for _ in range(args.warmup):
             batch.launch(st.cuda_stream)
         torch.cuda.synchronize()
+        replicas.barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        with Clocks(0) as clk:
+        with Clocks(local) as clk:
             e0.record(st)
             for _ in range(args.steps):
                 batch.launch(st.cuda_stream)
             e1.record(st)
             torch.cuda.synchronize()
-        g_s = e0.elapsed_time(e1) / 1e3 / args.steps
-        rel = max(float((Wg - W).abs().max() / W.abs().max()) for _, _, W, Wg in items)
+        g_s = replicas.max_over_ranks(e0.elapsed_time(e1) / 1e3 / args.steps, device=dev)
+        rel = replicas.max_over_ranks(
+            max(float((Wg - W).abs().max() / W.abs().max()) for _, _, W, Wg in items), device=dev)
         batch.close()
         return per_s, g_s, rel, clk.summary()
 
@@ -277,7 +289,7 @@ def batched_case(args):
         t0 = time.perf_counter()
         per_instance()
         torch.cuda.synchronize()
-        tune_s = time.perf_counter() - t0
+        tune_s = replicas.max_over_ranks(time.perf_counter() - t0, device=dev)
         for ctx, *_ in items:
             ctx.set_autotune(False)
         per_s, g_s, rel, clocks = measure()
@@ -288,15 +300,21 @@ def batched_case(args):
                            "calls_transforms_per_s": ntr / per_s}}
     for ctx, *_ in items:
         ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
     print(json.dumps({
         "metric": "Jacobian transforms/s, 64 uneven instances (o 4-12, v 30-110, 2-5 states)",
-        "value": ntr / g_s, "unit": "transforms/s", "n_gpus": 1, "steps": args.steps,
+        "value": ntr / g_s, "unit": "transforms/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": g_s * 1e3, "higher_is_better": True,
         "dtype": {"bf16x3": "bf16x3->f32->f64", "bf16": "bf16->f32->f64", "fp64": "f64"}[args.precision],
         "data": "synthetic",
         "config": {"workload": "batch64_o4-12_v30-110", "instances": len(inst), "transforms": ntr,
                    "precision": args.precision, "form": "one launch of the joined CUDA graph",
-                   "launch_shapes": "tuned" if args.autotune else "fixed rule"},
+                   "launch_shapes": "tuned" if args.autotune else "fixed rule",
+                   "parallelism": f"instances dealt round-robin to {world} rank(s)"},
+        "scaling": "strong",
         "per_instance_calls": {"transforms_per_s": ntr / per_s, "ms_per_step": per_s * 1e3},
         "graph_speedup": per_s / g_s,
         "tflops_dense": flops / g_s / 1e12,

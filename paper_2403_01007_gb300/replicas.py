@@ -1,10 +1,10 @@
-"""Replicas on several GPUs of one node: one process per GPU, each working on
-its own seeded instance of the workload.
+"""Several GPUs of one node: one process per GPU. A single system is run as
+replicas (each rank its own seeded instance); a batch of independent systems
+is dealt out across the ranks.
 
-The hot path does not shard (every instance is an independent problem), so
-ranks exchange nothing on the data path; the only collectives are the barrier
-around the timed region and the maximum of the elapsed times, from which the
-whole-job throughput is formed.
+Instances are independent problems, so ranks exchange nothing on the data
+path; the only collectives are the barrier around the timed region and the
+maximum of the elapsed times, from which the whole-job throughput is formed.
 """
 from __future__ import annotations
 
@@ -20,6 +20,14 @@ def rank_env():
 def instance_of(rank: int) -> int:
     """Seed instance of the workload handled by a rank (distinct per rank)."""
     return rank
+
+
+def shard(items, rank: int, world: int):
+    """The items of one rank when independent problems are dealt round-robin
+    (item k to rank k mod world): disjoint, and together all items."""
+    if not (0 <= rank < world):
+        raise ValueError("rank out of range")
+    return list(items)[rank::world]
 
 
 def barrier():

@@ -1,6 +1,7 @@
-"""Host logic of the multi-GPU replica run, on two CPU ranks over gloo.
+"""Host logic of the multi-GPU runs, on two CPU ranks over gloo.
 
-Each rank works on its own seeded instance; the ranks meet only at the barrier
+Each rank works on its own seeded instance (replicas of one system) or on its
+round-robin share of a batch of systems; the ranks meet only at the barrier
 around the timed region and in the maximum of the elapsed times, from which
 rank 0 forms the whole-job rate.
 """
@@ -36,8 +37,16 @@ def _rank_main(rank, port, out):
         ms = 10.0 + 5.0 * r                      # rank 1 is the slow one
         ms_max = replicas.max_over_ranks(ms)
         rate = replicas.whole_job_rate(4 * 6, w, ms_max)
+        # a batch of independent systems dealt to the ranks
+        import torch
+        mine = replicas.shard(syn.batch_instances(), r, w)
+        n = torch.tensor([float(sum(x.nstates for x in mine)), float(len(mine))],
+                         dtype=torch.float64)
+        dist.all_reduce(n)
+        seeds = sorted(x.seed for x in mine)
         replicas.barrier()
-        out.put((r, w, local, inst, float(np.sum(eps)), float(np.sum(L[:3])), ms_max, rate))
+        out.put((r, w, local, inst, float(np.sum(eps)), float(np.sum(L[:3])), ms_max, rate,
+                 n.tolist(), seeds))
     finally:
         dist.destroy_process_group()
 
@@ -63,6 +72,14 @@ def test_two_gloo_ranks_replica_logic():
     assert all(x[6] == 15.0 for x in res)
     expect = WORLD * 24 / 0.015
     assert all(x[7] == pytest.approx(expect) for x in res)
+    # the shards of the batch are disjoint and together the whole batch
+    from paper_2403_01007_gb300 import synthetic as syn
+    batch = syn.batch_instances()
+    total = [float(sum(x.nstates for x in batch)), float(len(batch))]
+    assert all(x[8] == total for x in res)
+    s0, s1 = set(res[0][9]), set(res[1][9])
+    assert not (s0 & s1) and (s0 | s1) == {x.seed for x in batch}
+    assert abs(len(s0) - len(s1)) <= 1
 
 
 def test_single_rank_defaults(monkeypatch):
@@ -72,3 +89,14 @@ def test_single_rank_defaults(monkeypatch):
     assert replicas.rank_env() == (0, 1, 0)
     assert replicas.max_over_ranks(3.5) == 3.5
     assert replicas.whole_job_rate(10, 1, 500.0) == pytest.approx(20.0)
+
+
+def test_shard_rules():
+    from paper_2403_01007_gb300 import replicas
+    items = list(range(11))
+    parts = [replicas.shard(items, r, 4) for r in range(4)]
+    assert sorted(sum(parts, [])) == items
+    assert [len(p) for p in parts] == [3, 3, 3, 2]
+    assert replicas.shard(items, 0, 1) == items
+    with pytest.raises(ValueError):
+        replicas.shard(items, 4, 4)
