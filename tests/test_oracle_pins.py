@@ -315,3 +315,38 @@ def test_states_of_different_symmetry_need_no_constraint():
     _, _, _, _, (Ya, Yb), O_same = ccsd_pair(1000)
     assert np.argmax(irrep_weights(Ya, o, v)) == np.argmax(irrep_weights(Yb, o, v))
     assert abs(O_same) > 1e-3
+
+
+# -------------------------------------------------------------- eigensolvers
+
+def test_dense_roots_are_full_ci_for_two_electrons():
+    """The dense EOM roots (explicit Jacobian assembled column by column,
+    then a library eigendecomposition) are all the FCI excitation energies
+    for two electrons."""
+    o, v, J = 1, 4, 5
+    eps, L, system, prob = tiny_system(o, v, J, seed=4, sd=0.25)
+    x, E0, _ = sv.ground_state(prob, tol=1e-12)
+    M = system.hbar_matrix(np.zeros(system.S.packed_dim))
+    fci = np.sort(np.linalg.eigvals(M).real)
+    w, _ = sv.eom_dense(prob, x, prob.dim, side="right")
+    assert np.abs(w - (fci[1:] - fci[0])).max() < 1e-9
+    wl, _ = sv.eom_dense(prob, x, prob.dim, side="left")
+    assert np.abs(wl - w).max() < 1e-9
+
+
+@pytest.mark.parametrize("side", ["right", "left"])
+def test_davidson_finds_the_lowest_dense_roots(side):
+    """The oracle's Davidson returns the nroots lowest eigenvalues of the
+    explicit Jacobian, with vectors that satisfy A X = w X (right) or
+    A^T X = w X (left) to the requested tolerance."""
+    o, v, J = 3, 4, 9
+    eps, L = syn.system(o, v, J, 0.2, 55)
+    prob = cc.Problem(eps, L, o)
+    x, _, _ = sv.ground_state(prob, tol=1e-12)
+    wd, _ = sv.eom_dense(prob, x, 4, side=side)
+    w, X = sv.eom(prob, x, 4, side=side, tol=1e-9)
+    assert np.abs(w - wd).max() < 1e-8
+    op = rp.jacobian_right if side == "right" else rp.jacobian_left
+    for k in range(4):
+        r = op(prob, x, X[k]).numpy() - w[k] * X[k]
+        assert np.linalg.norm(r) < 1e-8
