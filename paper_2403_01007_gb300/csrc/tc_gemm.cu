@@ -726,12 +726,18 @@ TcConfig TcGemm::tune(const TcShape& s, int64_t M, int64_t N, double alpha, cons
   }
   const int64_t mt = (M + BM - 1) / BM, nt = B.rows_pad / BN;
   const double abytes = (double)A.rows_pad * A.k_pad, bbytes = (double)B.rows_pad * B.k_pad;
-  cudaEvent_t e0, e1;
-  if (cudaEventCreate(&e0) != cudaSuccess) return fallback;
-  if (cudaEventCreate(&e1) != cudaSuccess) {
-    cudaEventDestroy(e0);
+  struct Events {   // destroyed on every exit, including a CUDA error thrown below
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~Events() {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } ev;
+  if (cudaEventCreate(&ev.a) != cudaSuccess || cudaEventCreate(&ev.b) != cudaSuccess) {
+    cudaGetLastError();
     return fallback;
   }
+  cudaEvent_t e0 = ev.a, e1 = ev.b;
   TcConfig best = fallback;
   double best_us = 1e300;
   const int reps = 3;
@@ -758,8 +764,6 @@ TcConfig TcGemm::tune(const TcShape& s, int64_t M, int64_t N, double alpha, cons
       best = c;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   check_error();
   TcTuneTable::global().put(s, best, best_us);
   return best;
@@ -800,7 +804,7 @@ void TcGemm::execute(const TcConfig& cfg, int64_t M, int64_t N, double alpha, co
     run(A, pairs[p].first, B, pairs[p].second, M, N, alpha, part_, M * N, OutView::dense(N),
         p + 1 != pairs.size(), splits, kbs, cfg.variant, cfg.nfast);
   const int64_t n = M * N;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sm_count_ * 16));
   k_sum_splits<<<grid, 256, 0, st_>>>(M, N, splits, part_, C, ov, accumulate ? 1 : 0);
   count_launch();
   cudaError_t e = cudaGetLastError();
