@@ -67,3 +67,40 @@ def test_tuned_launch_shapes_give_the_same_transforms(prec):
         assert np.array_equal(om2, om1) and e2 == e1
     finally:
         B.autotune_clear()
+
+
+def test_captured_graphs_use_the_tuned_shapes():
+    """Uneven instances tuned by one uncaptured call each, then captured and
+    joined into one launch: the graph reads the table (no tuning, no buffer
+    growth while capturing) and equals the per-instance calls bit for bit."""
+    B.autotune_clear()
+    items = []
+    try:
+        for k, (o, v) in enumerate([(3, 20), (4, 27), (5, 33)]):
+            J = 3 * (o + v)
+            eps, L = syn.system(o, v, J, 0.05, 4100 + k)
+            st = torch.cuda.Stream()
+            ctx = B.Context(o, v, J, eps, L, precision="bf16", stream=st.cuda_stream)
+            ctx.set_autotune(True)
+            ctx.residual(syn.random_vectors(o, v, 1, 4200 + k, scale=0.02)[0])
+            R = torch.tensor(syn.random_vectors(o, v, 3, 4300 + k, normalise=True), device="cuda")
+            W = torch.empty_like(R)
+            ref = ctx.jacobian_right(R).clone()          # tunes this instance's shapes
+            ctx.set_autotune(False)
+            items.append((ctx, R, W, ref))
+        n = B.autotune_entries()
+        assert n > 0
+        batch = B.GraphBatch([ctx.capture_transform(R, W) for ctx, R, W, _ in items])
+        try:
+            s = torch.cuda.Stream()
+            batch.launch(s.cuda_stream)
+            torch.cuda.synchronize()
+        finally:
+            batch.close()
+        assert B.autotune_entries() == n
+        for ctx, R, W, ref in items:
+            assert torch.equal(W, ref)
+    finally:
+        for ctx, *_ in items:
+            ctx.close()
+        B.autotune_clear()
