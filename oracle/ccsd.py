@@ -45,6 +45,8 @@ DT = torch.float64
 # --------------------------------------------------------------------------
 
 def pack(t1: torch.Tensor, t2: torch.Tensor) -> torch.Tensor:
+    """Packed layout of (t1[a][i], t2[a][i][b][j]): singles at a*o + i, then each doubles pair (ai)
+    <= (bj) once (the singles and doubles manifold of Sec. 2.1, with t_ij^ab = t_ji^ba)."""
     v, o = t1.shape
     ov = o * v
     M = t2.reshape(ov, ov)
@@ -53,6 +55,7 @@ def pack(t1: torch.Tensor, t2: torch.Tensor) -> torch.Tensor:
 
 
 def unpack(x, o: int, v: int):
+    """Inverse of pack: (t1[a][i], t2[a][i][b][j]) from the packed layout (Sec. 2.1)."""
     x = torch.as_tensor(x, dtype=DT)
     ov = o * v
     t1 = x[:ov].reshape(v, o)
@@ -65,7 +68,8 @@ def unpack(x, o: int, v: int):
 
 def bra_full(l2_packed_as_full: torch.Tensor) -> torch.Tensor:
     """Weights so that sum_packed L X = sum_full W X for symmetric X:
-    off-diagonal pairs count 1/2 each (they appear twice), diagonal 1."""
+    off-diagonal pairs count 1/2 each (they appear twice), diagonal 1.
+    Biorthonormal bras <mu~| of Sec. 2.1."""
     v, o = l2_packed_as_full.shape[0], l2_packed_as_full.shape[1]
     ov = o * v
     W = 0.5 * l2_packed_as_full.reshape(ov, ov).clone()
@@ -79,7 +83,9 @@ def bra_full(l2_packed_as_full: torch.Tensor) -> torch.Tensor:
 # --------------------------------------------------------------------------
 
 def one_electron(eps: torch.Tensor, L: torch.Tensor, o: int) -> torch.Tensor:
-    """h_pq = eps_p d_pq - sum_k (2 g_pqkk - g_pkkq), so that F = diag(eps)."""
+    """h_pq = eps_p d_pq - sum_k (2 g_pqkk - g_pkkq), so that F = diag(eps).
+    The Hamiltonian in h and g is that of Sec. 2.3.2; F = diag(eps) makes the reference canonical
+    Hartree-Fock, as the orbital conditions of Sec. 2.3.1 assume."""
     h = torch.diag(eps).clone()
     Lkk = torch.einsum("Jkk->J", L[:, :o, :o])
     h = h - 2.0 * torch.einsum("Jpq,J->pq", L, Lkk)
@@ -88,6 +94,8 @@ def one_electron(eps: torch.Tensor, L: torch.Tensor, o: int) -> torch.Tensor:
 
 
 def t1_matrix(t1: torch.Tensor, n: int) -> torch.Tensor:
+    """The singles amplitudes as an n x n matrix X[o + a][i] = t_ai, so that the T1 dressing
+    exp(-T1) H exp(T1) of Sec. 2.4.2 transforms the integrals as (1 - X) h (1 + X)."""
     v, o = t1.shape
     X = torch.zeros(n, n, dtype=DT)
     X = torch.cat([torch.zeros(o, n, dtype=DT),
@@ -107,7 +115,8 @@ def dress(h: torch.Tensor, L: torch.Tensor, t1: torch.Tensor):
 
 
 def fock(hh: torch.Tensor, Lh: torch.Tensor, o: int) -> torch.Tensor:
-    """F_pq = h_pq + sum_k (2 g_pqkk - g_pkkq) from (dressed) integrals."""
+    """F_pq = h_pq + sum_k (2 g_pqkk - g_pkkq) from (dressed) integrals.
+    Integrals of Sec. 2.3.2, T1-dressed as in Sec. 2.4.2."""
     Lkk = torch.einsum("Jkk->J", Lh[:, :o, :o])
     return (hh + 2.0 * torch.einsum("Jpq,J->pq", Lh, Lkk)
             - torch.einsum("Jpk,Jkq->pq", Lh[:, :, :o], Lh[:, :o, :]))
@@ -132,7 +141,8 @@ class Blocks:
 # --------------------------------------------------------------------------
 
 def ccsd_energy_residual(t1, t2, h, L, o):
-    """Return (E0, Omega1[a,i], Omega2[a,i,b,j]) of closed-shell CCSD."""
+    """Return (E0, Omega1[a,i], Omega2[a,i,b,j]) of closed-shell CCSD.
+    E0 and Omega_mu = <mu~|Hbar|HF> of Sec. 2.1, in the T1-dressed closed-shell form (Sec. 2.4.2)."""
     hh, Lh = dress(h, L, t1)
     F = fock(hh, Lh, o)
     g = Blocks(Lh, o)
@@ -195,6 +205,7 @@ class Problem:
 
     @property
     def dim(self) -> int:
+        """Size of the packed singles and doubles manifold (Sec. 2.1)."""
         ov = self.o * self.v
         return ov + ov * (ov + 1) // 2
 

@@ -41,7 +41,8 @@ import scipy.sparse as sp
 # --------------------------------------------------------------------------
 
 def packed_pairs(ov: int):
-    """List of (P, Q) with P <= Q in packed order."""
+    """List of (P, Q) with P <= Q in packed order.
+    The doubles of Sec. 2.1, each pair once."""
     out = []
     for Q in range(ov):
         for P in range(Q + 1):
@@ -81,7 +82,8 @@ class Space:
         return sign, s2 | (1 << p)
 
     def E(self, p: int, q: int) -> sp.csr_matrix:
-        """Singlet excitation operator E_pq = a+_pa a_qa + a+_pb a_qb."""
+        """Singlet excitation operator E_pq = a+_pa a_qa + a+_pb a_qb.
+        The operators of the Hamiltonian of Sec. 2.3.2 and of the excitations of Sec. 2.1."""
         key = (p, q)
         if key in self._E:
             return self._E[key]
@@ -145,21 +147,25 @@ class Space:
 
     @property
     def packed_dim(self):
+        """Size of the packed singles and doubles manifold (Sec. 2.1)."""
         ov = self.o * self.v
         return ov + ov * (ov + 1) // 2
 
     def ket(self, c0: float, c: np.ndarray) -> np.ndarray:
-        """Determinant vector of c0 |HF> + sum_mu c_mu |mu>."""
+        """Determinant vector of c0 |HF> + sum_mu c_mu |mu>.
+        Kets |mu> = tau_mu |HF> of Sec. 2.1."""
         return self.kets @ np.concatenate([[c0], c])
 
     def bra(self, c0: float, c: np.ndarray) -> np.ndarray:
-        """Determinant vector of the bra c0 <HF| + sum_mu c_mu <mu~|."""
+        """Determinant vector of the bra c0 <HF| + sum_mu c_mu <mu~|.
+        Bras <mu~| biorthonormal to the kets (Sec. 2.1)."""
         x = np.zeros(self.dim)
         x[self.rows] = np.concatenate([[c0], c]) @ self.Bpinv
         return x
 
     def project(self, psi: np.ndarray, check: bool = True) -> np.ndarray:
-        """Coefficients (c0, c_mu) of the <= doubles part of psi in the kets."""
+        """Coefficients (c0, c_mu) of the <= doubles part of psi in the kets.
+        The natural projection onto HF and the singles and doubles (Sec. 2.4.1)."""
         y = psi[self.rows]
         c = self.Bpinv @ y
         if check:
@@ -170,7 +176,8 @@ class Space:
 
     # ---- operators built from amplitudes ----------------------------------
     def op_singles(self, r1: np.ndarray) -> sp.csr_matrix:
-        """sum_ai r_ai E_ai, r1 indexed a*o + i."""
+        """sum_ai r_ai E_ai, r1 indexed a*o + i.
+        T1 of Sec. 2.1."""
         o, v = self.o, self.v
         M = sp.csr_matrix((self.dim, self.dim))
         for a in range(v):
@@ -180,7 +187,8 @@ class Space:
         return M
 
     def op_doubles(self, r2: np.ndarray) -> sp.csr_matrix:
-        """sum over packed mu of r_mu tau_mu (1/2 on the diagonal pairs)."""
+        """sum over packed mu of r_mu tau_mu (1/2 on the diagonal pairs).
+        T2 of Sec. 2.1."""
         o, v = self.o, self.v
         ov = o * v
         M = sp.csr_matrix((self.dim, self.dim))
@@ -194,11 +202,14 @@ class Space:
         return M
 
     def op_cluster(self, t: np.ndarray) -> sp.csr_matrix:
+        """The cluster operator T = sum_mu t_mu tau_mu of Sec. 2.1 (singles and doubles) as a sparse
+        matrix."""
         ov = self.o * self.v
         return self.op_singles(t[:ov]) + self.op_doubles(t[ov:])
 
     def hamiltonian(self, h: np.ndarray, g: np.ndarray) -> sp.csr_matrix:
-        """H = sum h_pq E_pq + 1/2 sum g_pqrs (E_pq E_rs - d_qr E_ps)."""
+        """H = sum h_pq E_pq + 1/2 sum g_pqrs (E_pq E_rs - d_qr E_ps).
+        Sec. 2.3.2."""
         n = self.n
         H = sp.csr_matrix((self.dim, self.dim))
         for p in range(n):
@@ -215,7 +226,8 @@ class Space:
 
 
 def expm_apply(T: sp.spmatrix, x: np.ndarray, sign: float = 1.0) -> np.ndarray:
-    """exp(sign*T) x by the power series; T is nilpotent on this space."""
+    """exp(sign*T) x by the power series; T is nilpotent on this space.
+    exp(T) of Sec. 2.1 applied to a determinant vector."""
     out = x.copy()
     term = x.copy()
     for k in range(1, 64):
@@ -237,10 +249,13 @@ class System:
 
     # Hbar acting on a vector: exp(-T) H exp(T) x
     def hbar_apply(self, T, x):
+        """Hbar x = exp(-T) H exp(T) x, the similarity-transformed Hamiltonian of Sec. 2.1."""
         return expm_apply(T, self.H @ expm_apply(T, x, +1.0), -1.0)
 
     def omega(self, t: np.ndarray, extra=None):
-        """(E0, Omega) with T = op_cluster(t) (+ extra operator, e.g. zeta X3)."""
+        """(E0, Omega) with T = op_cluster(t) (+ extra operator, e.g. zeta X3).
+        E0 = <HF|Hbar|HF> and Omega_mu = <mu~|Hbar|HF> of Sec. 2.1; with zeta X3 the SCC cluster
+        operator of Sec. 2.4.1."""
         T = self.S.op_cluster(t)
         if extra is not None:
             T = T + extra
@@ -326,13 +341,15 @@ def x3_operator(space: Space, ra: np.ndarray, rb: np.ndarray) -> sp.csr_matrix:
 
 
 def full_g(L: np.ndarray) -> np.ndarray:
-    """g_pqrs = sum_J L^J_pq L^J_rs."""
+    """g_pqrs = sum_J L^J_pq L^J_rs.
+    The two-electron integrals of the Hamiltonian of Sec. 2.3.2, from their Cholesky vectors."""
     return np.einsum("Jpq,Jrs->pqrs", L, L)
 
 
 def synthetic_h(eps: np.ndarray, g: np.ndarray, o: int) -> np.ndarray:
     """One-electron integrals that make F = diag(eps) exactly:
-    h_pq = eps_p d_pq - sum_k (2 g_pqkk - g_pkkq) (canonical HF reference)."""
+    h_pq = eps_p d_pq - sum_k (2 g_pqkk - g_pkkq) (canonical HF reference).
+    Canonical Hartree-Fock reference for the Hamiltonian of Sec. 2.3.2."""
     h = np.diag(eps).astype(np.float64)
     for k in range(o):
         h -= 2.0 * g[:, :, k, k] - g[:, k, k, :]

@@ -12,6 +12,8 @@ import numpy as np
 
 
 def unflatten(p, sizes):
+    """Per-layer (W[in][out], b[out]) from the flat parameter vector of the C interface. The learned
+    part is an extension of the method; the paper has none."""
     out, off = [], 0
     for (din, dout) in sizes:
         W = p[off:off + din * dout].reshape(din, dout)
@@ -23,6 +25,8 @@ def unflatten(p, sizes):
 
 
 def loss_and_grad(p, sizes, X, T):
+    """Mean-squared-error loss of the per-amplitude MLP and its gradient by backpropagation, in the
+    flat parameter layout. The learned part is an extension of the method; the paper has none."""
     layers = unflatten(np.asarray(p, dtype=np.float64), sizes)
     acts, pres = [np.asarray(X, dtype=np.float64)], []
     for k, (W, b) in enumerate(layers):

@@ -54,7 +54,8 @@ def _t(x):
 
 
 def singles_product(x, y, o, v):
-    """Packed ket of X1 Y1|HF> (doubles only): amplitude x_P y_Q + x_Q y_P."""
+    """Packed ket of X1 Y1|HF> (doubles only): amplitude x_P y_Q + x_Q y_P.
+    The T1 T1 and T1 R1 doubles of exp(T - T0) in the bra-frozen overlap O_mn of Sec. 2.3.4."""
     x1 = _t(x)[: o * v].reshape(v, o)
     y1 = _t(y)[: o * v].reshape(v, o)
     p = torch.einsum("ai,bj->aibj", x1, y1)
@@ -75,7 +76,8 @@ def frozen_overlap(t, t0, Lm, r0n, Rn, o, v):
 def scc_state(prob, tol=1e-12, ground_tol=1e-12, near=None):
     """Converged SCCSD for K = {a, b} (small systems: roots from the explicit
     Jacobian): t, zeta, right vectors (r0, R), left vectors L (L_k . R_k = 1),
-    omegas and E0. near: a state of a nearby system to start from."""
+    omegas and E0. near: a state of a nearby system to start from.
+    SCCSD of Sec. 2.2 and 2.4, the state the Lagrangian of Sec. 2.3.1 is taken at."""
     start = None if near is None else (near["zeta"], near["t"].numpy(), near["Ra"].numpy(),
                                        near["Rb"].numpy())
     s = sc.solve_scc(prob, tol=tol, ground_tol=ground_tol, dense=True, start=start)
@@ -103,7 +105,8 @@ def lagrangian(prob, st, target, P, M, h=None, L=None, lam=None):
 
     P: t, zeta, r0a, Ra, r0b, Rb.  M: zbar, lb0a, Lba, lb0b, Lbb, Ea, Eb, gbar.
     lam = (Lambda_a, Lambda_b), by default the left vectors of st; the frozen
-    bra L_m and t0 of a coupling always come from st."""
+    bra L_m and t0 of a coupling always come from st.
+    The Lagrangian of Sec. 2.3.1, with the SCCSD terms of Sec. 2.4.2."""
     h = prob.h if h is None else h
     L = prob.L if L is None else L
     o, v = prob.o, prob.v
@@ -138,13 +141,16 @@ def lagrangian(prob, st, target, P, M, h=None, L=None, lam=None):
 
 
 def params_of(st):
+    """The parameters of the Lagrangian of Sec. 2.3.1 (t, zeta, r0 and R of both states) as tensors
+    for differentiation."""
     return {"t": st["t"].clone(), "zeta": torch.tensor(st["zeta"], dtype=DT),
             "r0a": torch.tensor(st["r0a"], dtype=DT), "Ra": st["Ra"].clone(),
             "r0b": torch.tensor(st["r0b"], dtype=DT), "Rb": st["Rb"].clone()}
 
 
 def overlap_r0_derivatives(prob, st):
-    """(dO_ab/dr0_a, dO_ab/dr0_b) at the solution."""
+    """(dO_ab/dr0_a, dO_ab/dr0_b) at the solution.
+    The dO/dR0 terms of the stationarity equations (Sec. 2.3.3)."""
     P = params_of(st)
     f = lambda ra0, rb0: sc.overlap(P["t"], ra0, P["Ra"], rb0, P["Rb"], prob.o, prob.v)
     g = grad(f, argnums=(0, 1))(P["r0a"], P["r0b"])
@@ -171,7 +177,8 @@ def closed_forms(prob, st, target, zbar, Lba, Lbb, gbar, dO_dr0=None):
 
 def stationarity(prob, st, target, M):
     """Derivatives of the Lagrangian with respect to every parameter:
-    dict t, zeta, r0a, Ra, r0b, Rb (all zero at the multipliers)."""
+    dict t, zeta, r0a, Ra, r0b, Rb (all zero at the multipliers).
+    The stationarity conditions of Sec. 2.3.3 (gradient) and Sec. 2.3.4 (coupling)."""
     P = params_of(st)
     names = ["t", "zeta", "r0a", "Ra", "r0b", "Rb"]
     f = lambda *xs: lagrangian(prob, st, target, dict(zip(names, xs)), M)
@@ -180,13 +187,16 @@ def stationarity(prob, st, target, M):
 
 
 def lambda_stationarity(prob, st, target, M):
-    """Derivatives with respect to the bra vectors Lambda_a, Lambda_b."""
+    """Derivatives with respect to the bra vectors Lambda_a, Lambda_b.
+    The bra conditions of Sec. 2.3.3, which give the closed forms for Ebar and L0bar."""
     P = params_of(st)
     f = lambda La, Lb: lagrangian(prob, st, target, P, M, lam=(La, Lb))
     return grad(f, argnums=(0, 1))(st["La"].clone(), st["Lb"].clone())
 
 
 def unknowns_dim(prob):
+    """Number of unknowns (zetabar, Lbar_a, Lbar_b, gammabar) of the multiplier equations of Sec.
+    2.3.3."""
     return 3 * prob.dim + 1
 
 
@@ -196,7 +206,8 @@ def _split(u, dim):
 
 def residual_map(prob, st, target, dO_dr0=None):
     """u = (zbar, Lb_a, Lb_b, gbar) -> stationarity residual (t, R_a, R_b, zeta)
-    with the closed forms for lb0_k and Ebar_k substituted; affine in u."""
+    with the closed forms for lb0_k and Ebar_k substituted; affine in u.
+    The linear system of Sec. 2.3.3 (gradient) or Sec. 2.3.4 (coupling)."""
     dim = prob.dim
     dO = overlap_r0_derivatives(prob, st) if dO_dr0 is None else dO_dr0
 
@@ -212,7 +223,8 @@ def residual_map(prob, st, target, dO_dr0=None):
 def solve_multipliers(prob, st, target):
     """Dense solve of the stationarity equations (small systems only).
     Returns the full multiplier dict plus the gauge-free bras K_a, K_b and the
-    residual norm of the solved system."""
+    residual norm of the solved system.
+    Sec. 2.3.3 solves this system iteratively (e.g. Davidson); here it is dense."""
     dim = prob.dim
     N = unknowns_dim(prob)
     dO = overlap_r0_derivatives(prob, st)
@@ -253,7 +265,8 @@ def lagrangian_densities(prob, st, target, M):
 
 
 def perturbed_problem(prob, h1, L1, e):
-    """Copy of prob with integrals h + e h1, L + e L1 (fixed orbitals)."""
+    """Copy of prob with integrals h + e h1, L + e L1 (fixed orbitals).
+    The gradient and couplings are derivatives with respect to these integrals (Sec. 2.3.2)."""
     p = cc.Problem(prob.eps, prob.L, prob.o)
     p.h = prob.h + e * _t(h1)
     p.L = prob.L + e * _t(L1)

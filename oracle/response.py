@@ -33,23 +33,27 @@ def _t(x):
 
 
 def residual(prob, x, scc=None):
+    """(E0, Omega) of Sec. 2.1 at packed amplitudes x (SCC term of Sec. 2.4.2 with scc)."""
     return cc.energy_residual(_t(x), prob, scc=scc)
 
 
 def jacobian_right(prob, x, R, scc=None):
-    """A R (packed) at amplitudes x."""
+    """A R (packed) at amplitudes x.
+    A_mu,nu = d Omega_mu / d t_nu of Sec. 2.1 and 2.3.3, as a forward derivative."""
     f = lambda y: cc.energy_residual(y, prob, scc=scc)[1]
     return jvp(f, (_t(x),), (_t(R),))[1]
 
 
 def jacobian_left(prob, x, Lv, scc=None):
-    """A^T L (packed) at amplitudes x."""
+    """A^T L (packed) at amplitudes x.
+    The left transformation of Sec. 2.1, as a reverse derivative."""
     f = lambda y: cc.energy_residual(y, prob, scc=scc)[1]
     _, pull = vjp(f, _t(x))
     return pull(_t(Lv))[0]
 
 
 def eta(prob, x, scc=None):
+    """eta_nu = <HF|[Hbar, tau_nu]|HF> = d E0 / d t_nu (Sec. 2.1 and 2.3.3), as a gradient."""
     return grad(lambda y: cc.energy_residual(y, prob, scc=scc)[0])(_t(x))
 
 
@@ -63,7 +67,8 @@ def _r1_omega1(R, Om, o, v):
 
 
 def transition_element(prob, x, l0, Lv, r0, R, h, L, scc=None):
-    """<L|Hbar|R> as a function of the integrals (h, L^J)."""
+    """<L|Hbar|R> as a function of the integrals (h, L^J).
+    Sec. 2.3.2."""
     o, v = prob.o, prob.v
     x, Lv, R = _t(x), _t(Lv), _t(R)
     f = lambda y: cc.energy_residual(y, prob, h=h, L=L, scc=scc)
@@ -74,7 +79,9 @@ def transition_element(prob, x, l0, Lv, r0, R, h, L, scc=None):
 
 
 def densities(prob, x, l0, Lv, r0, R, scc=None):
-    """(d_pq[n][n], Gamma^J_pq[J][n][n]) for the bra (l0, L), ket (r0, R)."""
+    """(d_pq[n][n], Gamma^J_pq[J][n][n]) for the bra (l0, L), ket (r0, R).
+    The densities of Sec. 2.3.2 (with the Delta d of Sec. 2.4.2 for the SCC state), as derivatives
+    of the transition element with respect to h and L^J."""
     g = grad(lambda h, L: transition_element(prob, x, l0, Lv, r0, R, h, L, scc),
              argnums=(0, 1))(prob.h, prob.L)
     return g[0], g[1]

@@ -45,7 +45,8 @@ def _cc(t1, t2, h, L, o):
 
 
 def xi(t1, Rx, Ry, h, L, o, v):
-    """<mu~|Hhat R1(Rx) R2(Ry)|HF> in the packed layout."""
+    """<mu~|Hhat R1(Rx) R2(Ry)|HF> in the packed layout.
+    The SCC ground-state term of Sec. 2.4.2."""
     ov = o * v
     r1, r2 = cc.unpack(Rx, o, v)[0], cc.unpack(Ry, o, v)[1]
     z2 = torch.zeros(v, o, v, o, dtype=DT)
@@ -76,11 +77,13 @@ def xi(t1, Rx, Ry, h, L, o, v):
 
 
 def r2_packed(R, ov):
+    """The packed doubles part of a packed vector."""
     return torch.as_tensor(R, dtype=DT)[ov:]
 
 
 def projected_state(x_t, R0, R, o, v):
-    """(c0, c1[a,i], c2[a,i,b,j]): HF+S+D part of exp(T)(R0 + R)|HF>."""
+    """(c0, c1[a,i], c2[a,i,b,j]): HF+S+D part of exp(T)(R0 + R)|HF>.
+    The natural projection of Sec. 2.4.1."""
     t1, t2 = cc.unpack(x_t, o, v)
     r1, r2 = cc.unpack(R, o, v)
     c0 = torch.as_tensor(R0, dtype=DT)
@@ -93,7 +96,8 @@ def projected_state(x_t, R0, R, o, v):
 
 def metric_product(x, y):
     """Hilbert-space inner product of two HF+S+D kets given as (c0, c1, c2):
-    <S|S'> = 2 sum c1 c1', <D|D'> = sum c2 (2 c2' - c2' exchanged)."""
+    <S|S'> = 2 sum c1 c1', <D|D'> = sum c2 (2 c2' - c2' exchanged).
+    The inner product in O_kl of Sec. 2.2."""
     x0, x1, x2 = x
     y0, y1, y2 = y
     return (x0 * y0 + 2.0 * torch.sum(x1 * y1)
@@ -107,7 +111,8 @@ def overlap(x_t, Ra0, Ra, Rb0, Rb, o, v):
 
 
 def fix_sign(x):
-    """Sign convention for state vectors: largest |component| positive."""
+    """Sign convention for state vectors: largest |component| positive.
+    A convention of this code, not of the paper."""
     return -x if x[np.argmax(np.abs(x))] < 0 else x
 
 

@@ -21,6 +21,8 @@ from . import response as rp
 
 
 def denominators(prob) -> np.ndarray:
+    """Orbital-energy denominators D_ai = e_a - e_i and D_ai + D_bj in the packed layout. These are
+    the standard Jacobi preconditioner; the paper does not specify one."""
     o, v = prob.o, prob.v
     e = prob.eps.numpy()
     eo, ev = e[:o], e[o:]
@@ -31,7 +33,9 @@ def denominators(prob) -> np.ndarray:
 
 
 def ground_state(prob, tol=1e-10, maxit=200, scc=None, x0=None, diis=8):
-    """Converge Omega(t) = 0; returns (t, E0, iterations)."""
+    """Converge Omega(t) = 0; returns (t, E0, iterations).
+    Solves Omega(t) = 0 of Sec. 2.1 by Jacobi steps with DIIS, a standard method the paper does not
+    specify."""
     D = denominators(prob)
     x = np.zeros(prob.dim) if x0 is None else np.array(x0, dtype=np.float64)
     xs, rs = [], []
@@ -66,14 +70,16 @@ def ground_state(prob, tol=1e-10, maxit=200, scc=None, x0=None, diis=8):
 
 
 def jacobian_matrix(prob, x, scc=None):
-    """Explicit A (columns A e_nu) for small systems."""
+    """Explicit A (columns A e_nu) for small systems.
+    A of Sec. 2.3.3."""
     f = lambda y: rp.jacobian_right(prob, x, y, scc=scc)
     return torch.func.vmap(f)(torch.eye(prob.dim, dtype=torch.float64)).T.numpy()
 
 
 def eom_dense(prob, x, nroots, side="right", scc=None):
     """Lowest-Re roots from a dense eigendecomposition of the explicit
-    Jacobian (small systems; same conventions as eom)."""
+    Jacobian (small systems; same conventions as eom).
+    The EOM eigenproblem of Sec. 2.1."""
     A = jacobian_matrix(prob, x, scc=scc)
     w, V = np.linalg.eig(A if side == "right" else A.T)
     order = np.argsort(w.real)[:nroots]
@@ -87,7 +93,8 @@ def eom_dense(prob, x, nroots, side="right", scc=None):
 
 def eom(prob, x, nroots, side="right", tol=1e-8, maxit=200, scc=None,
         max_space=None, seed_vectors=None):
-    """Lowest-Re roots of the EOM Jacobian; returns (omega[nroots], V[nroots][dim])."""
+    """Lowest-Re roots of the EOM Jacobian; returns (omega[nroots], V[nroots][dim]).
+    The EOM eigenproblem of Sec. 2.1, by Davidson (the method Sec. 2.3.3 names)."""
     D = denominators(prob)
     dim = prob.dim
     op = (lambda r: rp.jacobian_right(prob, x, r, scc=scc).numpy()) if side == "right" \
