@@ -83,8 +83,11 @@ int sccsd_residual(sccsd_ctx* ctx, const double* t, double zeta, const double* R
 int sccsd_jacobian_right(sccsd_ctx* ctx, int nvec, const double* R, double* sigma,
                          double* etaR);
 
-/* sigma_k = A^T L_k (the left transformation) for nvec packed bras; nvec = 0
- * does nothing (L and sigma may be NULL). */
+/* sigma_k = A^T L_k (the left transformation) for nvec packed bras: the
+ * left EOM problem of Sec. 2.1 and the A^T products of the multiplier
+ * equations (Sec. 2.3.3), at the fixed state. nvec = 0 does nothing (L and
+ * sigma may be NULL); nvec < 0 is SCCSD_EINVAL; SCCSD_ESTATE before any
+ * sccsd_residual. */
 int sccsd_jacobian_left(sccsd_ctx* ctx, int nvec, const double* L, double* sigma);
 
 /* One- and two-particle (transition) densities of Sec. 2.3.2 for the bra
@@ -101,11 +104,14 @@ int sccsd_densities(sccsd_ctx* ctx, double l0, const double* L, double r0, const
  * on CUDA cores (SCCSD_FP64) or on tcgen05 tensor cores with BF16 slices
  * (SCCSD_BF16X3 / SCCSD_BF16, used when the product is large enough). All three
  * pointers must be device memory; the call returns after the work finished.
- * This is the contraction primitive of the hot path, exposed for validation. */
+ * This is the contraction primitive of the hot path, exposed for validation
+ * (an interface of this library; the paper has no counterpart). SCCSD_EINVAL
+ * for non-positive sizes, a NULL or host pointer or a bad precision. */
 int sccsd_gemm_tn(int precision, long long M, long long N, long long K, double alpha,
                   const double* A, const double* B, double* C, void* stream);
 
-/* Profiling. sccsd_profile(ctx, 1) resets the counters and starts timing
+/* Profiling (instrumentation of this library; the paper has no counterpart).
+ * sccsd_profile(ctx, 1) resets the counters and starts timing
  * every particle-particle ladder contraction (o^2 v^4 part) with CUDA events
  * on the context's stream; 0 stops it. sccsd_profile_read returns the summed
  * ladder time in ms, the number of ladder contractions, their algorithmic
@@ -164,7 +170,8 @@ int sccsd_solve_scc(sccsd_ctx* ctx, double tol, int maxit, double ground_tol, do
                     double* Rb, int* iterations);
 
 /* Switch the precision of the tensor-core-eligible contractions for later
- * calls (SCCSD_FP64 / SCCSD_BF16X3 / SCCSD_BF16). */
+ * calls (SCCSD_FP64 / SCCSD_BF16X3 / SCCSD_BF16). An implementation choice: the
+ * paper's program is FP64 throughout. SCCSD_EINVAL for another value. */
 int sccsd_set_precision(sccsd_ctx* ctx, int precision);
 
 /* Launch-shape tuning of the tensor-core contractions (an implementation
@@ -228,7 +235,9 @@ int sccsd_solve_ground(sccsd_ctx* ctx, const double* t0, double zeta, const doub
  * refine_tol or the residuals stall for 8 iterations (refine_tol <= 0: no
  * refinement). Outputs: omega[nroots],
  * vecs[nroots][dim] (unit-norm packed vectors, may be NULL), iterations.
- * SCCSD_ECOMPLEX if a complex pair appears among the wanted roots. */
+ * The system needs dim >= 48 (the subspace size), else SCCSD_EINVAL.
+ * SCCSD_ECOMPLEX if a complex pair appears among the wanted roots;
+ * SCCSD_ENOTCONV when maxit is reached (outputs hold the last Ritz pairs). */
 int sccsd_solve_states(sccsd_ctx* ctx, int nroots, int side, double tol, int maxit,
                        double refine_tol, double* omega, double* vecs, int* iterations);
 
@@ -309,14 +318,15 @@ int sccsd_solve_multipliers(sccsd_ctx* ctx, const double* vecs, const double* sc
                             int m_state, int n_state, double tol, int maxit, double refine_tol,
                             double* zbar, double* K, double* out_scal, double* D1,
                             double* Gamma, int* iterations);
-/* The packed amplitudes t of the context's current state (the last
- * sccsd_residual, or the result of a solver), e.g. the SCCSD ground state
- * after sccsd_solve_scc. */
+/* The packed amplitudes t (Sec. 2.1) of the context's current state (the
+ * last sccsd_residual, or the result of a solver), e.g. the SCCSD ground state
+ * after sccsd_solve_scc. SCCSD_ESTATE before any state exists. */
 int sccsd_state_amplitudes(sccsd_ctx* ctx, double* t);
 /* The stationarity residual r [3 dim + 1] = (d/dt, d/dR_a, d/dR_b, d/dzeta)
  * of the Lagrangian at the unknowns u [3 dim + 1] = (zbar, Lbar_a, Lbar_b,
- * gbar), with the closed forms for Lbar0_k and Ebar_k substituted (the map
- * the solver drives to zero; same inputs as sccsd_solve_multipliers). */
+ * gbar), with the closed forms for Lbar0_k and Ebar_k substituted: the
+ * stationarity conditions of Sec. 2.3.3 (gradient) or Sec. 2.3.4 (coupling),
+ * the map the solver drives to zero; same inputs as sccsd_solve_multipliers. */
 int sccsd_multiplier_residual(sccsd_ctx* ctx, const double* vecs, const double* scal, int kind,
                               int m_state, int n_state, const double* u, double* r);
 
@@ -324,8 +334,13 @@ int sccsd_multiplier_residual(sccsd_ctx* ctx, const double* vecs, const double* 
  * sccsd_capture_transform records W = A V (side 0, V packed kets, as
  * sccsd_jacobian_right) or W = A^T V (side 1, V packed bras, as
  * sccsd_jacobian_left) for nvec vectors at the fixed state of ctx into a CUDA
- * graph (cudaGraph_t, returned as void*), after one ordinary call with the same
- * arguments that sizes every buffer. V and W must be device memory and stay
+ * graph (cudaGraph_t, returned as void*); the call first runs the transform
+ * once uncaptured, which sizes every buffer. Batching is an interface of this
+ * library (the transforms are those of Sec. 2.1); the paper has no
+ * counterpart. SCCSD_EINVAL for host vectors, a context on the default
+ * stream or bad sizes; SCCSD_ESTATE before any sccsd_residual; the join and
+ * launch calls return SCCSD_EINVAL for NULL arguments and SCCSD_ECUDA for a
+ * failed CUDA call. V and W must be device memory and stay
  * valid while the graph is used; a launch reads V as it is then. The
  * context needs its own (non-default) stream. The graph reuses the context's
  * internal buffers: do not run other calls on the same context while a launch
@@ -341,8 +356,12 @@ int sccsd_graph_launch(void* exec, void* stream);
 void sccsd_graph_destroy(void* graph);
 void sccsd_graph_exec_destroy(void* exec);
 
-/* Size of a packed vector. */
+/* Size of a packed vector, ov + ov(ov+1)/2 (the singles and doubles of
+ * Sec. 2.1). */
 long long sccsd_dim(int o, int v);
+/* Text of the last failure on ctx (owned by ctx, valid until its next call),
+ * the text of an error code, and the release of a context with every device
+ * buffer it owns (NULL is ignored). */
 const char* sccsd_last_error(sccsd_ctx* ctx);
 const char* sccsd_strerror(int code);
 void sccsd_destroy(sccsd_ctx* ctx);
