@@ -311,3 +311,37 @@ def test_transform_edge_cases(host_lib):
     sl = ctx.jacobian_left(np.stack([R1, R2, a * R1 + b * R2]))
     assert np.abs(sl[2] - (a * sl[0] + b * sl[1])).max() < 1e-13
     ctx.close()
+
+
+def test_autotune_candidates_random_shapes():
+    """The candidate rules on 300 seeded random shapes (M up to 10^6, N up to
+    64 tiles, 1 to 2000 K blocks, operands of any relative size)."""
+    tmp = tempfile.mkdtemp()
+    exe = os.path.join(tmp, "tc_tune_main")
+    r = subprocess.run(["g++", "-O1", "-std=c++17", "-I", CSRC, os.path.join(CSRC, "tc_tune.cpp"),
+                        os.path.join(ROOT, "tests", "host_executor", "tc_tune_main.cpp"), "-o", exe],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        pytest.skip("host toolchain unavailable: " + r.stderr[-300:])
+    rng = np.random.default_rng(2024)
+    shapes = []
+    for _ in range(300):
+        M = int(rng.integers(1, 10 ** int(rng.integers(1, 7)) + 1))
+        n_pad = 256 * int(rng.integers(1, 65))
+        nk = int(rng.integers(1, 2001))
+        ab = float((-(-M // 128) * 128) * nk * 64)
+        bb = float(n_pad * nk * 64)
+        shapes.append((M, n_pad, nk, 152, ab, bb))
+    args = [str(x) for s in shapes for x in s]
+    out = subprocess.run([exe, *args], capture_output=True, text=True, check=True).stdout
+    blocks = out.split("\n\n")
+    for shape, block in zip(shapes, blocks):
+        M, n_pad, nk = shape[:3]
+        nt = n_pad // 256
+        cands = [tuple(int(x) for x in line.split()) for line in block.strip().splitlines()]
+        assert cands and cands[0][:4] == _default_rule(*shape), shape
+        assert all(c[4] == 1 for c in cands), shape
+        assert len(set(c[:4] for c in cands)) == len(cands), shape
+        assert any(c[2] == 1 and c[3] == nk for c in cands), shape
+        assert all(c[1] == 0 for c in cands) if nt == 1 else any(c[1] == 1 for c in cands)
+        assert len(cands) <= 20
