@@ -345,3 +345,25 @@ def test_autotune_candidates_random_shapes():
         assert any(c[2] == 1 and c[3] == nk for c in cands), shape
         assert all(c[1] == 0 for c in cands) if nt == 1 else any(c[1] == 1 for c in cands)
         assert len(cands) <= 20
+
+
+@pytest.mark.parametrize("size", [(2, 3, 6), (3, 4, 7)], ids=lambda s: "o%d_v%d" % s[:2])
+@pytest.mark.parametrize("with_scc", [False, True], ids=["ccsd", "sccsd"])
+def test_overlap_and_state_through_the_c_abi(host_lib, size, with_scc):
+    """O_ab of the natural projection (Sec. 2.4.1) through the C ABI equals the
+    oracle's, is symmetric in a and b, and uses T without zeta X3; the state
+    amplitudes read back are those of the last residual call."""
+    B, lib = host_lib
+    from oracle import scc as sc
+    o, v, J = size
+    eps, L = syn.system(o, v, J, 0.3, 61 + o)
+    t = syn.random_vectors(o, v, 1, 62, scale=0.1)[0]
+    Ra, Rb = syn.random_vectors(o, v, 2, 63, normalise=True)
+    ctx = B.Context(o, v, J, eps, L, lib=lib)
+    ctx.residual(t, scc=(0.37, Ra, Rb) if with_scc else None)
+    O = ctx.overlap(0.3, Ra, -0.2, Rb)
+    ref = float(sc.overlap(torch.tensor(t), 0.3, torch.tensor(Ra), -0.2, torch.tensor(Rb), o, v))
+    assert abs(O - ref) < 1e-13 * max(1.0, abs(ref))
+    assert abs(ctx.overlap(-0.2, Rb, 0.3, Ra) - O) < 1e-13 * max(1.0, abs(O))
+    assert np.array_equal(ctx.state_amplitudes(), t)
+    ctx.close()
