@@ -367,3 +367,81 @@ def test_overlap_and_state_through_the_c_abi(host_lib, size, with_scc):
     assert abs(ctx.overlap(-0.2, Rb, 0.3, Ra) - O) < 1e-13 * max(1.0, abs(O))
     assert np.array_equal(ctx.state_amplitudes(), t)
     ctx.close()
+
+
+def test_every_documented_argument_error(host_lib):
+    """The SCCSD_EINVAL (-1) and SCCSD_ESTATE (-4) cases the header documents,
+    through the C ABI before any device work, each leaving a message in
+    sccsd_last_error."""
+    B, lib = host_lib
+    nan = float("nan")
+    lib.sccsd_strerror.argtypes = [ctypes.c_int]
+    lib.sccsd_strerror.restype = ctypes.c_char_p
+    assert lib.sccsd_strerror(-1) == b"invalid argument"
+    h = ctypes.c_void_p()
+    eps = np.linspace(-1.0, 1.0, 5)
+    L = np.zeros((3, 5, 5))
+    assert lib.sccsd_init(None, 2, 3, 3, eps.ctypes.data, L.ctypes.data, 0, None) == -1
+    assert lib.sccsd_init(ctypes.byref(h), 2, 3, 3, eps.ctypes.data, L.ctypes.data, 3, None) == -1
+    assert lib.sccsd_init(ctypes.byref(h), 2, 0, 3, eps.ctypes.data, L.ctypes.data, 0, None) == -1
+    o, v, J = 2, 3, 6
+    eps, L = syn.system(o, v, J, 0.3, 71)
+    ctx = B.Context(o, v, J, eps, L, lib=lib)
+    d = ctx.dim
+    x = np.zeros(d)
+    X = x.ctypes.data
+    out = np.zeros(4 * d + 1)
+    Y = out.ctypes.data
+    n = o + v
+    D1 = np.zeros((n, n))
+    zi = ctypes.c_int()
+    zd = ctypes.c_double()
+
+    def expect(code, rc):
+        assert rc == code, rc
+        assert lib.sccsd_last_error(ctx.h)
+
+    # before any state
+    expect(-4, lib.sccsd_jacobian_left(ctx.h, 1, X, Y))
+    expect(-4, lib.sccsd_densities(ctx.h, 1.0, X, 0.0, X, D1.ctypes.data, None))
+    expect(-4, lib.sccsd_overlap(ctx.h, 0.0, X, 0.0, X, ctypes.addressof(zd)))
+    expect(-4, lib.sccsd_state_amplitudes(ctx.h, Y))
+    expect(-4, lib.sccsd_solve_states(ctx.h, 1, 0, 1e-8, 10, 0.0, Y, None, None))
+    # residual arguments
+    expect(-1, lib.sccsd_residual(ctx.h, None, 0.0, None, None, None, None))
+    expect(-1, lib.sccsd_residual(ctx.h, X, 0.0, X, None, None, None))
+    expect(-1, lib.sccsd_residual(ctx.h, X, nan, X, X, None, None))
+    assert lib.sccsd_residual(ctx.h, X, 0.0, None, None, None, None) == 0
+    # transforms, densities, overlap, state
+    expect(-1, lib.sccsd_jacobian_right(ctx.h, 1, None, Y, None))
+    expect(-1, lib.sccsd_densities(ctx.h, 1.0, None, 0.0, X, D1.ctypes.data, None))
+    expect(-1, lib.sccsd_densities(ctx.h, nan, X, 0.0, X, D1.ctypes.data, None))
+    expect(-1, lib.sccsd_overlap(ctx.h, 0.0, None, 0.0, X, ctypes.addressof(zd)))
+    expect(-1, lib.sccsd_state_amplitudes(ctx.h, None))
+    expect(-1, lib.sccsd_set_precision(ctx.h, 3))
+    # solvers
+    expect(-1, lib.sccsd_solve_ground(ctx.h, None, 0.0, None, None, 0.0, 10, 0.0, None, None, None))
+    expect(-1, lib.sccsd_solve_ground(ctx.h, None, 0.0, None, None, 1e-8, 0, 0.0, None, None, None))
+    expect(-1, lib.sccsd_solve_ground(ctx.h, None, 0.0, X, None, 1e-8, 10, 0.0, None, None, None))
+    for nroots, side, tol, maxit, om in [(0, 0, 1e-8, 10, Y), (13, 0, 1e-8, 10, Y),
+                                         (1, 2, 1e-8, 10, Y), (1, 0, 0.0, 10, Y),
+                                         (1, 0, 1e-8, 0, Y), (1, 0, 1e-8, 10, None)]:
+        expect(-1, lib.sccsd_solve_states(ctx.h, nroots, side, tol, maxit, 0.0, om, None, None))
+    for args in [(0.0, 10, 1e-8, 1e-8), (1e-8, 0, 1e-8, 1e-8), (1e-8, 10, 0.0, 1e-8),
+                 (1e-8, 10, 1e-8, -1.0)]:
+        expect(-1, lib.sccsd_solve_scc(ctx.h, *args, None, None, None, None, None, None, None))
+    # multipliers: bad targets and NULL inputs
+    vecs = np.zeros(5 * d)
+    scal = np.zeros(5)
+    u = np.zeros(3 * d + 1)
+    for kind, m, nn in [(0, 0, 2), (1, 0, 0), (1, 2, 0), (2, 0, 1)]:
+        expect(-1, lib.sccsd_solve_multipliers(ctx.h, vecs.ctypes.data, scal.ctypes.data, kind, m,
+                                               nn, 1e-8, 10, 0.0, None, None, None, None, None,
+                                               ctypes.addressof(zi)))
+        expect(-1, lib.sccsd_multiplier_residual(ctx.h, vecs.ctypes.data, scal.ctypes.data, kind,
+                                                 m, nn, u.ctypes.data, Y))
+    expect(-1, lib.sccsd_solve_multipliers(ctx.h, None, scal.ctypes.data, 0, 0, 0, 1e-8, 10, 0.0,
+                                           None, None, None, None, None, None))
+    expect(-1, lib.sccsd_multiplier_residual(ctx.h, vecs.ctypes.data, scal.ctypes.data, 0, 0, 0,
+                                             None, Y))
+    ctx.close()
