@@ -79,8 +79,80 @@ def scc_symmetric():
     }
 
 
+SCC_ACTIVE = dict(o=3, v=8, J=14, sd=0.1, seed=123)
+
+
+def _scc_active_values(s, prob):
+    from oracle import response as rp
+    e_hf = float(rp.residual(prob, np.zeros(prob.dim))[0])
+    return {"zeta": float(s["zeta"]), "e_corr": float(s["E0"] - e_hf),
+            "omega": [float(x) for x in s["omega"]]}
+
+
+def scc_active():
+    """A system where the constraint is active (zeta far from 0): the
+    self-consistent SCCSD solution of Sec. 2.2 and 2.4 for the two lowest
+    states, from the oracle's loop (ground state and Davidson roots
+    re-converged at each zeta, secant on O_ab). The converged t, R_a, R_b are
+    stored too, so that a check can evaluate the defining equations there."""
+    from oracle import ccsd as cc
+    from oracle import scc as sc
+    from paper_2403_01007_gb300 import synthetic as syn
+    p = SCC_ACTIVE
+    eps, L = syn.system(p["o"], p["v"], p["J"], p["sd"], p["seed"])
+    prob = cc.Problem(eps, L, p["o"])
+    s = sc.solve_scc(prob, tol=1e-10)
+    return {
+        "citation": "Sec. 2.2 (O_ab = 0 enforced by zeta) and Sec. 2.4.1-2.4.2 (SCCSD with "
+                    "X3 = R1^a R2^b - R1^b R2^a, natural projection)",
+        "produced_by": "tests/golden/make_golden.py: oracle.scc.solve_scc (Davidson roots)",
+        "inputs": {"generator": "synthetic.system", **p},
+        "values": _scc_active_values(s, prob),
+        "state": {"t": [float(x) for x in s["t"]], "Ra": [float(x) for x in s["Ra"]],
+                  "Rb": [float(x) for x in s["Rb"]]},
+    }
+
+
+def scc_active_verify(stored):
+    """The defining equations of the stored solution, evaluated by the oracle
+    (instead of re-running the two-minute loop): the SCC ground residual
+    Omega(t; zeta, R_a, R_b), the right eigen-equations A R_k = omega_k R_k of
+    the SCC Jacobian (Sec. 2.1), the constraint O_ab with r0_k = eta.R_k /
+    omega_k (Sec. 2.2, 2.4.1), and E_corr. Returns {name: (value, bound)}."""
+    import torch
+    from oracle import ccsd as cc
+    from oracle import response as rp
+    from oracle import scc as sc
+    from paper_2403_01007_gb300 import synthetic as syn
+    p = SCC_ACTIVE
+    eps, L = syn.system(p["o"], p["v"], p["J"], p["sd"], p["seed"])
+    prob = cc.Problem(eps, L, p["o"])
+    val, st = stored["values"], stored["state"]
+    t, Ra, Rb = (np.array(st[k]) for k in ("t", "Ra", "Rb"))
+    zeta = val["zeta"]
+    scc = (zeta, torch.tensor(Ra), torch.tensor(Rb))
+    E0, Om = rp.residual(prob, t, scc=scc)
+    e_hf = float(rp.residual(prob, np.zeros(prob.dim))[0])
+    out = {"ground residual": (float(torch.linalg.norm(Om)), 1e-8),
+           "e_corr": (abs(float(E0) - e_hf - val["e_corr"]), 1e-10)}
+    eta = rp.eta(prob, t, scc=scc).numpy()
+    r0 = []
+    for name, R, w in (("a", Ra, val["omega"][0]), ("b", Rb, val["omega"][1])):
+        AR = rp.jacobian_right(prob, t, R, scc=scc).numpy()
+        out["eigen-equation " + name] = (float(np.linalg.norm(AR - w * R)), 1e-7)
+        r0.append(float(eta @ R / w))
+    O = float(sc.overlap(torch.tensor(t), r0[0], torch.tensor(Ra), r0[1], torch.tensor(Rb),
+                         prob.o, prob.v))
+    out["O_ab"] = (abs(O), 1e-9)
+    return out
+
+
 FIXTURES = {"fci_two_electron_o1_v5.json": fci_two_electron,
-            "scc_symmetric_o3_v6.json": scc_symmetric}
+            "scc_symmetric_o3_v6.json": scc_symmetric,
+            "scc_active_o3_v8.json": scc_active}
+# fixtures whose full regeneration is slow: checked through their defining
+# equations instead
+VERIFY = {"scc_active_o3_v8.json": scc_active_verify}
 
 
 def load(name):
@@ -88,12 +160,14 @@ def load(name):
         return json.load(f)
 
 
-def main():
+def main(names=None):
     for name, fn in FIXTURES.items():
+        if names and name not in names:
+            continue
         with open(os.path.join(HERE, name), "w") as f:
             json.dump(fn(), f, indent=1)
             f.write("\n")
 
 
 if __name__ == "__main__":
-    main()
+    main(sys.argv[1:])

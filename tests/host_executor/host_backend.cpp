@@ -1,8 +1,12 @@
 // Test double of the device backend (tests only; never linked into the
 // library): every Backend method done with plain host loops, so that the
-// graph construction, its forward/reverse differentiation and the C ABI
-// marshalling can be checked on a machine without a GPU. The product library
-// always uses the CUDA backend and fails when it cannot.
+// graph construction, its forward/reverse differentiation, the C ABI
+// marshalling and the solvers' control flow (with host versions of the small
+// dense solver kernels) can be checked on a machine without a GPU. The product
+// library always uses the CUDA backend and fails when it cannot.
+#include <algorithm>
+#include <cmath>
+#include <complex>
 #include <cstring>
 #include <memory>
 #include <set>
@@ -118,11 +122,165 @@ std::unique_ptr<Backend> make_backend(void*, int) { return std::make_unique<Host
 }
 
 namespace sccsd {
-// device-only solver kernels: not available in the test double
-static void no_device() { throw std::runtime_error("solver kernels need the device backend"); }
-void launch_small_solve(cudaStream_t, int, const double*, const double*, double*, int*) { no_device(); }
-void launch_small_eig(cudaStream_t, int, const double*, double*, double*, double*, int, int*, int*) { no_device(); }
-void launch_diis(cudaStream_t, int, const double*, double*, int*) { no_device(); }
+static void no_device() { throw std::runtime_error("this kernel needs the device backend"); }
+
+// Host versions of the small dense solver kernels, written independently of
+// the device ones (same contracts, different textbook algorithms), so that the
+// solver control flow runs through the C ABI on the CPU.
+
+// x = A^-1 b by Gaussian elimination with partial pivoting (A row-major m x m)
+static int host_solve(int m, std::vector<double> A, std::vector<double>& b) {
+  for (int k = 0; k < m; ++k) {
+    int p = k;
+    for (int i = k + 1; i < m; ++i)
+      if (std::fabs(A[(size_t)i * m + k]) > std::fabs(A[(size_t)p * m + k])) p = i;
+    if (!(std::fabs(A[(size_t)p * m + k]) > 1e-300)) return 1;
+    if (p != k) {
+      for (int j = 0; j < m; ++j) std::swap(A[(size_t)k * m + j], A[(size_t)p * m + j]);
+      std::swap(b[k], b[p]);
+    }
+    for (int i = k + 1; i < m; ++i) {
+      const double f = A[(size_t)i * m + k] / A[(size_t)k * m + k];
+      for (int j = k; j < m; ++j) A[(size_t)i * m + j] -= f * A[(size_t)k * m + j];
+      b[i] -= f * b[k];
+    }
+  }
+  for (int i = m - 1; i >= 0; --i) {
+    double s = b[i];
+    for (int j = i + 1; j < m; ++j) s -= A[(size_t)i * m + j] * b[j];
+    b[i] = s / A[(size_t)i * m + i];
+  }
+  return 0;
+}
+
+void launch_small_solve(cudaStream_t, int m, const double* A, const double* b, double* x,
+                        int* info) {
+  std::vector<double> a(A, A + (size_t)m * m), y(b, b + m);
+  *info = host_solve(m, a, y);
+  std::copy(y.begin(), y.end(), x);
+}
+
+// Pulay DIIS: minimise |sum c_k r_k| with sum c_k = 1 from B_pq = r_p . r_q
+void launch_diis(cudaStream_t, int m, const double* B, double* c, int* info) {
+  const int n = m + 1;
+  double mx = 0.0;
+  for (int k = 0; k < m; ++k) mx = std::max(mx, std::fabs(B[(size_t)k * m + k]));
+  const double sc = mx > 0.0 ? 1.0 / mx : 1.0;
+  std::vector<double> A((size_t)n * n, -1.0), y(n, 0.0);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) A[(size_t)i * n + j] = B[(size_t)i * m + j] * sc;
+  A[(size_t)m * n + m] = 0.0;
+  y[m] = -1.0;
+  *info = host_solve(n, A, y);
+  std::copy(y.begin(), y.begin() + m, c);
+}
+
+// Eigenvalues of a real m x m matrix (row-major): Householder reduction to
+// Hessenberg form, then complex QR steps with Wilkinson shifts and deflation
+// (Golub & Van Loan, Sec. 7.4-7.5); eigenvectors of the wanted real roots by
+// inverse iteration on the original matrix (Sec. 7.6.1).
+void launch_small_eig(cudaStream_t, int m, const double* Hin, double* wr, double* wi, double* Y,
+                      int nwant, int* order, int* info) {
+  typedef std::complex<double> cd;
+  *info = 0;
+  std::vector<double> H(Hin, Hin + (size_t)m * m);
+  for (int k = 0; k + 2 < m; ++k) {
+    double nrm = 0.0;
+    for (int i = k + 1; i < m; ++i) nrm += H[(size_t)i * m + k] * H[(size_t)i * m + k];
+    nrm = std::sqrt(nrm);
+    if (nrm == 0.0) continue;
+    std::vector<double> v(m, 0.0);
+    const double a = H[(size_t)(k + 1) * m + k];
+    v[k + 1] = a + (a >= 0 ? nrm : -nrm);
+    for (int i = k + 2; i < m; ++i) v[i] = H[(size_t)i * m + k];
+    double vv = 0.0;
+    for (int i = k + 1; i < m; ++i) vv += v[i] * v[i];
+    if (vv == 0.0) continue;
+    for (int j = 0; j < m; ++j) {          // H = (I - 2vv^T/vv) H
+      double s = 0.0;
+      for (int i = k + 1; i < m; ++i) s += v[i] * H[(size_t)i * m + j];
+      s *= 2.0 / vv;
+      for (int i = k + 1; i < m; ++i) H[(size_t)i * m + j] -= s * v[i];
+    }
+    for (int i = 0; i < m; ++i) {          // H = H (I - 2vv^T/vv)
+      double s = 0.0;
+      for (int j = k + 1; j < m; ++j) s += H[(size_t)i * m + j] * v[j];
+      s *= 2.0 / vv;
+      for (int j = k + 1; j < m; ++j) H[(size_t)i * m + j] -= s * v[j];
+    }
+  }
+  std::vector<cd> T((size_t)m * m);
+  for (size_t e = 0; e < T.size(); ++e) T[e] = H[e];
+  auto at = [&](int i, int j) -> cd& { return T[(size_t)i * m + j]; };
+  int hi = m - 1, iters = 0;
+  while (hi > 0) {
+    if (++iters > 100 * m) { *info = 2; break; }
+    int lo = hi;
+    while (lo > 0 && std::abs(at(lo, lo - 1)) >
+                         1e-15 * (std::abs(at(lo, lo)) + std::abs(at(lo - 1, lo - 1))))
+      --lo;
+    if (lo == hi) { at(hi, hi - 1) = 0.0; --hi; continue; }
+    if (lo > 0) at(lo, lo - 1) = 0.0;
+    // Wilkinson shift: eigenvalue of the trailing 2 x 2 closer to its last entry
+    const cd a = at(hi - 1, hi - 1), b = at(hi - 1, hi), c = at(hi, hi - 1), d = at(hi, hi);
+    const cd tr = a + d, disc = std::sqrt((a - d) * (a - d) * 0.25 + b * c);
+    cd mu1 = tr * 0.5 + disc, mu2 = tr * 0.5 - disc;
+    cd mu = std::abs(mu1 - d) < std::abs(mu2 - d) ? mu1 : mu2;
+    if (iters % 11 == 0) mu += std::abs(at(hi, hi - 1));   // exceptional shift
+    for (int i = lo; i <= hi; ++i) at(i, i) -= mu;
+    std::vector<cd> cs(hi - lo), sn(hi - lo);
+    for (int k = lo; k < hi; ++k) {        // QR of the active block by Givens rotations
+      const cd x = at(k, k), y = at(k + 1, k);
+      const double r = std::sqrt(std::norm(x) + std::norm(y));
+      cd cc = 1.0, ss = 0.0;
+      if (r > 0.0) { cc = x / r; ss = y / r; }
+      cs[k - lo] = cc;
+      sn[k - lo] = ss;
+      for (int j = k; j <= hi; ++j) {
+        const cd u = at(k, j), w = at(k + 1, j);
+        at(k, j) = std::conj(cc) * u + std::conj(ss) * w;
+        at(k + 1, j) = -ss * u + cc * w;
+      }
+    }
+    for (int k = lo; k < hi; ++k) {        // R Q
+      const cd cc = cs[k - lo], ss = sn[k - lo];
+      for (int i = lo; i <= std::min(hi, k + 2); ++i) {
+        const cd u = at(i, k), w = at(i, k + 1);
+        at(i, k) = u * cc + w * ss;
+        at(i, k + 1) = -u * std::conj(ss) + w * std::conj(cc);
+      }
+    }
+    for (int i = lo; i <= hi; ++i) at(i, i) += mu;
+  }
+  for (int i = 0; i < m; ++i) {
+    const cd l = at(i, i);
+    wr[i] = l.real();
+    wi[i] = std::fabs(l.imag()) <= 1e-9 * std::max(1.0, std::abs(l)) ? 0.0 : l.imag();
+  }
+  std::vector<int> idx(m);
+  for (int i = 0; i < m; ++i) idx[i] = i;
+  std::stable_sort(idx.begin(), idx.end(), [&](int p, int q) { return wr[p] < wr[q]; });
+  for (int k = 0; k < nwant && k < m; ++k) {
+    order[k] = idx[k];
+    if (wi[idx[k]] != 0.0 && *info == 0) *info = 3;
+  }
+  if (*info != 0) return;
+  for (int k = 0; k < nwant; ++k) {
+    const double lam = wr[order[k]] + 1e-10 * std::max(1.0, std::fabs(wr[order[k]]));
+    std::vector<double> y(m);
+    for (int i = 0; i < m; ++i) y[i] = 1.0 + 0.01 * i;
+    for (int it = 0; it < 4; ++it) {
+      std::vector<double> A(Hin, Hin + (size_t)m * m);
+      for (int i = 0; i < m; ++i) A[(size_t)i * m + i] -= lam;
+      if (host_solve(m, A, y) != 0) { *info = 2; return; }
+      double nrm = 0.0;
+      for (double e : y) nrm += e * e;
+      nrm = std::sqrt(nrm);
+      for (double& e : y) e /= nrm;
+    }
+    for (int i = 0; i < m; ++i) Y[(size_t)i * nwant + k] = y[i];
+  }
+}
 void launch_denoms(cudaStream_t, int o, int v, const double* eps, double* D) {
   const int64_t ov = (int64_t)o * v;
   for (int64_t k = 0; k < ov; ++k) D[k] = eps[o + k / o] - eps[k % o];
@@ -130,7 +288,10 @@ void launch_denoms(cudaStream_t, int o, int v, const double* eps, double* D) {
   for (int64_t Q = 0; Q < ov; ++Q)
     for (int64_t P = 0; P <= Q; ++P) D[q++] = D[P] + D[Q];
 }
-void launch_jacobi(cudaStream_t, int64_t, const double*, const double*, const double*, double*) { no_device(); }
+void launch_jacobi(cudaStream_t, int64_t n, const double* t, const double* om, const double* D,
+                   double* out) {
+  for (int64_t k = 0; k < n; ++k) out[k] = t[k] - om[k] / D[k];
+}
 void launch_precond(cudaStream_t, int64_t n, const double* r, const double* D, double lam, double* out) {
   for (int64_t k = 0; k < n; ++k) {
     double d = lam - D[k];
@@ -147,7 +308,19 @@ void launch_floor(cudaStream_t, int64_t n, const double* ref, double frac, doubl
 void launch_scale(cudaStream_t, int64_t n, const double* d, const double* x, double* y) {
   for (int64_t k = 0; k < n; ++k) y[k] = d[k] * x[k];
 }
-void launch_ritz_residual(cudaStream_t, int, int64_t, const double*, const double*, const double*, const int*, double*) { no_device(); }
+void launch_ritz_residual(cudaStream_t, int nr, int64_t n, const double* ax, const double* x,
+                          const double* wr, const int* order, double* r) {
+  for (int k = 0; k < nr; ++k)
+    for (int64_t e = 0; e < n; ++e)
+      r[(int64_t)k * n + e] = ax[(int64_t)k * n + e] - wr[order[k]] * x[(int64_t)k * n + e];
+}
+}
+// The solver reads small results (info flags, root order, eigenvalues) with
+// cudaMemcpyAsync; in the test double all "device" memory is host memory.
+extern "C" cudaError_t cudaMemcpyAsync(void* dst, const void* src, size_t count,
+                                       cudaMemcpyKind, cudaStream_t) {
+  std::memmove(dst, src, count);
+  return cudaSuccess;
 }
 extern "C" long long sccsd_gemm_tn_noalloc_capacity(void) { return 0; }
 extern "C" int sccsd_gemm_tn_noalloc(long long, long long, long long, double, const double*, const double*, double*, void*) { return -1; }

