@@ -540,3 +540,42 @@ def test_davidson_needs_room_for_its_subspace(host_lib):
         ctx.solve_states(1)
     assert ei.value.code == -1
     ctx.close()
+
+
+def test_whole_method_through_the_c_abi(host_lib):
+    """The chain of the method on the CPU test double, on the system with an
+    active constraint: the SCCSD state (sccsd_solve_scc and the left roots),
+    then the multipliers of a gradient and of a coupling (Sec. 2.3). The
+    oracle's stationarity equations vanish at the C-ABI solution, and the
+    effective one-particle densities have trace 2o (the gradient of E with
+    respect to a uniform shift of h counts the electrons) and 0 (a coupling)."""
+    from oracle import multipliers as mu
+    B, lib = host_lib
+    g = _golden("scc_active_o3_v8.json")
+    p = g["inputs"]
+    o = p["o"]
+    eps, L = syn.system(o, p["v"], p["J"], p["sd"], p["seed"])
+    prob = cc.Problem(eps, L, o)
+    ctx = B.Context(o, p["v"], p["J"], eps, L, lib=lib)
+    state = ctx.scc_state(tol=1e-10, ground_tol=1e-11, eom_tol=1e-9, left_tol=1e-9)
+    assert abs(state["zeta"] - g["values"]["zeta"]) < 1e-7
+    st = {"t": torch.tensor(state["t"]), "Ra": torch.tensor(state["Ra"]),
+          "Rb": torch.tensor(state["Rb"]), "La": torch.tensor(state["La"]),
+          "Lb": torch.tensor(state["Lb"]), "zeta": state["zeta"], "r0a": state["r0a"],
+          "r0b": state["r0b"], "omega": (state["omega_a"], state["omega_b"])}
+    Ehf = float(cc.energy_residual(torch.zeros(prob.dim, dtype=torch.float64), prob)[0])
+    st["E0"] = Ehf + state["e_corr"]
+    dim = prob.dim
+    for target, trace in [(("gradient", 0), 2.0 * o), (("coupling", 0, 1), 0.0)]:
+        res = ctx.solve_multipliers(state, target, tol=1e-10, maxit=800)
+        assert abs(np.trace(res["D1"]) - trace) < 1e-8, target
+        d = [1.0 if (target[0] == "gradient" and k == target[1]) else 0.0 for k in range(2)]
+        r0 = [state["r0a"], state["r0b"]]
+        lam = [state["La"], state["Lb"]]
+        Lbar = [res["K"][k] - (d[k] - res["lb0"][k] * r0[k]) * lam[k] for k in range(2)]
+        u = np.concatenate([res["zbar"], Lbar[0], Lbar[1], [res["gbar"]]])
+        fmap = mu.residual_map(prob, st, target)
+        r = fmap(torch.tensor(u)).numpy()
+        b = fmap(torch.zeros(3 * dim + 1, dtype=torch.float64))
+        assert np.linalg.norm(r) < 1e-8 * max(1.0, float(torch.linalg.norm(b))), target
+    ctx.close()
