@@ -163,6 +163,8 @@ int sccsd_overlap(sccsd_ctx* ctx, double ra0, const double* Ra, double rb0, cons
  * secant method on O_ab, starting from zeta = 0 (plain CCSD), which selects
  * the root connected to CCSD (the paper notes the equation may have several,
  * Sec. 3.1.1). Converged when |O_ab| < tol and the zeta step is below 1e-8.
+ * In a mixed-precision context the inner solves finish in FP64, and r0 and
+ * O_ab, which decide zeta, are evaluated in FP64.
  * Outputs (may be NULL): zeta, e_corr, omega2[2], r0_2[2], Ra/Rb (packed),
  * iterations. Afterwards the fixed state is the SCC state of the last zeta. */
 int sccsd_solve_scc(sccsd_ctx* ctx, double tol, int maxit, double ground_tol, double eom_tol,
@@ -311,8 +313,9 @@ int sccsd_set_preconditioner(sccsd_ctx* ctx, const double* Dprec);
  *                coupling (Gamma needs D1).
  * Solver: right-preconditioned restarted GMRES on the affine stationarity map,
  * with an FP64 residual driving correction solves in the context's precision
- * when that is mixed and refine_tol > 0; maxit bounds the number of
- * applications of the map. Returns SCCSD_ENOTCONV (outputs hold the last
+ * when that is mixed and refine_tol > 0 (after two correction rounds in a row
+ * that cut the FP64 residual by less than a factor 10, the remaining ones are
+ * solved in FP64); maxit bounds the number of applications of the map. Returns SCCSD_ENOTCONV (outputs hold the last
  * iterate) when the FP64 residual norm does not reach tol. */
 int sccsd_solve_multipliers(sccsd_ctx* ctx, const double* vecs, const double* scal, int kind,
                             int m_state, int n_state, double tol, int maxit, double refine_tol,

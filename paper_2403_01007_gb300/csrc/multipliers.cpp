@@ -379,6 +379,13 @@ int sccsd_solve_multipliers(sccsd_ctx* c, const double* vecs, const double* scal
     int applied = 0;
     bool converged = false;
     const int max_outer = 12;
+    // correction solves run in the context's precision while they pay: two
+    // rounds in a row that cut the FP64 residual by less than a factor 10 mean
+    // the mixed operator is too far from the FP64 one for this system, and the
+    // remaining corrections are solved in FP64
+    bool mixed = refine;
+    int slow = 0;
+    double prev = 0.0;
     for (int outer = 0; outer <= max_outer && applied < maxit; ++outer) {
       if (refine) {
         switch_precision(c, SCCSD_FP64);
@@ -395,7 +402,16 @@ int sccsd_solve_multipliers(sccsd_ctx* c, const double* vecs, const double* scal
         break;
       }
       if (outer == max_outer) break;
-      if (refine) {
+      if (mixed && outer > 0) {
+        slow = rn > 0.1 * prev ? slow + 1 : 0;
+        if (slow >= 2) {
+          mixed = false;
+          if (getenv("SCCSD_LOG"))
+            fprintf(stderr, "multipliers: mixed corrections stalled, finishing in FP64\n");
+        }
+      }
+      prev = rn;
+      if (mixed) {
         switch_precision(c, p0);
         S.load_state();
       }

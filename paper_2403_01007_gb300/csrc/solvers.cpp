@@ -426,6 +426,36 @@ int sccsd_solve_states(sccsd_ctx* c, int nroots, int side, double tol, int maxit
 extern "C" {
 
 // Self-consistent SCCSD for the two lowest states (K = {a, b}, Sec. 2.4.2).
+namespace {
+
+// Runs in FP64 for its lifetime when the context computes in a mixed
+// precision, and restores that precision on every exit.
+struct Fp64Scope {
+  sccsd_ctx* c;
+  int p0;
+  explicit Fp64Scope(sccsd_ctx* ctx) : c(ctx), p0(ctx->be->get_precision()) {
+    if (p0 != SCCSD_FP64) switch_precision(c, SCCSD_FP64);
+  }
+  ~Fp64Scope() {
+    if (p0 != SCCSD_FP64) switch_precision(c, p0);
+  }
+};
+
+// eta.R_k for nb packed host kets at the fixed state (the eta part of the
+// right-transformation section only)
+void eta_dot(sccsd_ctx* c, int nb, const double* R, double* etaR) {
+  Model& m = *c->cur;
+  RightSec& S = right_section(m, nb);
+  load_packed_batch(c, m.g, R, nb, S.R1, S.R2, false);
+  m.g.run({S.etaR});
+  if (m.g.is_zero(S.etaR))
+    std::fill(etaR, etaR + nb, 0.0);
+  else
+    c->be->download(etaR, m.g.data(S.etaR), nb, false);
+}
+
+}  // namespace
+
 int sccsd_solve_scc(sccsd_ctx* c, double tol, int maxit, double ground_tol, double eom_tol,
                     double* zeta_out, double* e_corr, double* omega2, double* r0_2, double* Ra_out,
                     double* Rb_out, int* iterations) {
@@ -435,7 +465,7 @@ int sccsd_solve_scc(sccsd_ctx* c, double tol, int maxit, double ground_tol, doub
   int status = SCCSD_OK;
   int rc = guarded(c, [&] {
     const int64_t dim = c->dim;
-    std::vector<double> t(dim), vecs(2 * dim), sig(2 * dim), Ra(dim), Rb(dim);
+    std::vector<double> t(dim), vecs(2 * dim), Ra(dim), Rb(dim);
     double zeta = 0.0, E = 0.0, O = 0.0;
     double w[2] = {0.0, 0.0}, r0[2] = {0.0, 0.0};
     bool have_states = false, have_t = false;
@@ -464,11 +494,16 @@ int sccsd_solve_scc(sccsd_ctx* c, double tol, int maxit, double ground_tol, doub
         if (x[im] < 0)
           for (int64_t q = 0; q < dim; ++q) x[q] = -x[q];
       }
-      double etaR[2];
-      check(sccsd_jacobian_right(c, 2, vecs.data(), sig.data(), etaR));
-      r0[0] = etaR[0] / w[0];
-      r0[1] = etaR[1] / w[1];
-      check(sccsd_overlap(c, r0[0], vecs.data(), r0[1], vecs.data() + dim, &O));
+      {
+        // r0 = eta.R / omega and O_ab decide zeta: FP64 in a mixed context,
+        // like the solves above, which finish in FP64
+        Fp64Scope fp64(c);
+        double etaR[2];
+        eta_dot(c, 2, vecs.data(), etaR);
+        r0[0] = etaR[0] / w[0];
+        r0[1] = etaR[1] / w[1];
+        check(sccsd_overlap(c, r0[0], vecs.data(), r0[1], vecs.data() + dim, &O));
+      }
       if (getenv("SCCSD_LOG"))
         fprintf(stderr, "{\"solver\": \"scc\", \"iter\": %d, \"zeta\": %.12f, \"O_ab\": %.3e, \"omega\": [%.12f, %.12f]}\n",
                 it, zeta, O, w[0], w[1]);

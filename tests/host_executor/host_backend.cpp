@@ -7,7 +7,9 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <cstdint>
 #include <cstring>
+#include <functional>
 #include <memory>
 #include <set>
 #include <vector>
@@ -76,12 +78,80 @@ class HostBackend : public Backend {
     }
   }
   void* stream() override { return nullptr; }
-  void set_precision(int) override {}
-  int get_precision() const override { return 0; }
+  // Mixed precision emulated on the host: the tensor-core route takes every
+  // contraction with M, N >= 2 (the device adds a size threshold), operands
+  // become BF16 slices (one, or two with the three leading products), each
+  // slice product is accumulated in FP32 and the products are summed in FP64.
+  int prec = 0;
+  void set_precision(int p) override { prec = p; }
+  int get_precision() const override { return prec; }
   void set_capturing(bool) override {}
-  bool tc_will_use(int64_t, int64_t, int64_t, int64_t) override { return false; }
+  bool tc_will_use(int64_t nb, int64_t M, int64_t N, int64_t) override {
+    return prec != 0 && nb == 1 && M >= 2 && N >= 2;
+  }
   bool tc_cached(const OperandKey&) override { return false; }
-  void gemm_tc_keyed(int64_t, int64_t, int64_t, double, const MatView&, const OperandKey*, const MatView&, const OperandKey*, double*, const OutView*, bool) override {}
+  static float bf16(double x) {           // round to nearest even on the upper 16 bits
+    float f = (float)x;
+    uint32_t b;
+    std::memcpy(&b, &f, 4);
+    b += 0x7FFFu + ((b >> 16) & 1u);
+    b &= 0xFFFF0000u;
+    std::memcpy(&f, &b, 4);
+    return f;
+  }
+  static double view_el(const MatView& v, int64_t r, int64_t k) {
+    const int64_t R = v.n2r > 0 ? (r / v.n2r) * v.sr1 + (r % v.n2r) * v.sr2 : r * v.sr2;
+    const int64_t Q = v.n2k > 0 ? (k / v.n2k) * v.sk1 + (k % v.n2k) * v.sk2 : k * v.sk2;
+    return v.p[R + Q];
+  }
+  static int64_t level_off(int n, const int64_t* e, const int64_t* st, int64_t i) {
+    int64_t off = 0;
+    for (int l = n - 1; l > 0; --l) {
+      off += (i % e[l]) * st[l];
+      i /= e[l];
+    }
+    return off + i * st[0];
+  }
+  // slices of rows x K values
+  void slices(int64_t rows, int64_t K, const std::function<double(int64_t, int64_t)>& get,
+              std::vector<float>& out) const {
+    const int sl = prec == 1 ? 2 : 1;
+    out.assign((size_t)sl * rows * K, 0.0f);
+    for (int64_t r = 0; r < rows; ++r)
+      for (int64_t k = 0; k < K; ++k) {
+        const double x = get(r, k);
+        const float x0 = bf16(x);
+        out[(size_t)r * K + k] = x0;
+        if (sl == 2) out[(size_t)(rows + r) * K + k] = bf16(x - (double)x0);
+      }
+  }
+  double sliced_dot(const std::vector<float>& a, int64_t Ma, int64_t m, const std::vector<float>& b,
+                    int64_t Nb, int64_t n, int64_t K) const {
+    const int sl = prec == 1 ? 2 : 1;
+    double s = 0.0;
+    for (int i = 0; i < sl; ++i)
+      for (int j = 0; i + j < sl; ++j) {
+        float f = 0.0f;
+        const float* x = &a[(size_t)(i * Ma + m) * K];
+        const float* y = &b[(size_t)(j * Nb + n) * K];
+        for (int64_t k = 0; k < K; ++k) f += x[k] * y[k];
+        s += (double)f;
+      }
+    return s;
+  }
+  void gemm_tc_keyed(int64_t M, int64_t N, int64_t K, double alpha, const MatView& A,
+                     const OperandKey*, const MatView& B, const OperandKey*, double* C,
+                     const OutView* ov, bool acc) override {
+    std::vector<float> a, b;
+    slices(M, K, [&](int64_t r, int64_t k) { return view_el(A, r, k); }, a);
+    slices(N, K, [&](int64_t r, int64_t k) { return view_el(B, r, k); }, b);
+    const OutView o = ov ? *ov : OutView::dense(N);
+    for (int64_t m = 0; m < M; ++m)
+      for (int64_t n = 0; n < N; ++n) {
+        double& c = C[level_off(o.nr, o.re, o.rs, m) + level_off(o.nc, o.ce, o.cs, n)];
+        c = (acc ? c : 0.0) + alpha * sliced_dot(a, M, m, b, N, n, K);
+      }
+  }
   double* scratch(int slot, int64_t n) override {
     if (slot_n[slot] < n) { delete[] slots[slot]; slots[slot]=new double[n]; slot_n[slot]=n; }
     return slots[slot];
@@ -101,6 +171,14 @@ class HostBackend : public Backend {
   void ladder(const Graph& g, const double* L, int64_t ver, const double* X, double* Y, int64_t rows) override {
     if (ver != Gver) { build_G(g, L); Gver = ver; }
     int v=g.v; int64_t vv=(int64_t)v*v;
+    if (prec != 0) {                      // the same BF16-slice emulation as gemm_tc_keyed
+      std::vector<float> gs, xs;
+      slices(vv, vv, [&](int64_t r, int64_t k) { return G[r * vv + k]; }, gs);
+      slices(rows, vv, [&](int64_t r, int64_t k) { return X[r * vv + k]; }, xs);
+      for (int64_t ij=0; ij<rows; ++ij) for (int64_t ab=0; ab<vv; ++ab)
+        Y[ij*vv+ab] = sliced_dot(xs, rows, ij, gs, vv, ab, vv);
+      return;
+    }
     for (int64_t ij=0; ij<rows; ++ij) for (int64_t ab=0; ab<vv; ++ab) {
       double s=0; for (int64_t cd=0; cd<vv; ++cd) s+=G[ab*vv+cd]*X[ij*vv+cd]; Y[ij*vv+ab]=s; }
   }
@@ -118,7 +196,11 @@ class HostBackend : public Backend {
       out[((int64_t)q*v+a)*v+c]=s; }
   }
 };
-std::unique_ptr<Backend> make_backend(void*, int) { return std::make_unique<HostBackend>(); }
+std::unique_ptr<Backend> make_backend(void*, int precision) {
+  auto b = std::make_unique<HostBackend>();
+  b->prec = precision;
+  return b;
+}
 }
 
 namespace sccsd {

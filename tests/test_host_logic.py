@@ -579,3 +579,83 @@ def test_whole_method_through_the_c_abi(host_lib):
         b = fmap(torch.zeros(3 * dim + 1, dtype=torch.float64))
         assert np.linalg.norm(r) < 1e-8 * max(1.0, float(torch.linalg.norm(b))), target
     ctx.close()
+
+
+# --------------------------- mixed precision on the double (BF16 emulation)
+
+def test_mixed_precision_emulation_error_levels(host_lib):
+    """The double emulates the mixed modes (BF16 slices, FP32 accumulation):
+    A R differs from the oracle at the level of the split (BF16x3 about 16
+    bits, BF16 about 8), so the refinement tests below refine something."""
+    from oracle import solvers as sv
+    B, lib = host_lib
+    o, v, J = 3, 4, 9
+    eps, L = syn.system(o, v, J, 0.2, 55)
+    prob = cc.Problem(eps, L, o)
+    x, _, _ = sv.ground_state(prob, tol=1e-12)
+    R = syn.random_vectors(o, v, 1, 9, normalise=True)
+    ref = rp.jacobian_right(prob, x, R[0]).numpy()
+    for prec, lo, hi in [("bf16x3", 1e-8, 1e-4), ("bf16", 1e-5, 3e-2)]:
+        ctx = B.Context(o, v, J, eps, L, lib=lib, precision=prec)
+        ctx.residual(x)
+        err = np.abs(ctx.jacobian_right(R)[0] - ref).max() / np.abs(ref).max()
+        ctx.close()
+        assert lo < err < hi, (prec, err)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+def test_mixed_solvers_refine_to_fp64(host_lib, prec):
+    """Mixed iterations followed by FP64 refinement (the solvers' switch) give
+    the FP64 ground state and EOM roots (Sec. 2.1)."""
+    from oracle import solvers as sv
+    B, lib = host_lib
+    o, v, J = 3, 4, 9
+    eps, L = syn.system(o, v, J, 0.2, 55)
+    prob = cc.Problem(eps, L, o)
+    x, E0, _ = sv.ground_state(prob, tol=1e-12)
+    Ehf = float(rp.residual(prob, np.zeros(prob.dim))[0])
+    ctx = B.Context(o, v, J, eps, L, lib=lib, precision=prec)
+    e, t, _ = ctx.solve_ground(tol=1e-11, maxit=300, refine_tol=1e-4)
+    assert abs(e - (E0 - Ehf)) < 1e-10
+    for side in ("right", "left"):
+        w, _, _ = ctx.solve_states(3, side=side, tol=1e-9, refine_tol=1e-4)
+        wd, _ = sv.eom_dense(prob, x, 3, side=side)
+        assert np.abs(w - wd).max() < 1e-9, side
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+def test_mixed_scc_loop_refines_to_fp64(host_lib, prec):
+    """In a mixed context the SCC loop takes r0 = eta.R / omega and O_ab in
+    FP64, so zeta, the energies and the roots are the FP64 solution."""
+    B, lib = host_lib
+    g = _golden("scc_active_o3_v8.json")
+    p = g["inputs"]
+    eps, L = syn.system(p["o"], p["v"], p["J"], p["sd"], p["seed"])
+    ctx = B.Context(p["o"], p["v"], p["J"], eps, L, lib=lib, precision=prec)
+    r = ctx.solve_scc(tol=1e-10)
+    ctx.close()
+    assert abs(r["zeta"] - g["values"]["zeta"]) < 1e-7
+    assert np.abs(r["omega"] - np.array(g["values"]["omega"])).max() < 1e-8
+    assert abs(r["e_corr"] - g["values"]["e_corr"]) < 1e-9
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+def test_mixed_multipliers_refine_to_fp64(host_lib, prec):
+    """Mixed correction solves driven by FP64 residuals (Sec. 2.3.3 system)
+    give the FP64 effective densities; where the mixed corrections stall (BF16
+    here, with every contraction in BF16) the solver finishes in FP64."""
+    B, lib = host_lib
+    g = _golden("scc_active_o3_v8.json")
+    p = g["inputs"]
+    eps, L = syn.system(p["o"], p["v"], p["J"], p["sd"], p["seed"])
+    ctx = B.Context(p["o"], p["v"], p["J"], eps, L, lib=lib)
+    state = ctx.scc_state(tol=1e-10, ground_tol=1e-11, eom_tol=1e-9, left_tol=1e-9)
+    ref = ctx.solve_multipliers(state, ("gradient", 0), tol=1e-10, maxit=800)
+    ctx.close()
+    ctx = B.Context(p["o"], p["v"], p["J"], eps, L, lib=lib, precision=prec)
+    ctx.residual(state["t"], scc=(state["zeta"], state["Ra"], state["Rb"]))
+    res = ctx.solve_multipliers(state, ("gradient", 0), tol=1e-10, maxit=800, refine_tol=1e-6)
+    ctx.close()
+    assert np.abs(res["D1"] - ref["D1"]).max() < 1e-8
+    assert np.abs(res["Gamma"] - ref["Gamma"]).max() < 1e-8
