@@ -285,7 +285,8 @@ int sccsd_learned_guess(sccsd_ctx* ctx, sccsd_mlp* net, double* t0, double* Dpre
 /* Initial denominators of sccsd_solve_ground's update (packed, positive), or
  * NULL for the orbital-energy denominators D. The solver replaces them by its
  * own dressed denominators D' (from the dressed Fock diagonals at the current
- * amplitudes) at its first refresh, after two iterations. */
+ * amplitudes) at its first refresh, after two iterations. SCCSD_EINVAL (and
+ * the previous setting kept) if an entry is not finite and positive. */
 int sccsd_set_preconditioner(sccsd_ctx* ctx, const double* Dprec);
 
 /* ---- Lagrangian multipliers (gradients and couplings) ---------------------

@@ -1,5 +1,9 @@
 // C ABI of the learned initial guess and preconditioner.
 #include "context.h"
+#include <algorithm>
+#include <cmath>
+#include <stdexcept>
+#include <vector>
 
 using namespace sccsd;
 
@@ -131,8 +135,18 @@ int sccsd_set_preconditioner(sccsd_ctx* c, const double* Dprec) {
       c->use_dprec = false;
       return;
     }
+    // the update divides by these: every entry must be finite and positive
+    const bool dev = c->be->is_device(Dprec);
+    std::vector<double> h((size_t)c->dim);
+    if (dev)
+      c->be->download(h.data(), Dprec, c->dim, false);
+    else
+      std::copy(Dprec, Dprec + c->dim, h.begin());
+    for (double x : h)
+      if (!(x > 0.0) || !std::isfinite(x))
+        throw std::invalid_argument("preconditioner entries must be finite and positive");
     if (!c->Dprec) c->Dprec = c->be->alloc(c->dim);
-    c->be->upload(c->Dprec, Dprec, c->dim, c->be->is_device(Dprec));
+    c->be->upload(c->Dprec, h.data(), c->dim, false);
     c->use_dprec = true;
     c->be->sync();
   });

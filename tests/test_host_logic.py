@@ -659,3 +659,36 @@ def test_mixed_multipliers_refine_to_fp64(host_lib, prec):
     ctx.close()
     assert np.abs(res["D1"] - ref["D1"]).max() < 1e-8
     assert np.abs(res["Gamma"] - ref["Gamma"]).max() < 1e-8
+
+
+def test_ground_solver_guess_and_preconditioner(host_lib):
+    """The learned part only supplies a starting point and initial update
+    denominators: with any positive preconditioner and a nearby guess the
+    ground solver reaches the same state (the plain solver decides); a
+    preconditioner with a non-positive entry is rejected."""
+    from oracle import solvers as sv
+    B, lib = host_lib
+    o, v, J = 3, 4, 9
+    eps, L = syn.system(o, v, J, 0.2, 55)
+    prob = cc.Problem(eps, L, o)
+    x, E0, _ = sv.ground_state(prob, tol=1e-12)
+    Ehf = float(rp.residual(prob, np.zeros(prob.dim))[0])
+    D = sv.denominators(prob)
+    ctx = B.Context(o, v, J, eps, L, lib=lib)
+    rng = np.random.default_rng(3)
+    ctx.set_preconditioner(np.ascontiguousarray(D * rng.uniform(0.7, 1.6, D.size)))
+    t0 = x + 1e-3 * rng.normal(size=x.size)
+    e, t, _ = ctx.solve_ground(t0=t0, tol=1e-11, maxit=300)
+    assert abs(e - (E0 - Ehf)) < 1e-10 and np.abs(t - x).max() < 1e-9
+    bad = D.copy()
+    bad[7] = 0.0
+    with pytest.raises(B.SccsdError) as ei:
+        ctx.set_preconditioner(bad)
+    assert ei.value.code == -1
+    bad[7] = np.nan
+    with pytest.raises(B.SccsdError):
+        ctx.set_preconditioner(bad)
+    ctx.set_preconditioner(None)
+    e2, _, _ = ctx.solve_ground(tol=1e-11, maxit=300)
+    assert abs(e2 - e) < 1e-10
+    ctx.close()
