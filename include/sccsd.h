@@ -58,7 +58,10 @@ enum { SCCSD_FP64 = 0, SCCSD_BF16X3 = 1, SCCSD_BF16 = 2 };
 
 /* Create a context for one synthetic system (sizes, eps, L as above).
  * Computes h (the integrals of a canonical reference) and the HF energy.
- * stream: a cudaStream_t, or NULL for the default stream. */
+ * stream: a cudaStream_t, or NULL for the default stream. SCCSD_EINVAL for
+ * non-positive sizes, a bad precision, eps not finite, not ascending within
+ * the occupied and virtual blocks or without a gap between them, and L not
+ * finite or not symmetric in pq (to 1e-12 of its largest entry). */
 int sccsd_init(sccsd_ctx** ctx, int o, int v, int J, const double* eps, const double* L,
                int precision, void* stream);
 

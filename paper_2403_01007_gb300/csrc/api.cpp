@@ -140,7 +140,28 @@ int sccsd_init(sccsd_ctx** out, int o, int v, int J, const double* eps, const do
     c->be = make_backend(stream, precision);
     const int64_t n = c->n;
     c->L = c->be->alloc((int64_t)J * n * n);
-    c->be->upload(c->L, L, (int64_t)J * n * n, c->be->is_device(L));
+    const bool L_dev = c->be->is_device(L);
+    c->be->upload(c->L, L, (int64_t)J * n * n, L_dev);
+    {
+      // each L^J must be finite and symmetric in pq (to rounding)
+      std::vector<double> hL;
+      const double* Lh = L;
+      if (L_dev) {
+        hL.resize((size_t)J * n * n);
+        c->be->download(hL.data(), c->L, (int64_t)J * n * n, false);
+        Lh = hL.data();
+      }
+      double mx = 0.0;
+      for (int64_t k = 0; k < (int64_t)J * n * n; ++k) {
+        if (!std::isfinite(Lh[k])) throw std::invalid_argument("L is not finite");
+        mx = std::max(mx, std::fabs(Lh[k]));
+      }
+      for (int64_t q = 0; q < J; ++q)
+        for (int64_t a = 0; a < n; ++a)
+          for (int64_t b = a + 1; b < n; ++b)
+            if (std::fabs(Lh[(q * n + a) * n + b] - Lh[(q * n + b) * n + a]) > 1e-12 * mx)
+              throw std::invalid_argument("L^J is not symmetric in pq");
+    }
     std::vector<double> e(n);
     if (c->be->is_device(eps)) {
       c->be->download(e.data(), eps, n, false);

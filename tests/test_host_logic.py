@@ -692,3 +692,34 @@ def test_ground_solver_guess_and_preconditioner(host_lib):
     e2, _, _ = ctx.solve_ground(tol=1e-11, maxit=300)
     assert abs(e2 - e) < 1e-10
     ctx.close()
+
+
+def test_init_rejects_bad_integrals(host_lib):
+    """sccsd_init: L^J must be finite and symmetric in pq, eps ascending within
+    each block with a gap between them (SCCSD_EINVAL otherwise)."""
+    B, lib = host_lib
+    o, v, J = 2, 3, 4
+    eps, L = syn.system(o, v, J, 0.3, 81)
+    h = ctypes.c_void_p()
+
+    def init(e, l):
+        e = np.ascontiguousarray(e)
+        l = np.ascontiguousarray(l)
+        rc = lib.sccsd_init(ctypes.byref(h), o, v, J, e.ctypes.data, l.ctypes.data, 0, None)
+        if rc == 0:
+            lib.sccsd_destroy(h)
+        return rc
+
+    assert init(eps, L) == 0
+    bad = L.copy()
+    bad[1, 0, 3] += 1e-6                  # breaks L^J_pq = L^J_qp
+    assert init(eps, bad) == -1
+    bad = L.copy()
+    bad[2, 4, 4] = np.inf
+    assert init(eps, bad) == -1
+    e2 = eps.copy()
+    e2[o] = e2[o - 1]                     # no gap
+    assert init(e2, L) == -1
+    e3 = eps.copy()
+    e3[o:] = e3[o:][::-1]                 # virtual block descending
+    assert init(e3, L) == -1
