@@ -423,9 +423,6 @@ int sccsd_solve_states(sccsd_ctx* c, int nroots, int side, double tol, int maxit
 
 }  // extern "C"
 
-extern "C" {
-
-// Self-consistent SCCSD for the two lowest states (K = {a, b}, Sec. 2.4.2).
 namespace {
 
 // Runs in FP64 for its lifetime when the context computes in a mixed
@@ -456,6 +453,9 @@ void eta_dot(sccsd_ctx* c, int nb, const double* R, double* etaR) {
 
 }  // namespace
 
+extern "C" {
+
+// Self-consistent SCCSD for the two lowest states (K = {a, b}, Sec. 2.4.2).
 int sccsd_solve_scc(sccsd_ctx* c, double tol, int maxit, double ground_tol, double eom_tol,
                     double* zeta_out, double* e_corr, double* omega2, double* r0_2, double* Ra_out,
                     double* Rb_out, int* iterations) {
