@@ -400,23 +400,47 @@ int sccsd_set_autotune(sccsd_ctx* c, int enable) {
   return guarded(c, [&] { c->be->set_autotune(enable == 1); });
 }
 
+// these four have no context to report through: no exception leaves them
 int sccsd_autotune_export(char* buf, long long cap, long long* len) {
-  const std::string text = TcTuneTable::global().dump();
-  const long long need = (long long)text.size() + 1;
-  if (len) *len = need;
-  if (!buf || cap < need) return SCCSD_EINVAL;
-  std::memcpy(buf, text.c_str(), (size_t)need);
-  return SCCSD_OK;
+  try {
+    const std::string text = TcTuneTable::global().dump();
+    const long long need = (long long)text.size() + 1;
+    if (len) *len = need;
+    if (!buf || cap < need) return SCCSD_EINVAL;
+    std::memcpy(buf, text.c_str(), (size_t)need);
+    return SCCSD_OK;
+  } catch (const std::bad_alloc&) {
+    return SCCSD_ENOMEM;
+  } catch (...) {
+    return SCCSD_EINTERNAL;
+  }
 }
 
 int sccsd_autotune_import(const char* text) {
   if (!text) return SCCSD_EINVAL;
-  return TcTuneTable::global().load(std::string(text)) == 0 ? SCCSD_OK : SCCSD_EINVAL;
+  try {
+    return TcTuneTable::global().load(std::string(text)) == 0 ? SCCSD_OK : SCCSD_EINVAL;
+  } catch (const std::bad_alloc&) {
+    return SCCSD_ENOMEM;
+  } catch (...) {
+    return SCCSD_EINTERNAL;
+  }
 }
 
-void sccsd_autotune_clear(void) { TcTuneTable::global().clear(); }
+void sccsd_autotune_clear(void) {
+  try {
+    TcTuneTable::global().clear();
+  } catch (...) {
+  }
+}
 
-long long sccsd_autotune_entries(void) { return (long long)TcTuneTable::global().size(); }
+long long sccsd_autotune_entries(void) {
+  try {
+    return (long long)TcTuneTable::global().size();
+  } catch (...) {
+    return 0;
+  }
+}
 
 int sccsd_state_amplitudes(sccsd_ctx* c, double* t) {
   if (!c) return SCCSD_EINVAL;
