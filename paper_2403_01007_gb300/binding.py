@@ -169,11 +169,12 @@ def autotune_export(lib=None) -> str:
     lib = lib or load()
     n = ctypes.c_longlong()
     lib.sccsd_autotune_export(None, 0, ctypes.byref(n))
-    buf = ctypes.create_string_buffer(n.value)
-    rc = lib.sccsd_autotune_export(buf, n.value, ctypes.byref(n))
-    if rc != 0:
-        raise SccsdError(rc, "autotune export")
-    return buf.value.decode()
+    for _ in range(8):          # the table may grow between the two calls
+        buf = ctypes.create_string_buffer(n.value)
+        rc = lib.sccsd_autotune_export(buf, n.value, ctypes.byref(n))
+        if rc == 0:
+            return buf.value.decode()
+    raise SccsdError(rc, "autotune export")
 
 
 def autotune_import(text: str, lib=None):
