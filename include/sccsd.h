@@ -325,6 +325,17 @@ int sccsd_solve_multipliers(sccsd_ctx* ctx, const double* vecs, const double* sc
                             int m_state, int n_state, double tol, int maxit, double refine_tol,
                             double* zbar, double* K, double* out_scal, double* D1,
                             double* Gamma, int* iterations);
+/* Derivative of a gradient or coupling along a perturbation of the
+ * integrals (Sec. 2.3.2: the effective densities are the derivatives of the
+ * Lagrangian with respect to h and L^J, so at fixed orbitals)
+ *   *out = sum_pq D1[p][q] h1[p][q] + sum_Jpq Gamma[J][p][q] L1[J][p][q],
+ * with D1, Gamma from sccsd_solve_multipliers and h1 [n][n], L1 [J][n][n] the
+ * change of h and L^J per unit of the perturbation (Gamma and L1 may both be
+ * NULL). Computed by FP64 reductions on the device in every precision mode.
+ * For a perturbation of eps and L through sccsd_init, h1 includes the change
+ * of h that L1 causes (h is derived from eps and L). */
+int sccsd_integral_derivative(sccsd_ctx* ctx, const double* D1, const double* Gamma,
+                              const double* h1, const double* L1, double* out);
 /* The packed amplitudes t (Sec. 2.1) of the context's current state (the
  * last sccsd_residual, or the result of a solver), e.g. the SCCSD ground state
  * after sccsd_solve_scc. SCCSD_ESTATE before any state exists. */

@@ -97,6 +97,8 @@ def _declare(lib):
     lib.sccsd_multiplier_residual.argtypes = [_dp, _dp, _dp, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_int, _dp, _dp]
     lib.sccsd_multiplier_residual.restype = ctypes.c_int
+    lib.sccsd_integral_derivative.argtypes = [_dp, _dp, _dp, _dp, _dp, _dp]
+    lib.sccsd_integral_derivative.restype = ctypes.c_int
     lib.sccsd_state_amplitudes.argtypes = [_dp, _dp]
     lib.sccsd_state_amplitudes.restype = ctypes.c_int
     lib.sccsd_capture_transform.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp, _dp,
@@ -444,6 +446,19 @@ class Context:
 
     def set_preconditioner(self, D=None):
         self._check(self.lib.sccsd_set_preconditioner(self.h, _ptr(D)))
+
+    def integral_derivative(self, D1, Gamma, h1, L1):
+        """sum D1 h1 + sum Gamma L1: a gradient or coupling along a perturbation
+        (h1, L1) of the integrals, from the effective densities."""
+        def c(x):   # NumPy arrays made contiguous; tensors (host or device) as given
+            if x is None or hasattr(x, "data_ptr"):
+                return x
+            return np.ascontiguousarray(x, dtype=np.float64)
+        out = ctypes.c_double()
+        self._check(self.lib.sccsd_integral_derivative(
+            self.h, _ptr(c(D1)), _ptr(c(Gamma)), _ptr(c(h1)), _ptr(c(L1)),
+            ctypes.addressof(out)))
+        return out.value
 
     def state_amplitudes(self):
         t = np.empty(self.dim)

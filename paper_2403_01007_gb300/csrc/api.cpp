@@ -442,6 +442,32 @@ long long sccsd_autotune_entries(void) {
   }
 }
 
+int sccsd_integral_derivative(sccsd_ctx* c, const double* D1, const double* Gamma,
+                              const double* h1, const double* L1, double* out) {
+  if (!c) return SCCSD_EINVAL;
+  if (!D1 || !h1 || !out || (Gamma == nullptr) != (L1 == nullptr))
+    return fail(c, SCCSD_EINVAL, "NULL argument");
+  return guarded(c, [&] {
+    ensure_small(c);
+    Dev d{c};
+    const int64_t n2 = (int64_t)c->n * c->n, jn2 = (int64_t)c->J * n2;
+    // host arrays are staged in solver buffers; device arrays are read in place
+    auto on_device = [&](size_t slot, const double* x, int64_t len) -> const double* {
+      if (c->be->is_device(x)) return x;
+      double* b = solver_buf(c, slot, len);
+      c->be->upload(b, x, len, false);
+      return b;
+    };
+    double s = d.dot(on_device(70, D1, n2), on_device(71, h1, n2), n2);
+    if (Gamma) s += d.dot(on_device(72, Gamma, jn2), on_device(73, L1, jn2), jn2);
+    if (c->be->is_device(out))
+      c->be->upload(out, &s, 1, false);
+    else
+      *out = s;
+    c->be->sync();
+  });
+}
+
 int sccsd_state_amplitudes(sccsd_ctx* c, double* t) {
   if (!c) return SCCSD_EINVAL;
   if (!t) return fail(c, SCCSD_EINVAL, "t is NULL");
