@@ -331,6 +331,20 @@ class System:
         rows = S.rows
         return float(pa[rows] @ pb[rows])
 
+    def overlap_states(self, t, ra0, ra, rb0, rb):
+        """SCC orthogonality with the state projection (Sec. 2.4.1):
+        O_ab = sum_kl <psi_a|R_k> (S^-1)_kl <R_l|psi_b>, S_kl = <R_k|R_l>, for
+        K = {a, b}, with |R_k> = R0_k|HF> + R_k and psi = exp(T)|R>, T without X3;
+        every inner product over full determinant vectors."""
+        S = self.S
+        T = S.op_cluster(t)
+        ka, kb = S.ket(ra0, ra), S.ket(rb0, rb)
+        pa, pb = expm_apply(T, ka, +1.0), expm_apply(T, kb, +1.0)
+        Smat = np.array([[ka @ ka, ka @ kb], [kb @ ka, kb @ kb]])
+        m = np.array([pa @ ka, pa @ kb])
+        nvec = np.array([ka @ pb, kb @ pb])
+        return float(m @ np.linalg.solve(Smat, nvec))
+
 
 def x3_operator(space: Space, ra: np.ndarray, rb: np.ndarray) -> sp.csr_matrix:
     """X3 = R1^a R2^b - R1^b R2^a (Sec. 2.4.1) as a determinant-space matrix."""

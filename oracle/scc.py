@@ -110,6 +110,20 @@ def overlap(x_t, Ra0, Ra, Rb0, Rb, o, v):
                           projected_state(x_t, Rb0, Rb, o, v))
 
 
+def overlap_states(x_t, Ra0, Ra, Rb0, Rb, o, v):
+    """O_ab of the state projection P = sum_kl |R_k> (S^-1)_kl <R_l| over
+    K = {a, b} (Sec. 2.4.1), S_kl = <R_k|R_l>: <psi_a|R_k> needs only the
+    HF+S+D part of psi_a = exp(T)|R_a>, since |R_k> lives there."""
+    zero = torch.zeros(torch.as_tensor(x_t).shape, dtype=DT)
+    ca, cb = projected_state(x_t, Ra0, Ra, o, v), projected_state(x_t, Rb0, Rb, o, v)
+    ra, rb = projected_state(zero, Ra0, Ra, o, v), projected_state(zero, Rb0, Rb, o, v)
+    S = torch.stack([torch.stack([metric_product(ra, ra), metric_product(ra, rb)]),
+                     torch.stack([metric_product(rb, ra), metric_product(rb, rb)])])
+    m = torch.stack([metric_product(ca, ra), metric_product(ca, rb)])
+    n = torch.stack([metric_product(ra, cb), metric_product(rb, cb)])
+    return m @ torch.linalg.solve(S, n)
+
+
 def fix_sign(x):
     """Sign convention for state vectors: largest |component| positive.
     A convention of this code, not of the paper."""

@@ -154,6 +154,24 @@ def test_overlap_vs_brute_force(tiny):
     assert abs(float(got) - ref) < 1e-12
 
 
+def test_state_projection_overlap_vs_brute_force(tiny):
+    """O_ab with the state projection of Sec. 2.4.1 against full determinant
+    vectors; at T = 0 the projector reproduces its own span, so O_ab is the
+    plain Hilbert overlap <R_a|R_b>."""
+    o, v, eps, L, system, prob = tiny
+    t = syn.random_vectors(o, v, 1, 7, scale=0.1)[0]
+    Ra, Rb = syn.random_vectors(o, v, 2, 17, normalise=True)
+    ref = system.overlap_states(t, 0.3, Ra, -0.2, Rb)
+    got = sc.overlap_states(torch.tensor(t), 0.3, torch.tensor(Ra), -0.2, torch.tensor(Rb), o, v)
+    assert abs(float(got) - ref) < 1e-12 * max(1.0, abs(ref))
+    z = np.zeros_like(t)
+    S = system.S
+    plain = float(S.ket(0.3, Ra) @ S.ket(-0.2, Rb))
+    assert abs(system.overlap_states(z, 0.3, Ra, -0.2, Rb) - plain) < 1e-12
+    got0 = sc.overlap_states(torch.tensor(z), 0.3, torch.tensor(Ra), -0.2, torch.tensor(Rb), o, v)
+    assert abs(float(got0) - plain) < 1e-12
+
+
 # --------------------------------------------------------- exactness for N = 2
 
 def test_two_electron_ccsd_is_full_ci():
