@@ -157,6 +157,20 @@ long long sccsd_gemm_tn_noalloc_capacity(void);
 int sccsd_overlap(sccsd_ctx* ctx, double ra0, const double* Ra, double rb0, const double* Rb,
                   double* O);
 
+/* SCC orthogonality with the state projection P = sum_kl |R_k> (S^-1)_kl <R_l|
+ * over K = {a, b} (Sec. 2.4.1), S_kl = <R_k|R_l>, |R_k> = R0_k |HF> + R_k:
+ *   O_ab = sum_kl <psi_a|R_k> (S^-1)_kl <R_l|psi_b>,
+ * with psi and the inner product as for sccsd_overlap. Result in *O;
+ * SCCSD_EINVAL if R_a and R_b are linearly dependent. */
+int sccsd_overlap_states(sccsd_ctx* ctx, double ra0, const double* Ra, double rb0,
+                         const double* Rb, double* O);
+
+/* The projection sccsd_solve_scc constrains: 0 the natural projection
+ * (SCCSD(E), the default), 1 the state projection (SCCSD(K)), Sec. 2.4.1.
+ * sccsd_solve_multipliers supports the natural projection only and returns
+ * SCCSD_EINVAL after a switch to 1. */
+int sccsd_set_projection(sccsd_ctx* ctx, int projection);
+
 /* Self-consistent SCCSD for the two lowest states, K = {a, b} (Sec. 2.4.2):
  * find zeta with O_ab = 0 (Sec. 2.2). For each zeta the ground state is
  * converged with zeta X3 built from the current R_a, R_b (ground_tol), the two

@@ -131,7 +131,7 @@ def fix_sign(x):
 
 
 def solve_scc(prob, tol=1e-10, maxit=40, ground_tol=1e-11, eom_tol=1e-9, dense=False,
-              start=None):
+              start=None, projection="natural"):
     """Self-consistent SCCSD for the two lowest states a, b (K = {a, b},
     Sec. 2.4.2): find zeta with O_ab(zeta) = 0, where at each zeta the ground
     state T(zeta) is converged with X3 built from the current R_a, R_b and the
@@ -139,7 +139,8 @@ def solve_scc(prob, tol=1e-10, maxit=40, ground_tol=1e-11, eom_tol=1e-9, dense=F
     (block form of the EOM matrix, Sec. 2.1). The root is followed from zeta = 0
     (plain CCSD) by the secant method on O_ab. dense=True takes the roots from
     the explicit Jacobian (small systems); start = (zeta, t, Ra, Rb) of a
-    nearby solution replaces the zeta = 0 start. Returns a dict."""
+    nearby solution replaces the zeta = 0 start. projection = "state" constrains
+    O_ab of the state projection instead (SCCSD(K), Sec. 2.4.1). Returns a dict."""
     from . import solvers as sv
     from . import response as rp
     o, v = prob.o, prob.v
@@ -155,7 +156,8 @@ def solve_scc(prob, tol=1e-10, maxit=40, ground_tol=1e-11, eom_tol=1e-9, dense=F
         Xa, Xb = fix_sign(X[0]), fix_sign(X[1])
         eta = rp.eta(prob, x, scc=scc).numpy()
         r0a, r0b = float(eta @ Xa / w[0]), float(eta @ Xb / w[1])
-        O = float(overlap(torch.tensor(x), r0a, torch.tensor(Xa), r0b, torch.tensor(Xb), o, v))
+        ovl = overlap if projection == "natural" else overlap_states
+        O = float(ovl(torch.tensor(x), r0a, torch.tensor(Xa), r0b, torch.tensor(Xb), o, v))
         hist.append((zeta, O))
         Ra, Rb = Xa, Xb
         if abs(O) < tol and len(hist) > 1 and abs(hist[-1][0] - hist[-2][0]) < 1e-8:

@@ -60,6 +60,10 @@ def _declare(lib):
                                        ctypes.c_int, ctypes.c_double, _dp, _dp, _dp]
     lib.sccsd_solve_states.restype = ctypes.c_int
     lib.sccsd_overlap.argtypes = [_dp, ctypes.c_double, _dp, ctypes.c_double, _dp, _dp]
+    lib.sccsd_overlap_states.argtypes = [_dp, ctypes.c_double, _dp, ctypes.c_double, _dp, _dp]
+    lib.sccsd_overlap_states.restype = ctypes.c_int
+    lib.sccsd_set_projection.argtypes = [_dp, ctypes.c_int]
+    lib.sccsd_set_projection.restype = ctypes.c_int
     lib.sccsd_overlap.restype = ctypes.c_int
     lib.sccsd_solve_scc.argtypes = [_dp, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
@@ -409,11 +413,23 @@ class Context:
         return w, V, it.value
 
     def overlap(self, ra0, Ra, rb0, Rb):
-        """SCC orthogonality O_ab at the fixed state."""
+        """SCC orthogonality O_ab at the fixed state (natural projection)."""
         out = ctypes.c_double()
         self._check(self.lib.sccsd_overlap(self.h, float(ra0), _ptr(Ra), float(rb0), _ptr(Rb),
                                            ctypes.addressof(out)))
         return out.value
+
+    def overlap_states(self, ra0, Ra, rb0, Rb):
+        """SCC orthogonality O_ab with the state projection over K = {a, b}."""
+        out = ctypes.c_double()
+        self._check(self.lib.sccsd_overlap_states(self.h, float(ra0), _ptr(Ra), float(rb0),
+                                                  _ptr(Rb), ctypes.addressof(out)))
+        return out.value
+
+    def set_projection(self, projection):
+        """0 / "natural": SCCSD(E); 1 / "state": SCCSD(K), for sccsd_solve_scc."""
+        p = {"natural": 0, "state": 1}.get(projection, projection)
+        self._check(self.lib.sccsd_set_projection(self.h, int(p)))
 
     def solve_scc(self, tol=1e-10, maxit=40, ground_tol=1e-11, eom_tol=1e-9):
         """Self-consistent SCCSD for the two lowest states; returns a dict."""

@@ -385,6 +385,39 @@ int sccsd_overlap(sccsd_ctx* c, double ra0, const double* Ra, double rb0, const 
   });
 }
 
+int sccsd_overlap_states(sccsd_ctx* c, double ra0, const double* Ra, double rb0,
+                         const double* Rb, double* O) {
+  if (!c) return SCCSD_EINVAL;
+  if (!Ra || !Rb || !O) return fail(c, SCCSD_EINVAL, "NULL argument");
+  if (!c->cur) return fail(c, SCCSD_ESTATE, "call sccsd_residual or a solver first");
+  return guarded(c, [&] {
+    Model& m = *c->cur;
+    OverlapSec& S = overlap_section(m);
+    OverlapKSec& K = overlap_k_section(m);
+    set_scalar(c, m.g, S.ra0, ra0);
+    set_scalar(c, m.g, S.rb0, rb0);
+    load_packed(c, m.g, Ra, S.ra1, S.ra2, false);
+    load_packed(c, m.g, Rb, S.rb1, S.rb2, false);
+    m.g.run({K.maa, K.mab, K.nab, K.nbb, K.Saa, K.Sab, K.Sbb});
+    auto v = [&](int id) { return get_scalar(c, m.g, id); };
+    const double maa = v(K.maa), mab = v(K.mab), nab = v(K.nab), nbb = v(K.nbb);
+    const double Saa = v(K.Saa), Sab = v(K.Sab), Sbb = v(K.Sbb);
+    const double det = Saa * Sbb - Sab * Sab;
+    if (!(std::fabs(det) > 1e-14 * std::max(1.0, Saa * Sbb)))
+      throw std::invalid_argument("R_a and R_b are linearly dependent");
+    // m^T S^-1 n with the 2 x 2 inverse written out
+    *O = (maa * (Sbb * nab - Sab * nbb) + mab * (Saa * nbb - Sab * nab)) / det;
+    c->be->sync();
+  });
+}
+
+int sccsd_set_projection(sccsd_ctx* c, int projection) {
+  if (!c) return SCCSD_EINVAL;
+  if (projection != 0 && projection != 1) return fail(c, SCCSD_EINVAL, "projection must be 0 or 1");
+  c->projection = projection;
+  return SCCSD_OK;
+}
+
 int sccsd_set_precision(sccsd_ctx* c, int precision) {
   if (!c) return SCCSD_EINVAL;
   if (precision < SCCSD_FP64 || precision > SCCSD_BF16) return fail(c, SCCSD_EINVAL, "bad precision");

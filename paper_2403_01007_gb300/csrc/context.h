@@ -36,7 +36,15 @@ struct LeftSec {
 struct OverlapSec {
   int ra0, ra1, ra2, rb0, rb1, rb2;
   int O;
+  int ca1, ca2, cb1, cb2;           // HF+S+D parts of exp(T)|R_a>, exp(T)|R_b>
   size_t op_begin = 0, op_end = 0;  // the section's ops
+};
+
+// The scalars of O_ab with the state projection over K = {a, b}:
+// m_k = <psi_a|R_k>, n_l = <R_l|psi_b>, S_kl = <R_k|R_l> (same inputs as
+// OverlapSec); O_ab = m^T S^-1 n is formed on the host.
+struct OverlapKSec {
+  int maa, mab, nab, nbb, Saa, Sab, Sbb;
 };
 
 // Gradient of <K|Hbar|R> (bra (k0, K), ket (r0, R) in the density inputs) with
@@ -56,6 +64,7 @@ struct Model {
   Graph g;
   bool scc = false;
   std::unique_ptr<OverlapSec> ovl;
+  std::unique_ptr<OverlapKSec> ovk;
   Graph::Ranges fwd;
   std::vector<int> vol_inputs;
   std::map<int64_t, RightSec> right;  // batched right transformations by batch size
@@ -78,6 +87,7 @@ struct Model {
 std::unique_ptr<Model> build_model(Backend* be, int o, int v, int J, bool scc);
 // lazily built graph sections (model.cpp)
 OverlapSec& overlap_section(Model& M);
+OverlapKSec& overlap_k_section(Model& M);
 RightSec& right_section(Model& M, int64_t nb);
 LeftSec& left_section(Model& M, int64_t nb);
 LagSec& lag_section(Model& M);
@@ -103,6 +113,7 @@ struct sccsd_ctx {
   double* D = nullptr;        // packed orbital-energy denominators
   double* Dprec = nullptr;    // user/learned preconditioner of the ground-state update
   bool use_dprec = false;
+  int projection = 0;  // SCC overlap: 0 natural, 1 state projection (Sec. 2.4.1)
   std::vector<double*> sv;    // solver work buffers
   std::vector<int64_t> sv_n;  // their sizes (doubles)
   double* sv_small = nullptr; // small matrices and vectors

@@ -124,6 +124,10 @@ OverlapSec& overlap_section(Model& M) {
   int ca1, ca2, cb1, cb2;
   state(S->ra0, S->ra1, S->ra2, ca1, ca2);
   state(S->rb0, S->rb1, S->rb2, cb1, cb2);
+  S->ca1 = ca1;
+  S->ca2 = ca2;
+  S->cb1 = cb1;
+  S->cb2 = cb2;
   int q = g.add("ijab", {{cb2, "ijab", 2.0}, {cb2, "jiab", -1.0}});
   S->O = g.add("", {{g.contract(S->ra0, "", S->rb0, "", ""), "", 1.0},
                     {g.contract(ca1, "ai", cb1, "ai", ""), "", 2.0},
@@ -133,6 +137,30 @@ OverlapSec& overlap_section(Model& M) {
   g.set_volatile_inputs(M.vol_inputs);
   M.ovl = std::move(S);
   return *M.ovl;
+}
+
+OverlapKSec& overlap_k_section(Model& M) {
+  if (M.ovk) return *M.ovk;
+  OverlapSec& O = overlap_section(M);
+  Graph& g = M.g;
+  auto S = std::make_unique<OverlapKSec>();
+  // <x|y> over HF+S+D kets: x0 y0 + 2 x1.y1 + x2.(2 y2 - y2 with j <-> i)
+  auto metric = [&](int x0, int x1, int x2, int y0, int y1, int y2) {
+    int q = g.add("ijab", {{y2, "ijab", 2.0}, {y2, "jiab", -1.0}});
+    return g.add("", {{g.contract(x0, "", y0, "", ""), "", 1.0},
+                      {g.contract(x1, "ai", y1, "ai", ""), "", 2.0},
+                      {g.contract(x2, "ijab", q, "ijab", ""), "", 1.0}});
+  };
+  // the c0 part of exp(T)|R> is R0 itself
+  S->maa = metric(O.ra0, O.ca1, O.ca2, O.ra0, O.ra1, O.ra2);
+  S->mab = metric(O.ra0, O.ca1, O.ca2, O.rb0, O.rb1, O.rb2);
+  S->nab = metric(O.ra0, O.ra1, O.ra2, O.rb0, O.cb1, O.cb2);
+  S->nbb = metric(O.rb0, O.rb1, O.rb2, O.rb0, O.cb1, O.cb2);
+  S->Saa = metric(O.ra0, O.ra1, O.ra2, O.ra0, O.ra1, O.ra2);
+  S->Sab = metric(O.ra0, O.ra1, O.ra2, O.rb0, O.rb1, O.rb2);
+  S->Sbb = metric(O.rb0, O.rb1, O.rb2, O.rb0, O.rb1, O.rb2);
+  M.ovk = std::move(S);
+  return *M.ovk;
 }
 
 // sigma = A R for nb trial vectors at once (forward mode with a batch label)

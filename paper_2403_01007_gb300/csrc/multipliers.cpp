@@ -359,6 +359,8 @@ int sccsd_solve_multipliers(sccsd_ctx* c, const double* vecs, const double* scal
                 : (kind != 1 || m_state < 0 || m_state > 1 || n_state < 0 || n_state > 1 ||
                    m_state == n_state))
     return fail(c, SCCSD_EINVAL, "bad target");
+  if (c->projection != 0)
+    return fail(c, SCCSD_EINVAL, "multipliers are implemented for the natural projection only");
   int status = SCCSD_OK;
   int rc = guarded(c, [&] {
     MultSolver S{};

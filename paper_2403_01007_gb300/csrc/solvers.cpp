@@ -502,7 +502,9 @@ int sccsd_solve_scc(sccsd_ctx* c, double tol, int maxit, double ground_tol, doub
         eta_dot(c, 2, vecs.data(), etaR);
         r0[0] = etaR[0] / w[0];
         r0[1] = etaR[1] / w[1];
-        check(sccsd_overlap(c, r0[0], vecs.data(), r0[1], vecs.data() + dim, &O));
+        check(c->projection == 1
+                  ? sccsd_overlap_states(c, r0[0], vecs.data(), r0[1], vecs.data() + dim, &O)
+                  : sccsd_overlap(c, r0[0], vecs.data(), r0[1], vecs.data() + dim, &O));
       }
       if (getenv("SCCSD_LOG"))
         fprintf(stderr, "{\"solver\": \"scc\", \"iter\": %d, \"zeta\": %.12f, \"O_ab\": %.3e, \"omega\": [%.12f, %.12f]}\n",

@@ -89,7 +89,7 @@ def _scc_active_values(s, prob):
             "omega": [float(x) for x in s["omega"]]}
 
 
-def scc_active():
+def scc_active(projection="natural"):
     """A system where the constraint is active (zeta far from 0): the
     self-consistent SCCSD solution of Sec. 2.2 and 2.4 for the two lowest
     states, from the oracle's loop (ground state and Davidson roots
@@ -101,12 +101,12 @@ def scc_active():
     p = SCC_ACTIVE
     eps, L = syn.system(p["o"], p["v"], p["J"], p["sd"], p["seed"])
     prob = cc.Problem(eps, L, p["o"])
-    s = sc.solve_scc(prob, tol=1e-10)
+    s = sc.solve_scc(prob, tol=1e-10, projection=projection)
     return {
         "citation": "Sec. 2.2 (O_ab = 0 enforced by zeta) and Sec. 2.4.1-2.4.2 (SCCSD with "
-                    "X3 = R1^a R2^b - R1^b R2^a, natural projection)",
+                    "X3 = R1^a R2^b - R1^b R2^a, %s projection)" % projection,
         "produced_by": "tests/golden/make_golden.py: oracle.scc.solve_scc (Davidson roots)",
-        "inputs": {"generator": "synthetic.system", **p},
+        "inputs": {"generator": "synthetic.system", **p, "projection": projection},
         "values": _scc_active_values(s, prob),
         "state": {"t": [float(x) for x in s["t"]], "Ra": [float(x) for x in s["Ra"]],
                   "Rb": [float(x) for x in s["Rb"]]},
@@ -141,18 +141,21 @@ def scc_active_verify(stored):
         AR = rp.jacobian_right(prob, t, R, scc=scc).numpy()
         out["eigen-equation " + name] = (float(np.linalg.norm(AR - w * R)), 1e-7)
         r0.append(float(eta @ R / w))
-    O = float(sc.overlap(torch.tensor(t), r0[0], torch.tensor(Ra), r0[1], torch.tensor(Rb),
-                         prob.o, prob.v))
+    ovl = sc.overlap_states if stored["inputs"].get("projection") == "state" else sc.overlap
+    O = float(ovl(torch.tensor(t), r0[0], torch.tensor(Ra), r0[1], torch.tensor(Rb),
+                  prob.o, prob.v))
     out["O_ab"] = (abs(O), 1e-9)
     return out
 
 
 FIXTURES = {"fci_two_electron_o1_v5.json": fci_two_electron,
             "scc_symmetric_o3_v6.json": scc_symmetric,
-            "scc_active_o3_v8.json": scc_active}
+            "scc_active_o3_v8.json": scc_active,
+            "scc_state_projection_o3_v8.json": lambda: scc_active("state")}
 # fixtures whose full regeneration is slow: checked through their defining
 # equations instead
-VERIFY = {"scc_active_o3_v8.json": scc_active_verify}
+VERIFY = {"scc_active_o3_v8.json": scc_active_verify,
+          "scc_state_projection_o3_v8.json": scc_active_verify}
 
 
 def load(name):

@@ -791,3 +791,57 @@ def test_gradient_and_coupling_by_finite_differences(host_lib):
     with pytest.raises(B.SccsdError):
         ctx.integral_derivative(grad["D1"], grad["Gamma"], np.diag(de), None)
     ctx.close()
+
+
+# ------------------------------------- SCCSD(K): the state projection (Sec. 2.4.1)
+
+@pytest.mark.parametrize("with_scc", [False, True], ids=["ccsd", "sccsd"])
+def test_state_projection_overlap_through_the_c_abi(host_lib, with_scc):
+    from oracle import scc as sc
+    B, lib = host_lib
+    o, v, J = 3, 4, 7
+    eps, L = syn.system(o, v, J, 0.3, 64)
+    t = syn.random_vectors(o, v, 1, 65, scale=0.1)[0]
+    Ra, Rb = syn.random_vectors(o, v, 2, 66, normalise=True)
+    ctx = B.Context(o, v, J, eps, L, lib=lib)
+    ctx.residual(t, scc=(0.2, Ra, Rb) if with_scc else None)
+    O = ctx.overlap_states(0.3, Ra, -0.2, Rb)
+    ref = float(sc.overlap_states(torch.tensor(t), 0.3, torch.tensor(Ra), -0.2, torch.tensor(Rb),
+                                  o, v))
+    assert abs(O - ref) < 1e-13 * max(1.0, abs(ref))
+    with pytest.raises(B.SccsdError):
+        ctx.overlap_states(0.3, Ra, 0.6, 2.0 * Ra)      # linearly dependent states
+    ctx.close()
+
+
+def test_state_projection_scc_loop_through_the_c_abi(host_lib):
+    """SCCSD(K): the SCC loop constraining O_ab of the state projection reaches
+    the stored oracle solution; the multiplier equations, implemented for the
+    natural projection only, refuse this context."""
+    from oracle import scc as sc
+    B, lib = host_lib
+    g = _golden("scc_state_projection_o3_v8.json")
+    p = g["inputs"]
+    eps, L = syn.system(p["o"], p["v"], p["J"], p["sd"], p["seed"])
+    ctx = B.Context(p["o"], p["v"], p["J"], eps, L, lib=lib)
+    with pytest.raises(B.SccsdError):
+        ctx.set_projection(2)
+    ctx.set_projection("state")
+    r = ctx.solve_scc(tol=1e-10)
+    t = ctx.state_amplitudes()
+    assert abs(r["zeta"] - g["values"]["zeta"]) < 1e-7
+    assert np.abs(r["omega"] - np.array(g["values"]["omega"])).max() < 1e-8
+    assert abs(r["e_corr"] - g["values"]["e_corr"]) < 1e-9
+    O = float(sc.overlap_states(torch.tensor(t), r["r0"][0], torch.tensor(r["Ra"]), r["r0"][1],
+                                torch.tensor(r["Rb"]), p["o"], p["v"]))
+    assert abs(O) < 1e-9
+    # the natural-projection solution of the same system differs (small, as the paper notes)
+    nat = _golden("scc_active_o3_v8.json")["values"]["zeta"]
+    assert 1e-4 < abs(r["zeta"] - nat) < 1e-2
+    state = {"t": t, "Ra": r["Ra"], "Rb": r["Rb"], "La": r["Ra"], "Lb": r["Rb"],
+             "zeta": r["zeta"], "r0a": r["r0"][0], "r0b": r["r0"][1],
+             "omega_a": r["omega"][0], "omega_b": r["omega"][1]}
+    with pytest.raises(B.SccsdError) as ei:
+        ctx.solve_multipliers(state, ("gradient", 0))
+    assert ei.value.code == -1
+    ctx.close()
