@@ -167,8 +167,8 @@ int sccsd_overlap_states(sccsd_ctx* ctx, double ra0, const double* Ra, double rb
 
 /* The projection sccsd_solve_scc constrains: 0 the natural projection
  * (SCCSD(E), the default), 1 the state projection (SCCSD(K)), Sec. 2.4.1.
- * sccsd_solve_multipliers supports the natural projection only and returns
- * SCCSD_EINVAL after a switch to 1. */
+ * sccsd_solve_multipliers and sccsd_multiplier_residual use the same choice
+ * for the gbar O_ab term of the Lagrangian. */
 int sccsd_set_projection(sccsd_ctx* ctx, int projection);
 
 /* Self-consistent SCCSD for the two lowest states, K = {a, b} (Sec. 2.4.2):
@@ -309,7 +309,8 @@ int sccsd_set_preconditioner(sccsd_ctx* ctx, const double* Dprec);
 /* ---- Lagrangian multipliers (gradients and couplings) ---------------------
  * sccsd_solve_multipliers solves the stationarity equations of the SCCSD
  * Lagrangian (Sec. 2.3.1 and 2.3.3 of the paper) for K = {a, b} with the
- * natural projection, at fixed orbitals (no orbital multipliers), for
+ * context's projection (sccsd_set_projection; natural by default), at fixed
+ * orbitals (no orbital multipliers), for
  *   kind 0: the gradient of state n_state (0 = a, 1 = b), or
  *   kind 1: the derivative coupling <psi_m|d psi_n> from the bra-frozen
  *           overlap O_mn (Sec. 2.3.4), m_state != n_state.

@@ -73,14 +73,20 @@ def frozen_overlap(t, t0, Lm, r0n, Rn, o, v):
     return torch.dot(_t(Lm), ket)
 
 
-def scc_state(prob, tol=1e-12, ground_tol=1e-12, near=None):
+def _overlap_of(st):
+    """O_ab of the state's projection: natural (default) or state (Sec. 2.4.1)."""
+    return sc.overlap_states if st.get("projection", "natural") == "state" else sc.overlap
+
+
+def scc_state(prob, tol=1e-12, ground_tol=1e-12, near=None, projection="natural"):
     """Converged SCCSD for K = {a, b} (small systems: roots from the explicit
     Jacobian): t, zeta, right vectors (r0, R), left vectors L (L_k . R_k = 1),
     omegas and E0. near: a state of a nearby system to start from.
     SCCSD of Sec. 2.2 and 2.4, the state the Lagrangian of Sec. 2.3.1 is taken at."""
     start = None if near is None else (near["zeta"], near["t"].numpy(), near["Ra"].numpy(),
                                        near["Rb"].numpy())
-    s = sc.solve_scc(prob, tol=tol, ground_tol=ground_tol, dense=True, start=start)
+    s = sc.solve_scc(prob, tol=tol, ground_tol=ground_tol, dense=True, start=start,
+                     projection=projection)
     scc = (s["zeta"], _t(s["Ra"]), _t(s["Rb"]))
     wl, XL = sv.eom_dense(prob, s["t"], 2, side="left", scc=scc)
     La = XL[0] / (XL[0] @ s["Ra"])
@@ -88,7 +94,8 @@ def scc_state(prob, tol=1e-12, ground_tol=1e-12, near=None):
     return {"t": _t(s["t"]), "zeta": float(s["zeta"]), "Ra": _t(s["Ra"]), "Rb": _t(s["Rb"]),
             "r0a": float(s["r0"][0]), "r0b": float(s["r0"][1]), "La": _t(La), "Lb": _t(Lb),
             "omega": (float(s["omega"][0]), float(s["omega"][1])), "E0": float(s["E0"]),
-            "omega_left": (float(wl[0]), float(wl[1])), "o": prob.o, "v": prob.v}
+            "omega_left": (float(wl[0]), float(wl[1])), "o": prob.o, "v": prob.v,
+            "projection": projection}
 
 
 def _target(target):
@@ -135,7 +142,7 @@ def lagrangian(prob, st, target, P, M, h=None, L=None, lam=None):
         r0, R = kets[k]
         val = val + T(l0, Lb, k) - E[k] * (l0 * r0 + torch.dot(Lb, R))
         val = val + Ebar[k] * (1.0 - torch.dot(lam[k], R))
-    val = val + M["gbar"] * sc.overlap(t, P["r0a"], P["Ra"], P["r0b"], P["Rb"], o, v)
+    val = val + M["gbar"] * _overlap_of(st)(t, P["r0a"], P["Ra"], P["r0b"], P["Rb"], o, v)
     _, Om = cc.energy_residual(t, prob, h=h, L=L, scc=scc)
     return val + torch.dot(M["zbar"], Om)
 
@@ -152,7 +159,7 @@ def overlap_r0_derivatives(prob, st):
     """(dO_ab/dr0_a, dO_ab/dr0_b) at the solution.
     The dO/dR0 terms of the stationarity equations (Sec. 2.3.3)."""
     P = params_of(st)
-    f = lambda ra0, rb0: sc.overlap(P["t"], ra0, P["Ra"], rb0, P["Rb"], prob.o, prob.v)
+    f = lambda ra0, rb0: _overlap_of(st)(P["t"], ra0, P["Ra"], rb0, P["Rb"], prob.o, prob.v)
     g = grad(f, argnums=(0, 1))(P["r0a"], P["r0b"])
     return float(g[0]), float(g[1])
 

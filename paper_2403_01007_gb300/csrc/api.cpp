@@ -399,14 +399,10 @@ int sccsd_overlap_states(sccsd_ctx* c, double ra0, const double* Ra, double rb0,
     load_packed(c, m.g, Ra, S.ra1, S.ra2, false);
     load_packed(c, m.g, Rb, S.rb1, S.rb2, false);
     m.g.run({K.maa, K.mab, K.nab, K.nbb, K.Saa, K.Sab, K.Sbb});
-    auto v = [&](int id) { return get_scalar(c, m.g, id); };
-    const double maa = v(K.maa), mab = v(K.mab), nab = v(K.nab), nbb = v(K.nbb);
-    const double Saa = v(K.Saa), Sab = v(K.Sab), Sbb = v(K.Sbb);
-    const double det = Saa * Sbb - Sab * Sab;
-    if (!(std::fabs(det) > 1e-14 * std::max(1.0, Saa * Sbb)))
-      throw std::invalid_argument("R_a and R_b are linearly dependent");
-    // m^T S^-1 n with the 2 x 2 inverse written out
-    *O = (maa * (Sbb * nab - Sab * nbb) + mab * (Saa * nbb - Sab * nab)) / det;
+    const int ids[7] = {K.maa, K.mab, K.nab, K.nbb, K.Saa, K.Sab, K.Sbb};
+    double sv[7];
+    for (int i = 0; i < 7; ++i) sv[i] = get_scalar(c, m.g, ids[i]);
+    *O = overlap_k_value(sv);
     c->be->sync();
   });
 }

@@ -45,6 +45,15 @@ struct OverlapSec {
 // OverlapSec); O_ab = m^T S^-1 n is formed on the host.
 struct OverlapKSec {
   int maa, mab, nab, nbb, Saa, Sab, Sbb;
+  size_t op_begin = 0, op_end = 0;
+};
+
+// Gradient of sum_i w_i s_i over the seven scalars s of OverlapKSec, with
+// respect to t and both states; with w_i = gbar dO_ab/ds_i (formed on the host
+// at the state) it is the gradient of gbar O_ab of the state projection.
+struct OvlKGradSec {
+  int w[7];
+  int dt1, dt2, da0, da1, da2, db0, db1, db2;
 };
 
 // Gradient of <K|Hbar|R> (bra (k0, K), ket (r0, R) in the density inputs) with
@@ -65,6 +74,7 @@ struct Model {
   bool scc = false;
   std::unique_ptr<OverlapSec> ovl;
   std::unique_ptr<OverlapKSec> ovk;
+  std::unique_ptr<OvlKGradSec> ovkg;
   Graph::Ranges fwd;
   std::vector<int> vol_inputs;
   std::map<int64_t, RightSec> right;  // batched right transformations by batch size
@@ -88,6 +98,29 @@ std::unique_ptr<Model> build_model(Backend* be, int o, int v, int J, bool scc);
 // lazily built graph sections (model.cpp)
 OverlapSec& overlap_section(Model& M);
 OverlapKSec& overlap_k_section(Model& M);
+OvlKGradSec& overlap_k_grad_section(Model& M);
+
+// O_ab = m^T S^-1 n of the state projection from its scalars
+// s = (m_a, m_b, n_a, n_b, S_aa, S_ab, S_bb) (the 2 x 2 inverse written out),
+// and its partial derivatives dO/ds_i; throws if S is singular.
+inline double overlap_k_value(const double* s, double* w = nullptr) {
+  const double maa = s[0], mab = s[1], nab = s[2], nbb = s[3];
+  const double Saa = s[4], Sab = s[5], Sbb = s[6];
+  const double det = Saa * Sbb - Sab * Sab;
+  if (!(std::fabs(det) > 1e-14 * std::max(1.0, Saa * Sbb)))
+    throw std::invalid_argument("R_a and R_b are linearly dependent");
+  const double N = maa * (Sbb * nab - Sab * nbb) + mab * (Saa * nbb - Sab * nab);
+  if (w) {
+    w[0] = (Sbb * nab - Sab * nbb) / det;
+    w[1] = (Saa * nbb - Sab * nab) / det;
+    w[2] = (maa * Sbb - mab * Sab) / det;
+    w[3] = (mab * Saa - maa * Sab) / det;
+    w[4] = mab * nbb / det - N * Sbb / (det * det);
+    w[5] = -(maa * nbb + mab * nab) / det + 2.0 * N * Sab / (det * det);
+    w[6] = maa * nab / det - N * Saa / (det * det);
+  }
+  return N / det;
+}
 RightSec& right_section(Model& M, int64_t nb);
 LeftSec& left_section(Model& M, int64_t nb);
 LagSec& lag_section(Model& M);

@@ -144,6 +144,7 @@ OverlapKSec& overlap_k_section(Model& M) {
   OverlapSec& O = overlap_section(M);
   Graph& g = M.g;
   auto S = std::make_unique<OverlapKSec>();
+  S->op_begin = g.ops.size();
   // <x|y> over HF+S+D kets: x0 y0 + 2 x1.y1 + x2.(2 y2 - y2 with j <-> i)
   auto metric = [&](int x0, int x1, int x2, int y0, int y1, int y2) {
     int q = g.add("ijab", {{y2, "ijab", 2.0}, {y2, "jiab", -1.0}});
@@ -159,8 +160,37 @@ OverlapKSec& overlap_k_section(Model& M) {
   S->Saa = metric(O.ra0, O.ra1, O.ra2, O.ra0, O.ra1, O.ra2);
   S->Sab = metric(O.ra0, O.ra1, O.ra2, O.rb0, O.rb1, O.rb2);
   S->Sbb = metric(O.rb0, O.rb1, O.rb2, O.rb0, O.rb1, O.rb2);
+  S->op_end = g.ops.size();
   M.ovk = std::move(S);
   return *M.ovk;
+}
+
+OvlKGradSec& overlap_k_grad_section(Model& M) {
+  if (M.ovkg) return *M.ovkg;
+  OverlapSec& O = overlap_section(M);
+  OverlapKSec& K = overlap_k_section(M);
+  Graph& g = M.g;
+  auto S = std::make_unique<OvlKGradSec>();
+  const int sc[7] = {K.maa, K.mab, K.nab, K.nbb, K.Saa, K.Sab, K.Sbb};
+  std::map<int, int> seeds;
+  for (int i = 0; i < 7; ++i) {
+    S->w[i] = g.input({}, "wK" + std::to_string(i));
+    seeds[sc[i]] = S->w[i];
+  }
+  auto adj = g.adjoint(seeds, {M.t1, M.t2, O.ra0, O.ra1, O.ra2, O.rb0, O.rb1, O.rb2},
+                       {{O.op_begin, O.op_end}, {K.op_begin, K.op_end}});
+  S->dt1 = adj[M.t1];
+  S->dt2 = adj[M.t2];
+  S->da0 = adj[O.ra0];
+  S->da1 = adj[O.ra1];
+  S->da2 = adj[O.ra2];
+  S->db0 = adj[O.rb0];
+  S->db1 = adj[O.rb1];
+  S->db2 = adj[O.rb2];
+  for (int i = 0; i < 7; ++i) M.vol_inputs.push_back(S->w[i]);
+  g.set_volatile_inputs(M.vol_inputs);
+  M.ovkg = std::move(S);
+  return *M.ovkg;
 }
 
 // sigma = A R for nb trial vectors at once (forward mode with a batch label)

@@ -36,6 +36,8 @@ struct MultSolver {
   int64_t dim, N;
   const double* vec[5];  // t, Ra, Rb, La, Lb (device, packed)
   double zeta, r0[2], omega[2], E0 = 0.0, dO[2] = {0.0, 0.0};
+  int proj = 0;              // 0 natural, 1 state projection of O_ab
+  double wK[7] = {0.0};      // dO_ab/ds for the state projection's scalars
   double *tmp, *zero, *zero1, *zero2, *Kb[2], *Bc, *Ot, *Pd;
   cudaStream_t st() const { return (cudaStream_t)c->be->stream(); }
 
@@ -123,15 +125,27 @@ struct MultSolver {
     add_grad(S.gRa1, S.gRa2, 1.0, rR[0]);
     add_grad(S.gRb1, S.gRb2, 1.0, rR[1]);
     rz += scalar_node(S.gz);
-    OvlGradSec& Og = overlap_grad_section(*m);
-    set_scalar(c, g, Og.gbar, gbar);
-    std::vector<int> tg;
-    for (int x : {Og.dt1, Og.dt2, Og.da1, Og.da2, Og.db1, Og.db2})
-      if (!g.is_zero(x)) tg.push_back(x);
-    g.run(tg);
-    add_grad(Og.dt1, Og.dt2, 1.0, rt);
-    add_grad(Og.da1, Og.da2, 1.0, rR[0]);
-    add_grad(Og.db1, Og.db2, 1.0, rR[1]);
+    if (proj == 1) {
+      OvlKGradSec& Og = overlap_k_grad_section(*m);
+      for (int i = 0; i < 7; ++i) set_scalar(c, g, Og.w[i], gbar * wK[i]);
+      std::vector<int> tg;
+      for (int x : {Og.dt1, Og.dt2, Og.da1, Og.da2, Og.db1, Og.db2})
+        if (!g.is_zero(x)) tg.push_back(x);
+      g.run(tg);
+      add_grad(Og.dt1, Og.dt2, 1.0, rt);
+      add_grad(Og.da1, Og.da2, 1.0, rR[0]);
+      add_grad(Og.db1, Og.db2, 1.0, rR[1]);
+    } else {
+      OvlGradSec& Og = overlap_grad_section(*m);
+      set_scalar(c, g, Og.gbar, gbar);
+      std::vector<int> tg;
+      for (int x : {Og.dt1, Og.dt2, Og.da1, Og.da2, Og.db1, Og.db2})
+        if (!g.is_zero(x)) tg.push_back(x);
+      g.run(tg);
+      add_grad(Og.dt1, Og.dt2, 1.0, rt);
+      add_grad(Og.da1, Og.da2, 1.0, rR[0]);
+      add_grad(Og.db1, Og.db2, 1.0, rR[1]);
+    }
     if (kind == 1) {
       launch_axpby(st(), dim, 1.0, Ot, 1.0, rt);
       launch_axpby(st(), dim, 1.0, vec[3 + ms], 1.0, rR[ns]);
@@ -143,14 +157,32 @@ struct MultSolver {
 
   void precompute() {
     Graph& g = m->g;
-    OvlGradSec& Og = overlap_grad_section(*m);
-    set_scalar(c, g, Og.gbar, 1.0);
-    std::vector<int> tg;
-    for (int x : {Og.da0, Og.db0})
-      if (!g.is_zero(x)) tg.push_back(x);
-    if (!tg.empty()) g.run(tg);
-    dO[0] = scalar_node(Og.da0);
-    dO[1] = scalar_node(Og.db0);
+    if (proj == 1) {
+      // the state projection's scalars at the state fix the weights dO/ds
+      OverlapKSec& K = overlap_k_section(*m);
+      const int ids[7] = {K.maa, K.mab, K.nab, K.nbb, K.Saa, K.Sab, K.Sbb};
+      g.run(std::vector<int>(ids, ids + 7));
+      double sv[7];
+      for (int i = 0; i < 7; ++i) sv[i] = scalar_node(ids[i]);
+      overlap_k_value(sv, wK);
+      OvlKGradSec& Og = overlap_k_grad_section(*m);
+      for (int i = 0; i < 7; ++i) set_scalar(c, g, Og.w[i], wK[i]);
+      std::vector<int> tg;
+      for (int x : {Og.da0, Og.db0})
+        if (!g.is_zero(x)) tg.push_back(x);
+      if (!tg.empty()) g.run(tg);
+      dO[0] = scalar_node(Og.da0);
+      dO[1] = scalar_node(Og.db0);
+    } else {
+      OvlGradSec& Og = overlap_grad_section(*m);
+      set_scalar(c, g, Og.gbar, 1.0);
+      std::vector<int> tg;
+      for (int x : {Og.da0, Og.db0})
+        if (!g.is_zero(x)) tg.push_back(x);
+      if (!tg.empty()) g.run(tg);
+      dO[0] = scalar_node(Og.da0);
+      dO[1] = scalar_node(Og.db0);
+    }
     if (kind == 1) {
       // dO_mn/dt = r0_n L_m + <L_m| tau R1_n>, the seeds of a transition element
       load_packed(c, g, vec[3 + ms], m->Lb1, m->Lb2, true);
@@ -307,6 +339,7 @@ void mult_setup(sccsd_ctx* c, MultSolver& S, const double* vecs, const double* s
     const int64_t dim = c->dim, N = 3 * dim + 1;
     const int64_t ov = (int64_t)c->o * c->v;
     S.c = c;
+    S.proj = c->projection;
     S.kind = kind;
     S.ms = m_state;
     S.ns = n_state;
@@ -359,8 +392,6 @@ int sccsd_solve_multipliers(sccsd_ctx* c, const double* vecs, const double* scal
                 : (kind != 1 || m_state < 0 || m_state > 1 || n_state < 0 || n_state > 1 ||
                    m_state == n_state))
     return fail(c, SCCSD_EINVAL, "bad target");
-  if (c->projection != 0)
-    return fail(c, SCCSD_EINVAL, "multipliers are implemented for the natural projection only");
   int status = SCCSD_OK;
   int rc = guarded(c, [&] {
     MultSolver S{};

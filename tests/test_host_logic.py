@@ -725,13 +725,16 @@ def test_init_rejects_bad_integrals(host_lib):
     assert init(e3, L) == -1
 
 
-def test_gradient_and_coupling_by_finite_differences(host_lib):
+@pytest.mark.parametrize("projection", ["natural", "state"])
+def test_gradient_and_coupling_by_finite_differences(host_lib, projection):
     """Sec. 2.3.2: the gradient dE_a/dx and the coupling <psi_a|d psi_b/dx> at
     fixed orbitals, along random perturbations x of eps and of L, assembled by
     sccsd_integral_derivative from the effective densities of the multiplier
     solves, equal central differences of fully re-converged SCCSD energies
     E_a = E_HF + E_corr + omega_a and bra-frozen overlaps O_ab (Sec. 2.3.4),
-    all through the C ABI, on the system with an active constraint."""
+    all through the C ABI, on the system with an active constraint; for
+    SCCSD(E) and SCCSD(K) (Sec. 2.4.1). For SCCSD(K) the oracle's stationarity
+    equations also vanish at the C-ABI multipliers."""
     from oracle import multipliers as mu
     B, lib = host_lib
     g = _golden("scc_active_o3_v8.json")
@@ -742,6 +745,7 @@ def test_gradient_and_coupling_by_finite_differences(host_lib):
 
     def solve(e, l):
         ctx = B.Context(o, v, J, e, l, lib=lib)
+        ctx.set_projection(projection)
         st = ctx.scc_state(tol=1e-11, ground_tol=1e-12, eom_tol=1e-10, left_tol=1e-10)
         return ctx, st
 
@@ -753,6 +757,24 @@ def test_gradient_and_coupling_by_finite_differences(host_lib):
     grad = ctx.solve_multipliers(st, ("gradient", 0), tol=1e-11, maxit=800)
     coup = ctx.solve_multipliers(st, ("coupling", 0, 1), tol=1e-11, maxit=800)
     t0, La0, Lb0 = (np.array(st[k]) for k in ("t", "La", "Lb"))
+    if projection == "state":
+        prob = cc.Problem(eps, L, o)
+        ost = {"t": torch.tensor(st["t"]), "Ra": torch.tensor(st["Ra"]),
+               "Rb": torch.tensor(st["Rb"]), "La": torch.tensor(st["La"]),
+               "Lb": torch.tensor(st["Lb"]), "zeta": st["zeta"], "r0a": st["r0a"],
+               "r0b": st["r0b"], "omega": (st["omega_a"], st["omega_b"]),
+               "E0": e_hf(eps, L) + st["e_corr"], "projection": "state"}
+        for target in [("gradient", 0), ("coupling", 0, 1)]:
+            res = ctx.solve_multipliers(st, target, tol=1e-11, maxit=800, densities=False)
+            d = [1.0 if (target[0] == "gradient" and k == target[1]) else 0.0 for k in range(2)]
+            r0 = [st["r0a"], st["r0b"]]
+            lam = [st["La"], st["Lb"]]
+            Lbar = [res["K"][k] - (d[k] - res["lb0"][k] * r0[k]) * lam[k] for k in range(2)]
+            u = np.concatenate([res["zbar"], Lbar[0], Lbar[1], [res["gbar"]]])
+            fmap = mu.residual_map(prob, ost, target)
+            r = fmap(torch.tensor(u)).numpy()
+            b = fmap(torch.zeros(u.size, dtype=torch.float64))
+            assert np.linalg.norm(r) < 1e-8 * max(1.0, float(torch.linalg.norm(b))), target
 
     def observables(e, l):
         c2, s2 = solve(e, l)
@@ -816,8 +838,7 @@ def test_state_projection_overlap_through_the_c_abi(host_lib, with_scc):
 
 def test_state_projection_scc_loop_through_the_c_abi(host_lib):
     """SCCSD(K): the SCC loop constraining O_ab of the state projection reaches
-    the stored oracle solution; the multiplier equations, implemented for the
-    natural projection only, refuse this context."""
+    the stored oracle solution."""
     from oracle import scc as sc
     B, lib = host_lib
     g = _golden("scc_state_projection_o3_v8.json")
@@ -838,10 +859,4 @@ def test_state_projection_scc_loop_through_the_c_abi(host_lib):
     # the natural-projection solution of the same system differs (small, as the paper notes)
     nat = _golden("scc_active_o3_v8.json")["values"]["zeta"]
     assert 1e-4 < abs(r["zeta"] - nat) < 1e-2
-    state = {"t": t, "Ra": r["Ra"], "Rb": r["Rb"], "La": r["Ra"], "Lb": r["Rb"],
-             "zeta": r["zeta"], "r0a": r["r0"][0], "r0b": r["r0"][1],
-             "omega_a": r["omega"][0], "omega_b": r["omega"][1]}
-    with pytest.raises(B.SccsdError) as ei:
-        ctx.solve_multipliers(state, ("gradient", 0))
-    assert ei.value.code == -1
     ctx.close()
