@@ -727,43 +727,26 @@ def test_init_rejects_bad_integrals(host_lib):
 
 @pytest.mark.parametrize("projection", ["natural", "state"])
 def test_gradient_and_coupling_by_finite_differences(host_lib, projection):
-    """Sec. 2.3.2: the gradient dE_a/dx and the coupling <psi_a|d psi_b/dx> at
-    fixed orbitals, along random perturbations x of eps and of L, assembled by
-    sccsd_integral_derivative from the effective densities of the multiplier
-    solves, equal central differences of fully re-converged SCCSD energies
-    E_a = E_HF + E_corr + omega_a and bra-frozen overlaps O_ab (Sec. 2.3.4),
-    all through the C ABI, on the system with an active constraint; for
-    SCCSD(E) and SCCSD(K) (Sec. 2.4.1). For SCCSD(K) the oracle's stationarity
+    """Gradients and couplings along perturbations of eps and L by finite
+    differences of re-converged states through the C ABI (tests/
+    derivative_checks.py), for SCCSD(E) and SCCSD(K) (Sec. 2.4.1), on the
+    system with an active constraint; for SCCSD(K) the oracle's stationarity
     equations also vanish at the C-ABI multipliers."""
+    import derivative_checks as dc
     from oracle import multipliers as mu
     B, lib = host_lib
     g = _golden("scc_active_o3_v8.json")
     p = g["inputs"]
     o, v, J = p["o"], p["v"], p["J"]
-    n = o + v
     eps, L = syn.system(o, v, J, p["sd"], p["seed"])
 
-    def solve(e, l):
-        ctx = B.Context(o, v, J, e, l, lib=lib)
-        ctx.set_projection(projection)
-        st = ctx.scc_state(tol=1e-11, ground_tol=1e-12, eom_tol=1e-10, left_tol=1e-10)
-        return ctx, st
-
-    def e_hf(e, l):
-        prob = cc.Problem(e, l, o)
-        return float(rp.residual(prob, np.zeros(prob.dim))[0])
-
-    ctx, st = solve(eps, L)
-    grad = ctx.solve_multipliers(st, ("gradient", 0), tol=1e-11, maxit=800)
-    coup = ctx.solve_multipliers(st, ("coupling", 0, 1), tol=1e-11, maxit=800)
-    t0, La0, Lb0 = (np.array(st[k]) for k in ("t", "La", "Lb"))
-    if projection == "state":
+    def oracle_equations(ctx, st):
         prob = cc.Problem(eps, L, o)
         ost = {"t": torch.tensor(st["t"]), "Ra": torch.tensor(st["Ra"]),
                "Rb": torch.tensor(st["Rb"]), "La": torch.tensor(st["La"]),
                "Lb": torch.tensor(st["Lb"]), "zeta": st["zeta"], "r0a": st["r0a"],
                "r0b": st["r0b"], "omega": (st["omega_a"], st["omega_b"]),
-               "E0": e_hf(eps, L) + st["e_corr"], "projection": "state"}
+               "E0": dc.e_hf(eps, L, o) + st["e_corr"], "projection": projection}
         for target in [("gradient", 0), ("coupling", 0, 1)]:
             res = ctx.solve_multipliers(st, target, tol=1e-11, maxit=800, densities=False)
             d = [1.0 if (target[0] == "gradient" and k == target[1]) else 0.0 for k in range(2)]
@@ -776,44 +759,12 @@ def test_gradient_and_coupling_by_finite_differences(host_lib, projection):
             b = fmap(torch.zeros(u.size, dtype=torch.float64))
             assert np.linalg.norm(r) < 1e-8 * max(1.0, float(torch.linalg.norm(b))), target
 
-    def observables(e, l):
-        c2, s2 = solve(e, l)
-        c2.close()
-        Rb = np.array(s2["Rb"])
-        sc_ = 1.0 / float(Lb0 @ Rb)          # L_b(x0) . R_b(x) = 1
-        O = float(mu.frozen_overlap(torch.tensor(s2["t"]), torch.tensor(t0), torch.tensor(La0),
-                                    s2["r0b"] * sc_, torch.tensor(Rb * sc_), o, v))
-        return e_hf(e, l) + s2["e_corr"] + s2["omega_a"], O
-
-    rng = np.random.default_rng(7)
-    de = rng.normal(size=n)
-    dL = rng.normal(size=(J, n, n))
-    dL = 0.5 * (dL + dL.transpose(0, 2, 1))
-    # h = diag(eps) - sum_k (2 g_pqkk - g_pkkq) changes with eps and, to first order, with L
-    Lkk, dLkk = np.einsum("Jkk->J", L[:, :o, :o]), np.einsum("Jkk->J", dL[:, :o, :o])
-    dh_L = -(2 * np.einsum("Jpq,J->pq", dL, Lkk) + 2 * np.einsum("Jpq,J->pq", L, dLkk)
-             - np.einsum("Jpk,Jkq->pq", dL[:, :, :o], L[:, :o, :])
-             - np.einsum("Jpk,Jkq->pq", L[:, :, :o], dL[:, :o, :]))
-    h = 1e-5
-    for direction in ("eps", "L"):
-        if direction == "eps":
-            plus, minus = observables(eps + h * de, L), observables(eps - h * de, L)
-            h1, L1 = np.diag(de), None
-            Gg = Gc = None
-        else:
-            plus, minus = observables(eps, L + h * dL), observables(eps, L - h * dL)
-            h1, L1 = dh_L, dL
-            Gg, Gc = grad["Gamma"], coup["Gamma"]
-        fd_E = (plus[0] - minus[0]) / (2 * h)
-        fd_O = (plus[1] - minus[1]) / (2 * h)
-        dE = ctx.integral_derivative(grad["D1"], Gg, h1, L1)
-        dO = ctx.integral_derivative(coup["D1"], Gc, h1, L1)
-        assert abs(dE - fd_E) < 1e-7 * max(1.0, abs(fd_E)), (direction, dE, fd_E)
-        assert abs(dO - fd_O) < 1e-7 * max(1.0, abs(fd_O)), (direction, dO, fd_O)
+    dc.check(lambda e, l: B.Context(o, v, J, e, l, lib=lib), eps, L, o, v, J, projection,
+             extra=oracle_equations if projection == "state" else None)
+    ctx = B.Context(o, v, J, eps, L, lib=lib)
     with pytest.raises(B.SccsdError):
-        ctx.integral_derivative(grad["D1"], grad["Gamma"], np.diag(de), None)
+        ctx.integral_derivative(np.eye(o + v), np.zeros((J, o + v, o + v)), np.eye(o + v), None)
     ctx.close()
-
 
 # ------------------------------------- SCCSD(K): the state projection (Sec. 2.4.1)
 
