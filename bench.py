@@ -393,10 +393,12 @@ def chain_case(args):
     w = getattr(syn, args.workload if args.workload != "LARGE" else "MEDIUM")
     eps, L = syn.workload_system(w)
     ctx = B.Context(w.o, w.v, w.J, eps, L, precision=args.precision)
+    ctx.set_projection(args.projection)
     out = {"metric": "SCCSD gradient and coupling chain, seconds per stage", "unit": "s",
            "higher_is_better": False, "data": "synthetic",
            "config": {"workload": w.name, "o": w.o, "v": w.v, "J": w.J,
-                      "precision": args.precision, "refinement": "FP64"}}
+                      "precision": args.precision, "refinement": "FP64",
+                      "projection": args.projection}}
     t0 = time.perf_counter()
     state = ctx.scc_state(tol=1e-9, ground_tol=1e-10, eom_tol=1e-8, left_tol=1e-7,
                           left_maxit=600)
@@ -494,6 +496,8 @@ def main():
                     help="evaluate the learned guess/preconditioner on fresh systems")
     ap.add_argument("--n-train", type=int, default=24)
     ap.add_argument("--n-eval", type=int, default=12)
+    ap.add_argument("--projection", default="natural", choices=["natural", "state"],
+                    help="with --chain: the SCC projection, SCCSD(E) or SCCSD(K)")
     ap.add_argument("--autotune", action="store_true",
                     help="tune the launch shapes in the warm-up (with --batched: time the "
                          "fixed rule, then tune and time again)")
