@@ -254,7 +254,8 @@ int sccsd_solve_ground(sccsd_ctx* ctx, const double* t0, double zeta, const doub
  * refine_tol or the residuals stall for 8 iterations (refine_tol <= 0: no
  * refinement). Outputs: omega[nroots],
  * vecs[nroots][dim] (unit-norm packed vectors, may be NULL), iterations.
- * The system needs dim >= 48 (the subspace size), else SCCSD_EINVAL.
+ * The subspace holds min(48, dim) vectors and needs room for 2 nroots + 2,
+ * else SCCSD_EINVAL.
  * SCCSD_ECOMPLEX if a complex pair appears among the wanted roots;
  * SCCSD_ENOTCONV when maxit is reached (outputs hold the last Ritz pairs). */
 int sccsd_solve_states(sccsd_ctx* ctx, int nroots, int side, double tol, int maxit,

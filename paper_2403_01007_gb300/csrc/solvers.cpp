@@ -214,8 +214,9 @@ int sccsd_solve_states(sccsd_ctx* c, int nroots, int side, double tol, int maxit
     Dev d{c};
     ensure_small(c);
     const int64_t dim = c->dim;
-    const int mmax = kMaxSpace;
-    if (dim < mmax) throw std::invalid_argument("problem too small for the requested roots");
+    // the subspace holds at most kMaxSpace vectors, and never more than dim
+    const int mmax = (int)std::min<int64_t>(kMaxSpace, dim);
+    if (2 * nroots + 2 > mmax) throw std::invalid_argument("problem too small for the requested roots");
     double* V = solver_buf(c, 10, (int64_t)kMaxSpace * dim);
     double* W = solver_buf(c, 11, (int64_t)kMaxSpace * dim);
     double* Xr = solver_buf(c, 12, 12 * dim);

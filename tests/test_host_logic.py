@@ -530,14 +530,23 @@ def test_scc_loop_through_the_c_abi(host_lib):
     assert abs(r["zeta"]) > 0.3           # the constraint is active
 
 
-def test_davidson_needs_room_for_its_subspace(host_lib):
+def test_davidson_on_small_systems_is_full_ci_for_two_electrons(host_lib):
+    """The subspace shrinks to the problem (min(48, dim) vectors): for two
+    electrons (o=1, v=5, dim 20) the Davidson roots through the C ABI are the
+    stored full-CI excitation energies (CCSD is exact, Sec. 2.1); a request
+    that leaves no room for 2 nroots + 2 vectors is refused."""
     B, lib = host_lib
-    o, v, J = 2, 4, 6                     # dim 44 < 48
-    eps, L = syn.system(o, v, J, 0.2, 57)
-    ctx = B.Context(o, v, J, eps, L, lib=lib)
-    ctx.residual(np.zeros(ctx.dim))
+    g = _golden("fci_two_electron_o1_v5.json")
+    p = g["inputs"]
+    eps, L = syn.system(p["o"], p["v"], p["J"], p["sd"], p["seed"])
+    ctx = B.Context(p["o"], p["v"], p["J"], eps, L, lib=lib)
+    e, _, _ = ctx.solve_ground(tol=1e-12, maxit=300)
+    assert abs(e - g["values"]["e_corr"]) < 1e-10
+    for side in ("right", "left"):
+        w, _, _ = ctx.solve_states(3, side=side, tol=1e-10)
+        assert np.abs(w - np.array(g["values"]["excitation_energies"][:3])).max() < 1e-9, side
     with pytest.raises(B.SccsdError) as ei:
-        ctx.solve_states(1)
+        ctx.solve_states(10)              # 22 vectors > dim 20
     assert ei.value.code == -1
     ctx.close()
 
