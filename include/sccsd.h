@@ -109,7 +109,8 @@ int sccsd_densities(sccsd_ctx* ctx, double l0, const double* L, double r0, const
  * pointers must be device memory; the call returns after the work finished.
  * This is the contraction primitive of the hot path, exposed for validation
  * (an interface of this library; the paper has no counterpart). SCCSD_EINVAL
- * for non-positive sizes, a NULL or host pointer or a bad precision. */
+ * for negative sizes, a NULL or host pointer or a bad precision; M or N = 0
+ * writes nothing, K = 0 sets C to zero. */
 int sccsd_gemm_tn(int precision, long long M, long long N, long long K, double alpha,
                   const double* A, const double* B, double* C, void* stream);
 

@@ -357,12 +357,16 @@ int sccsd_gemm_tn(int precision, long long M, long long N, long long K, double a
                   const double* A, const double* B, double* C, void* stream) {
   if (M < 0 || N < 0 || K < 0 || !A || !B || !C) return SCCSD_EINVAL;
   if (precision < SCCSD_FP64 || precision > SCCSD_BF16) return SCCSD_EINVAL;
+  if (M == 0 || N == 0) return SCCSD_OK;  // an empty C: nothing to write
   sccsd_ctx tmp;
   return guarded(&tmp, [&] {
     auto be = make_backend(stream, precision);
     for (const double* p : {A, B, (const double*)C})
       if (!be->is_device(p)) throw std::invalid_argument("sccsd_gemm_tn needs device pointers");
-    be->gemm_tn(1, M, N, K, alpha, A, B, C, precision != SCCSD_FP64);
+    if (K == 0)
+      be->fill(C, M * N, 0.0);  // the empty sum
+    else
+      be->gemm_tn(1, M, N, K, alpha, A, B, C, precision != SCCSD_FP64);
     be->sync();
   });
 }

@@ -383,6 +383,12 @@ def test_every_documented_argument_error(host_lib):
     lib.sccsd_strerror.argtypes = [ctypes.c_int]
     lib.sccsd_strerror.restype = ctypes.c_char_p
     assert lib.sccsd_strerror(-1) == b"invalid argument"
+    one = np.zeros(4)
+    P = one.ctypes.data
+    assert lib.sccsd_gemm_tn(0, -1, 2, 2, 1.0, P, P, P, None) == -1
+    assert lib.sccsd_gemm_tn(3, 2, 2, 2, 1.0, P, P, P, None) == -1
+    assert lib.sccsd_gemm_tn(0, 0, 2, 2, 1.0, P, P, P, None) == 0     # empty C
+    assert lib.sccsd_gemm_tn(0, 2, 2, 2, 1.0, P, P, P, None) == -1    # host pointers
     h = ctypes.c_void_p()
     eps = np.linspace(-1.0, 1.0, 5)
     L = np.zeros((3, 5, 5))
