@@ -68,32 +68,33 @@ def _declare(lib):
     lib.sccsd_solve_scc.argtypes = [_dp, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
     lib.sccsd_solve_scc.restype = ctypes.c_int
-    # The MLP entry points live in their own translation unit; the host test
-    # double of the executor links without it (the export test checks that
-    # the product library has every declared symbol).
-    if hasattr(lib, "sccsd_mlp_create"):
-        lib.sccsd_mlp_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int,
-                                         ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, _dp]
-        lib.sccsd_mlp_destroy.argtypes = [_dp]
-        lib.sccsd_mlp_destroy.restype = None
-        lib.sccsd_mlp_last_error.argtypes = [_dp]
-        lib.sccsd_mlp_last_error.restype = ctypes.c_char_p
-        lib.sccsd_mlp_num_params.argtypes = [_dp]
-        lib.sccsd_mlp_num_params.restype = ctypes.c_longlong
-        lib.sccsd_mlp_get_params.argtypes = [_dp, _dp]
-        lib.sccsd_mlp_set_params.argtypes = [_dp, _dp]
-        lib.sccsd_mlp_forward.argtypes = [_dp, _dp, ctypes.c_longlong, _dp]
-        lib.sccsd_mlp_gradient.argtypes = [_dp, _dp, _dp, ctypes.c_longlong, _dp, _dp]
-        lib.sccsd_mlp_train_step.argtypes = [_dp, _dp, _dp, ctypes.c_longlong, ctypes.c_float, _dp]
-        lib.sccsd_learned_features.argtypes = [_dp, _dp, _dp]
-        lib.sccsd_learned_targets.argtypes = [_dp, _dp, ctypes.c_double, _dp]
-        lib.sccsd_learned_guess.argtypes = [_dp, _dp, _dp, _dp]
-        lib.sccsd_set_preconditioner.argtypes = [_dp, _dp]
-        for f in ("sccsd_mlp_create", "sccsd_mlp_get_params", "sccsd_mlp_set_params",
-                  "sccsd_mlp_forward", "sccsd_mlp_gradient", "sccsd_mlp_train_step",
-                  "sccsd_learned_features", "sccsd_learned_targets", "sccsd_learned_guess",
-                  "sccsd_set_preconditioner"):
-            getattr(lib, f).restype = ctypes.c_int
+    # The MLP entry points live in their own translation unit (mlp.cu), which
+    # the host test double links without; every entry point the library
+    # exports gets its signature (the export test checks that the product
+    # library has every declared symbol). Undeclared pointer arguments would be
+    # passed as C ints.
+    _int = ctypes.c_int
+    learned = {
+        "sccsd_mlp_create": ([ctypes.POINTER(ctypes.c_void_p), _int, _int, _int, _int,
+                              ctypes.c_ulonglong, _dp], _int),
+        "sccsd_mlp_destroy": ([_dp], None),
+        "sccsd_mlp_last_error": ([_dp], ctypes.c_char_p),
+        "sccsd_mlp_num_params": ([_dp], ctypes.c_longlong),
+        "sccsd_mlp_get_params": ([_dp, _dp], _int),
+        "sccsd_mlp_set_params": ([_dp, _dp], _int),
+        "sccsd_mlp_forward": ([_dp, _dp, ctypes.c_longlong, _dp], _int),
+        "sccsd_mlp_gradient": ([_dp, _dp, _dp, ctypes.c_longlong, _dp, _dp], _int),
+        "sccsd_mlp_train_step": ([_dp, _dp, _dp, ctypes.c_longlong, ctypes.c_float, _dp], _int),
+        "sccsd_learned_features": ([_dp, _dp, _dp], _int),
+        "sccsd_learned_targets": ([_dp, _dp, ctypes.c_double, _dp], _int),
+        "sccsd_learned_guess": ([_dp, _dp, _dp, _dp], _int),
+        "sccsd_set_preconditioner": ([_dp, _dp], _int),
+    }
+    for name, (args, res) in learned.items():
+        if hasattr(lib, name):
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
     lib.sccsd_solve_multipliers.argtypes = [_dp, _dp, _dp, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                             ctypes.c_double, _dp, _dp, _dp, _dp, _dp, _dp]
