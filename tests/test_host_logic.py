@@ -55,8 +55,11 @@ def host_lib():
                                             "solvers.cpp", "multipliers.cpp", "learned_api.cpp",
                                             "capture.cpp", "tc_tune.cpp")]
     srcs.append(os.path.join(ROOT, "tests", "host_executor", "host_backend.cpp"))
-    # SCCSD_HOST_SANITIZE=1 builds the executor with AddressSanitizer (run the
-    # tests with the sanitizer runtime preloaded) to catch out-of-range buffer use
+    # SCCSD_HOST_SANITIZE=1 builds the executor with AddressSanitizer to catch
+    # out-of-range buffer use; run the tests with the sanitizer runtime and the
+    # C++ runtime preloaded (LD_PRELOAD="$(gcc -print-file-name=libasan.so)
+    # $(gcc -print-file-name=libstdc++.so)", ASAN_OPTIONS=detect_leaks=0), or
+    # the first C++ exception trips the sanitizer's own interceptor
     san = ["-g", "-fsanitize=address", "-fno-omit-frame-pointer"] \
         if os.environ.get("SCCSD_HOST_SANITIZE") else []
     # -Bsymbolic: the double's own cudaMemcpyAsync (host memory only) must win
