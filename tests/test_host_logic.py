@@ -833,32 +833,42 @@ def test_state_projection_scc_loop_through_the_c_abi(host_lib):
 
 def test_random_shapes_match_the_oracle(host_lib):
     """Property check over random tiny shapes (o 1..3, v 1..5, J 1..6, any
-    seeds): residual, A R and A^T L through the C ABI equal the oracle's, so
-    the graph's index bookkeeping holds for degenerate and ragged layouts."""
+    seeds, with or without the SCC terms): residual, A R, A^T L and the
+    densities through the C ABI equal the oracle's, so the graph's index
+    bookkeeping holds for degenerate and ragged layouts."""
     hyp = pytest.importorskip("hypothesis")
     st = pytest.importorskip("hypothesis.strategies")
     B, lib = host_lib
 
     @hyp.settings(max_examples=25, deadline=None, derandomize=True)
     @hyp.given(o=st.integers(1, 3), v=st.integers(1, 5), J=st.integers(1, 6),
-               seed=st.integers(0, 10_000))
-    def check(o, v, J, seed):
+               seed=st.integers(0, 10_000), with_scc=st.booleans())
+    def check(o, v, J, seed, with_scc):
         eps, L = syn.system(o, v, J, 0.3, seed)
         prob = cc.Problem(eps, L, o)
         t = syn.random_vectors(o, v, 1, seed + 1, scale=0.1)[0]
         R = syn.random_vectors(o, v, 2, seed + 2, normalise=True)
+        Ra, Rb = syn.random_vectors(o, v, 2, seed + 3, normalise=True)
+        scc = (0.3, Ra, Rb) if with_scc else None
+        scct = (0.3, torch.tensor(Ra), torch.tensor(Rb)) if with_scc else None
         ctx = B.Context(o, v, J, eps, L, lib=lib)
         try:
-            e, om = ctx.residual(t)
-            E0, Om = rp.residual(prob, t)
+            e, om = ctx.residual(t, scc=scc)
+            E0, Om = rp.residual(prob, t, scc=scct)
             Ehf = float(rp.residual(prob, np.zeros(prob.dim))[0])
             assert abs(e - (float(E0) - Ehf)) < 1e-12
             assert np.abs(om - Om.numpy()).max() < 1e-12
             s = ctx.jacobian_right(R)
             sl = ctx.jacobian_left(R)
             for k in range(2):
-                assert np.abs(s[k] - rp.jacobian_right(prob, t, R[k]).numpy()).max() < 1e-12
-                assert np.abs(sl[k] - rp.jacobian_left(prob, t, R[k]).numpy()).max() < 1e-12
+                ref = rp.jacobian_right(prob, t, R[k], scc=scct).numpy()
+                assert np.abs(s[k] - ref).max() < 1e-12
+                ref = rp.jacobian_left(prob, t, R[k], scc=scct).numpy()
+                assert np.abs(sl[k] - ref).max() < 1e-12
+            D1, G = ctx.densities(0.4, R[0], -0.7, R[1])
+            D1r, Gr = rp.densities(prob, t, 0.4, R[0], -0.7, R[1], scc=scct)
+            assert np.abs(D1 - D1r.numpy()).max() < 1e-12
+            assert np.abs(G - Gr.numpy()).max() < 1e-12
         finally:
             ctx.close()
 
