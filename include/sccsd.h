@@ -353,6 +353,13 @@ int sccsd_solve_multipliers(sccsd_ctx* ctx, const double* vecs, const double* sc
  * of h that L1 causes (h is derived from eps and L). */
 int sccsd_integral_derivative(sccsd_ctx* ctx, const double* D1, const double* Gamma,
                               const double* h1, const double* L1, double* out);
+/* The same along a perturbation of this library's inputs: deps [n] and dL
+ * [J][n][n] (symmetric in pq; dL and Gamma may both be NULL) per unit of the
+ * perturbation. h follows eps and L as in sccsd_init, so h1 = diag(deps) plus
+ * the first-order change of -2 sum_J L^J s_J + sum_Jk L^J_pk L^J_kq
+ * (s_J = sum_k L^J_kk over occupied k), formed by the library's kernels. */
+int sccsd_input_derivative(sccsd_ctx* ctx, const double* D1, const double* Gamma,
+                           const double* deps, const double* dL, double* out);
 /* The packed amplitudes t (Sec. 2.1) of the context's current state (the
  * last sccsd_residual, or the result of a solver), e.g. the SCCSD ground state
  * after sccsd_solve_scc. SCCSD_ESTATE before any state exists. */

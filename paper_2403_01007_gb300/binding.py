@@ -104,6 +104,8 @@ def _declare(lib):
     lib.sccsd_multiplier_residual.restype = ctypes.c_int
     lib.sccsd_integral_derivative.argtypes = [_dp, _dp, _dp, _dp, _dp, _dp]
     lib.sccsd_integral_derivative.restype = ctypes.c_int
+    lib.sccsd_input_derivative.argtypes = [_dp, _dp, _dp, _dp, _dp, _dp]
+    lib.sccsd_input_derivative.restype = ctypes.c_int
     lib.sccsd_state_amplitudes.argtypes = [_dp, _dp]
     lib.sccsd_state_amplitudes.restype = ctypes.c_int
     lib.sccsd_capture_transform.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp, _dp,
@@ -474,6 +476,19 @@ class Context:
         out = ctypes.c_double()
         self._check(self.lib.sccsd_integral_derivative(
             self.h, _ptr(c(D1)), _ptr(c(Gamma)), _ptr(c(h1)), _ptr(c(L1)),
+            ctypes.addressof(out)))
+        return out.value
+
+    def input_derivative(self, D1, Gamma, deps, dL):
+        """A gradient or coupling along a perturbation (deps, dL) of eps and L,
+        the inputs of the context (h follows them)."""
+        def c(x):
+            if x is None or hasattr(x, "data_ptr"):
+                return x
+            return np.ascontiguousarray(x, dtype=np.float64)
+        out = ctypes.c_double()
+        self._check(self.lib.sccsd_input_derivative(
+            self.h, _ptr(c(D1)), _ptr(c(Gamma)), _ptr(c(deps)), _ptr(c(dL)),
             ctypes.addressof(out)))
         return out.value
 

@@ -501,6 +501,55 @@ int sccsd_integral_derivative(sccsd_ctx* c, const double* D1, const double* Gamm
   });
 }
 
+int sccsd_input_derivative(sccsd_ctx* c, const double* D1, const double* Gamma,
+                           const double* deps, const double* dL, double* out) {
+  if (!c) return SCCSD_EINVAL;
+  if (!D1 || !deps || !out || (Gamma == nullptr) != (dL == nullptr))
+    return fail(c, SCCSD_EINVAL, "NULL argument");
+  double* dh = nullptr;
+  const int rc = guarded(c, [&] {
+    const int64_t o = c->o, n = c->n, J = c->J;
+    // the change of h per unit of the perturbation: h = diag(eps) - 2 sum_J L^J s_J
+    // + sum_Jk L^J_pk L^J_kq with s_J = sum_k L^J_kk (k occupied), to first order
+    std::vector<double> de(n);
+    if (c->be->is_device(deps))
+      c->be->download(de.data(), deps, n, false);
+    else
+      std::copy(deps, deps + n, de.begin());
+    std::vector<double> E((size_t)n * n, 0.0);
+    for (int64_t p = 0; p < n; ++p) E[p * n + p] = de[p];
+    Graph g;
+    g.be = c->be.get();
+    int Ein = g.input({n, n}, "dE");
+    int hh = Ein;
+    int Lin = -1, dLin = -1;
+    if (dL) {
+      Lin = g.input({J, n, n}, "L");
+      dLin = g.input({J, n, n}, "dL");
+      int din = g.input({o, o}, "delta");
+      int s = g.contract(g.slice(Lin, {0, 0, 0}, {J, o, o}), "Jkl", din, "kl", "J");
+      int ds = g.contract(g.slice(dLin, {0, 0, 0}, {J, o, o}), "Jkl", din, "kl", "J");
+      hh = g.add("pq", {{Ein, "pq", 1.0},
+                        {g.contract(dLin, "Jpq", s, "J", "pq"), "pq", -2.0},
+                        {g.contract(Lin, "Jpq", ds, "J", "pq"), "pq", -2.0},
+                        {g.contract(g.slice(dLin, {0, 0, 0}, {J, n, o}), "Jpk",
+                                    g.slice(Lin, {0, 0, 0}, {J, o, n}), "Jkq", "pq"), "pq", 1.0},
+                        {g.contract(g.slice(Lin, {0, 0, 0}, {J, n, o}), "Jpk",
+                                    g.slice(dLin, {0, 0, 0}, {J, o, n}), "Jkq", "pq"), "pq", 1.0}});
+      g.set_input(Lin, c->L, true);
+      g.set_input(dLin, dL, c->be->is_device(dL));
+      g.set_input(din, c->delta, true);
+    }
+    g.set_input(Ein, E.data(), false);
+    g.run({hh});
+    dh = solver_buf(c, 74, n * n);
+    c->be->upload(dh, g.data(hh), n * n, true);
+    c->be->sync();
+  });
+  if (rc != SCCSD_OK) return rc;
+  return sccsd_integral_derivative(c, D1, Gamma, dh, dL, out);
+}
+
 int sccsd_state_amplitudes(sccsd_ctx* c, double* t) {
   if (!c) return SCCSD_EINVAL;
   if (!t) return fail(c, SCCSD_EINVAL, "t is NULL");

@@ -68,6 +68,13 @@ def check(make_ctx, eps, L, o, v, J, projection, h=1e-5, rel=1e-7, seed=7, extra
         dO = ctx.integral_derivative(coup["D1"], Gc, h1, L1)
         assert abs(dE - fd_E) < rel * max(1.0, abs(fd_E)), (direction, dE, fd_E)
         assert abs(dO - fd_O) < rel * max(1.0, abs(fd_O)), (direction, dO, fd_O)
+        # the same through the inputs (eps, L), with h's change formed by the library
+        d_eps = de if direction == "eps" else np.zeros(n)
+        d_L = None if direction == "eps" else dL
+        iE = ctx.input_derivative(grad["D1"], Gg, d_eps, d_L)
+        iO = ctx.input_derivative(coup["D1"], Gc, d_eps, d_L)
+        assert abs(iE - dE) < 1e-10 * max(1.0, abs(dE)), (direction, iE, dE)
+        assert abs(iO - dO) < 1e-10 * max(1.0, abs(dO)), (direction, iO, dO)
         out[direction] = (abs(dE - fd_E), abs(dO - fd_O))
     if extra is not None:
         extra(ctx, st)
