@@ -458,6 +458,14 @@ def test_every_documented_argument_error(host_lib):
                                            None, None, None, None, None, None))
     expect(-1, lib.sccsd_multiplier_residual(ctx.h, vecs.ctypes.data, scal.ctypes.data, 0, 0, 0,
                                              None, Y))
+    # derivative assembly: NULL inputs, or Gamma without its perturbation
+    D1 = np.zeros((n, n))
+    expect(-1, lib.sccsd_integral_derivative(ctx.h, None, None, D1.ctypes.data, None,
+                                             ctypes.addressof(zd)))
+    expect(-1, lib.sccsd_integral_derivative(ctx.h, D1.ctypes.data, D1.ctypes.data,
+                                             D1.ctypes.data, None, ctypes.addressof(zd)))
+    expect(-1, lib.sccsd_input_derivative(ctx.h, D1.ctypes.data, None, None, None,
+                                          ctypes.addressof(zd)))
     ctx.close()
 
 
