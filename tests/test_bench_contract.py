@@ -39,3 +39,20 @@ def test_reference_arm_is_silent_on_other_ranks():
     r = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+def test_ladder_flop_counts():
+    """Executed (dense) and minimal (+/- packed) ladder flops per trial vector:
+    at o=21 v=200 about 1.41e12 and 3.53e11; the packed count is the number of
+    unique-pair multiply-adds of the symmetric and antisymmetric parts."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert abs(bench.ladder_flops_dense(21, 200) / 1.4112e12 - 1.0) < 1e-3
+    assert abs(bench.ladder_flops_packed(21, 200) / 3.53e11 - 1.0) < 2e-3
+    o, v = 3, 4
+    plus = sum(1 for i in range(o) for j in range(i, o) for a in range(v) for b in range(a, v)
+               for c in range(v) for d in range(c, v))
+    minus = sum(1 for i in range(o) for j in range(i + 1, o) for a in range(v)
+                for b in range(a + 1, v) for c in range(v) for d in range(c + 1, v))
+    assert bench.ladder_flops_packed(o, v) == 2.0 * (plus + minus)
+    assert bench.ladder_flops_dense(o, v) == 2.0 * o * o * v ** 4
