@@ -386,6 +386,10 @@ def test_every_documented_argument_error(host_lib):
     lib.sccsd_strerror.argtypes = [ctypes.c_int]
     lib.sccsd_strerror.restype = ctypes.c_char_p
     assert lib.sccsd_strerror(-1) == b"invalid argument"
+    texts = {lib.sccsd_strerror(code) for code in range(0, -8, -1)}
+    assert len(texts) == 8 and all(texts)          # one distinct text per code
+    lib.sccsd_destroy(None)                        # a NULL context is ignored
+    assert lib.sccsd_last_error(None)
     one = np.zeros(4)
     P = one.ctypes.data
     assert lib.sccsd_gemm_tn(0, -1, 2, 2, 1.0, P, P, P, None) == -1
