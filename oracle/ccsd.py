@@ -212,7 +212,9 @@ class Problem:
 
 def energy_residual(x, prob: Problem, h=None, L=None, scc=None):
     """(E0, Omega packed) at packed amplitudes x; scc = (zeta, Ra, Rb) adds
-    the similarity-constraint term zeta <mu~|[Hhat, X3]|HF> (Sec. 2.4.2)."""
+    the similarity-constraint term zeta <mu~|[Hhat, X3]|HF> (Sec. 2.4.2). A
+    list of such triples, one per pair k < l of constrained states, adds one
+    term per pair: T + sum_kl zeta_kl X_kl (Sec. 2.2 for several states)."""
     h = prob.h if h is None else h
     L = prob.L if L is None else L
     o, v = prob.o, prob.v
@@ -220,7 +222,8 @@ def energy_residual(x, prob: Problem, h=None, L=None, scc=None):
     E0, O1, O2 = ccsd_energy_residual(t1, t2, h, L, o)
     Om = pack(O1, O2)
     if scc is not None:
-        zeta, Ra, Rb = scc
         from .scc import xi
-        Om = Om + zeta * (xi(t1, Ra, Rb, h, L, o, v) - xi(t1, Rb, Ra, h, L, o, v))
+        pairs = scc if isinstance(scc, list) else [scc]
+        for zeta, Ra, Rb in pairs:
+            Om = Om + zeta * (xi(t1, Ra, Rb, h, L, o, v) - xi(t1, Rb, Ra, h, L, o, v))
     return E0, Om

@@ -346,6 +346,21 @@ class System:
         return float(m @ np.linalg.solve(Smat, nvec))
 
 
+def overlaps_states(system, t, states):
+    """O_kl of the state projection over all of K = {(R0_k, R_k)} (Sec. 2.4.1)
+    for every pair k < l, over full determinant vectors: O_kl = sum_mn
+    <psi_k|R_m> (S^-1)_mn <R_n|psi_l>, psi = exp(T)|R>, T without X."""
+    S = system.S
+    T = S.op_cluster(t)
+    kets = [S.ket(r0, r) for r0, r in states]
+    psis = [expm_apply(T, k, +1.0) for k in kets]
+    K = len(states)
+    Smat = np.array([[kets[m] @ kets[n] for n in range(K)] for m in range(K)])
+    M = np.array([[psis[k] @ kets[m] for m in range(K)] for k in range(K)])
+    W = np.linalg.solve(Smat, M.T)
+    return {(k, l): float(M[k] @ W[:, l]) for k in range(K) for l in range(k + 1, K)}
+
+
 def x3_operator(space: Space, ra: np.ndarray, rb: np.ndarray) -> sp.csr_matrix:
     """X3 = R1^a R2^b - R1^b R2^a (Sec. 2.4.1) as a determinant-space matrix."""
     ov = space.o * space.v

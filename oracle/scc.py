@@ -169,3 +169,65 @@ def solve_scc(prob, tol=1e-10, maxit=40, ground_tol=1e-11, eom_tol=1e-9, dense=F
             (z1, o1), (z2, o2) = hist[-2], hist[-1]
             zeta = z2 - o2 * (z2 - z1) / (o2 - o1) if o2 != o1 else z2
     raise RuntimeError("SCC zeta iteration did not converge")
+
+
+# ---------------------------------------------------- several constrained states
+
+def overlaps(x_t, states, o, v, projection="natural"):
+    """O_kl for every pair k < l of the states [(R0_k, R_k), ...] in K
+    (Sec. 2.2): natural projection as in overlap(), or the state projection
+    over all of K, P = sum_mn |R_m> (S^-1)_mn <R_n| (Sec. 2.4.1), so that
+    O_kl = sum_mn <psi_k|R_m> (S^-1)_mn <R_n|psi_l>. Returns {(k, l): O_kl}."""
+    K = len(states)
+    if projection == "natural":
+        return {(k, l): overlap(x_t, states[k][0], states[k][1], states[l][0], states[l][1], o, v)
+                for k in range(K) for l in range(k + 1, K)}
+    zero = torch.zeros(torch.as_tensor(x_t).shape, dtype=DT)
+    c = [projected_state(x_t, r0, R, o, v) for r0, R in states]
+    r = [projected_state(zero, r0, R, o, v) for r0, R in states]
+    S = torch.stack([torch.stack([metric_product(r[m], r[n]) for n in range(K)]) for m in range(K)])
+    M = torch.stack([torch.stack([metric_product(c[k], r[m]) for m in range(K)]) for k in range(K)])
+    W = torch.linalg.solve(S, M.T)                 # S^-1 <R_n|psi_l>, column l
+    return {(k, l): M[k] @ W[:, l] for k in range(K) for l in range(k + 1, K)}
+
+
+def solve_scc_states(prob, nstates, tol=1e-10, maxit=60, ground_tol=1e-11, eom_tol=1e-9,
+                     dense=True, projection="natural"):
+    """Self-consistent SCCSD for the nstates lowest states, K = {1..nstates}
+    (Sec. 2.2 with several states): one zeta_kl per pair k < l, with
+    T + sum_kl zeta_kl X_kl, X_kl = R1^k R2^l - R1^l R2^k (Sec. 2.4.1); at every
+    zeta the ground state and the nstates lowest right roots are re-converged,
+    and zeta solves O_kl = 0 for all pairs by Broyden's method from zeta = 0
+    (plain CCSD) with the unit matrix as the first Jacobian estimate (the
+    two-state loop's first step). Returns a dict."""
+    from . import solvers as sv
+    from . import response as rp
+    o, v = prob.o, prob.v
+    pairs = [(k, l) for k in range(nstates) for l in range(k + 1, nstates)]
+    zeta = np.zeros(len(pairs))
+    Jb = np.eye(len(pairs))
+    R, x, prev = None, None, None
+    for it in range(1, maxit + 1):
+        scc = None if R is None else [(float(zeta[p]), torch.tensor(R[k]), torch.tensor(R[l]))
+                                      for p, (k, l) in enumerate(pairs)]
+        x, E0, _ = sv.ground_state(prob, tol=ground_tol, scc=scc, x0=x)
+        if dense:
+            w, X = sv.eom_dense(prob, x, nstates, side="right", scc=scc)
+        else:
+            w, X = sv.eom(prob, x, nstates, side="right", tol=eom_tol, scc=scc)
+        R = [fix_sign(X[k]) for k in range(nstates)]
+        eta = rp.eta(prob, x, scc=scc).numpy()
+        r0 = [float(eta @ R[k] / w[k]) for k in range(nstates)]
+        states = [(r0[k], torch.tensor(R[k])) for k in range(nstates)]
+        Od = overlaps(torch.tensor(x), states, o, v, projection)
+        O = np.array([float(Od[p]) for p in pairs])
+        if np.abs(O).max() < tol and prev is not None and np.abs(zeta - prev[0]).max() < 1e-8:
+            return {"zeta": dict(zip(pairs, zeta.tolist())), "O": dict(zip(pairs, O.tolist())),
+                    "E0": E0, "omega": w, "t": x, "R": R, "r0": r0, "iterations": it}
+        if prev is not None:
+            dz, dO = zeta - prev[0], O - prev[1]
+            if dz @ dz > 0:
+                Jb = Jb + np.outer(dO - Jb @ dz, dz) / (dz @ dz)
+        prev = (zeta.copy(), O.copy())
+        zeta = zeta - np.linalg.solve(Jb, O)
+    raise RuntimeError("SCC zeta iteration did not converge")

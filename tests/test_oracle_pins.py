@@ -126,6 +126,53 @@ def test_scc_terms_vs_brute_force(tiny):
     assert np.abs(rp.jacobian_left(prob, t, Lv, scc=scc).numpy() - A.T @ Lv).max() < 1e-12
 
 
+def test_several_constrained_pairs_vs_brute_force(tiny):
+    """K of three states (Sec. 2.2): T + sum_kl zeta_kl X_kl over the pairs
+    k < l; the residual and both Jacobians against the determinant engine with
+    the summed operators, and the overlaps of both projections against full
+    determinant vectors; with two states they are the two-state functions."""
+    o, v, eps, L, system, prob = tiny
+    t = syn.random_vectors(o, v, 1, 7, scale=0.1)[0]
+    Ra, Rb, Rc, R, Lv = syn.random_vectors(o, v, 5, 13, normalise=True)
+    pairs = [(0.37, Ra, Rb), (-0.21, Ra, Rc), (0.15, Rb, Rc)]
+    X = sum(z * det.x3_operator(system.S, x, y) for z, x, y in pairs)
+    scc = [(z, torch.tensor(x), torch.tensor(y)) for z, x, y in pairs]
+    E0, om = system.omega(t, extra=X)
+    e, O = rp.residual(prob, t, scc=scc)
+    assert abs(float(e) - E0) < 1e-12
+    assert np.abs(O.numpy() - om).max() < 1e-12
+    A, _ = system.jacobian(t, extra=X)
+    assert np.abs(rp.jacobian_right(prob, t, R, scc=scc).numpy() - A @ R).max() < 1e-12
+    assert np.abs(rp.jacobian_left(prob, t, Lv, scc=scc).numpy() - A.T @ Lv).max() < 1e-12
+    states = [(0.3, Ra), (-0.2, Rb), (0.1, Rc)]
+    tt = torch.tensor(t)
+    ts = [(r0, torch.tensor(r)) for r0, r in states]
+    ref = det.overlaps_states(system, t, states)
+    got = sc.overlaps(tt, ts, o, v, "state")
+    for kl in ref:
+        assert abs(float(got[kl]) - ref[kl]) < 1e-12 * max(1.0, abs(ref[kl]))
+    nat = sc.overlaps(tt, ts, o, v, "natural")
+    for (k, l), val in nat.items():
+        assert abs(float(val) - system.overlap(t, *states[k], *states[l])) < 1e-12
+    two = sc.overlaps(tt, ts[:2], o, v, "state")
+    assert abs(float(two[(0, 1)]) - float(sc.overlap_states(tt, *ts[0], *ts[1], o, v))) < 1e-13
+
+
+def test_several_states_loop_reduces_to_two_states():
+    """With two states Broyden's update is the secant step, so the loop for
+    several constrained states is the two-state loop; on the symmetric system
+    whose two lowest states differ in symmetry both stop at zeta = 0 with the
+    CCSD energies (Sec. 3.1.1)."""
+    o, v, J = 3, 6, 18
+    eps, L, _, _ = syn.symmetric_system(o, v, J, 0.2, 1007, SYM_OCC, SYM_VIR)
+    prob = cc.Problem(eps, L, o)
+    two = sc.solve_scc(prob, tol=1e-12, ground_tol=1e-12, dense=True)
+    gen = sc.solve_scc_states(prob, 2, tol=1e-12, ground_tol=1e-12, dense=True)
+    assert abs(gen["zeta"][(0, 1)]) < 1e-12 and abs(two["zeta"]) < 1e-12
+    assert np.allclose(gen["omega"], two["omega"], rtol=0, atol=1e-12)
+    assert abs(gen["E0"] - two["E0"]) < 1e-12
+
+
 @pytest.mark.parametrize("with_scc", [False, True])
 def test_densities_vs_brute_force(tiny, with_scc):
     o, v, eps, L, system, prob = tiny
