@@ -885,3 +885,34 @@ def test_random_shapes_match_the_oracle(host_lib):
             ctx.close()
 
     check()
+
+
+def test_binding_signatures_match_the_header():
+    """Every ctypes signature the binding declares has as many arguments as the
+    prototype in include/sccsd.h (a missing or miscounted argument would pass
+    pointers as C ints or shift every later argument)."""
+    from paper_2403_01007_gb300 import binding
+    txt = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    protos = {}
+    for m in re.finditer(r"\b(sccsd_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", txt):
+        args = m.group(2).strip()
+        protos[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+
+    class Fn:
+        argtypes = None
+
+    class FakeLib:
+        def __getattr__(self, name):
+            f = Fn()
+            object.__setattr__(self, name, f)
+            return f
+
+    lib = binding._declare(FakeLib())
+    declared = {k: v.argtypes for k, v in vars(lib).items() if isinstance(v, Fn)}
+    checked = 0
+    for name, argtypes in declared.items():
+        if argtypes is None or name not in protos:
+            continue
+        assert len(argtypes) == protos[name], (name, len(argtypes), protos[name])
+        checked += 1
+    assert checked >= 40
