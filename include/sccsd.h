@@ -137,13 +137,21 @@ int sccsd_profile_read(sccsd_ctx* ctx, double* ladder_ms, long long* ladder_call
  * partial sums live in a file-scope device array of
  * sccsd_gemm_tn_noalloc_capacity() doubles (8 MiB), which every device that
  * loads the library holds until exit. The first call on a device looks up that
- * array's device address (with the device current), so make it before any
- * stream capture. M*N above the capacity is rejected with SCCSD_EINVAL; larger
- * K only lowers the number of K chunks. A, B and C must be device memory.
+ * array's device address and the device's multiprocessor count (with the
+ * device current), so make it before any stream capture. Both are cached for
+ * the life of the process: after cudaDeviceReset on a device the cached
+ * address is stale, so do not call this entry point on that device again.
+ * Sizes as for sccsd_gemm_tn: negative sizes or a NULL pointer give
+ * SCCSD_EINVAL, M or N = 0 writes nothing, K = 0 sets C to zero. M*N above the
+ * capacity is rejected with SCCSD_EINVAL before any CUDA call; larger K only
+ * lowers the number of K chunks. A, B and C must be device memory.
  * All calls share the one array: calls that overlap on the GPU (two streams,
  * two host threads) race on it, so serialise them. Every partial sum is written
  * before it is read, so stale contents from the previous call do no harm.
- * Returns after the stream has finished the call's work. */
+ * The work is enqueued on `stream` in order and the call returns without
+ * waiting for it: C is ready once the stream reaches that point. A launch
+ * failure is returned as SCCSD_ECUDA; a fault during execution shows up at the
+ * caller's next synchronisation of the stream. */
 int sccsd_gemm_tn_noalloc(long long M, long long N, long long K, double alpha, const double* A,
                           const double* B, double* C, void* stream);
 long long sccsd_gemm_tn_noalloc_capacity(void);
@@ -261,6 +269,16 @@ int sccsd_solve_ground(sccsd_ctx* ctx, const double* t0, double zeta, const doub
  * SCCSD_ENOTCONV when maxit is reached (outputs hold the last Ritz pairs). */
 int sccsd_solve_states(sccsd_ctx* ctx, int nroots, int side, double tol, int maxit,
                        double refine_tol, double* omega, double* vecs, int* iterations);
+
+/* Biorthonormal scaling of left eigenvectors (Sec. 2.1: the left and right
+ * EOM vectors of a state satisfy <L_k|R_k> = 1; with the biorthonormal bra
+ * basis the bracket is the plain dot product of the packed vectors):
+ *   L_k <- L_k / (L_k . R_k),  k = 0 .. nvec-1,
+ * R [nvec][dim] packed kets, L [nvec][dim] packed bras, overwritten in place;
+ * host or device pointers; FP64 dot products on the device. nvec = 0 does
+ * nothing. SCCSD_EINVAL for a NULL pointer, nvec < 0, or a dot product that is
+ * zero or not finite (L is then left scaled up to the offending k). */
+int sccsd_normalize_left(sccsd_ctx* ctx, int nvec, const double* R, double* L);
 
 /* ---- Learned initial guess and preconditioner ----------------------------
  * A per-amplitude MLP (BF16 weights and activations, FP32 accumulation) maps

@@ -56,6 +56,8 @@ def _declare(lib):
     lib.sccsd_solve_ground.argtypes = [_dp, _dp, ctypes.c_double, _dp, _dp, ctypes.c_double,
                                        ctypes.c_int, ctypes.c_double, _dp, _dp, _dp]
     lib.sccsd_solve_ground.restype = ctypes.c_int
+    lib.sccsd_normalize_left.argtypes = [_dp, ctypes.c_int, _dp, _dp]
+    lib.sccsd_normalize_left.restype = ctypes.c_int
     lib.sccsd_solve_states.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                        ctypes.c_int, ctypes.c_double, _dp, _dp, _dp]
     lib.sccsd_solve_states.restype = ctypes.c_int
@@ -219,12 +221,15 @@ def gemm_tn(A, B, C, alpha=1.0, precision="fp64", lib=None):
     return C
 
 
-def gemm_tn_noalloc(A, B, C, alpha=1.0, lib=None):
-    """FP64 C = alpha * A @ B.T on device tensors without any device allocation."""
+def gemm_tn_noalloc(A, B, C, alpha=1.0, stream=None, lib=None):
+    """FP64 C = alpha * A @ B.T on device tensors without any device allocation.
+    The work is enqueued on `stream` (a torch.cuda.Stream, default the legacy
+    default stream) and the call returns without waiting for it."""
     lib = lib or load()
     M, K = A.shape
     N = B.shape[0]
-    rc = lib.sccsd_gemm_tn_noalloc(M, N, K, float(alpha), _ptr(A), _ptr(B), _ptr(C), None)
+    sp = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    rc = lib.sccsd_gemm_tn_noalloc(M, N, K, float(alpha), _ptr(A), _ptr(B), _ptr(C), sp)
     if rc != 0:
         raise SccsdError(rc, lib.sccsd_strerror(rc).decode())
     return C
@@ -415,6 +420,19 @@ class Context:
                                                 ctypes.addressof(it)))
         return w, V, it.value
 
+    def normalize_left(self, R, L):
+        """L_k scaled in place so that L_k . R_k = 1 (the library's kernels do
+        the arithmetic); R and L are [nvec][dim] host arrays or device tensors."""
+        def c(x):
+            if hasattr(x, "data_ptr"):
+                return x
+            return np.ascontiguousarray(x, dtype=np.float64)
+        R = c(R)
+        L = c(L)
+        nvec = int(L.shape[0]) if L.ndim == 2 else 1
+        self._check(self.lib.sccsd_normalize_left(self.h, nvec, _ptr(R), _ptr(L)))
+        return L
+
     def overlap(self, ra0, Ra, rb0, Rb):
         """SCC orthogonality O_ab at the fixed state (natural projection)."""
         out = ctypes.c_double()
@@ -504,9 +522,8 @@ class Context:
         r = self.solve_scc(tol=tol, maxit=maxit, ground_tol=ground_tol, eom_tol=eom_tol)
         t = self.state_amplitudes()
         wl, VL, _ = self.solve_states(2, side="left", tol=left_tol, maxit=left_maxit)
-        La = VL[0] / (VL[0] @ r["Ra"])
-        Lb = VL[1] / (VL[1] @ r["Rb"])
-        return {"t": t, "Ra": r["Ra"], "Rb": r["Rb"], "La": La, "Lb": Lb, "zeta": r["zeta"],
+        VL = self.normalize_left(np.stack([r["Ra"], r["Rb"]]), VL)
+        return {"t": t, "Ra": r["Ra"], "Rb": r["Rb"], "La": VL[0], "Lb": VL[1], "zeta": r["zeta"],
                 "r0a": float(r["r0"][0]), "r0b": float(r["r0"][1]),
                 "omega_a": float(r["omega"][0]), "omega_b": float(r["omega"][1]),
                 "omega_left": wl, "e_corr": r["e_corr"]}

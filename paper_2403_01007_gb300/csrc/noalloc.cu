@@ -86,23 +86,41 @@ __global__ void k_reduce_noalloc(long long n, int splits, const double* __restri
   }
 }
 
-// Device address of g_noalloc_partials, looked up once per device.
-std::mutex g_mu;
-void* g_addr[256] = {nullptr};
+// K = 0: the empty sum
+__global__ void k_zero_noalloc(long long n, double* __restrict__ C) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    C[e] = 0.0;
+}
 
-int scratch_address(double** out) {
+// Per device, looked up once with that device current: the device address of
+// g_noalloc_partials and the number of multiprocessors (the split count is
+// sized for it).
+struct DeviceInfo {
+  void* addr = nullptr;
+  int sms = 0;
+};
+std::mutex g_mu;
+DeviceInfo g_dev[256];
+
+int device_info(double** out, int* sms) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return SCCSD_ECUDA;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
+  DeviceInfo& d = g_dev[dev];
+  if (!d.addr) {
     void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess || !p) {
+    int n = 0;
+    if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess || !p ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
       cudaGetLastError();
       return SCCSD_ECUDA;
     }
-    g_addr[dev] = p;
+    d.addr = p;
+    d.sms = n;
   }
-  *out = (double*)g_addr[dev];
+  *out = (double*)d.addr;
+  *sms = d.sms;
   return SCCSD_OK;
 }
 
@@ -121,30 +139,39 @@ extern "C" long long sccsd_gemm_tn_noalloc_capacity(void) { return kNoallocCapac
 
 extern "C" int sccsd_gemm_tn_noalloc(long long M, long long N, long long K, double alpha,
                                      const double* A, const double* B, double* C, void* stream) {
-  if (M < 1 || N < 1 || K < 1 || !A || !B || !C) return SCCSD_EINVAL;
-  if (M * N > kNoallocCapacity) return SCCSD_EINVAL;  // even one K chunk would not fit
+  if (M < 0 || N < 0 || K < 0 || !A || !B || !C) return SCCSD_EINVAL;
+  if (M == 0 || N == 0) return SCCSD_OK;  // an empty C: nothing to write
+  // M * N above the capacity (tested without forming the product, which could
+  // overflow): even one K chunk would not fit
+  if (N > kNoallocCapacity / M) return SCCSD_EINVAL;
+  if ((M + TM - 1) / TM > 65535) return SCCSD_EINVAL;
   if (!on_device(A) || !on_device(B) || !on_device(C)) return SCCSD_EINVAL;
-  double* part = nullptr;
-  int rc = scratch_address(&part);
-  if (rc != SCCSD_OK) return rc;
   cudaStream_t st = (cudaStream_t)stream;
+  const long long n = M * N;
+  const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  if (K == 0) {
+    k_zero_noalloc<<<blocks, 256, 0, st>>>(n, C);
+    return cudaGetLastError() == cudaSuccess ? SCCSD_OK : SCCSD_ECUDA;
+  }
+  double* part = nullptr;
+  int sms = 0;
+  int rc = device_info(&part, &sms);
+  if (rc != SCCSD_OK) return rc;
   const long long tiles = ((M + TM - 1) / TM) * ((N + TN - 1) / TN);
-  long long splits = (4 * 152 + tiles - 1) / tiles;
+  // about four CTAs per multiprocessor, at least 256 K values per split, and
+  // never more partial sums than the shared array holds
+  long long splits = (4LL * sms + tiles - 1) / tiles;
   if (splits > K / 256) splits = K / 256;
-  if (splits > kNoallocCapacity / (M * N)) splits = kNoallocCapacity / (M * N);
+  if (splits > kNoallocCapacity / n) splits = kNoallocCapacity / n;
   if (splits > 1024) splits = 1024;
   if (splits < 1) splits = 1;
   long long kc = (K + splits - 1) / splits;
   kc = (kc + TK - 1) / TK * TK;
-  splits = (K + kc - 1) / kc;
-  if ((M + TM - 1) / TM > 65535) return SCCSD_EINVAL;
+  splits = (K + kc - 1) / kc;  // never above the clamped value: kc only grew
   dim3 grid((unsigned)((N + TN - 1) / TN), (unsigned)((M + TM - 1) / TM), (unsigned)splits);
   k_splitk_noalloc<<<grid, 256, 0, st>>>(M, N, K, kc, A, B, part);
   if (cudaGetLastError() != cudaSuccess) return SCCSD_ECUDA;
-  long long n = M * N;
-  int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
   k_reduce_noalloc<<<blocks, 256, 0, st>>>(n, (int)splits, part, alpha, C);
   if (cudaGetLastError() != cudaSuccess) return SCCSD_ECUDA;
-  if (cudaStreamSynchronize(st) != cudaSuccess) return SCCSD_ECUDA;
   return SCCSD_OK;
 }

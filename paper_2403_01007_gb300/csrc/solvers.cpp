@@ -203,6 +203,51 @@ int sccsd_solve_ground(sccsd_ctx* c, const double* t0, double zeta, const double
   return SCCSD_OK;
 }
 
+int sccsd_normalize_left(sccsd_ctx* c, int nvec, const double* R, double* L) {
+  if (!c) return SCCSD_EINVAL;
+  if (nvec < 0) return fail(c, SCCSD_EINVAL, "nvec < 0");
+  if (nvec == 0) return SCCSD_OK;
+  if (!R || !L) return fail(c, SCCSD_EINVAL, "R or L is NULL");
+  int status = SCCSD_OK;
+  int k_bad = -1;
+  int rc = guarded(c, [&] {
+    Dev d{c};
+    ensure_small(c);
+    const int64_t dim = c->dim;
+    const bool rdev = c->be->is_device(R), ldev = c->be->is_device(L);
+    double* rb = solver_buf(c, 80, dim);
+    double* lb = solver_buf(c, 81, dim);
+    for (int k = 0; k < nvec && status == SCCSD_OK; ++k) {
+      const double* rk = R + (int64_t)k * dim;
+      double* lk = L + (int64_t)k * dim;
+      const double* rd = rk;
+      double* ld = lk;
+      if (!rdev) {
+        c->be->upload(rb, rk, dim, false);
+        rd = rb;
+      }
+      if (!ldev) {
+        c->be->upload(lb, lk, dim, false);
+        ld = lb;
+      }
+      // <L_k|R_k> is the plain dot product in the biorthonormal bra basis
+      const double s = d.dot(ld, rd, dim);
+      if (!std::isfinite(s) || std::fabs(s) < 1e-300) {
+        status = SCCSD_EINVAL;
+        k_bad = k;
+        break;
+      }
+      d.axpby(dim, 1.0 / s, ld, 0.0, ld);
+      if (!ldev) c->be->download(lk, ld, dim, false);
+    }
+    c->be->sync();
+  });
+  if (rc != SCCSD_OK) return rc;
+  if (status != SCCSD_OK)
+    return fail(c, status, "L_k . R_k is zero or not finite for k = " + std::to_string(k_bad));
+  return SCCSD_OK;
+}
+
 int sccsd_solve_states(sccsd_ctx* c, int nroots, int side, double tol, int maxit,
                        double refine_tol, double* omega, double* vecs, int* iterations) {
   if (!c) return SCCSD_EINVAL;

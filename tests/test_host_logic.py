@@ -46,6 +46,32 @@ def test_library_exports_every_declared_symbol():
     ctypes.CDLL(lib_path)
 
 
+def test_noalloc_size_checks_come_before_any_cuda_call():
+    """sccsd_gemm_tn_noalloc rejects M*N above its fixed array, negative sizes
+    and NULL pointers before it touches CUDA (so this runs without a GPU),
+    including products M*N that overflow a 64-bit integer; empty outputs return
+    OK at once."""
+    from paper_2403_01007_gb300 import binding
+    lib_path = binding.LIB_PATH
+    if not os.path.exists(lib_path):
+        from paper_2403_01007_gb300 import build
+        build.build()
+    lib = binding.load()
+    cap = lib.sccsd_gemm_tn_noalloc_capacity()
+    buf = (ctypes.c_double * 4)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    f = lib.sccsd_gemm_tn_noalloc
+    # M * N = 2^64 wraps to 0; 2^20 * (2^44 + 1) wraps to exactly the capacity
+    for (M, N) in [(1 << 21, 1 << 43), (1 << 20, (1 << 44) + 1), (cap, 2), (2, cap),
+                   (1 << 62, 1 << 62)]:
+        assert f(M, N, 16, 1.0, p, p, p, None) == -1, (M, N)
+    assert f(-1, 2, 2, 1.0, p, p, p, None) == -1
+    assert f(2, 2, -1, 1.0, p, p, p, None) == -1
+    assert f(2, 2, 2, 1.0, None, p, p, None) == -1
+    assert f(0, 5, 5, 1.0, p, p, p, None) == 0
+    assert f(5, 0, 5, 1.0, p, p, p, None) == 0
+
+
 @pytest.fixture(scope="module")
 def host_lib():
     from paper_2403_01007_gb300 import binding
@@ -525,6 +551,45 @@ def test_davidson_through_the_c_abi(host_lib, side):
     for k in range(3):
         assert abs(np.linalg.norm(V[k]) - 1.0) < 1e-12
         assert np.linalg.norm(AV[k] - w[k] * V[k]) < 1e-8
+    ctx.close()
+
+
+def test_left_normalisation_through_the_c_abi(host_lib):
+    """sccsd_normalize_left scales each left eigenvector so that <L_k|R_k> = 1
+    (Sec. 2.1; the plain dot product in the biorthonormal bra basis). Checked
+    on the Davidson roots of both sides: after scaling, L_k . R_l is the
+    identity (left and right vectors of distinct roots are biorthogonal), and
+    the left vectors still satisfy their eigen-equation. Zero products and
+    NULL pointers are rejected; nvec = 0 is a no-op."""
+    from oracle import solvers as sv
+    B, lib = host_lib
+    o, v, J = 3, 4, 9
+    eps, L = syn.system(o, v, J, 0.2, 55)
+    prob = cc.Problem(eps, L, o)
+    x, _, _ = sv.ground_state(prob, tol=1e-12)
+    ctx = B.Context(o, v, J, eps, L, lib=lib)
+    ctx.residual(x)
+    wr, VR, _ = ctx.solve_states(3, side="right", tol=1e-10)
+    wl, VL, _ = ctx.solve_states(3, side="left", tol=1e-10)
+    assert np.abs(wr - wl).max() < 1e-9
+    raw = VL.copy()
+    out = ctx.normalize_left(VR, VL)
+    S = out @ VR.T
+    assert np.abs(S - np.eye(3)).max() < 1e-7
+    for k in range(3):
+        # the same direction, only rescaled by 1 / (L_k . R_k)
+        assert np.abs(out[k] - raw[k] / (raw[k] @ VR[k])).max() < 1e-13
+    AL = ctx.jacobian_left(np.ascontiguousarray(out))
+    for k in range(3):
+        assert np.linalg.norm(AL[k] - wl[k] * out[k]) < 1e-7 * np.linalg.norm(out[k])
+    # errors: a left vector orthogonal to its right vector, NULL, nvec < 0
+    Z = np.zeros((1, ctx.dim))
+    with pytest.raises(B.SccsdError) as ei:
+        ctx.normalize_left(VR[:1].copy(), Z)
+    assert ei.value.code == -1
+    assert lib.sccsd_normalize_left(ctx.h, 1, None, None) == -1
+    assert lib.sccsd_normalize_left(ctx.h, -1, None, None) == -1
+    assert lib.sccsd_normalize_left(ctx.h, 0, None, None) == 0
     ctx.close()
 
 
