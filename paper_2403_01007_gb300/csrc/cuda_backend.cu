@@ -257,6 +257,98 @@ __global__ void k_sum_parts(int64_t n, int splits, const double* __restrict__ pa
   }
 }
 
+// ------------------------------------------------------------------ ladder
+//
+// Sum_cd g_acbd X_ij^cd with g_acbd = sum_J L^J_ac L^J_bd (the vvvv block of
+// the Hamiltonian, Sec. 2.4.2) in the symmetric / antisymmetric form: with
+// G+-_(ab)(cd) = g_acbd +- g_adbc over pairs a <= b, c <= d, and
+//   X~+_ij(cd) = X_ij^cd + X_ij^dc (c < d), X_ij^cc (c = d),
+//   X-_ij(cd)  = X_ij^cd - X_ij^dc (c < d),
+// the result is Y_ij^ab = P_ij(ab) + s M_ij(ab) with
+//   P = 1/2 sum_(c<=d) G+ X~+,   M = 1/2 sum_(c<d) G- X-,
+// s = +1 for a <= b and -1 for a > b. Every operand the residual graph hands
+// to the ladder has the pair symmetry X_ij^cd = X_ji^dc, so X~+ is symmetric
+// and X- antisymmetric in ij: P is needed for i <= j only and M for i < j.
+// Pair indices are row-major over the upper triangle: p(a, b) = a (v - 1) -
+// a (a - 1) / 2 + b for a <= b (likewise q(c, d) and the occupied pairs).
+
+// X~+[(z, i<=j)][q] and X-[(z, i<j)][q] from X[(z, i, j)][(c, d)]; with the
+// pair symmetry X_ij^dc is read as X_ji^cd, so both reads walk d
+__global__ void k_ladder_pack_x(const double* __restrict__ X, int o, int v, int64_t nb,
+                                const int* __restrict__ pairs, double* __restrict__ Xp,
+                                double* __restrict__ Xm, int64_t ld) {
+  const int64_t Po = (int64_t)o * (o + 1) / 2, Pm = (int64_t)o * (o - 1) / 2;
+  const int64_t Pv = (int64_t)v * (v + 1) / 2, vv = (int64_t)v * v;
+  for (int64_t blk = blockIdx.x; blk < nb * Po; blk += gridDim.x) {
+    const int64_t z = blk / Po;
+    int r = (int)(blk % Po), i = 0;
+    while (r >= o - i) {
+      r -= o - i;
+      ++i;
+    }
+    const int j = i + r;
+    const double* xij = X + ((z * o + i) * o + j) * vv;
+    const double* xji = X + ((z * o + j) * o + i) * vv;
+    double* op = Xp + blk * ld;
+    double* om = i < j ? Xm + (z * Pm + (int64_t)i * (o - 1) - (int64_t)i * (i - 1) / 2 + (j - i - 1)) * ld
+                       : nullptr;
+    for (int64_t q = threadIdx.x; q < Pv; q += blockDim.x) {
+      const int cd = __ldg(pairs + q);
+      const int c = cd >> 16, d = cd & 0xffff;
+      const int64_t e = (int64_t)c * v + d;
+      const double a = xij[e], b = xji[e];
+      op[q] = c == d ? 0.5 * (a + b) : a + b;
+      if (om) om[q] = c == d ? 0.0 : a - b;
+    }
+  }
+}
+
+// Y[(z, i, j)][(a, b)] from P[(z, i<=j)][p] and M[(z, i<j)][p]
+__global__ void k_ladder_unpack(const double* __restrict__ P, const double* __restrict__ M,
+                                int64_t ld, int o, int v, int64_t nb, double* __restrict__ Y) {
+  const int64_t oo = (int64_t)o * o, vv = (int64_t)v * v;
+  const int64_t Po = (int64_t)o * (o + 1) / 2, Pm = (int64_t)o * (o - 1) / 2;
+  for (int64_t row = blockIdx.x; row < nb * oo; row += gridDim.x) {
+    const int64_t z = row / oo;
+    const int i = (int)((row / o) % o), j = (int)(row % o);
+    const int i0 = i < j ? i : j, j0 = i < j ? j : i;
+    const double* pr = P + (z * Po + (int64_t)i0 * (o - 1) - (int64_t)i0 * (i0 - 1) / 2 + j0) * ld;
+    const double* mr =
+        i0 < j0 ? M + (z * Pm + (int64_t)i0 * (o - 1) - (int64_t)i0 * (i0 - 1) / 2 + (j0 - i0 - 1)) * ld
+                : nullptr;
+    const double sij = i <= j ? 1.0 : -1.0;
+    double* y = Y + row * vv;
+    for (int64_t e = threadIdx.x; e < vv; e += blockDim.x) {
+      const int a = (int)(e / v), b = (int)(e % v);
+      const int a0 = a < b ? a : b, b0 = a < b ? b : a;
+      const int64_t p = (int64_t)a0 * (v - 1) - (int64_t)a0 * (a0 - 1) / 2 + b0;
+      double val = pr[p];
+      if (mr && a0 < b0) val += (a <= b ? sij : -sij) * mr[p];
+      y[e] = val;
+    }
+  }
+}
+
+// G+ and G- rows of pairs from a block of the full integrals,
+// Gc[((a - a0) v + c)][((b - a0) v + d)] = g_acbd (FP64 build)
+__global__ void k_ladder_pack_g(const double* __restrict__ Gc, int64_t ldg, int v, int a0,
+                                const int* __restrict__ pairs, int64_t p_begin, int64_t npairs,
+                                double* __restrict__ Gp, double* __restrict__ Gm, int64_t ld) {
+  const int64_t Pv = (int64_t)v * (v + 1) / 2;
+  for (int64_t w = blockIdx.x; w < npairs; w += gridDim.x) {
+    const int ab = __ldg(pairs + p_begin + w);
+    const int a = ab >> 16, b = ab & 0xffff;
+    const double* W = Gc + (int64_t)(a - a0) * v * ldg + (int64_t)(b - a0) * v;  // W[c][d] = W[c ldg + d]
+    for (int64_t q = threadIdx.x; q < Pv; q += blockDim.x) {
+      const int cd = __ldg(pairs + q);
+      const int c = cd >> 16, d = cd & 0xffff;
+      const double x = W[(int64_t)c * ldg + d], y = W[(int64_t)d * ldg + c];
+      Gp[w * ld + q] = x + y;
+      Gm[w * ld + q] = c == d ? 0.0 : x - y;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ backend
 
 class CudaBackend : public Backend {
@@ -265,16 +357,16 @@ class CudaBackend : public Backend {
   int precision;
   std::vector<double*> slots = std::vector<double*>(8, nullptr);
   std::vector<int64_t> slot_n = std::vector<int64_t>(8, 0);
-  // ladder integrals G[(ab)][(cd)] = sum_J L^J_ac L^J_bd (FP64), and the
-  // tensor-core operand form when a mixed precision mode is active
-  double* G = nullptr;
-  int64_t G_version = -1;
-  const double* G_src = nullptr;
-  int64_t Gtc_version = -1;
-  const double* Gtc_src = nullptr;
-  int Gtc_slices = 0;
   std::unique_ptr<TcGemm> tc;
-  TcOperand G_tc;
+  // ladder: pair table of the current v (device, a << 16 | b), the virtual
+  // block of L in tensor-core form (kept while L is unchanged), the packed
+  // operands of one call and the G+- slabs of one chunk of pairs
+  int* pairs_dev = nullptr;
+  int pairs_v = -1;
+  TcOperand lt_op, xp_op, xm_op, gp_op, gm_op;
+  int64_t lt_version = -1;
+  const double* lt_src = nullptr;
+  int lt_slices = 0;
   bool prof = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
   double prof_ms = 0.0, prof_flops = 0.0;
@@ -306,7 +398,9 @@ class CudaBackend : public Backend {
     }
     for (double* p : slots)
       if (p) cudaFree(p);
-    if (G) cudaFree(G);
+    if (tc)
+      for (TcOperand* op : {&lt_op, &xp_op, &xm_op, &gp_op, &gm_op}) tc->release(*op);
+    if (pairs_dev) cudaFree(pairs_dev);
     tc.reset();
   }
 
@@ -379,6 +473,7 @@ class CudaBackend : public Backend {
     if (tc)
       for (auto& kv : opcache) tc->release(kv.second.op);
     opcache.clear();
+    lt_version = -1;
   }
   void fill(double* p, int64_t n, double v) override {
     if (n <= 0) return;
@@ -663,28 +758,6 @@ class CudaBackend : public Backend {
     return slots[slot];
   }
 
-  // G[(ab)][(cd)] = sum_J L^J_ac L^J_bd over the virtual block of L, built on
-  // the device from the Cholesky vectors: exactly in FP64 for the FP64 mode,
-  // on the tensor cores for the mixed modes (then split into BF16 slices)
-  void build_ladder_integrals(const Graph& g, const double* L, bool exact, double* dst) {
-    const int64_t o = g.o, v = g.v, J = g.J, n = o + v, vv = v * v;
-    // Lt[(ac)][J] = L[J][o+a][o+c]
-    double* Lt = scratch(3, vv * J);
-    {
-      int64_t dims[3] = {v, v, J};
-      int64_t ostr[3] = {v * J, J, 1};
-      int64_t istr[3] = {n, 1, n * n};
-      copy_view(3, dims, Lt, ostr, L + o * n + o, istr, 1.0, false);
-    }
-    double* Gp = scratch(4, vv * vv);  // Gp[(ac)][(bd)]
-    gemm_tn(1, vv, vv, J, 1.0, Lt, Lt, Gp, !exact);
-    // G[a][b][c][d] = Gp[a][c][b][d]
-    int64_t dims[4] = {v, v, v, v};
-    int64_t ostr[4] = {v * vv, vv, v, 1};
-    int64_t istr[4] = {v * vv, v, vv, 1};
-    copy_view(4, dims, dst, ostr, Gp, istr, 1.0, false);
-  }
-
   void* record_event() override {
     cudaEvent_t e;
     CK(cudaEventCreate(&e));
@@ -740,82 +813,217 @@ class CudaBackend : public Backend {
     if (launches) *launches = g_launches - launches0;
   }
 
+  // device table of the packed pairs (a, b), a <= b, of v indices
+  const int* pair_table(int v) {
+    if (pairs_v == v) return pairs_dev;
+    const int64_t Pv = (int64_t)v * (v + 1) / 2;
+    if (v > 65535) throw std::runtime_error("ladder: v too large for the pair table");
+    std::vector<int> h((size_t)Pv);
+    int64_t k = 0;
+    for (int a = 0; a < v; ++a)
+      for (int b = a; b < v; ++b) h[(size_t)k++] = (a << 16) | b;
+    if (pairs_dev) {
+      CK(cudaStreamSynchronize(st));
+      cudaFree(pairs_dev);
+      pairs_dev = nullptr;
+      pairs_v = -1;
+    }
+    if (capturing) throw std::runtime_error("device allocation during graph capture (warm-up missing)");
+    if (cudaMalloc(&pairs_dev, sizeof(int) * (size_t)Pv) != cudaSuccess) {
+      cudaGetLastError();
+      throw OomError("ladder pair table");
+    }
+    CK(cudaMemcpyAsync(pairs_dev, h.data(), sizeof(int) * (size_t)Pv, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    pairs_v = v;
+    return pairs_dev;
+  }
+
+  // Y[(z ij)][(ab)] = sum_(cd) g_acbd X[(z ij)][(cd)], the ladder integrals
+  // formed from the Cholesky vectors inside the call (never stored whole).
   void ladder(const Graph& g, const double* L, int64_t ver, const double* X, double* Y,
               int64_t rows) override {
-    const int64_t v = g.v, vv = v * v;
+    const int o = g.o, v = g.v, J = g.J;
+    const int64_t n = (int64_t)o + v, oo = (int64_t)o * o, nb = rows / oo;
+    const int64_t Pv = (int64_t)v * (v + 1) / 2;
+    const int64_t Po = (int64_t)o * (o + 1) / 2, Pm = (int64_t)o * (o - 1) / 2;
+    const int64_t np = nb * Po, nm = nb * Pm;
     const bool mixed = tc && precision != 0;
-    if (!mixed) {
-      if (!G || G_version != ver || G_src != L) {
-        if (!G) G = alloc(vv * vv);
-        build_ladder_integrals(g, L, true, G);
-        G_version = ver;
-        G_src = L;
-      }
-    } else if (Gtc_version != ver || Gtc_src != L || Gtc_slices != tc->slices()) {
-      // reuse the exact integrals when they are current, else build on tensor cores
-      const double* src = G;
-      if (!G || G_version != ver || G_src != L) {
-        double* tmp = scratch(6, vv * vv);
-        build_ladder_integrals(g, L, false, tmp);
-        src = tmp;
-      }
-      tc->prepare_operand(src, vv, vv, G_tc);
-      Gtc_version = ver;
-      Gtc_src = L;
-      Gtc_slices = tc->slices();
-    }
+    const int* pairs = pair_table(v);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (prof) {
       CK(cudaEventCreate(&e0));
       CK(cudaEventCreate(&e1));
       CK(cudaEventRecord(e0, st));
     }
-    // Y[(z ij)][(ab)] = sum_(cd) X[(z ij)][(cd)] G[(ab)][(cd)]
-    if (mixed)
-      tc->gemm_prepared_b(rows, vv, vv, 1.0, X, G_tc, Y, !prof);
-    else
-      dgemm(1, rows, vv, vv, 1.0, X, G, Y);
+    // packed operands X~+, X- (FP64) and the results P, M [rows][Pv]
+    double* Xp = scratch(0, np * Pv);
+    double* Xm = scratch(1, std::max<int64_t>(1, nm) * Pv);
+    double* Pr = scratch(2, np * Pv);
+    double* Mr = scratch(3, std::max<int64_t>(1, nm) * Pv);
+    k_ladder_pack_x<<<grid_for(np * 256, 256), 256, 0, st>>>(X, o, v, nb, pairs, Xp, Xm, Pv);
+    check_launch("ladder_pack_x");
+    if (mixed) {
+      tc->prepare_operand(Xp, np, Pv, xp_op);
+      if (nm > 0) tc->prepare_operand(Xm, nm, Pv, xm_op);
+    }
+    if (mixed && v <= TcGemm::ladder_build_max_v()) {
+      // fused build on the tensor cores, one chunk of pairs at a time
+      if (lt_version != ver || lt_src != L || lt_slices != tc->slices()) {
+        tc->prepare_ladder_lt(L, o, v, J, lt_op);
+        lt_version = ver;
+        lt_src = L;
+        lt_slices = tc->slices();
+      }
+      // chunks of whole 256-pair tiles sized so that the contraction of one
+      // chunk is about one wave of the persistent grid
+      int sms = 152;
+      {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess)
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      }
+      const int64_t mt = std::max<int64_t>(1, (np + 127) / 128);
+      int64_t nt = std::max<int64_t>(1, sms / mt);
+      const int64_t chunk = std::min<int64_t>(nt * 256, ((Pv + 255) / 256) * 256);
+      tc->alloc_operand(chunk, Pv, tc->slices(), gp_op);
+      tc->alloc_operand(chunk, Pv, tc->slices(), gm_op);
+      for (int64_t p0 = 0; p0 < Pv; p0 += chunk) {
+        const int64_t cnt = std::min<int64_t>(chunk, Pv - p0);
+        // the slabs as operands of this chunk's rows only (fewer N tiles in the
+        // last chunk); the build writes its slices at the same row stride
+        TcOperand gp = gp_op, gm = gm_op;
+        gp.rows = gm.rows = cnt;
+        gp.rows_pad = gm.rows_pad = (cnt + 255) / 256 * 256;
+        tc->ladder_build(lt_op, v, pairs, p0, cnt, gp, gm);
+        tc->gemm_ops(np, cnt, 0.5, xp_op, gp, Pr + p0, OutView::dense(Pv), false);
+        if (nm > 0) tc->gemm_ops(nm, cnt, 0.5, xm_op, gm, Mr + p0, OutView::dense(Pv), false);
+      }
+    } else {
+      // build g_acbd for a block of a values with FP64 GEMMs, form G+- of its
+      // pairs, contract (FP64, or on the tensor cores in a mixed mode)
+      const int64_t vv = (int64_t)v * v;
+      double* Lt = scratch(4, vv * J);  // Lt[(a c)][J]
+      {
+        int64_t dims[3] = {v, v, J};
+        int64_t ostr[3] = {(int64_t)v * J, J, 1};
+        int64_t istr[3] = {n, 1, n * n};
+        copy_view(3, dims, Lt, ostr, L + o * n + o, istr, 1.0, false);
+      }
+      const int64_t budget = (int64_t)1 << 27;  // doubles of one integral block (1 GiB)
+      for (int a0 = 0; a0 < v;) {
+        const int64_t cols = (int64_t)(v - a0) * v;
+        int na = (int)std::max<int64_t>(1, std::min<int64_t>(v - a0, budget / (cols * v)));
+        const int a1 = a0 + na;
+        const int64_t p0 = (int64_t)a0 * (v - 1) - (int64_t)a0 * (a0 - 1) / 2 + a0;
+        const int64_t p1 = a1 < v ? (int64_t)a1 * (v - 1) - (int64_t)a1 * (a1 - 1) / 2 + a1 : Pv;
+        const int64_t cnt = p1 - p0;
+        double* Gc = scratch(5, (int64_t)na * v * cols);
+        gemm_tn(1, (int64_t)na * v, cols, J, 1.0, Lt + (int64_t)a0 * v * J, Lt + (int64_t)a0 * v * J,
+                Gc, false);
+        // (slot 7 holds the split-K partial sums of the FP64 GEMMs)
+        double* Gp = scratch(6, 2 * cnt * Pv);
+        double* Gm = Gp + cnt * Pv;
+        k_ladder_pack_g<<<grid_for(cnt * 256, 256), 256, 0, st>>>(Gc, cols, v, a0, pairs, p0, cnt, Gp,
+                                                                  Gm, Pv);
+        check_launch("ladder_pack_g");
+        if (mixed) {
+          tc->prepare_operand(Gp, cnt, Pv, gp_op);
+          tc->gemm_ops(np, cnt, 0.5, xp_op, gp_op, Pr + p0, OutView::dense(Pv), false);
+          if (nm > 0) {
+            tc->prepare_operand(Gm, cnt, Pv, gm_op);
+            tc->gemm_ops(nm, cnt, 0.5, xm_op, gm_op, Mr + p0, OutView::dense(Pv), false);
+          }
+        } else {
+          // C[n][w] for the pairs of this block, then into P[n][p0 + w]
+          double* Cc = scratch(5, std::max(np, nm) * cnt);
+          dgemm(1, np, cnt, Pv, 0.5, Xp, Gp, Cc);
+          int64_t dims[2] = {np, cnt}, ostr[2] = {Pv, 1}, istr[2] = {cnt, 1};
+          copy_view(2, dims, Pr + p0, ostr, Cc, istr, 1.0, false);
+          if (nm > 0) {
+            dgemm(1, nm, cnt, Pv, 0.5, Xm, Gm, Cc);
+            int64_t dm[2] = {nm, cnt};
+            copy_view(2, dm, Mr + p0, ostr, Cc, istr, 1.0, false);
+          }
+        }
+        a0 = a1;
+      }
+    }
+    k_ladder_unpack<<<grid_for(nb * oo * 256, 256), 256, 0, st>>>(Pr, Mr, Pv, o, v, nb, Y);
+    check_launch("ladder_unpack");
     if (prof) {
       CK(cudaEventRecord(e1, st));
       ev.push_back({e0, e1});
       ++prof_calls;
-      prof_flops += 2.0 * (double)rows * (double)vv * (double)vv;
+      // algorithmic count: the (ac) <-> (bd) symmetric build v^2 (v^2 + 1) / 2 . 2J
+      // plus the packed contraction 2 [Po Pv^2 + o(o-1)/2 (v(v-1)/2)^2] per vector
+      const double vv = (double)v * v, pm = (double)v * (v - 1) / 2;
+      prof_flops += vv * (vv + 1.0) / 2.0 * 2.0 * J +
+                    2.0 * (double)nb * ((double)Po * Pv * Pv + (double)Pm * pm * pm);
     }
   }
 
+  // adjoint of the ladder with respect to the Cholesky vectors (two-particle
+  // density, vvvv block): out[J][(a c)] = sum_bd (D[a,b,c,d] + D[b,a,d,c]) L^J_bd
+  // with D[a,b,c,d] = sum_n Yb[n][(a b)] X[n][(c d)], formed for a block of a
+  // values at a time (the full v^4 D is never stored)
   void ladder_adj_l(const Graph& g, const double* L, const double* Yb, const double* X,
                     double* out) override {
     const int64_t o = g.o, v = g.v, J = g.J, n = o + v, vv = v * v, oo = o * o;
-    // D[(ab)][(cd)] = sum_ij Yb[(ij)][(ab)] X[(ij)][(cd)]
-    double* YT = scratch(3, vv * oo);
-    double* XT = scratch(5, vv * oo);
-    {
-      int64_t dims[2] = {vv, oo}, ostr[2] = {oo, 1}, istr[2] = {1, vv};
-      copy_view(2, dims, YT, ostr, Yb, istr, 1.0, false);
-      copy_view(2, dims, XT, ostr, X, istr, 1.0, false);
-    }
-    double* D = scratch(4, vv * vv);
-    gemm_tn(1, vv, vv, oo, 1.0, YT, XT, D, true);
-    // M2[(ac)][(bd)] = D[(ab)][(cd)] + D[(ba)][(dc)]
-    double* M2 = scratch(6, vv * vv);
-    {
-      int64_t dims[4] = {v, v, v, v};  // a c b d
-      int64_t ostr[4] = {v * vv, vv, v, 1};
-      int64_t i1[4] = {v * vv, v, vv, 1};  // D[a][b][c][d]
-      int64_t i2[4] = {vv, 1, v * vv, v};  // D[b][a][d][c]
-      copy_view(4, dims, M2, ostr, D, i1, 1.0, false);
-      copy_view(4, dims, M2, ostr, D, i2, 1.0, true);
-    }
-    // out'[(ac)][J] = sum_(bd) M2[(ac)][(bd)] Lvv[J][(bd)]
-    double* Lvv = scratch(5, J * vv);
+    double* Lvv = scratch(5, J * vv);  // Lvv[J][(b d)]
     {
       int64_t dims[3] = {J, v, v}, ostr[3] = {vv, v, 1}, istr[3] = {n * n, n, 1};
       copy_view(3, dims, Lvv, ostr, L + o * n + o, istr, 1.0, false);
     }
-    double* op = scratch(3, vv * J);
-    gemm_tn(1, vv, J, vv, 1.0, M2, Lvv, op, true);
-    int64_t dims[2] = {J, vv}, ostr[2] = {vv, 1}, istr[2] = {1, J};
-    copy_view(2, dims, out, ostr, op, istr, 1.0, false);
+    const int64_t budget = (int64_t)1 << 26;  // doubles of one D block (512 MiB)
+    for (int64_t a0 = 0; a0 < v;) {
+      const int64_t na = std::max<int64_t>(1, std::min<int64_t>(v - a0, budget / (v * vv)));
+      const int64_t rows = na * v;
+      // D1[(a b)][(c d)] = sum_n Yb[n][(a b)] X[n][(c d)], a in the block
+      MatView A1;
+      A1.p = Yb + a0 * v;
+      A1.sr2 = 1;
+      A1.sk2 = vv;
+      MatView B1;
+      B1.p = X;
+      B1.sr2 = 1;
+      B1.sk2 = vv;
+      double* D1 = scratch(3, rows * vv);
+      gemm_view(1, rows, vv, oo, 1.0, A1, B1, D1, true);
+      // D2[(a b)][(c d)] = sum_n Yb[n][(b a)] X[n][(d c)]
+      MatView A2;
+      A2.p = Yb + a0;
+      A2.n2r = v;
+      A2.sr1 = 1;
+      A2.sr2 = v;
+      A2.sk2 = vv;
+      MatView B2;
+      B2.p = X;
+      B2.n2r = v;
+      B2.sr1 = 1;
+      B2.sr2 = v;
+      B2.sk2 = vv;
+      double* D2 = scratch(4, rows * vv);
+      gemm_view(1, rows, vv, oo, 1.0, A2, B2, D2, true);
+      {
+        int64_t dims[1] = {rows * vv}, os[1] = {1};
+        copy_view(1, dims, D1, os, D2, os, 1.0, true);
+      }
+      // op[(a c)][J] = sum_(b d) D[a][b][c][d] Lvv[J][(b d)]
+      MatView A3;
+      A3.p = D1;
+      A3.n2r = v;
+      A3.sr1 = v * vv;
+      A3.sr2 = v;
+      A3.n2k = v;
+      A3.sk1 = vv;
+      A3.sk2 = 1;
+      double* op = scratch(6, rows * J);
+      gemm_view(1, rows, J, vv, 1.0, A3, MatView::dense(Lvv, J, vv), op, true);
+      int64_t dims[2] = {J, rows}, ostr[2] = {vv, 1}, istr[2] = {1, J};
+      copy_view(2, dims, out + a0 * v, ostr, op, istr, 1.0, false);
+      a0 += na;
+    }
   }
 };
 

@@ -478,6 +478,303 @@ __global__ void k_sum_splits(int64_t M, int64_t N, int splits, const double* __r
   }
 }
 
+// ------------------------------------------------------------------ ladder build
+//
+// The particle-particle ladder of the T1-transformed Hamiltonian (Sec. 2.4.2)
+// contracts the amplitudes with the vvvv integrals g_acbd = sum_J L^J_ac L^J_bd
+// of the Cholesky vectors. They are never stored: for each pair (a, b), a <= b,
+// of a chunk this kernel forms the v x v block W[c][d] = g_acbd on the tensor
+// cores (M = c, N = d, K = J; A = the rows (a, c) and B = the rows (b, d) of the
+// operand Lt[(p, q)][J] = L^J_pq over the virtual block) and writes
+//   G+[pair][q(c, d)] = W[c][d] + W[d][c],   G-[pair][q(c, d)] = W[c][d] - W[d][c]
+// for c <= d (q the packed index c*v - c(c-1)/2 + d - c) as BF16 slices of two
+// K-major operands of the contraction kernel above. The symmetric and
+// antisymmetric combinations halve the contraction twice over (pairs a <= b
+// and c <= d), and W[d][c] comes from the same accumulator, so each g_acbd is
+// computed once per unordered pair (ac) <-> (bd) ... up to the diagonal blocks.
+// Warp roles:
+//   warp 4    : TMA producer; one stage = A rows a*v .. a*v+127 (and, for
+//               v > 128, a*v+128 .. a*v+255) and B rows b*v .. b*v+NB-1 of one
+//               64-wide K block; slice products (0,0), (0,1), (1,0) in turn
+//   warp 5    : one elected thread issues the MMAs into accumulator 0 (rows
+//               c < 128, TMEM columns 0 ..) and 1 (rows c >= 128, columns
+//               256 ..), N = NB = v rounded up to 16
+//   warps 0-3 : epilogue; thread t owns TMEM lane t, i.e. rows c = t and
+//               c = 128 + t. Phase 1 writes the upper triangle W[c][d], d > c,
+//               to shared memory (FP32); phase 2 takes the lower triangle from
+//               TMEM, forms the two combinations with the stored transpose and
+//               stores them (consecutive lanes write consecutive q).
+// Every mbarrier wait is bounded as in k_tc_gemm.
+constexpr int LB_THREADS = 192;
+
+__global__ void __launch_bounds__(LB_THREADS, 1)
+    k_ladder_build(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   int v, int NB, int two, int nkb, int nprod, int64_t slice_rows, int stages,
+                   const int* __restrict__ pairs, int64_t p_begin, int64_t npairs,
+                   __nv_bfloat16* __restrict__ gp, __nv_bfloat16* __restrict__ gm,
+                   int64_t out_ld, int64_t out_sstride, int nsl, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int a_bytes = A_BYTES * (two ? 2 : 1);
+  const int stage_bytes = a_bytes + NB * BK * 2;
+  uint64_t* full = (uint64_t*)(smem + stages * stage_bytes);
+  uint64_t* empty = full + stages;
+  uint64_t* acc_full = empty + stages;
+  uint64_t* acc_empty = acc_full + 1;
+  uint32_t* tmem_slot = (uint32_t*)(acc_empty + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  float* S = (float*)(smem + stages * stage_bytes + 256);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(acc_full)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(acc_empty)));
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 4) {
+    if (lane == 0) {
+      int64_t issued_last[8];
+      for (int s = 0; s < 8; ++s) issued_last[s] = -1;
+      int64_t g = 0;
+      for (int64_t w = blockIdx.x; w < npairs && !*abort_flag; w += gridDim.x) {
+        const int ab = __ldg(pairs + p_begin + w);
+        const int a = ab >> 16, b = ab & 0xffff;
+        for (int pr = 0; pr < nprod && !*abort_flag; ++pr) {
+          const int sa = pr == 2 ? 1 : 0, sb = pr == 1 ? 1 : 0;
+          const int ra = (int)(sa * slice_rows) + a * v, rb = (int)(sb * slice_rows) + b * v;
+          for (int kb = 0; kb < nkb; ++kb, ++g) {
+            const int s = (int)(g % stages);
+            if (g >= stages) {
+              if (!mbar_wait(smem_u32(&empty[s]), (uint32_t)((g / stages) - 1) & 1, err, 11)) {
+                *abort_flag = 1;
+                break;
+              }
+            }
+            if (*abort_flag) break;
+            const uint32_t fb = smem_u32(&full[s]);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                         "r"(stage_bytes)
+                         : "memory");
+            uint8_t* st = smem + (size_t)s * stage_bytes;
+            const int x = kb * BK;
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(st)),
+                "l"((uint64_t)&tmA), "r"(fb), "r"(x), "r"(ra)
+                : "memory");
+            if (two)
+              asm volatile(
+                  "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                  " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(st + A_BYTES)),
+                  "l"((uint64_t)&tmA), "r"(fb), "r"(x), "r"(ra + BM)
+                  : "memory");
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(st + a_bytes)),
+                "l"((uint64_t)&tmB), "r"(fb), "r"(x), "r"(rb)
+                : "memory");
+            issued_last[s] = g;
+          }
+        }
+      }
+      for (int s = 0; s < stages; ++s)
+        if (issued_last[s] >= 0)
+          mbar_wait(smem_u32(&full[s]), (uint32_t)(issued_last[s] / stages) & 1, err, 12);
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc(BM, NB);
+      int64_t g = 0, i = 0;
+      for (int64_t w = blockIdx.x; w < npairs && !*abort_flag; w += gridDim.x, ++i) {
+        if (i >= 1) {
+          // the epilogue has read both accumulators of the previous pair
+          if (!mbar_wait(smem_u32(acc_empty), (uint32_t)((i - 1) & 1), err, 15)) {
+            *abort_flag = 1;
+            break;
+          }
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        bool ok = true;
+        for (int pr = 0; pr < nprod && ok; ++pr) {
+          for (int kb = 0; kb < nkb; ++kb, ++g) {
+            const int s = (int)(g % stages);
+            if (!mbar_wait(smem_u32(&full[s]), (uint32_t)(g / stages) & 1, err, 13) ||
+                *abort_flag) {
+              *abort_flag = 1;
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            uint8_t* st = smem + (size_t)s * stage_bytes;
+            const uint32_t a0 = smem_u32(st), b0 = smem_u32(st + a_bytes);
+#pragma unroll
+            for (int k = 0; k < BK / 16; ++k) {
+              const uint64_t bd = make_desc_sw128(b0 + k * 32);
+              const uint32_t acc = (pr > 0 || kb > 0 || k > 0) ? 1u : 0u;
+              const uint64_t ad0 = make_desc_sw128(a0 + k * 32);
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                  "l"(ad0), "l"(bd), "r"(idesc), "r"(acc));
+              if (two) {
+                const uint64_t ad1 = make_desc_sw128(a0 + A_BYTES + k * 32);
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                        tmem + (uint32_t)BN),
+                    "l"(ad1), "l"(bd), "r"(idesc), "r"(acc));
+              }
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_u32(&empty[s]))
+                : "memory");
+          }
+        }
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(acc_full))
+            : "memory");
+        if (!ok) break;
+      }
+    }
+  } else {
+    // epilogue: warp q reads TMEM lanes 32q .. 32q+31
+    const int q = warp;
+    const int nch = (NB + 31) / 32;
+    int64_t i = 0;
+    // The four warps meet at a named barrier twice per pair, so none of them
+    // leaves the loop early: after an abort they only skip the work (and the
+    // waits), and the barrier count stays the same in every warp.
+    bool dead = false;
+    for (int64_t w = blockIdx.x; w < npairs; w += gridDim.x, ++i) {
+      // the previous pair's phase 2 (reads of S) is complete in all four warps
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (!dead && *abort_flag) dead = true;
+      if (!dead) {
+        const bool ok = mbar_wait(smem_u32(acc_full), (uint32_t)(i & 1), err, 14);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!ok || *abort_flag) {
+          *abort_flag = 1;
+          dead = true;
+        }
+      }
+      // phase 1: upper triangle W[c][d], d > c, to shared memory
+      for (int h = 0; h <= two && !dead; ++h) {
+        const int cw = h * BM + q * 32;  // first row of this warp
+        const int c = cw + lane;
+        const int64_t base_c = (int64_t)c * (v - 1) - (int64_t)c * (c - 1) / 2;
+        for (int ch = 0; ch < nch; ++ch) {
+          if (ch * 32 + 31 <= cw || cw >= v) continue;  // warp-uniform: no d > c here
+          uint32_t r[32];
+          const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * BN + ch * 32);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+              "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, "
+              "[%32];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
+                "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+                "=r"(r[30]), "=r"(r[31])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (c < v) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int d = ch * 32 + j;
+              if (d > c && d < v) S[base_c + d] = __uint_as_float(r[j]);
+            }
+          }
+        }
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      // phase 2: lower triangle d <= c with the stored transpose; the pair's
+      // output rows
+      const int64_t row = w;
+      __nv_bfloat16* op = gp + row * out_ld;
+      __nv_bfloat16* om = gm + row * out_ld;
+      for (int h = 0; h <= two && !dead; ++h) {
+        const int cw = h * BM + q * 32;
+        const int c = cw + lane;
+        if (cw >= v) continue;
+        for (int ch = 0; ch < nch; ++ch) {
+          if (ch * 32 > cw + 31) break;  // warp-uniform: every d > every c
+          uint32_t r[32];
+          const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * BN + ch * 32);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+              "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, "
+              "[%32];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
+                "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+                "=r"(r[30]), "=r"(r[31])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (c < v) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int d = ch * 32 + j;
+              if (d > c) continue;
+              const float x = __uint_as_float(r[j]);
+              const int64_t qi = (int64_t)d * (v - 1) - (int64_t)d * (d - 1) / 2 + c;
+              float sp, sm;
+              if (d == c) {
+                sp = 2.0f * x;
+                sm = 0.0f;
+              } else {
+                const float u = S[qi];  // W[d][c]
+                sp = u + x;
+                sm = u - x;
+              }
+              const __nv_bfloat16 hp = __float2bfloat16(sp), hm = __float2bfloat16(sm);
+              op[qi] = hp;
+              om[qi] = hm;
+              if (nsl > 1) {
+                op[out_sstride + qi] = __float2bfloat16(sp - __bfloat162float(hp));
+                om[out_sstride + qi] = __float2bfloat16(sm - __bfloat162float(hm));
+              }
+            }
+          }
+        }
+      }
+      // both accumulators read: hand them back to the MMA issuer
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0 && !dead)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(acc_empty))
+                     : "memory");
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS));
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -549,8 +846,8 @@ bool TcGemm::worthwhile(int64_t nb, int64_t M, int64_t N, int64_t K) const {
   return nb == 1 && M >= 2 && N >= 2 && (double)M * N * K >= 1.0e6;
 }
 
-void TcGemm::convert(const MatView& X, int64_t rows, int64_t K, TcOperand& out) {
-  const int64_t rp = round_up(rows, BN), kp = round_up(K, BK);
+void TcGemm::convert(const MatView& X, int64_t rows, int64_t K, TcOperand& out, int64_t spare) {
+  const int64_t rp = round_up(rows + spare, BN), kp = round_up(K, BK);
   const size_t need = (size_t)rp * kp * 2 * nslices_;
   if (out.bytes < need) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -809,6 +1106,112 @@ void TcGemm::execute(const TcConfig& cfg, int64_t M, int64_t N, double alpha, co
   count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw CudaError(std::string("sum_splits: ") + cudaGetErrorString(e));
+}
+
+void TcGemm::alloc_operand(int64_t rows, int64_t k, int slices, TcOperand& out) {
+  const int64_t rp = round_up(std::max<int64_t>(rows, 1), BN), kp = round_up(std::max<int64_t>(k, 1), BK);
+  const size_t need = (size_t)rp * kp * 2 * slices;
+  if (out.bytes < need) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st_, &cs);
+    if (cs != cudaStreamCaptureStatusNone)
+      throw std::runtime_error("tensor-core buffer growth during graph capture (warm-up missing)");
+    if (out.data) {
+      cudaStreamSynchronize(st_);
+      cudaFree(out.data);
+      out.data = nullptr;
+      out.bytes = 0;
+    }
+    if (cudaMalloc(&out.data, need) != cudaSuccess) {
+      cudaGetLastError();
+      throw OomError("tensor-core operand buffer of " + std::to_string(need) + " bytes");
+    }
+    out.bytes = need;
+    // the K padding must read as zeros; the kernels never write it
+    if (cudaMemsetAsync(out.data, 0, need, st_) != cudaSuccess)
+      throw CudaError("tensor-core operand memset failed");
+  } else if (out.rows_pad != rp || out.k_pad != kp || out.slices != slices) {
+    if (cudaMemsetAsync(out.data, 0, need, st_) != cudaSuccess)
+      throw CudaError("tensor-core operand memset failed");
+  }
+  out.rows = rows;
+  out.k = k;
+  out.rows_pad = rp;
+  out.k_pad = kp;
+  out.slices = slices;
+}
+
+void TcGemm::prepare_ladder_lt(const double* L, int o, int v, int J, TcOperand& out) {
+  const int64_t n = (int64_t)o + v;
+  MatView X;  // element (r = p v + q, k = J) = L[J][o + p][o + q]
+  X.p = L + o * n + o;
+  X.n2r = v;
+  X.sr1 = n;
+  X.sr2 = 1;
+  X.sk2 = n * n;
+  convert(X, (int64_t)v * v, J, out, 256);
+  // the spare rows only feed accumulator rows and columns that are never
+  // read; zero them so that they hold no stale bits either
+  const int64_t used = (int64_t)v * v;
+  for (int s = 0; s < out.slices; ++s) {
+    char* base = (char*)out.data + ((size_t)s * out.rows_pad + used) * out.k_pad * 2;
+    const size_t len = (size_t)(out.rows_pad - used) * out.k_pad * 2;
+    if (cudaMemsetAsync(base, 0, len, st_) != cudaSuccess)
+      throw CudaError("ladder operand memset failed");
+  }
+}
+
+namespace {
+int ladder_nb(int v) { return (int)round_up(v, 16); }
+int ladder_stage_bytes(int v) { return A_BYTES * (v > BM ? 2 : 1) + ladder_nb(v) * BK * 2; }
+int ladder_tri_bytes(int v) { return (int)round_up((int64_t)v * (v + 1) / 2 * 4, 16); }
+constexpr int kSmemMax = 232448;  // dynamic shared memory a block may opt in to
+int ladder_stages(int v) {
+  const int room = kSmemMax - 1024 - 256 - ladder_tri_bytes(v);
+  return std::min(4, room / ladder_stage_bytes(v));
+}
+}  // namespace
+
+int TcGemm::ladder_build_max_v() {
+  int v = 2 * BM;
+  while (v > 1 && ladder_stages(v) < 2) --v;
+  return v;
+}
+
+void TcGemm::ladder_build(const TcOperand& Lt, int v, const int* pairs, int64_t p_begin,
+                          int64_t npairs, TcOperand& Gp, TcOperand& Gm) {
+  if (npairs <= 0) return;
+  if (v < 1 || v > ladder_build_max_v()) throw std::runtime_error("ladder build: v out of range");
+  const int NB = ladder_nb(v), two = v > BM ? 1 : 0;
+  const int stages = ladder_stages(v);
+  const int64_t Pv = (int64_t)v * (v + 1) / 2;
+  if (Lt.rows != (int64_t)v * v || Lt.rows_pad < Lt.rows + 256)
+    throw std::runtime_error("ladder build: Lt operand without its spare rows");
+  if (Gp.k != Pv || Gm.k != Pv || Gp.rows < npairs || Gm.rows < npairs ||
+      Gp.slices != Lt.slices || Gm.slices != Lt.slices || Gp.k_pad != Gm.k_pad ||
+      Gp.rows_pad != Gm.rows_pad)
+    throw std::runtime_error("ladder build: output operands of the wrong shape");
+  // one map over all slices of Lt (slice s starts at row s * rows_pad); box
+  // heights 128 (A: rows c) and NB (B: rows d)
+  CUtensorMap ma = make_map(Lt.data, (int64_t)Lt.slices * Lt.rows_pad, Lt.k_pad, BM);
+  CUtensorMap mb = make_map(Lt.data, (int64_t)Lt.slices * Lt.rows_pad, Lt.k_pad, NB);
+  const int smem = 1024 + stages * ladder_stage_bytes(v) + 256 + ladder_tri_bytes(v);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_ladder_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSmemMax);
+    if (e != cudaSuccess) throw CudaError(std::string("ladder build smem attribute: ") + cudaGetErrorString(e));
+    attr_set = true;
+  }
+  const int nprod = Lt.slices == 1 ? 1 : 3;
+  const int grid = (int)std::min<int64_t>(npairs, sm_count_);
+  k_ladder_build<<<grid, LB_THREADS, smem, st_>>>(
+      ma, mb, v, NB, two, (int)(Lt.k_pad / BK), nprod, Lt.rows_pad, stages, pairs, p_begin, npairs,
+      (__nv_bfloat16*)Gp.data, (__nv_bfloat16*)Gm.data, Gp.k_pad, Gp.rows_pad * Gp.k_pad,
+      Lt.slices, d_err_);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw CudaError(std::string("ladder build launch: ") + cudaGetErrorString(e));
 }
 
 void TcGemm::gemm(int64_t nb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,

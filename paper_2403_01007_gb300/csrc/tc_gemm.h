@@ -54,11 +54,25 @@ class TcGemm {
   // tuning off also frees the scratch output of the tuning runs
   void set_tune(bool on);
   void release(TcOperand& op);
+  // an operand of `rows` rows (K = k) in slice form, all zero; its rows are
+  // written later by a kernel (the ladder build below)
+  void alloc_operand(int64_t rows, int64_t k, int slices, TcOperand& out);
+  // Lt[(p, q)][J] = L^J_{o+p, o+q} (the virtual block of the Cholesky vectors,
+  // L [J][n][n]) in slice form, with 256 spare rows after the v^2 used ones so
+  // that the build kernel's tiles past the last row stay inside the buffer
+  void prepare_ladder_lt(const double* L, int o, int v, int J, TcOperand& out);
+  // largest v the fused ladder build handles (its shared-memory triangle)
+  static int ladder_build_max_v();
+  // G+ and G- rows of the pairs p_begin .. p_begin + npairs - 1 (pair table:
+  // a << 16 | b, a <= b) from Lt, as slices of Gp and Gm (rows 0 .. npairs-1,
+  // K = v (v + 1) / 2 packed (c <= d)); see k_ladder_build
+  void ladder_build(const TcOperand& Lt, int v, const int* pairs, int64_t p_begin,
+                    int64_t npairs, TcOperand& Gp, TcOperand& Gm);
   int slices() const { return nslices_; }
   void set_precision(int precision) { nslices_ = precision == 1 ? 2 : 1; }
 
  private:
-  void convert(const MatView& X, int64_t rows, int64_t K, TcOperand& out);
+  void convert(const MatView& X, int64_t rows, int64_t K, TcOperand& out, int64_t spare = 0);
   void run(const TcOperand& A, int sa, const TcOperand& B, int sb, int64_t M, int64_t N,
            double alpha, double* C, int64_t split_stride, const OutView& ov, bool accumulate,
            int splits, int kbs, int variant, int nfast);

@@ -171,6 +171,23 @@ class HostBackend : public Backend {
   void ladder(const Graph& g, const double* L, int64_t ver, const double* X, double* Y, int64_t rows) override {
     if (ver != Gver) { build_G(g, L); Gver = ver; }
     int v=g.v; int64_t vv=(int64_t)v*v;
+    {
+      // the device ladder packs X by its pair symmetry X_ij^cd = X_ji^dc; every
+      // operand the graph hands to the ladder must have it
+      const int o = g.o;
+      const int64_t oo = (int64_t)o * o, nb = rows / oo;
+      double big = 0.0, bad = 0.0;
+      for (int64_t z = 0; z < nb; ++z)
+        for (int i = 0; i < o; ++i) for (int j = 0; j < o; ++j)
+          for (int c = 0; c < v; ++c) for (int d = 0; d < v; ++d) {
+            const double x = X[((z * oo) + (int64_t)i * o + j) * vv + (int64_t)c * v + d];
+            const double y = X[((z * oo) + (int64_t)j * o + i) * vv + (int64_t)d * v + c];
+            big = std::max(big, std::fabs(x));
+            bad = std::max(bad, std::fabs(x - y));
+          }
+      if (bad > 1e-12 * std::max(1.0, big))
+        throw std::runtime_error("ladder operand without pair symmetry");
+    }
     if (prec != 0) {                      // the same BF16-slice emulation as gemm_tc_keyed
       std::vector<float> gs, xs;
       slices(vv, vv, [&](int64_t r, int64_t k) { return G[r * vv + k]; }, gs);
