@@ -434,6 +434,79 @@ def chain_case(args):
     return 0
 
 
+def solve_case(args):
+    """Converged solves at o=21 v=200 J=663 (or --workload): the ground state
+    (|Omega|_2 < solve_tol) and the lowest --nstates right EOM roots
+    (|A R - omega R| < state_tol), once in the mixed precision with FP64
+    refinement (defect correction of the amplitudes, FP64 anchors of the
+    Davidson subspace) and once in plain FP64, on the same inputs. Reports the
+    wall time of each arm (host clock around the synchronous calls), the
+    iteration and FP64-evaluation counts, and the differences of E_corr and of
+    every omega between the arms."""
+    import torch
+    from paper_2403_01007_gb300 import binding as B
+    torch.cuda.set_device(0)
+    w = getattr(syn, args.workload)
+    eps, L = syn.workload_system(w)
+    dev = torch.device("cuda", 0)
+    arms = [args.precision] + ([] if args.no_fp64_arm or args.precision == "fp64" else ["fp64"])
+    out = {}
+    for prec in arms:
+        logf = tempfile.TemporaryFile(mode="w+")
+        saved = os.dup(2)
+        os.dup2(logf.fileno(), 2)
+        os.environ["SCCSD_LOG"] = "1"
+        try:
+            ctx = B.Context(w.o, w.v, w.J, torch.tensor(eps, device=dev),
+                            torch.tensor(L, device=dev), precision=prec)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e, _, itg = ctx.solve_ground(tol=args.solve_tol, maxit=args.solve_maxit,
+                                         refine_tol=0.0 if prec == "fp64" else 1e-5)
+            t1 = time.perf_counter()
+            wk, _, its = ctx.solve_states(args.nstates, "right", tol=args.state_tol,
+                                          maxit=args.solve_maxit,
+                                          refine_tol=0.0 if prec == "fp64" else 1e-4, vecs=False)
+            t2 = time.perf_counter()
+            ctx.close()
+        finally:
+            os.environ.pop("SCCSD_LOG", None)
+            sys.stderr.flush()
+            os.dup2(saved, 2)
+            os.close(saved)
+        logf.seek(0)
+        done = {}
+        for line in logf:
+            if line.startswith("{") and ("_done" in line):
+                try:
+                    d = json.loads(line)
+                    done[d["solver"]] = d
+                except ValueError:
+                    pass
+        logf.close()
+        out[prec] = {"e_corr": e, "omega": [float(x) for x in wk], "ground_iterations": itg,
+                     "davidson_iterations": its, "ground_s": t1 - t0, "states_s": t2 - t1,
+                     "total_s": t2 - t0, "ground_refinement": done.get("ground_done"),
+                     "davidson_refinement": done.get("davidson_done")}
+    mixed = out[args.precision]
+    line = {"metric": f"time to converged ground state and {args.nstates} right roots, "
+                      f"{w.name}: mixed vs FP64 GPU",
+            "value": mixed["total_s"], "unit": "s", "higher_is_better": False,
+            "data": "synthetic",
+            "config": {"workload": w.name, "o": w.o, "v": w.v, "J": w.J, "nstates": args.nstates,
+                       "precision": args.precision, "ground_tol": args.solve_tol,
+                       "state_tol": args.state_tol, "refinement": "FP64 residuals"},
+            "arms": out}
+    if "fp64" in out and args.precision != "fp64":
+        ref = out["fp64"]
+        line["fp64_total_s"] = ref["total_s"]
+        line["time_to_solution_speedup"] = ref["total_s"] / mixed["total_s"]
+        line["abs_diff_e_corr"] = abs(mixed["e_corr"] - ref["e_corr"])
+        line["max_abs_diff_omega"] = max(abs(a - b) for a, b in zip(mixed["omega"], ref["omega"]))
+    print(json.dumps(line))
+    return 0
+
+
 def learned_case(args):
     """Learned guess and preconditioner, reduced form of the C5 workload: train
     on solver-generated amplitudes of n_train systems at o=8, v=60, then solve
@@ -518,7 +591,15 @@ def main():
                          "fixed rule, then tune and time again)")
     ap.add_argument("--batched", action="store_true",
                     help="64 uneven instances: joined CUDA graph vs per-instance calls")
+    ap.add_argument("--solve", action="store_true",
+                    help="converged ground state and right roots, mixed (refined) vs FP64")
+    ap.add_argument("--nstates", type=int, default=6)
+    ap.add_argument("--solve-tol", type=float, default=1e-8)
+    ap.add_argument("--state-tol", type=float, default=1e-6)
+    ap.add_argument("--solve-maxit", type=int, default=400)
     args = ap.parse_args()
+    if args.solve and args.impl == "ours":
+        return solve_case(args)
     if args.batched and args.impl == "ours":
         return batched_case(args)
     if args.learned and args.impl == "ours":

@@ -1,6 +1,7 @@
 // CUDA backend of the graph executor: FP64 kernels for strided copies,
 // packing, reductions and contractions, plus dispatch of tensor-core
 // eligible contractions to the tcgen05 path.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -273,10 +274,31 @@ __global__ void k_sum_parts(int64_t n, int splits, const double* __restrict__ pa
 // a (a - 1) / 2 + b for a <= b (likewise q(c, d) and the occupied pairs).
 
 // X~+[(z, i<=j)][q] and X-[(z, i<j)][q] from X[(z, i, j)][(c, d)]; with the
-// pair symmetry X_ij^dc is read as X_ji^cd, so both reads walk d
+// pair symmetry X_ij^dc is read as X_ji^cd, so both reads walk d. Written as
+// FP64 rows of stride ld, or (Out = __nv_bfloat16) as `nsl` BF16 slices of a
+// tensor-core operand (rows of stride ld, slices sstride apart; x = sum of the
+// slices, each the BF16 rounding of what the previous ones left).
+template <class Out>
+__device__ __forceinline__ void put_val(Out* p, int64_t i, double x, int nsl, int64_t sstride);
+template <>
+__device__ __forceinline__ void put_val<double>(double* p, int64_t i, double x, int, int64_t) {
+  p[i] = x;
+}
+template <>
+__device__ __forceinline__ void put_val<__nv_bfloat16>(__nv_bfloat16* p, int64_t i, double x,
+                                                       int nsl, int64_t sstride) {
+  for (int s = 0; s < nsl; ++s) {
+    const __nv_bfloat16 b = __double2bfloat16(x);
+    p[s * sstride + i] = b;
+    x -= (double)__bfloat162float(b);
+  }
+}
+
+template <class Out>
 __global__ void k_ladder_pack_x(const double* __restrict__ X, int o, int v, int64_t nb,
-                                const int* __restrict__ pairs, double* __restrict__ Xp,
-                                double* __restrict__ Xm, int64_t ld) {
+                                const int* __restrict__ pairs, Out* __restrict__ Xp,
+                                Out* __restrict__ Xm, int64_t ld, int nsl, int64_t sp_stride,
+                                int64_t sm_stride) {
   const int64_t Po = (int64_t)o * (o + 1) / 2, Pm = (int64_t)o * (o - 1) / 2;
   const int64_t Pv = (int64_t)v * (v + 1) / 2, vv = (int64_t)v * v;
   for (int64_t blk = blockIdx.x; blk < nb * Po; blk += gridDim.x) {
@@ -289,16 +311,16 @@ __global__ void k_ladder_pack_x(const double* __restrict__ X, int o, int v, int6
     const int j = i + r;
     const double* xij = X + ((z * o + i) * o + j) * vv;
     const double* xji = X + ((z * o + j) * o + i) * vv;
-    double* op = Xp + blk * ld;
-    double* om = i < j ? Xm + (z * Pm + (int64_t)i * (o - 1) - (int64_t)i * (i - 1) / 2 + (j - i - 1)) * ld
-                       : nullptr;
+    Out* op = Xp + blk * ld;
+    Out* om = i < j ? Xm + (z * Pm + (int64_t)i * (o - 1) - (int64_t)i * (i - 1) / 2 + (j - i - 1)) * ld
+                    : nullptr;
     for (int64_t q = threadIdx.x; q < Pv; q += blockDim.x) {
       const int cd = __ldg(pairs + q);
       const int c = cd >> 16, d = cd & 0xffff;
       const int64_t e = (int64_t)c * v + d;
       const double a = xij[e], b = xji[e];
-      op[q] = c == d ? 0.5 * (a + b) : a + b;
-      if (om) om[q] = c == d ? 0.0 : a - b;
+      put_val<Out>(op, q, c == d ? 0.5 * (a + b) : a + b, nsl, sp_stride);
+      if (om) put_val<Out>(om, q, c == d ? 0.0 : a - b, nsl, sm_stride);
     }
   }
 }
@@ -856,17 +878,27 @@ class CudaBackend : public Backend {
       CK(cudaEventCreate(&e1));
       CK(cudaEventRecord(e0, st));
     }
-    // packed operands X~+, X- (FP64) and the results P, M [rows][Pv]
-    double* Xp = scratch(0, np * Pv);
-    double* Xm = scratch(1, std::max<int64_t>(1, nm) * Pv);
+    // packed operands X~+, X- (FP64, or BF16 slices of tensor-core operands in
+    // a mixed mode) and the results P, M [rows][Pv]
+    double* Xp = nullptr;
+    double* Xm = nullptr;
     double* Pr = scratch(2, np * Pv);
     double* Mr = scratch(3, std::max<int64_t>(1, nm) * Pv);
-    k_ladder_pack_x<<<grid_for(np * 256, 256), 256, 0, st>>>(X, o, v, nb, pairs, Xp, Xm, Pv);
-    check_launch("ladder_pack_x");
     if (mixed) {
-      tc->prepare_operand(Xp, np, Pv, xp_op);
-      if (nm > 0) tc->prepare_operand(Xm, nm, Pv, xm_op);
+      const int nsl = tc->slices();
+      tc->alloc_operand(np, Pv, nsl, xp_op);
+      tc->alloc_operand(std::max<int64_t>(1, nm), Pv, nsl, xm_op);
+      xm_op.rows = nm;
+      k_ladder_pack_x<__nv_bfloat16><<<grid_for(np * 256, 256), 256, 0, st>>>(
+          X, o, v, nb, pairs, (__nv_bfloat16*)xp_op.data, (__nv_bfloat16*)xm_op.data, xp_op.k_pad,
+          nsl, xp_op.rows_pad * xp_op.k_pad, xm_op.rows_pad * xm_op.k_pad);
+    } else {
+      Xp = scratch(0, np * Pv);
+      Xm = scratch(1, std::max<int64_t>(1, nm) * Pv);
+      k_ladder_pack_x<double><<<grid_for(np * 256, 256), 256, 0, st>>>(X, o, v, nb, pairs, Xp, Xm,
+                                                                      Pv, 1, 0, 0);
     }
+    check_launch("ladder_pack_x");
     if (mixed && v <= TcGemm::ladder_build_max_v()) {
       // fused build on the tensor cores, one chunk of pairs at a time
       if (lt_version != ver || lt_src != L || lt_slices != tc->slices()) {

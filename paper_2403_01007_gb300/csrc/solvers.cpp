@@ -125,6 +125,7 @@ int sccsd_solve_ground(sccsd_ctx* c, const double* t0, double zeta, const double
     double* Dp = solver_buf(c, 7, dim);
     double* fdg = solver_buf(c, 8, c->o + c->v);
     bool have_dp = false;
+    int refine_fp64_evals = 0, inner_its = 0;
     int next_refresh = 3;
     for (it = 1; it <= maxit; ++it) {
       E = eval_residual(c, t, zeta, ra, rb, om);
@@ -141,7 +142,74 @@ int sccsd_solve_ground(sccsd_ctx* c, const double* t0, double zeta, const double
       }
       // the mixed phase ends below refine_tol, or when it stalls at its noise floor
       if (!fp64_phase && (nrm < refine_tol || since_best >= 6)) {
-        // mixed-precision phase done: refine in FP64 from the current amplitudes
+        // Iterative refinement (defect correction): the FP64 residual
+        // r = Omega(t) drives a correction solve A d = -r with the mixed
+        // Jacobian (its error scales with d, not with t), t <- t + d. Each
+        // round gains about the mixed arithmetic's relative accuracy, so a
+        // few FP64 residuals replace the FP64 iteration tail. When a round
+        // gains less than 3x, the remaining iterations run in FP64.
+        const double* Dpre = have_dp ? Dp : (c->use_dprec ? c->Dprec : c->D);
+        double* dl = solver_buf(c, 9, dim);
+        double* Ad = solver_buf(c, 19, dim);
+        double* rr = solver_buf(c, 20, dim);
+        const double inner_rtol = p0 == SCCSD_BF16X3 ? 1e-4 : 1e-2;
+        double prev = 1e300;
+        bool done = false;
+        for (int round = 0; round < 12 && !done; ++round) {
+          switch_precision(c, SCCSD_FP64);
+          E = eval_residual(c, t, zeta, ra, rb, rr);
+          const double rn = std::sqrt(d.dot(rr, rr, dim));
+          switch_precision(c, p0);
+          ++refine_fp64_evals;
+          if (getenv("SCCSD_LOG"))
+            fprintf(stderr, "{\"solver\": \"ground_refine\", \"round\": %d, \"fp64_residual\": %.3e, \"e_corr\": %.12f}\n",
+                    round, rn, E - c->e_hf);
+          if (!std::isfinite(rn)) throw std::runtime_error("ground state diverged (non-finite residual)");
+          nrm = rn;
+          if (rn < tol) {
+            done = true;
+            break;
+          }
+          if (rn > prev / 3.0) break;  // not gaining: finish in FP64
+          prev = rn;
+          // the mixed state at t for the Jacobian transforms
+          eval_residual(c, t, zeta, ra, rb, om);
+          // A d = -r by the Jacobi-preconditioned linear iteration with DIIS
+          c->be->fill(dl, dim, 0.0);
+          int lh = 0, lhead = 0;
+          const double goal = std::max(inner_rtol * rn, 0.3 * tol);
+          for (int k = 0; k < 300; ++k) {
+            transform(c, 0, 1, dl, Ad);
+            d.axpby(dim, 1.0, rr, 1.0, Ad);      // rho = A d + r
+            const double rho = std::sqrt(d.dot(Ad, Ad, dim));
+            ++inner_its;
+            if (!std::isfinite(rho)) throw std::runtime_error("correction solve diverged");
+            if (rho < goal) break;
+            launch_jacobi(d.st(), dim, dl, Ad, Dpre, tn);   // tn = d - rho / D
+            const int sl = lhead;
+            lhead = (lhead + 1) % kDiis;
+            lh = std::min(lh + 1, kDiis);
+            d.copy(X + (int64_t)sl * dim, tn, dim);
+            d.copy(Rr + (int64_t)sl * dim, tn, dim);
+            d.axpby(dim, -1.0, dl, 1.0, Rr + (int64_t)sl * dim);
+            if (lh >= 2) {
+              c->be->gemm_tn(1, lh, lh, dim, 1.0, Rr, Rr, Bm, false);
+              launch_diis(d.st(), lh, Bm, cf, c->sv_info);
+              int info = 0;
+              cudaMemcpyAsync(&info, c->sv_info, sizeof(int), cudaMemcpyDeviceToHost, d.st());
+              c->be->sync();
+              if (info == 0)
+                d.combine(1, lh, cf, X, dl);
+              else
+                d.copy(dl, tn, dim);
+            } else {
+              d.copy(dl, tn, dim);
+            }
+          }
+          d.axpby(dim, 1.0, dl, 1.0, t);
+        }
+        if (done) break;
+        // FP64 iterations from the current amplitudes
         switch_precision(c, SCCSD_FP64);
         fp64_phase = true;
         nh = 0;
@@ -191,6 +259,9 @@ int sccsd_solve_ground(sccsd_ctx* c, const double* t0, double zeta, const double
       }
     }
     if (it > maxit) status = SCCSD_ENOTCONV;
+    if (getenv("SCCSD_LOG") && refine)
+      fprintf(stderr, "{\"solver\": \"ground_done\", \"iterations\": %d, \"fp64_refine_residuals\": %d, \"correction_transforms\": %d, \"fp64_phase\": %d}\n",
+              std::min(it, maxit), refine_fp64_evals, inner_its, (int)fp64_phase);
     if (refine) switch_precision(c, p0);
     if (refine) eval_residual(c, t, zeta, ra, rb, om);  // fix the state for later transforms
     if (t_out) c->be->download(t_out, t, dim, c->be->is_device(t_out));
@@ -330,11 +401,35 @@ int sccsd_solve_states(sccsd_ctx* c, int nroots, int side, double tol, int maxit
     const int p0 = c->be->get_precision();
     const bool refine = p0 != SCCSD_FP64 && refine_tol > 0.0;
     bool fp64_phase = !refine;
+    bool pure = false;   // every image in the subspace is an FP64 transform
+    int anchors = 0;
     std::vector<double> lam(nroots), res(nroots);
-    int it = 0;
-    bool converged = false;
     double best = 1e300;
     int since_best = 0;
+    auto anchor = [&]() {
+      // V = orthonormalised current Ritz vectors, W = their FP64 images
+      have_prev = false;
+      d.copy(V, Xr, (int64_t)nroots * dim);
+      m = 0;
+      for (int k = 0; k < nroots; ++k) {
+        double* vk = V + (int64_t)m * dim;
+        if (k != m) d.copy(vk, Xr + (int64_t)k * dim, dim);
+        orthogonalize(vk, nullptr, m);
+        double nn = std::sqrt(d.dot(vk, vk, dim));
+        if (nn < 1e-10) continue;
+        d.axpby(dim, 0.0, vk, 1.0 / nn, vk);
+        ++m;
+      }
+      switch_precision(c, SCCSD_FP64);
+      transform(c, side, m, V, W);
+      switch_precision(c, p0);
+      pure = true;
+      ++anchors;
+      best = 1e300;
+      since_best = 0;
+    };
+    int it = 0;
+    bool converged = false;
     for (it = 1; it <= maxit; ++it) {
       // subspace matrix and its lowest roots
       c->be->gemm_tn(1, m, m, dim, 1.0, V, W, S, false);
@@ -374,28 +469,28 @@ int sccsd_solve_states(sccsd_ctx* c, int nroots, int side, double tol, int maxit
       } else {
         ++since_best;
       }
+      // Refinement with FP64 anchors: when the mixed iterations reach
+      // refine_tol (or stall), the subspace restarts from the Ritz vectors
+      // with their FP64 images; the expansion vectors that follow are
+      // transformed in the mixed precision, whose error then scales with the
+      // size of the corrections, not of the roots. Convergence is accepted
+      // only on a subspace of FP64 images alone (after a fresh anchor).
       if (!fp64_phase && (worst < refine_tol || since_best >= 8)) {
-        // restart in FP64 from the current Ritz vectors
-        switch_precision(c, SCCSD_FP64);
         fp64_phase = true;
-        have_prev = false;
-        d.copy(V, Xr, (int64_t)nroots * dim);
-        m = 0;
-        for (int k = 0; k < nroots; ++k) {
-          double* vk = V + (int64_t)m * dim;
-          if (k != m) d.copy(vk, Xr + (int64_t)k * dim, dim);
-          orthogonalize(vk, nullptr, m);
-          double nn = std::sqrt(d.dot(vk, vk, dim));
-          if (nn < 1e-10) continue;
-          d.axpby(dim, 0.0, vk, 1.0 / nn, vk);
-          ++m;
-        }
-        transform(c, side, m, V, W);
+        anchor();
         continue;
       }
       if (fp64_phase && worst < tol) {
-        converged = true;
-        break;
+        if (!refine || pure) {
+          converged = true;
+          break;
+        }
+        anchor();   // verify: residuals of FP64 images only
+        continue;
+      }
+      if (refine && fp64_phase && since_best >= 8) {
+        anchor();   // the mixed corrections stalled: new FP64 anchor
+        continue;
       }
       // preconditioned residuals of the unconverged roots
       std::vector<int> want;
@@ -445,9 +540,13 @@ int sccsd_solve_states(sccsd_ctx* c, int nroots, int side, double tol, int maxit
       }
       if (added == 0) throw std::runtime_error("Davidson subspace stagnated");
       transform(c, side, added, V + (int64_t)m * dim, W + (int64_t)m * dim);
+      if (refine) pure = false;
       m += added;
     }
     if (!converged) status = SCCSD_ENOTCONV;
+    if (getenv("SCCSD_LOG") && refine)
+      fprintf(stderr, "{\"solver\": \"davidson_done\", \"iterations\": %d, \"fp64_anchors\": %d}\n",
+              std::min(it, maxit), anchors);
     if (refine) switch_precision(c, p0);
     for (int k = 0; k < nroots; ++k) omega[k] = lam[k];
     if (vecs) {

@@ -52,6 +52,28 @@ def test_eom_states_small(small):
 
 
 @pytest.mark.parametrize("precision", ["bf16", "bf16x3"])
+def test_mixed_refinement_small_against_oracle(small, precision):
+    """o=5 v=19: the mixed-precision ground state and 3 right/left roots,
+    refined by FP64 residuals (defect correction for the amplitudes, FP64
+    anchors for the Davidson subspace), equal the FP64 oracle: E_corr and
+    every omega within 1e-8 Eh (Sec. 2.1 equations solved to the tolerance)."""
+    B, w, eps, L, prob, x, ecorr = small
+    ctx = B.Context(w.o, w.v, w.J, eps, L, precision=precision)
+    e, t, _ = ctx.solve_ground(tol=1e-10, maxit=300, refine_tol=1e-4)
+    assert abs(e - ecorr) < 1e-8
+    assert np.abs(t - x).max() < 1e-8
+    wo, _ = sv.eom(prob, x, 3, side="right", tol=1e-9)
+    for side in ("right", "left"):
+        wk, V, _ = ctx.solve_states(3, side, tol=1e-8, maxit=400, refine_tol=1e-4)
+        assert np.abs(wk - wo).max() < 1e-8, side
+        op = rp.jacobian_right if side == "right" else rp.jacobian_left
+        for k in range(3):
+            r = op(prob, x, V[k]).numpy() - wk[k] * V[k]
+            assert np.linalg.norm(r) < 1e-7
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", ["bf16", "bf16x3"])
 def test_mixed_precision_refinement_medium(precision):
     """o=10 v=90 J=300: the mixed-precision solvers, refined in FP64 at the
     end, reproduce the FP64 GPU results to 1e-8 Eh (energy and roots)."""
