@@ -56,6 +56,69 @@ def ladder_flops_packed(o, v):
     return 2.0 * (Po * Pv ** 2 + o * (o - 1) / 2 * (v * (v - 1) / 2) ** 2)
 
 
+def ladder_flops_algorithmic(o, v, J, nvec):
+    """Algorithmic flops of one ladder call of nvec vectors (scope table): the
+    (ac) <-> (bd) symmetric build v^2 (v^2 + 1) / 2 . 2J plus the packed
+    contraction per vector."""
+    vv = v * v
+    return vv * (vv + 1) / 2 * 2.0 * J + nvec * ladder_flops_packed(o, v)
+
+
+def ladder_flops_executed(o, v, J, nvec, precision):
+    """Flops the tensor-core kernels execute for one ladder call: the build
+    runs one 128-row MMA tile per half (two halves when v > 128) of N = v
+    rounded up to 16 over J rounded up to 64, for every pair a <= b, with 1 or 3
+    slice products; the contraction runs 128 x 256 tiles over K = v(v+1)/2
+    rounded up to 64, for the + rows (nvec o(o+1)/2) and the - rows
+    (nvec o(o-1)/2), with 1 or 3 slice products."""
+    import math
+    prod = 3 if precision == "bf16x3" else 1
+    Pv = v * (v + 1) // 2
+    halves = 2 if v > 128 else 1
+    nb = 16 * math.ceil(v / 16)
+    jp = 64 * math.ceil(J / 64)
+    build = Pv * halves * 128 * nb * jp * 2.0 * prod
+    kp = 64 * math.ceil(Pv / 64)
+    npl, nmi = nvec * o * (o + 1) // 2, nvec * o * (o - 1) // 2
+    rows = 128 * (math.ceil(npl / 128) + math.ceil(nmi / 128))
+    contract = rows * 256 * math.ceil(Pv / 256) * kp * 2.0 * prod
+    return build + contract
+
+
+# DRAM bytes of one o=21 v=200 6-vector BF16 ladder call: the sum over its
+# launches (build, contractions, packing) of dram__bytes_read.sum +
+# dram__bytes_write.sum from the ncu capture summarised in
+# profiles/ladder_o21_v200_bf16.md; None until that capture matches the kernels
+LADDER_TRAFFIC_O21_V200 = None
+
+
+def ladder_traffic(w, args):
+    if (w.o, w.v, w.J) == (21, 200, 663) and args.nvec == 6 and args.precision == "bf16":
+        return LADDER_TRAFFIC_O21_V200
+    return None
+
+
+def fp64_peak(torch):
+    """Measured FP64 GEMM rate of this GPU (cuBLAS DGEMM 8192^3, best of 3):
+    the ceiling of the FP64 path, whose contractions run on the CUDA cores."""
+    n = 8192
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    del a, b
+    return 2.0 * n ** 3 / best / 1e12, "cuBLAS DGEMM 8192^3 measured in this run (best of 3)"
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -133,47 +196,70 @@ def dist_env():
     return replicas.rank_env()
 
 
-def cpu_oracle_sample(steps=1, warmup=0):
-    """Time the FP64 CPU oracle on one o=10, v=90, J=300 right transformation
-    per step; return (transforms/s scaled to o=21 v=200, seconds per sample)."""
+def _mem_available_gb():
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) / 1e6
+    except OSError:
+        pass
+    return 0.0
+
+
+# host memory the oracle's o=21 v=200 transformation needs (peak RSS measured
+# at 56 GB: the full vvvv integrals, their tangent and the einsum temporaries)
+ORACLE_LARGE_GB = 70.0
+
+
+def cpu_oracle_sample():
+    """Time the FP64 CPU oracle (as it stands, all host threads) on one right
+    transformation A R of the benchmark's workload, o=21 v=200 J=663; return
+    (transforms/s, seconds, threads, sample text). If the host lacks the memory
+    for it, one transformation of o=10 v=90 J=300 is timed instead and scaled
+    by the dense-flop ratio, and the text says so."""
     import torch
     from oracle import ccsd as cc
     from oracle import response as rp
-    w = syn.MEDIUM
+    big = (_mem_available_gb() >= ORACLE_LARGE_GB
+           and os.environ.get("SCCSD_ORACLE_SAMPLE", "") != "small")
+    w = syn.LARGE if big else syn.MEDIUM
     eps, L = syn.workload_system(w)
     prob = cc.Problem(eps, L, w.o)
-    t = syn.random_vectors(w.o, w.v, 1, 5, scale=1e-3)[0]
-    R = syn.random_vectors(w.o, w.v, 1, 6, normalise=True)[0]
-    for _ in range(warmup):
-        rp.jacobian_right(prob, t, R)
-    times = []
-    for _ in range(max(1, steps)):
-        t0 = time.perf_counter()
-        rp.jacobian_right(prob, t, R)
-        times.append(time.perf_counter() - t0)
-    sec = statistics.median(times)
+    t = syn.random_vectors(w.o, w.v, 1, syn.seed_of(w.config, 50), scale=1e-3)[0]
+    R = syn.random_vectors(w.o, w.v, 1, syn.seed_of(w.config, 60), normalise=True)[0]
+    t0 = time.perf_counter()
+    rp.jacobian_right(prob, t, R)
+    sec = time.perf_counter() - t0
+    threads = torch.get_num_threads()
+    if big:
+        return 1.0 / sec, sec, threads, (
+            f"one A R of the FP64 CPU oracle at o=21 v=200 J=663 ({sec:.1f} s, {threads} threads)")
     ratio = transform_flops(syn.LARGE.o, syn.LARGE.v) / transform_flops(w.o, w.v)
-    return 1.0 / (sec * ratio), sec, torch.get_num_threads()
+    return 1.0 / (sec * ratio), sec, threads, (
+        f"host memory below {ORACLE_LARGE_GB:.0f} GB: one A R of the FP64 CPU oracle at o=10 v=90 "
+        f"J=300 ({sec:.2f} s, {threads} threads), scaled by the dense-flop ratio to o=21 v=200")
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle timed on the host cores. One step
+    is one oracle transformation of the o=21 v=200 workload (a few minutes on
+    16 cores), so a single step is timed whatever --steps says."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     t0 = time.perf_counter()
-    val, sec, threads = cpu_oracle_sample(steps=args.steps, warmup=args.warmup)
+    val, sec, threads, sample = cpu_oracle_sample()
     wall = time.perf_counter() - t0
-    sample = (f"FP64 CPU oracle, one A R transformation of o=10 v=90 J=300 per step "
-              f"({sec:.2f} s), scaled by the dense-flop ratio to o=21 v=200 J=663")
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": "transforms/s",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "timed_steps": 1,
         "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": syn.LARGE.name, "o": syn.LARGE.o, "v": syn.LARGE.v,
-                   "J": syn.LARGE.J, "nvec": args.nvec, "precision": args.precision,
+                   "J": syn.LARGE.J, "nvec": 1, "precision": "fp64",
                    "parallelism": "replicas1",
-                   "l2": "inputs larger than L2 (ladder integrals alone exceed 129 MB)"},
+                   "l2": "inputs larger than L2 (the vvvv integrals alone are 12.8 GB)"},
         "cpu_baseline": {"value": val, "unit": "transforms/s", "cores": threads,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": "transforms/s", "h2d_bytes_per_step": 0,
@@ -694,10 +780,12 @@ def main():
         sig_fp64 = s64
         rel = float(np.abs(sig_mixed - s64).max() / np.abs(s64).max())
         t64 = args.fp64_steps * args.nvec / (ms64 / 1e3)
+        p64, p64_src = fp64_peak(torch)
         fp64 = {"transforms_per_s": t64, "ms_per_step": ms64 / args.fp64_steps,
                 "warmup": 1, "steps": args.fp64_steps,
                 "mixed_speedup": value / world / t64,
-                "max_rel_diff_mixed_vs_fp64": rel}
+                "max_rel_diff_mixed_vs_fp64": rel,
+                "fp64_gemm_peak_tflops": p64, "fp64_peak_source": p64_src}
 
     # the 3-product split arm (BF16x3) on the same inputs
     x3 = None
@@ -734,33 +822,38 @@ def main():
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0:
-        val, sec, threads = cpu_oracle_sample(steps=5)
+        val, sec, threads, sample = cpu_oracle_sample()
         cpu = {"value": val, "unit": "transforms/s", "cores": threads, "kind": "oracle",
-               "sample": f"five A R of the FP64 CPU oracle at o=10 v=90 J=300 (median {sec:.2f} s "
-                         f"each), scaled by the dense-flop ratio to o=21 v=200 J=663"}
+               "sample": sample}
 
-    peak = peaks.get("bf16_tflops_sustained", 1700.0)
-    slices = {"bf16x3": 3, "bf16": 1, "fp64": 1}[args.precision]
-    achieved = lad_flops / (lad_ms / 1e3) / 1e12 if lad_ms > 0 else None
-    # the kernel executes the dense ladder; the packed form needs fewer flops
-    packed_ratio = ladder_flops_packed(w.o, w.v) / ladder_flops_dense(w.o, w.v)
-    achieved_packed = achieved * packed_ratio if achieved else None
+    # Roofline of the particle-particle ladder, one call = one batch of nvec
+    # vectors: the algorithmic flops of the scope table (the (ac) <-> (bd)
+    # symmetric build of the integrals from the Cholesky vectors plus the
+    # +- packed contraction), over the device time of the whole call (build,
+    # contraction, packing) from CUDA events on the context's stream, against
+    # the measured BF16 burst peak (the ladder runs for milliseconds inside a
+    # step of tens of milliseconds). The executed count (padded tiles, BF16x3
+    # slice products) is a secondary key.
+    burst = peaks.get("bf16_tflops", 1900.0)
+    calls = max(lad_calls, 1)
+    lad_call_ms = lad_ms / calls
+    alg_call = lad_flops / calls
+    exe_call = ladder_flops_executed(w.o, w.v, w.J, args.nvec, args.precision)
+    achieved = alg_call / (lad_call_ms / 1e3) / 1e12 if lad_ms > 0 else None
     if args.precision == "fp64":
-        roof = {"bound": "alu", "achieved": achieved, "peak": 1.2, "unit": "TFLOP/s",
-                "frac": achieved / 1.2 if achieved else None, "traffic": None,
-                "kernel": "k_dgemm_tn (ladder)", "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s), rounded down to 1.2"}
+        p64, p64_src = fp64_peak(torch)
+        roof = {"bound": "alu", "achieved": achieved, "peak": p64, "unit": "TFLOP/s",
+                "frac": achieved / p64 if achieved and p64 else None, "traffic": None,
+                "kernel": "ladder (FP64 build and contraction on the CUDA cores), one call",
+                "peak_source": p64_src}
     else:
-        # DRAM bytes of one full-size ladder launch (6 x o^2 rows, N = K = v^2) from a 1-pass
-        # ncu capture (profiles/k_tc_gemm_ladder.md)
-        traffic = 9.19e9 if (w.o, w.v) == (21, 200) and args.nvec == 6 else None
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if achieved else None, "traffic": traffic,
-                "kernel": "k_tc_gemm (ladder)", "peak_source": f"bf16 sustained, {peak_src}",
-                "executed_tflops": achieved * slices if achieved else None,
-                "algorithmic_tflops": achieved_packed,
-                "algorithmic_frac": achieved_packed / peak if achieved_packed else None,
-                "flops_per_vector": {"executed_dense": ladder_flops_dense(w.o, w.v),
-                                     "algorithmic_packed": ladder_flops_packed(w.o, w.v)},
+        roof = {"bound": "tensor", "achieved": achieved, "peak": burst, "unit": "TFLOP/s",
+                "frac": achieved / burst if achieved else None,
+                "traffic": ladder_traffic(w, args),
+                "kernel": "ladder: k_ladder_build + k_tc_gemm contraction + pack/unpack, one call",
+                "peak_source": f"bf16 burst, {peak_src}",
+                "flops_per_call": {"algorithmic": alg_call, "executed": exe_call},
+                "executed_tflops": exe_call / (lad_call_ms / 1e3) / 1e12 if lad_ms > 0 else None,
                 "ladder_share_of_step": lad_ms / ms if ms > 0 else None}
     line = {
         "metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": world,
@@ -773,8 +866,9 @@ def main():
                    "l2": "inputs larger than L2 (ladder integrals alone exceed 129 MB)"},
         "roofline": roof,
         "autotune": tuning,
-        "ladder": {"ms_per_call": lad_ms / max(lad_calls, 1), "calls": lad_calls,
-                   "tflops_executed": achieved, "tflops_algorithmic": achieved_packed},
+        "ladder": {"ms_per_call": lad_call_ms, "calls": lad_calls,
+                   "tflops_algorithmic": achieved,
+                   "tflops_executed": roof.get("executed_tflops")},
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": e2e,

@@ -116,13 +116,15 @@ int sccsd_gemm_tn(int precision, long long M, long long N, long long K, double a
 
 /* Profiling (instrumentation of this library; the paper has no counterpart).
  * sccsd_profile(ctx, 1) resets the counters and starts timing
- * every particle-particle ladder contraction (o^2 v^4 part) with CUDA events
- * on the context's stream; 0 stops it. sccsd_profile_read returns the summed
- * ladder time in ms, the number of ladder contractions, their algorithmic
- * flop count (2 o^2 v^4 per trial vector; trial vectors are batched up to 8
- * per contraction) and the number of kernels this library
- * launched since the reset (any output may be NULL). Timing adds one stream
- * synchronisation per read. */
+ * every particle-particle ladder call (the vvvv integrals built from the
+ * Cholesky vectors, packing, contraction) with CUDA events on the context's
+ * stream; 0 stops it. sccsd_profile_read returns the summed ladder time in ms,
+ * the number of ladder calls, their algorithmic flop count (the (ac) <-> (bd)
+ * symmetric build v^2 (v^2 + 1) / 2 . 2J per call plus the +- packed
+ * contraction 2 [P_o P_v^2 + o(o-1)/2 (v(v-1)/2)^2] per trial vector, P_x =
+ * x(x+1)/2; trial vectors are batched up to 8 per call) and the number of
+ * kernels this library launched since the reset (any output may be NULL).
+ * Timing adds one stream synchronisation per read. */
 int sccsd_profile(sccsd_ctx* ctx, int enable);
 int sccsd_profile_read(sccsd_ctx* ctx, double* ladder_ms, long long* ladder_calls,
                        double* ladder_flops, long long* launches);
@@ -243,8 +245,13 @@ long long sccsd_autotune_entries(void);
  * t0 (packed ket) or from zero (whose first step is the MP2 guess). With a mixed precision and
  * refine_tol > 0 the iterations run in that precision until |Omega| <
  * refine_tol, or until they stall (no 10% improvement in 6 iterations: the
- * noise floor of the mixed arithmetic), and finish in FP64 (iterative
- * refinement); the FP64 residual then decides convergence (|Omega|_2 < tol). Outputs (each may be NULL):
+ * noise floor of the mixed arithmetic), and are then refined by defect
+ * correction: the FP64 residual r = Omega(t) is formed, A d = -r is solved
+ * with the mixed-precision Jacobian (Jacobi preconditioner with DIIS, to 1e-4
+ * of |r| for SCCSD_BF16X3 and 1e-2 for SCCSD_BF16), and t <- t + d; each round
+ * gains about the mixed arithmetic's relative accuracy. A round that gains
+ * less than 3x hands the remaining iterations to FP64. The FP64 residual
+ * decides convergence (|Omega|_2 < tol). Outputs (each may be NULL):
  * t_out (packed), e_corr, iterations. The converged state is fixed for the
  * Jacobian and density calls. SCCSD_ENOTCONV when maxit is reached (outputs
  * hold the last iterate). */
@@ -259,9 +266,12 @@ int sccsd_solve_ground(sccsd_ctx* ctx, const double* t0, double zeta, const doub
  * dressed one-body intermediates (f_a - f_i for singles, f_a + f_b - f_i - f_j
  * for doubles); restarts keep the current and previous Ritz vectors. The
  * subspace eigenproblem and all vector work run on the device. Convergence: |A x - omega x| / |x| < tol for every
- * root. Mixed precisions refine in FP64 once every residual is below
- * refine_tol or the residuals stall for 8 iterations (refine_tol <= 0: no
- * refinement). Outputs: omega[nroots],
+ * root. Mixed precisions refine once every residual is below refine_tol or the
+ * residuals stall for 8 iterations (refine_tol <= 0: no refinement): the
+ * subspace restarts from the Ritz vectors with their FP64 images (an FP64
+ * anchor), later expansion vectors are transformed in the mixed precision
+ * (their error scales with the corrections), and convergence is accepted
+ * only on a subspace of FP64 images alone, i.e. after a fresh anchor. Outputs: omega[nroots],
  * vecs[nroots][dim] (unit-norm packed vectors, may be NULL), iterations.
  * The subspace holds min(48, dim) vectors and needs room for 2 nroots + 2,
  * else SCCSD_EINVAL.

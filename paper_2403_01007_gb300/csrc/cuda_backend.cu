@@ -325,29 +325,79 @@ __global__ void k_ladder_pack_x(const double* __restrict__ X, int o, int v, int6
   }
 }
 
-// Y[(z, i, j)][(a, b)] from P[(z, i<=j)][p] and M[(z, i<j)][p]
-__global__ void k_ladder_unpack(const double* __restrict__ P, const double* __restrict__ M,
-                                int64_t ld, int o, int v, int64_t nb, double* __restrict__ Y) {
-  const int64_t oo = (int64_t)o * o, vv = (int64_t)v * v;
+// Y[(z, i, j)][(a, b)] from P[(z, i<=j)][p] and M[(z, i<j)][p]. A block takes
+// one occupied pair i0 <= j0 and one 32 x 32 tile of (a, b) with a-tile <=
+// b-tile: it reads the P and M entries of the tile once (b fastest), and
+// writes Y_i0j0^ab = P + M, Y_j0i0^ab = P - M and, through shared memory, the
+// transposed elements Y_i0j0^ba = P - M, Y_j0i0^ba = P + M (a fastest), so that
+// every read and write walks consecutive addresses.
+constexpr int UT = 32;  // unpack tile edge
+
+__global__ void __launch_bounds__(256) k_ladder_unpack(const double* __restrict__ P,
+                                                       const double* __restrict__ M, int64_t ld,
+                                                       int o, int v, int64_t nb,
+                                                       double* __restrict__ Y) {
+  __shared__ double tp[UT][UT + 1], tm[UT][UT + 1];
+  const int64_t vv = (int64_t)v * v, oo = (int64_t)o * o;
   const int64_t Po = (int64_t)o * (o + 1) / 2, Pm = (int64_t)o * (o - 1) / 2;
-  for (int64_t row = blockIdx.x; row < nb * oo; row += gridDim.x) {
-    const int64_t z = row / oo;
-    const int i = (int)((row / o) % o), j = (int)(row % o);
-    const int i0 = i < j ? i : j, j0 = i < j ? j : i;
-    const double* pr = P + (z * Po + (int64_t)i0 * (o - 1) - (int64_t)i0 * (i0 - 1) / 2 + j0) * ld;
+  const int nt = (v + UT - 1) / UT;
+  const int64_t tiles = (int64_t)nt * (nt + 1) / 2;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  for (int64_t blk = blockIdx.x; blk < nb * Po * tiles; blk += gridDim.x) {
+    const int64_t rowp = blk / tiles;
+    int t = (int)(blk % tiles), ta = 0;
+    while (t >= nt - ta) {
+      t -= nt - ta;
+      ++ta;
+    }
+    const int tb = ta + t;
+    const int64_t z = rowp / Po;
+    int r = (int)(rowp % Po), i0 = 0;
+    while (r >= o - i0) {
+      r -= o - i0;
+      ++i0;
+    }
+    const int j0 = i0 + r;
+    const double* pr = P + rowp * ld;
     const double* mr =
         i0 < j0 ? M + (z * Pm + (int64_t)i0 * (o - 1) - (int64_t)i0 * (i0 - 1) / 2 + (j0 - i0 - 1)) * ld
                 : nullptr;
-    const double sij = i <= j ? 1.0 : -1.0;
-    double* y = Y + row * vv;
-    for (int64_t e = threadIdx.x; e < vv; e += blockDim.x) {
-      const int a = (int)(e / v), b = (int)(e % v);
-      const int a0 = a < b ? a : b, b0 = a < b ? b : a;
-      const int64_t p = (int64_t)a0 * (v - 1) - (int64_t)a0 * (a0 - 1) / 2 + b0;
-      double val = pr[p];
-      if (mr && a0 < b0) val += (a <= b ? sij : -sij) * mr[p];
-      y[e] = val;
+    double* y1 = Y + ((z * o + i0) * o + j0) * vv;   // row (i0, j0)
+    double* y2 = Y + ((z * o + j0) * o + i0) * vv;   // row (j0, i0)
+    const int a0 = ta * UT, b0 = tb * UT;
+    // load the tile's P and M entries (a <= b), b fastest
+    for (int k = ty; k < UT; k += 8) {
+      const int a = a0 + k, b = b0 + tx;
+      double pv = 0.0, mv = 0.0;
+      if (a < v && b < v) {
+        const int lo = a < b ? a : b, hi = a < b ? b : a;
+        const int64_t p = (int64_t)lo * (v - 1) - (int64_t)lo * (lo - 1) / 2 + hi;
+        pv = pr[p];
+        if (mr && lo < hi) mv = (a <= b ? 1.0 : -1.0) * mr[p];
+      }
+      tp[k][tx] = pv;
+      tm[k][tx] = mv;
     }
+    __syncthreads();
+    // direct elements (a, b): Y_i0j0 = P + M, Y_j0i0 = P - M
+    for (int k = ty; k < UT; k += 8) {
+      const int a = a0 + k, b = b0 + tx;
+      if (a < v && b < v && (ta < tb || a <= b)) {
+        const int64_t e = (int64_t)a * v + b;
+        y1[e] = tp[k][tx] + tm[k][tx];
+        if (i0 < j0) y2[e] = tp[k][tx] - tm[k][tx];
+      }
+    }
+    // transposed elements (b, a) of the tile, a fastest: Y_i0j0 = P - M, Y_j0i0 = P + M
+    for (int k = ty; k < UT; k += 8) {
+      const int b = b0 + k, a = a0 + tx;
+      if (a < v && b < v && (ta < tb || a < b)) {
+        const int64_t e = (int64_t)b * v + a;
+        y1[e] = tp[tx][k] - tm[tx][k];
+        if (i0 < j0) y2[e] = tp[tx][k] + tm[tx][k];
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -981,7 +1031,11 @@ class CudaBackend : public Backend {
         a0 = a1;
       }
     }
-    k_ladder_unpack<<<grid_for(nb * oo * 256, 256), 256, 0, st>>>(Pr, Mr, Pv, o, v, nb, Y);
+    {
+      const int64_t ntl = (v + UT - 1) / UT;
+      k_ladder_unpack<<<grid_for(np * ntl * (ntl + 1) / 2 * 256, 256), 256, 0, st>>>(Pr, Mr, Pv, o,
+                                                                                      v, nb, Y);
+    }
     check_launch("ladder_unpack");
     if (prof) {
       CK(cudaEventRecord(e1, st));

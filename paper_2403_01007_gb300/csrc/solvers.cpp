@@ -152,14 +152,17 @@ int sccsd_solve_ground(sccsd_ctx* c, const double* t0, double zeta, const double
         double* dl = solver_buf(c, 9, dim);
         double* Ad = solver_buf(c, 19, dim);
         double* rr = solver_buf(c, 20, dim);
-        const double inner_rtol = p0 == SCCSD_BF16X3 ? 1e-4 : 1e-2;
+        // the correction solves start in the context's precision and move up
+        // to the split BF16 form when a round gains too little
+        int pc = p0;
+        double inner_rtol = pc == SCCSD_BF16X3 ? 1e-4 : 1e-2;
         double prev = 1e300;
         bool done = false;
         for (int round = 0; round < 12 && !done; ++round) {
           switch_precision(c, SCCSD_FP64);
           E = eval_residual(c, t, zeta, ra, rb, rr);
           const double rn = std::sqrt(d.dot(rr, rr, dim));
-          switch_precision(c, p0);
+          switch_precision(c, pc);
           ++refine_fp64_evals;
           if (getenv("SCCSD_LOG"))
             fprintf(stderr, "{\"solver\": \"ground_refine\", \"round\": %d, \"fp64_residual\": %.3e, \"e_corr\": %.12f}\n",
@@ -170,8 +173,17 @@ int sccsd_solve_ground(sccsd_ctx* c, const double* t0, double zeta, const double
             done = true;
             break;
           }
-          if (rn > prev / 3.0) break;  // not gaining: finish in FP64
-          prev = rn;
+          if (rn > prev / 3.0) {
+            if (pc == SCCSD_BF16) {
+              // not gaining in BF16: the next corrections in the split form
+              pc = SCCSD_BF16X3;
+              inner_rtol = 1e-4;
+              switch_precision(c, pc);
+            } else {
+              break;  // not gaining: finish in FP64
+            }
+          }
+          prev = std::min(prev, rn);
           // the mixed state at t for the Jacobian transforms
           eval_residual(c, t, zeta, ra, rb, om);
           // A d = -r by the Jacobi-preconditioned linear iteration with DIIS
@@ -403,6 +415,7 @@ int sccsd_solve_states(sccsd_ctx* c, int nroots, int side, double tol, int maxit
     bool fp64_phase = !refine;
     bool pure = false;   // every image in the subspace is an FP64 transform
     int anchors = 0;
+    int pc = p0;         // precision of the expansion transforms after an anchor
     std::vector<double> lam(nroots), res(nroots);
     double best = 1e300;
     int since_best = 0;
@@ -422,9 +435,13 @@ int sccsd_solve_states(sccsd_ctx* c, int nroots, int side, double tol, int maxit
       }
       switch_precision(c, SCCSD_FP64);
       transform(c, side, m, V, W);
-      switch_precision(c, p0);
-      pure = true;
       ++anchors;
+      // repeated anchors mean the expansions are too inexact: split BF16
+      // after four, FP64 after eight
+      if (anchors >= 8) pc = SCCSD_FP64;
+      else if (anchors >= 4 && pc == SCCSD_BF16) pc = SCCSD_BF16X3;
+      switch_precision(c, pc);
+      pure = true;
       best = 1e300;
       since_best = 0;
     };
@@ -540,7 +557,7 @@ int sccsd_solve_states(sccsd_ctx* c, int nroots, int side, double tol, int maxit
       }
       if (added == 0) throw std::runtime_error("Davidson subspace stagnated");
       transform(c, side, added, V + (int64_t)m * dim, W + (int64_t)m * dim);
-      if (refine) pure = false;
+      if (refine && pc != SCCSD_FP64) pure = false;
       m += added;
     }
     if (!converged) status = SCCSD_ENOTCONV;

@@ -490,22 +490,48 @@ __global__ void k_sum_splits(int64_t M, int64_t N, int splits, const double* __r
 // for c <= d (q the packed index c*v - c(c-1)/2 + d - c) as BF16 slices of two
 // K-major operands of the contraction kernel above. The symmetric and
 // antisymmetric combinations halve the contraction twice over (pairs a <= b
-// and c <= d), and W[d][c] comes from the same accumulator, so each g_acbd is
-// computed once per unordered pair (ac) <-> (bd) ... up to the diagonal blocks.
+// and c <= d), and W[d][c] comes from the same block, so each g_acbd is
+// computed once per unordered pair (ac) <-> (bd), up to the diagonal blocks.
+// Rows c < 128 and c >= 128 (v > 128) are two halves with their own TMEM
+// accumulators (columns 0 .. and 256 ..), computed one after the other, so
+// that the epilogue of one half overlaps the MMAs of the next.
 // Warp roles:
-//   warp 4    : TMA producer; one stage = A rows a*v .. a*v+127 (and, for
-//               v > 128, a*v+128 .. a*v+255) and B rows b*v .. b*v+NB-1 of one
-//               64-wide K block; slice products (0,0), (0,1), (1,0) in turn
-//   warp 5    : one elected thread issues the MMAs into accumulator 0 (rows
-//               c < 128, TMEM columns 0 ..) and 1 (rows c >= 128, columns
-//               256 ..), N = NB = v rounded up to 16
-//   warps 0-3 : epilogue; thread t owns TMEM lane t, i.e. rows c = t and
-//               c = 128 + t. Phase 1 writes the upper triangle W[c][d], d > c,
-//               to shared memory (FP32); phase 2 takes the lower triangle from
-//               TMEM, forms the two combinations with the stored transpose and
-//               stores them (consecutive lanes write consecutive q).
-// Every mbarrier wait is bounded as in k_tc_gemm.
-constexpr int LB_THREADS = 192;
+//   warp 8    : TMA producer; one stage = A rows a*v + 128 h .. + 127 and B
+//               rows b*v .. b*v + NB - 1 of one 64-wide K block; slice
+//               products (0,0), (0,1), (1,0) in turn
+//   warp 9    : one elected thread issues the MMAs of each half into its
+//               accumulator, N = NB = v rounded up to 16
+//   warps 0-7 : epilogue; warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows c)
+//               and the column chunks of parity w / 4. Phase 1 writes the
+//               upper triangle W[c][d], d > c, to shared memory (FP32); phase
+//               2 takes the lower triangle from TMEM, forms both combinations
+//               with the stored transpose and packs them in place as BF16
+//               pairs (the second slice, when there is one, goes straight to
+//               global memory); once both halves are done the packed
+//               triangle is streamed out with 16-byte loads and 8-byte
+//               stores, while the MMAs of the next pair already run.
+// Every mbarrier wait is bounded as in k_tc_gemm; the epilogue warps meet at
+// named barriers on every path, so an abort never leaves one of them waiting.
+constexpr int LB_EPI = 8;                      // epilogue warps
+constexpr int LB_THREADS = (LB_EPI + 2) * 32;
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+      "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, "
+      "[%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void epi_bar() {
+  asm volatile("bar.sync 1, %0;" ::"n"(LB_EPI * 32) : "memory");
+}
 
 __global__ void __launch_bounds__(LB_THREADS, 1)
     k_ladder_build(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -515,15 +541,18 @@ __global__ void __launch_bounds__(LB_THREADS, 1)
                    int64_t out_ld, int64_t out_sstride, int nsl, int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const int a_bytes = A_BYTES * (two ? 2 : 1);
-  const int stage_bytes = a_bytes + NB * BK * 2;
+  const int stage_bytes = A_BYTES + NB * BK * 2;
   uint64_t* full = (uint64_t*)(smem + stages * stage_bytes);
   uint64_t* empty = full + stages;
-  uint64_t* acc_full = empty + stages;
-  uint64_t* acc_empty = acc_full + 1;
-  uint32_t* tmem_slot = (uint32_t*)(acc_empty + 1);
+  uint64_t* acc_full = empty + stages;   // [2], one per half
+  uint64_t* acc_empty = acc_full + 2;    // [2]
+  uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   float* S = (float*)(smem + stages * stage_bytes + 256);
+  uint32_t* Su = (uint32_t*)S;
+  const int64_t Pv = (int64_t)v * (v + 1) / 2;
+  const int64_t P4 = (Pv + 3) / 4;
+  const int H = two ? 2 : 1;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -531,11 +560,16 @@ __global__ void __launch_bounds__(LB_THREADS, 1)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
     }
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(acc_full)));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(acc_empty)));
+    for (int h = 0; h < 2; ++h) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&acc_full[h])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acc_empty[h])),
+                   "n"(LB_EPI));
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  // the padding of the last group of four entries reads as zero in phase 3
+  if (threadIdx.x < 4 && Pv + threadIdx.x < 4 * P4) Su[Pv + threadIdx.x] = 0u;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
@@ -547,7 +581,7 @@ __global__ void __launch_bounds__(LB_THREADS, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 4) {
+  if (warp == LB_EPI) {
     if (lane == 0) {
       int64_t issued_last[8];
       for (int s = 0; s < 8; ++s) issued_last[s] = -1;
@@ -555,41 +589,38 @@ __global__ void __launch_bounds__(LB_THREADS, 1)
       for (int64_t w = blockIdx.x; w < npairs && !*abort_flag; w += gridDim.x) {
         const int ab = __ldg(pairs + p_begin + w);
         const int a = ab >> 16, b = ab & 0xffff;
-        for (int pr = 0; pr < nprod && !*abort_flag; ++pr) {
-          const int sa = pr == 2 ? 1 : 0, sb = pr == 1 ? 1 : 0;
-          const int ra = (int)(sa * slice_rows) + a * v, rb = (int)(sb * slice_rows) + b * v;
-          for (int kb = 0; kb < nkb; ++kb, ++g) {
-            const int s = (int)(g % stages);
-            if (g >= stages) {
-              if (!mbar_wait(smem_u32(&empty[s]), (uint32_t)((g / stages) - 1) & 1, err, 11)) {
-                *abort_flag = 1;
-                break;
+        for (int h = 0; h < H && !*abort_flag; ++h) {
+          for (int pr = 0; pr < nprod && !*abort_flag; ++pr) {
+            const int sa = pr == 2 ? 1 : 0, sb = pr == 1 ? 1 : 0;
+            const int ra = (int)(sa * slice_rows) + a * v + h * BM;
+            const int rb = (int)(sb * slice_rows) + b * v;
+            for (int kb = 0; kb < nkb; ++kb, ++g) {
+              const int s = (int)(g % stages);
+              if (g >= stages) {
+                if (!mbar_wait(smem_u32(&empty[s]), (uint32_t)((g / stages) - 1) & 1, err, 11)) {
+                  *abort_flag = 1;
+                  break;
+                }
               }
-            }
-            if (*abort_flag) break;
-            const uint32_t fb = smem_u32(&full[s]);
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
-                         "r"(stage_bytes)
-                         : "memory");
-            uint8_t* st = smem + (size_t)s * stage_bytes;
-            const int x = kb * BK;
-            asm volatile(
-                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-                " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(st)),
-                "l"((uint64_t)&tmA), "r"(fb), "r"(x), "r"(ra)
-                : "memory");
-            if (two)
+              if (*abort_flag) break;
+              const uint32_t fb = smem_u32(&full[s]);
+              asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                           "r"(stage_bytes)
+                           : "memory");
+              uint8_t* st = smem + (size_t)s * stage_bytes;
+              const int x = kb * BK;
+              asm volatile(
+                  "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                  " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(st)),
+                  "l"((uint64_t)&tmA), "r"(fb), "r"(x), "r"(ra)
+                  : "memory");
               asm volatile(
                   "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
                   " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(st + A_BYTES)),
-                  "l"((uint64_t)&tmA), "r"(fb), "r"(x), "r"(ra + BM)
+                  "l"((uint64_t)&tmB), "r"(fb), "r"(x), "r"(rb)
                   : "memory");
-            asm volatile(
-                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-                " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(st + a_bytes)),
-                "l"((uint64_t)&tmB), "r"(fb), "r"(x), "r"(rb)
-                : "memory");
-            issued_last[s] = g;
+              issued_last[s] = g;
+            }
           }
         }
       }
@@ -597,173 +628,155 @@ __global__ void __launch_bounds__(LB_THREADS, 1)
         if (issued_last[s] >= 0)
           mbar_wait(smem_u32(&full[s]), (uint32_t)(issued_last[s] / stages) & 1, err, 12);
     }
-  } else if (warp == 5) {
+  } else if (warp == LB_EPI + 1) {
     if (lane == 0) {
       const uint32_t idesc = make_idesc(BM, NB);
       int64_t g = 0, i = 0;
-      for (int64_t w = blockIdx.x; w < npairs && !*abort_flag; w += gridDim.x, ++i) {
-        if (i >= 1) {
-          // the epilogue has read both accumulators of the previous pair
-          if (!mbar_wait(smem_u32(acc_empty), (uint32_t)((i - 1) & 1), err, 15)) {
-            *abort_flag = 1;
-            break;
-          }
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        bool ok = true;
-        for (int pr = 0; pr < nprod && ok; ++pr) {
-          for (int kb = 0; kb < nkb; ++kb, ++g) {
-            const int s = (int)(g % stages);
-            if (!mbar_wait(smem_u32(&full[s]), (uint32_t)(g / stages) & 1, err, 13) ||
-                *abort_flag) {
+      bool ok = true;
+      for (int64_t w = blockIdx.x; w < npairs && ok && !*abort_flag; w += gridDim.x, ++i) {
+        for (int h = 0; h < H && ok; ++h) {
+          if (i >= 1) {
+            // the epilogue has read this half's accumulator of the previous pair
+            if (!mbar_wait(smem_u32(&acc_empty[h]), (uint32_t)((i - 1) & 1), err, 15)) {
               *abort_flag = 1;
               ok = false;
               break;
             }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            uint8_t* st = smem + (size_t)s * stage_bytes;
-            const uint32_t a0 = smem_u32(st), b0 = smem_u32(st + a_bytes);
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t dst = tmem + (uint32_t)(h * BN);
+          for (int pr = 0; pr < nprod && ok; ++pr) {
+            for (int kb = 0; kb < nkb; ++kb, ++g) {
+              const int s = (int)(g % stages);
+              if (!mbar_wait(smem_u32(&full[s]), (uint32_t)(g / stages) & 1, err, 13) ||
+                  *abort_flag) {
+                *abort_flag = 1;
+                ok = false;
+                break;
+              }
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+              uint8_t* st = smem + (size_t)s * stage_bytes;
+              const uint32_t a0 = smem_u32(st), b0 = smem_u32(st + A_BYTES);
 #pragma unroll
-            for (int k = 0; k < BK / 16; ++k) {
-              const uint64_t bd = make_desc_sw128(b0 + k * 32);
-              const uint32_t acc = (pr > 0 || kb > 0 || k > 0) ? 1u : 0u;
-              const uint64_t ad0 = make_desc_sw128(a0 + k * 32);
-              asm volatile(
-                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                  "l"(ad0), "l"(bd), "r"(idesc), "r"(acc));
-              if (two) {
-                const uint64_t ad1 = make_desc_sw128(a0 + A_BYTES + k * 32);
+              for (int k = 0; k < BK / 16; ++k) {
+                const uint64_t ad = make_desc_sw128(a0 + k * 32);
+                const uint64_t bd = make_desc_sw128(b0 + k * 32);
+                const uint32_t acc = (pr > 0 || kb > 0 || k > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                        tmem + (uint32_t)BN),
-                    "l"(ad1), "l"(bd), "r"(idesc), "r"(acc));
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dst),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
               }
+              asm volatile(
+                  "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                      smem_u32(&empty[s]))
+                  : "memory");
             }
-            asm volatile(
-                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    smem_u32(&empty[s]))
-                : "memory");
           }
+          // this half's accumulator is ready (or the pipeline was abandoned)
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                  smem_u32(&acc_full[h]))
+              : "memory");
         }
-        asm volatile(
-            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(acc_full))
-            : "memory");
-        if (!ok) break;
       }
     }
   } else {
-    // epilogue: warp q reads TMEM lanes 32q .. 32q+31
-    const int q = warp;
+    // epilogue warp: TMEM lanes 32 q .. 32 q + 31, column chunks ch = cg, cg + 2, ...
+    const int q = warp & 3, cg = warp >> 2;
     const int nch = (NB + 31) / 32;
     int64_t i = 0;
-    // The four warps meet at a named barrier twice per pair, so none of them
-    // leaves the loop early: after an abort they only skip the work (and the
-    // waits), and the barrier count stays the same in every warp.
     bool dead = false;
     for (int64_t w = blockIdx.x; w < npairs; w += gridDim.x, ++i) {
-      // the previous pair's phase 2 (reads of S) is complete in all four warps
-      asm volatile("bar.sync 1, 128;" ::: "memory");
+      // the previous pair's phase 3 (reads of S) is complete in every warp
+      epi_bar();
       if (!dead && *abort_flag) dead = true;
-      if (!dead) {
-        const bool ok = mbar_wait(smem_u32(acc_full), (uint32_t)(i & 1), err, 14);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (!ok || *abort_flag) {
-          *abort_flag = 1;
-          dead = true;
+      __nv_bfloat16* op = gp + w * out_ld;
+      __nv_bfloat16* om = gm + w * out_ld;
+      for (int h = 0; h < H; ++h) {
+        if (!dead) {
+          const bool ok = mbar_wait(smem_u32(&acc_full[h]), (uint32_t)(i & 1), err, 14);
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          if (!ok || *abort_flag) {
+            *abort_flag = 1;
+            dead = true;
+          }
         }
-      }
-      // phase 1: upper triangle W[c][d], d > c, to shared memory
-      for (int h = 0; h <= two && !dead; ++h) {
         const int cw = h * BM + q * 32;  // first row of this warp
         const int c = cw + lane;
-        const int64_t base_c = (int64_t)c * (v - 1) - (int64_t)c * (c - 1) / 2;
-        for (int ch = 0; ch < nch; ++ch) {
-          if (ch * 32 + 31 <= cw || cw >= v) continue;  // warp-uniform: no d > c here
-          uint32_t r[32];
-          const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * BN + ch * 32);
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
-              "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, "
-              "[%32];"
-              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-                "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
-                "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-                "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
-                "=r"(r[30]), "=r"(r[31])
-              : "r"(taddr));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          if (c < v) {
+        const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * BN);
+        // phase 1: upper triangle W[c][d], d > c, to shared memory
+        if (!dead && cw < v) {
+          const int64_t base_c = (int64_t)c * (v - 1) - (int64_t)c * (c - 1) / 2;
+          for (int ch = cg; ch < nch; ch += 2) {
+            if (ch * 32 + 31 <= cw) continue;  // warp-uniform: no d > c here
+            uint32_t r[32];
+            tmem_ld32(tbase + (uint32_t)(ch * 32), r);
+            if (c < v) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int d = ch * 32 + j;
-              if (d > c && d < v) S[base_c + d] = __uint_as_float(r[j]);
-            }
-          }
-        }
-      }
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      // phase 2: lower triangle d <= c with the stored transpose; the pair's
-      // output rows
-      const int64_t row = w;
-      __nv_bfloat16* op = gp + row * out_ld;
-      __nv_bfloat16* om = gm + row * out_ld;
-      for (int h = 0; h <= two && !dead; ++h) {
-        const int cw = h * BM + q * 32;
-        const int c = cw + lane;
-        if (cw >= v) continue;
-        for (int ch = 0; ch < nch; ++ch) {
-          if (ch * 32 > cw + 31) break;  // warp-uniform: every d > every c
-          uint32_t r[32];
-          const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * BN + ch * 32);
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
-              "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, "
-              "[%32];"
-              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-                "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
-                "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-                "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
-                "=r"(r[30]), "=r"(r[31])
-              : "r"(taddr));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          if (c < v) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int d = ch * 32 + j;
-              if (d > c) continue;
-              const float x = __uint_as_float(r[j]);
-              const int64_t qi = (int64_t)d * (v - 1) - (int64_t)d * (d - 1) / 2 + c;
-              float sp, sm;
-              if (d == c) {
-                sp = 2.0f * x;
-                sm = 0.0f;
-              } else {
-                const float u = S[qi];  // W[d][c]
-                sp = u + x;
-                sm = u - x;
-              }
-              const __nv_bfloat16 hp = __float2bfloat16(sp), hm = __float2bfloat16(sm);
-              op[qi] = hp;
-              om[qi] = hm;
-              if (nsl > 1) {
-                op[out_sstride + qi] = __float2bfloat16(sp - __bfloat162float(hp));
-                om[out_sstride + qi] = __float2bfloat16(sm - __bfloat162float(hm));
+              for (int j = 0; j < 32; ++j) {
+                const int d = ch * 32 + j;
+                if (d > c && d < v) S[base_c + d] = __uint_as_float(r[j]);
               }
             }
           }
         }
+        epi_bar();
+        // phase 2: lower triangle d <= c with the stored transpose, packed in place
+        if (!dead && cw < v) {
+          for (int ch = cg; ch < nch; ch += 2) {
+            if (ch * 32 > cw + 31) continue;  // warp-uniform: every d > every c
+            uint32_t r[32];
+            tmem_ld32(tbase + (uint32_t)(ch * 32), r);
+            if (c < v) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j) {
+                const int d = ch * 32 + j;
+                if (d > c) continue;
+                const float x = __uint_as_float(r[j]);
+                const int64_t qi = (int64_t)d * (v - 1) - (int64_t)d * (d - 1) / 2 + c;
+                float sp, sm;
+                if (d == c) {
+                  sp = 2.0f * x;
+                  sm = 0.0f;
+                } else {
+                  const float u = S[qi];  // W[d][c]
+                  sp = u + x;
+                  sm = u - x;
+                }
+                const __nv_bfloat16 hp = __float2bfloat16(sp), hm = __float2bfloat16(sm);
+                Su[qi] = (uint32_t)__bfloat16_as_ushort(hp) |
+                         ((uint32_t)__bfloat16_as_ushort(hm) << 16);
+                if (nsl > 1) {
+                  op[out_sstride + qi] = __float2bfloat16(sp - __bfloat162float(hp));
+                  om[out_sstride + qi] = __float2bfloat16(sm - __bfloat162float(hm));
+                }
+              }
+            }
+          }
+        }
+        // this half's accumulator is read: hand it back to the MMA issuer
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0 && !dead)
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[h]))
+                       : "memory");
       }
-      // both accumulators read: hand them back to the MMA issuer
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0 && !dead)
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(acc_empty))
-                     : "memory");
+      // phase 3: the packed triangle to the pair's two rows
+      epi_bar();
+      if (!dead) {
+        const uint4* S4 = (const uint4*)Su;
+        for (int64_t g4 = threadIdx.x; g4 < P4; g4 += LB_EPI * 32) {
+          const uint4 e = S4[g4];
+          uint2 pp, mm;
+          pp.x = (e.x & 0xffffu) | (e.y << 16);
+          pp.y = (e.z & 0xffffu) | (e.w << 16);
+          mm.x = (e.x >> 16) | (e.y & 0xffff0000u);
+          mm.y = (e.z >> 16) | (e.w & 0xffff0000u);
+          *(uint2*)(op + 4 * g4) = pp;
+          *(uint2*)(om + 4 * g4) = mm;
+        }
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1163,12 +1176,12 @@ void TcGemm::prepare_ladder_lt(const double* L, int o, int v, int J, TcOperand& 
 
 namespace {
 int ladder_nb(int v) { return (int)round_up(v, 16); }
-int ladder_stage_bytes(int v) { return A_BYTES * (v > BM ? 2 : 1) + ladder_nb(v) * BK * 2; }
-int ladder_tri_bytes(int v) { return (int)round_up((int64_t)v * (v + 1) / 2 * 4, 16); }
+int ladder_stage_bytes(int v) { return A_BYTES + ladder_nb(v) * BK * 2; }
+int ladder_tri_bytes(int v) { return (int)round_up((int64_t)v * (v + 1) / 2, 4) * 4; }
 constexpr int kSmemMax = 232448;  // dynamic shared memory a block may opt in to
 int ladder_stages(int v) {
   const int room = kSmemMax - 1024 - 256 - ladder_tri_bytes(v);
-  return std::min(4, room / ladder_stage_bytes(v));
+  return std::min(6, room / ladder_stage_bytes(v));
 }
 }  // namespace
 

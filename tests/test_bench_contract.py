@@ -11,6 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _run(env_extra):
     env = dict(os.environ)
     env.update(env_extra)
+    env["SCCSD_ORACLE_SAMPLE"] = "small"   # the o=21 v=200 sample needs ~60 GB and minutes
     return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
                            "--steps", "1", "--warmup", "0"],
                           capture_output=True, text=True, env=env, cwd=ROOT, timeout=600)
@@ -56,3 +57,17 @@ def test_ladder_flop_counts():
                 for b in range(a + 1, v) for c in range(v) for d in range(c + 1, v))
     assert bench.ladder_flops_packed(o, v) == 2.0 * (plus + minus)
     assert bench.ladder_flops_dense(o, v) == 2.0 * o * o * v ** 4
+
+
+def test_ladder_call_flop_counts():
+    """One 6-vector ladder call at o=21 v=200 J=663: the scope table's
+    algorithmic count (symmetric build 1.06e12 plus 6 packed contractions of
+    3.53e11) and the executed count of the kernels' padded tiles, which is
+    larger but within 1.5x."""
+    sys.path.insert(0, ROOT)
+    import bench
+    alg = bench.ladder_flops_algorithmic(21, 200, 663, 6)
+    assert abs(alg / (1.0607e12 + 6 * 3.5298e11) - 1.0) < 2e-3
+    exe = bench.ladder_flops_executed(21, 200, 663, 6, "bf16")
+    assert alg < exe < 1.5 * alg
+    assert bench.ladder_flops_executed(21, 200, 663, 6, "bf16x3") == 3 * exe
