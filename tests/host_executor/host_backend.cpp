@@ -14,6 +14,7 @@
 #include <set>
 #include <vector>
 #include <cstdio>
+#include <cstdlib>
 #include <stdexcept>
 #include <cuda_runtime.h>
 #include "../../paper_2403_01007_gb300/csrc/backend.h"
@@ -31,7 +32,20 @@ class HostBackend : public Backend {
   void download(double* d, const double* s, int64_t n, bool) override { std::memmove(d, s, n*8); }
   void fill(double* p, int64_t n, double v) override { for (int64_t i=0;i<n;++i) p[i]=v; }
   bool is_device(const void* p) override { return mine.count(p) > 0; }
-  void sync() override {}
+  // Stand-in for an expired bounded wait in a tensor-core kernel: the device
+  // backend reads the kernel's error flag at a synchronisation and throws this
+  // CudaError. SCCSD_HOST_FAKE_WAIT_EXPIRY=k makes the k-th synchronisation
+  // after it is set (counting from 0) report it once.
+  long long fake_syncs = 0;
+  void sync() override {
+    const char* e = getenv("SCCSD_HOST_FAKE_WAIT_EXPIRY");
+    if (!e) {
+      fake_syncs = 0;
+      return;
+    }
+    if (fake_syncs++ == atoll(e))
+      throw CudaError("tensor-core pipeline wait expired (code 3)");
+  }
   void unpack(const double* x, int o, int v, double* t1, double* t2, bool bra) override {
     int64_t ov = (int64_t)o*v;
     for (int64_t k=0;k<ov;++k) t1[k]=x[k];

@@ -554,6 +554,36 @@ def test_davidson_through_the_c_abi(host_lib, side):
     ctx.close()
 
 
+def test_expired_device_wait_maps_to_ecuda_and_the_context_recovers(host_lib):
+    """An expired bounded wait in a tensor-core kernel is recorded in the
+    kernel's error flag and raised by the backend at the next synchronisation
+    (the device kernels never trap). The C ABI reports it as SCCSD_ECUDA with
+    the wait text in sccsd_last_error, and the context stays usable: the next
+    call gives the oracle's result. The expiry is injected on the host (the
+    test double raises the backend's error at a chosen synchronisation)."""
+    B, lib = host_lib
+    o, v, J = 2, 3, 6
+    eps, L = syn.system(o, v, J, 0.3, 4)
+    prob = cc.Problem(eps, L, o)
+    x = syn.random_vectors(o, v, 1, 5, scale=0.1)[0]
+    R = syn.random_vectors(o, v, 2, 6, normalise=True)
+    ctx = B.Context(o, v, J, eps, L, lib=lib)
+    ctx.residual(x)
+    os.environ["SCCSD_HOST_FAKE_WAIT_EXPIRY"] = "0"
+    try:
+        with pytest.raises(B.SccsdError) as ei:
+            ctx.jacobian_right(R)
+    finally:
+        del os.environ["SCCSD_HOST_FAKE_WAIT_EXPIRY"]
+    assert ei.value.code == -3
+    assert "wait expired" in str(ei.value)
+    sig = ctx.jacobian_right(R)
+    for k in range(2):
+        ref = rp.jacobian_right(prob, x, R[k]).numpy()
+        assert np.abs(sig[k] - ref).max() < 1e-12
+    ctx.close()
+
+
 def test_left_normalisation_through_the_c_abi(host_lib):
     """sccsd_normalize_left scales each left eigenvector so that <L_k|R_k> = 1
     (Sec. 2.1; the plain dot product in the biorthonormal bra basis). Checked
