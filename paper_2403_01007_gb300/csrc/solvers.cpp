@@ -125,7 +125,8 @@ int sccsd_solve_ground(sccsd_ctx* c, const double* t0, double zeta, const double
     double* Dp = solver_buf(c, 7, dim);
     double* fdg = solver_buf(c, 8, c->o + c->v);
     bool have_dp = false;
-    int refine_fp64_evals = 0, inner_its = 0;
+    int refine_fp64_evals = 0, inner_its = 0, refine_fail = 0;
+    double gate = 1e300;
     int next_refresh = 3;
     for (it = 1; it <= maxit; ++it) {
       E = eval_residual(c, t, zeta, ra, rb, om);
@@ -140,8 +141,12 @@ int sccsd_solve_ground(sccsd_ctx* c, const double* t0, double zeta, const double
       } else {
         ++since_best;
       }
-      // the mixed phase ends below refine_tol, or when it stalls at its noise floor
-      if (!fp64_phase && (nrm < refine_tol || since_best >= 6)) {
+      // the mixed phase ends below refine_tol, or when it stalls at its noise
+      // floor; after a refinement attempt that did not hold (strongly
+      // correlated systems can stall far from the solution, where the
+      // linearised correction overshoots) a stall counts only below 1% of
+      // the residual of that attempt
+      if (!fp64_phase && (nrm < refine_tol || (since_best >= 6 && nrm < gate))) {
         // Iterative refinement (defect correction): the FP64 residual
         // r = Omega(t) drives a correction solve A d = -r with the mixed
         // Jacobian (its error scales with d, not with t), t <- t + d. Each
@@ -152,12 +157,13 @@ int sccsd_solve_ground(sccsd_ctx* c, const double* t0, double zeta, const double
         double* dl = solver_buf(c, 9, dim);
         double* Ad = solver_buf(c, 19, dim);
         double* rr = solver_buf(c, 20, dim);
+        double* tp = solver_buf(c, 21, dim);   // amplitudes before the last correction
         // the correction solves start in the context's precision and move up
         // to the split BF16 form when a round gains too little
         int pc = p0;
         double inner_rtol = pc == SCCSD_BF16X3 ? 1e-4 : 1e-2;
         double prev = 1e300;
-        bool done = false;
+        bool done = false, worse = false;
         for (int round = 0; round < 12 && !done; ++round) {
           switch_precision(c, SCCSD_FP64);
           E = eval_residual(c, t, zeta, ra, rb, rr);
@@ -173,6 +179,14 @@ int sccsd_solve_ground(sccsd_ctx* c, const double* t0, double zeta, const double
             done = true;
             break;
           }
+          if (rn > prev) {
+            // the last correction made things worse (too far from the
+            // solution for the linearised step): undo it and let the mixed
+            // iterations go on
+            d.copy(t, tp, dim);
+            worse = true;
+            break;
+          }
           if (rn > prev / 3.0) {
             if (pc == SCCSD_BF16) {
               // not gaining in BF16: the next corrections in the split form
@@ -183,7 +197,7 @@ int sccsd_solve_ground(sccsd_ctx* c, const double* t0, double zeta, const double
               break;  // not gaining: finish in FP64
             }
           }
-          prev = std::min(prev, rn);
+          prev = rn;
           // the mixed state at t for the Jacobian transforms
           eval_residual(c, t, zeta, ra, rb, om);
           // A d = -r by the Jacobi-preconditioned linear iteration with DIIS
@@ -218,9 +232,21 @@ int sccsd_solve_ground(sccsd_ctx* c, const double* t0, double zeta, const double
               d.copy(dl, tn, dim);
             }
           }
+          d.copy(tp, t, dim);
           d.axpby(dim, 1.0, dl, 1.0, t);
         }
         if (done) break;
+        if (worse && ++refine_fail < 3) {
+          // back to the mixed iterations from the best amplitudes, with a
+          // lower gate for the next attempt
+          switch_precision(c, p0);
+          gate = std::min(gate, prev) * 1e-2;
+          best = 1e300;
+          since_best = 0;
+          nh = 0;
+          head = 0;
+          continue;
+        }
         // FP64 iterations from the current amplitudes
         switch_precision(c, SCCSD_FP64);
         fp64_phase = true;

@@ -49,7 +49,11 @@ class Workload:
 # Workloads of the paper-scale benchmark ladder (small, medium, large).
 SMALL = Workload("o5_v19_J72", 5, 19, 72, 0.05, 1)
 MEDIUM = Workload("o10_v90_J300", 10, 90, 300, 0.03, 2)
-LARGE = Workload("o21_v200_J663", 21, 200, 663, 0.03, 3)
+# o=21 v=200: entries N(0, 0.02^2). With 0.03 (the o=10 v=90 width) the system
+# is not a convergent coupled-cluster problem at this size (MP2 first step
+# -4022 Eh, FP64 ground iterations still at |Omega| = 8e-3 after 180 steps);
+# the narrower width is the fallback the scope table prescribes for that case.
+LARGE = Workload("o21_v200_J663", 21, 200, 663, 0.02, 3)
 
 
 def seed_of(config: int, instance: int = 0) -> int:
