@@ -88,10 +88,15 @@ __global__ void k_small_solve(int m, const double* __restrict__ A, const double*
 // Eigenvalues (wr, wi) of H (m x m, row-major) and unit right eigenvectors of
 // the nwant real eigenvalues with the lowest real part (columns of Y, m x nwant,
 // row-major [i][k]); order[k] = index into wr of the k-th wanted root.
-// info: 0 ok, 2 = QR did not converge, 3 = a wanted root is complex.
+// info: 0 ok, 2 = QR did not converge, 3 = a wanted root is complex. With
+// allow_complex, a complex pair among the wanted roots gives info 4 instead,
+// and the pair's two columns of Y span its real invariant plane: the first by
+// inverse iteration at the real part, the second H x - Re(lambda) x of it,
+// orthonormalised (a Davidson subspace can carry such pairs before its roots
+// settle).
 __global__ void k_small_eig(int m, const double* __restrict__ Hin, double* __restrict__ wr,
                             double* __restrict__ wi, double* __restrict__ Y, int nwant,
-                            int* __restrict__ order, int* info) {
+                            int* __restrict__ order, int* info, int allow_complex) {
   __shared__ double H[kSmallMax * kSmallMax];
   __shared__ double W[kSmallMax * kSmallMax];
   __shared__ double v[kSmallMax];
@@ -266,7 +271,7 @@ __global__ void k_small_eig(int m, const double* __restrict__ Hin, double* __res
           sorder[j] = t;
         }
     for (int k = 0; k < nwant && s_info == 0; ++k)
-      if (li[sorder[k]] != 0.0) s_info = 3;
+      if (li[sorder[k]] != 0.0) s_info = allow_complex ? 4 : 3;
   }
   __syncthreads();
   for (int i = tid; i < m; i += nt) {
@@ -274,13 +279,42 @@ __global__ void k_small_eig(int m, const double* __restrict__ Hin, double* __res
     wi[i] = li[i];
   }
   for (int k = tid; k < nwant; k += nt) order[k] = sorder[k];
-  if (s_info != 0) {
+  if (s_info != 0 && s_info != 4) {
     if (tid == 0) *info = s_info;
     return;
   }
   // --- eigenvectors by inverse iteration on the original matrix
   for (int k = 0; k < nwant; ++k) {
     const double lam = lr[sorder[k]];
+    const int ik = sorder[k];
+    if (k > 0 && li[ik] != 0.0 && li[sorder[k - 1]] == -li[ik] && lr[sorder[k - 1]] == lam) {
+      // second member of a complex pair: H x - lam x of the first (still in x)
+      for (int i = tid; i < m; i += nt) {
+        double y = -lam * x[i];
+        for (int j = 0; j < m; ++j) y += Hin[i * m + j] * x[j];
+        v[i] = y;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        double dt = 0.0;
+        for (int i = 0; i < m; ++i) dt += v[i] * x[i];
+        double nrm = 0.0;
+        for (int i = 0; i < m; ++i) {
+          v[i] -= dt * x[i];
+          nrm += v[i] * v[i];
+        }
+        nrm = sqrt(nrm);
+        int imax = 0;
+        for (int i = 1; i < m; ++i)
+          if (fabs(v[i]) > fabs(v[imax])) imax = i;
+        const double sgn = v[imax] < 0 ? -1.0 : 1.0;
+        for (int i = 0; i < m; ++i) x[i] = nrm > 0.0 ? sgn * v[i] / nrm : 0.0;
+      }
+      __syncthreads();
+      for (int i = tid; i < m; i += nt) Y[i * nwant + k] = x[i];
+      __syncthreads();
+      continue;
+    }
     double scale = 0.0;
     for (int e = 0; e < m * m; ++e) scale = fmax(scale, fabs(Hin[e]));
     const double shift = lam + 1e-10 * fmax(1.0, scale);
@@ -308,7 +342,7 @@ __global__ void k_small_eig(int m, const double* __restrict__ Hin, double* __res
     for (int i = tid; i < m; i += nt) Y[i * nwant + k] = x[i];
     __syncthreads();
   }
-  if (tid == 0) *info = 0;
+  if (tid == 0) *info = s_info;
 }
 
 }  // namespace sccsd
@@ -345,8 +379,8 @@ void launch_small_solve(cudaStream_t st, int m, const double* A, const double* b
   k_small_solve<<<1, 128, 0, st>>>(m, A, b, x, info);
 }
 void launch_small_eig(cudaStream_t st, int m, const double* H, double* wr, double* wi, double* Y,
-                      int nwant, int* order, int* info) {
-  k_small_eig<<<1, 128, 0, st>>>(m, H, wr, wi, Y, nwant, order, info);
+                      int nwant, int* order, int* info, int allow_complex) {
+  k_small_eig<<<1, 128, 0, st>>>(m, H, wr, wi, Y, nwant, order, info, allow_complex);
 }
 void launch_diis(cudaStream_t st, int m, const double* B, double* c, int* info) {
   k_diis<<<1, 128, 0, st>>>(m, B, c, info);

@@ -10,7 +10,7 @@ namespace sccsd {
 void launch_small_solve(cudaStream_t st, int m, const double* A, const double* b, double* x,
                         int* info);
 void launch_small_eig(cudaStream_t st, int m, const double* H, double* wr, double* wi, double* Y,
-                      int nwant, int* order, int* info);
+                      int nwant, int* order, int* info, int allow_complex = 0);
 void launch_diis(cudaStream_t st, int m, const double* B, double* c, int* info);
 void launch_denoms(cudaStream_t st, int o, int v, const double* eps, double* D);
 void launch_jacobi(cudaStream_t st, int64_t n, const double* t, const double* om, const double* D,

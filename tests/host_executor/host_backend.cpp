@@ -293,7 +293,7 @@ void launch_diis(cudaStream_t, int m, const double* B, double* c, int* info) {
 // (Golub & Van Loan, Sec. 7.4-7.5); eigenvectors of the wanted real roots by
 // inverse iteration on the original matrix (Sec. 7.6.1).
 void launch_small_eig(cudaStream_t, int m, const double* Hin, double* wr, double* wi, double* Y,
-                      int nwant, int* order, int* info) {
+                      int nwant, int* order, int* info, int allow_complex) {
   typedef std::complex<double> cd;
   *info = 0;
   std::vector<double> H(Hin, Hin + (size_t)m * m);
@@ -375,10 +375,28 @@ void launch_small_eig(cudaStream_t, int m, const double* Hin, double* wr, double
   std::stable_sort(idx.begin(), idx.end(), [&](int p, int q) { return wr[p] < wr[q]; });
   for (int k = 0; k < nwant && k < m; ++k) {
     order[k] = idx[k];
-    if (wi[idx[k]] != 0.0 && *info == 0) *info = 3;
+    if (wi[idx[k]] != 0.0 && *info == 0) *info = allow_complex ? 4 : 3;
   }
-  if (*info != 0) return;
+  if (*info != 0 && *info != 4) return;
+  std::vector<double> prev(m, 0.0);
   for (int k = 0; k < nwant; ++k) {
+    const int ik = order[k];
+    if (k > 0 && wi[ik] != 0.0 && wi[order[k - 1]] == -wi[ik] && wr[order[k - 1]] == wr[ik]) {
+      // second member of a complex pair: the other direction of its real
+      // invariant plane, H y - Re(lambda) y of the first, orthonormalised
+      std::vector<double> z(m);
+      for (int i = 0; i < m; ++i) {
+        double s = -wr[ik] * prev[i];
+        for (int j = 0; j < m; ++j) s += Hin[(size_t)i * m + j] * prev[j];
+        z[i] = s;
+      }
+      double dt = 0.0, nrm = 0.0;
+      for (int i = 0; i < m; ++i) dt += z[i] * prev[i];
+      for (int i = 0; i < m; ++i) { z[i] -= dt * prev[i]; nrm += z[i] * z[i]; }
+      nrm = std::sqrt(nrm);
+      for (int i = 0; i < m; ++i) Y[(size_t)i * nwant + k] = nrm > 0.0 ? z[i] / nrm : 0.0;
+      continue;
+    }
     const double lam = wr[order[k]] + 1e-10 * std::max(1.0, std::fabs(wr[order[k]]));
     std::vector<double> y(m);
     for (int i = 0; i < m; ++i) y[i] = 1.0 + 0.01 * i;
@@ -392,6 +410,7 @@ void launch_small_eig(cudaStream_t, int m, const double* Hin, double* wr, double
       for (double& e : y) e /= nrm;
     }
     for (int i = 0; i < m; ++i) Y[(size_t)i * nwant + k] = y[i];
+    prev = y;
   }
 }
 void launch_denoms(cudaStream_t, int o, int v, const double* eps, double* D) {
