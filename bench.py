@@ -679,9 +679,9 @@ def main():
                     help="64 uneven instances: joined CUDA graph vs per-instance calls")
     ap.add_argument("--solve", action="store_true",
                     help="converged ground state and right roots, mixed (refined) vs FP64")
-    ap.add_argument("--nstates", type=int, default=6)
+    ap.add_argument("--nstates", type=int, default=2)
     ap.add_argument("--solve-tol", type=float, default=1e-8)
-    ap.add_argument("--state-tol", type=float, default=1e-6)
+    ap.add_argument("--state-tol", type=float, default=1e-5)
     ap.add_argument("--solve-maxit", type=int, default=400)
     args = ap.parse_args()
     if args.solve and args.impl == "ours":

@@ -277,20 +277,33 @@ __global__ void k_sum_parts(int64_t n, int splits, const double* __restrict__ pa
 // pair symmetry X_ij^dc is read as X_ji^cd, so both reads walk d. Written as
 // FP64 rows of stride ld, or (Out = __nv_bfloat16) as `nsl` BF16 slices of a
 // tensor-core operand (rows of stride ld, slices sstride apart; x = sum of the
-// slices, each the BF16 rounding of what the previous ones left).
+// slices, each the BF16 rounding of what the previous ones left, formed in
+// double so that the last slice keeps the remainder).
+// values x[0], x[1] at i0, i0 + 1 (the second only when i0 + 1 < n); i0 even
 template <class Out>
-__device__ __forceinline__ void put_val(Out* p, int64_t i, double x, int nsl, int64_t sstride);
+__device__ __forceinline__ void put_pair(Out* p, int64_t i0, const double* x, int64_t n, int nsl,
+                                         int64_t sstride);
 template <>
-__device__ __forceinline__ void put_val<double>(double* p, int64_t i, double x, int, int64_t) {
-  p[i] = x;
+__device__ __forceinline__ void put_pair<double>(double* p, int64_t i0, const double* x, int64_t n,
+                                                 int, int64_t) {
+  p[i0] = x[0];
+  if (i0 + 1 < n) p[i0 + 1] = x[1];
 }
 template <>
-__device__ __forceinline__ void put_val<__nv_bfloat16>(__nv_bfloat16* p, int64_t i, double x,
-                                                       int nsl, int64_t sstride) {
+__device__ __forceinline__ void put_pair<__nv_bfloat16>(__nv_bfloat16* p, int64_t i0,
+                                                        const double* x, int64_t n, int nsl,
+                                                        int64_t sstride) {
+  double r0 = x[0], r1 = x[1];
   for (int s = 0; s < nsl; ++s) {
-    const __nv_bfloat16 b = __double2bfloat16(x);
-    p[s * sstride + i] = b;
-    x -= (double)__bfloat162float(b);
+    __nv_bfloat162 b;
+    b.x = __float2bfloat16_rn((float)r0);
+    b.y = __float2bfloat16_rn((float)r1);
+    if (i0 + 1 < n)
+      *reinterpret_cast<__nv_bfloat162*>(p + s * sstride + i0) = b;
+    else
+      p[s * sstride + i0] = b.x;
+    r0 -= (double)__bfloat162float(b.x);
+    r1 -= (double)__bfloat162float(b.y);
   }
 }
 
@@ -314,13 +327,24 @@ __global__ void k_ladder_pack_x(const double* __restrict__ X, int o, int v, int6
     Out* op = Xp + blk * ld;
     Out* om = i < j ? Xm + (z * Pm + (int64_t)i * (o - 1) - (int64_t)i * (i - 1) / 2 + (j - i - 1)) * ld
                     : nullptr;
-    for (int64_t q = threadIdx.x; q < Pv; q += blockDim.x) {
-      const int cd = __ldg(pairs + q);
-      const int c = cd >> 16, d = cd & 0xffff;
-      const int64_t e = (int64_t)c * v + d;
-      const double a = xij[e], b = xji[e];
-      put_val<Out>(op, q, c == d ? 0.5 * (a + b) : a + b, nsl, sp_stride);
-      if (om) put_val<Out>(om, q, c == d ? 0.0 : a - b, nsl, sm_stride);
+    // two consecutive q per thread (one 4-byte store per BF16 slice)
+    for (int64_t q0 = 2 * (int64_t)threadIdx.x; q0 < Pv; q0 += 2 * (int64_t)blockDim.x) {
+      double pv[2], mv[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t q = q0 + h;
+        pv[h] = mv[h] = 0.0;
+        if (q < Pv) {
+          const int cd = __ldg(pairs + q);
+          const int c = cd >> 16, d = cd & 0xffff;
+          const int64_t e = (int64_t)c * v + d;
+          const double a = xij[e], b = xji[e];
+          pv[h] = c == d ? 0.5 * (a + b) : a + b;
+          mv[h] = c == d ? 0.0 : a - b;
+        }
+      }
+      put_pair<Out>(op, q0, pv, Pv, nsl, sp_stride);
+      if (om) put_pair<Out>(om, q0, mv, Pv, nsl, sm_stride);
     }
   }
 }

@@ -523,7 +523,9 @@ int sccsd_solve_states(sccsd_ctx* c, int nroots, int side, double tol, int maxit
       // transformed in the mixed precision, whose error then scales with the
       // size of the corrections, not of the roots. Convergence is accepted
       // only on a subspace of FP64 images alone (after a fresh anchor).
-      if (!fp64_phase && (worst < refine_tol || since_best >= 8)) {
+      // (a stall counts only within 10x of refine_tol: far from convergence a
+      // non-symmetric Davidson can plateau for a while without a noise floor)
+      if (!fp64_phase && (worst < refine_tol || (since_best >= 8 && worst < 10.0 * refine_tol))) {
         fp64_phase = true;
         anchor();
         continue;
@@ -537,7 +539,7 @@ int sccsd_solve_states(sccsd_ctx* c, int nroots, int side, double tol, int maxit
         anchor();   // verify: residuals of FP64 images only
         continue;
       }
-      if (refine && fp64_phase && since_best >= 8) {
+      if (refine && fp64_phase && since_best >= 12) {
         anchor();   // the mixed corrections stalled: new FP64 anchor
         continue;
       }

@@ -496,13 +496,13 @@ __global__ void k_sum_splits(int64_t M, int64_t N, int splits, const double* __r
 // accumulators (columns 0 .. and 256 ..), computed one after the other, so
 // that the epilogue of one half overlaps the MMAs of the next.
 // Warp roles:
-//   warp 8    : TMA producer; one stage = A rows a*v + 128 h .. + 127 and B
+//   warp 16   : TMA producer; one stage = A rows a*v + 128 h .. + 127 and B
 //               rows b*v .. b*v + NB - 1 of one 64-wide K block; slice
 //               products (0,0), (0,1), (1,0) in turn
-//   warp 9    : one elected thread issues the MMAs of each half into its
+//   warp 17   : one elected thread issues the MMAs of each half into its
 //               accumulator, N = NB = v rounded up to 16
-//   warps 0-7 : epilogue; warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows c)
-//               and the column chunks of parity w / 4. Phase 1 writes the
+//   warps 0-15: epilogue; warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows c)
+//               and the column chunks ch with ch % 4 = w / 4. Phase 1 writes the
 //               upper triangle W[c][d], d > c, to shared memory (FP32); phase
 //               2 takes the lower triangle from TMEM, forms both combinations
 //               with the stored transpose and packs them in place as BF16
@@ -512,7 +512,7 @@ __global__ void k_sum_splits(int64_t M, int64_t N, int splits, const double* __r
 //               stores, while the MMAs of the next pair already run.
 // Every mbarrier wait is bounded as in k_tc_gemm; the epilogue warps meet at
 // named barriers on every path, so an abort never leaves one of them waiting.
-constexpr int LB_EPI = 8;                      // epilogue warps
+constexpr int LB_EPI = 16;                     // epilogue warps (four per TMEM lane quadrant)
 constexpr int LB_THREADS = (LB_EPI + 2) * 32;
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
@@ -682,7 +682,7 @@ __global__ void __launch_bounds__(LB_THREADS, 1)
       }
     }
   } else {
-    // epilogue warp: TMEM lanes 32 q .. 32 q + 31, column chunks ch = cg, cg + 2, ...
+    // epilogue warp: TMEM lanes 32 q .. 32 q + 31, column chunks ch = cg, cg + 4, ...
     const int q = warp & 3, cg = warp >> 2;
     const int nch = (NB + 31) / 32;
     int64_t i = 0;
@@ -707,16 +707,18 @@ __global__ void __launch_bounds__(LB_THREADS, 1)
         const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * BN);
         // phase 1: upper triangle W[c][d], d > c, to shared memory
         if (!dead && cw < v) {
-          const int64_t base_c = (int64_t)c * (v - 1) - (int64_t)c * (c - 1) / 2;
-          for (int ch = cg; ch < nch; ch += 2) {
+          // S index of (c, d) is base_c + d
+          const int base_c = c * (v - 1) - c * (c - 1) / 2;
+          for (int ch = cg; ch < nch; ch += 4) {
             if (ch * 32 + 31 <= cw) continue;  // warp-uniform: no d > c here
             uint32_t r[32];
             tmem_ld32(tbase + (uint32_t)(ch * 32), r);
             if (c < v) {
+              float* Sr = S + base_c + ch * 32;
 #pragma unroll
               for (int j = 0; j < 32; ++j) {
                 const int d = ch * 32 + j;
-                if (d > c && d < v) S[base_c + d] = __uint_as_float(r[j]);
+                if (d > c && d < v) Sr[j] = __uint_as_float(r[j]);
               }
             }
           }
@@ -724,17 +726,18 @@ __global__ void __launch_bounds__(LB_THREADS, 1)
         epi_bar();
         // phase 2: lower triangle d <= c with the stored transpose, packed in place
         if (!dead && cw < v) {
-          for (int ch = cg; ch < nch; ch += 2) {
+          for (int ch = cg; ch < nch; ch += 4) {
             if (ch * 32 > cw + 31) continue;  // warp-uniform: every d > every c
             uint32_t r[32];
             tmem_ld32(tbase + (uint32_t)(ch * 32), r);
-            if (c < v) {
+            // S index of (d, c) is base_d + c; base_d is the same in every lane
+            int base_d = (ch * 32) * (v - 1) - (ch * 32) * (ch * 32 - 1) / 2;
 #pragma unroll
-              for (int j = 0; j < 32; ++j) {
-                const int d = ch * 32 + j;
-                if (d > c) continue;
+            for (int j = 0; j < 32; ++j) {
+              const int d = ch * 32 + j;
+              if (d <= c && c < v) {
                 const float x = __uint_as_float(r[j]);
-                const int64_t qi = (int64_t)d * (v - 1) - (int64_t)d * (d - 1) / 2 + c;
+                const int qi = base_d + c;
                 float sp, sm;
                 if (d == c) {
                   sp = 2.0f * x;
@@ -752,6 +755,7 @@ __global__ void __launch_bounds__(LB_THREADS, 1)
                   om[out_sstride + qi] = __float2bfloat16(sm - __bfloat162float(hm));
                 }
               }
+              base_d += v - 1 - d;
             }
           }
         }
