@@ -1,11 +1,14 @@
 """Batched uneven instances: per-instance Jacobian transforms captured into
 CUDA graphs and joined into one launch must give the transforms of the
-ordinary per-instance calls, and must read their input vectors at launch
-time (Sec. 2.1 EOM transforms; the batching itself is not in the paper)."""
+ordinary per-instance calls and of the FP64 oracle for every instance, and
+must read their input vectors at launch time (Sec. 2.1 EOM transforms; the
+batching itself is not in the paper)."""
 import numpy as np
 import pytest
 import torch
 
+from oracle import ccsd as cc
+from oracle import response as rp
 from paper_2403_01007_gb300 import binding as B
 from paper_2403_01007_gb300 import synthetic as syn
 
@@ -27,7 +30,8 @@ def _instances(n, seed, prec):
         ctx.residual(t)
         R = torch.tensor(syn.random_vectors(o, v, nst, seed * 1000 + 700 + k, normalise=True),
                          device="cuda")
-        out.append(dict(ctx=ctx, stream=st, R=R, W=torch.empty_like(R), o=o, v=v, k=k))
+        out.append(dict(ctx=ctx, stream=st, R=R, W=torch.empty_like(R), o=o, v=v, k=k,
+                        eps=eps, L=L, t=t))
     return out
 
 
@@ -61,6 +65,17 @@ def test_joined_graph_equals_per_instance_calls(prec, side):
                 torch.cuda.synchronize()
                 assert torch.isfinite(x["W"]).all()
                 assert _rel(x["W"], ref) < tol, (x["o"], x["v"], _rel(x["W"], ref))
+                # and each instance's launched transforms against the FP64 oracle
+                # (within the split's error in BF16)
+                prob = cc.Problem(x["eps"], x["L"], x["o"])
+                fn = rp.jacobian_right if side == "right" else rp.jacobian_left
+                Wh = x["W"].cpu().numpy()
+                Rh = x["R"].cpu().numpy()
+                otol = 1e-11 if prec == "fp64" else 3e-2
+                for kv in range(Rh.shape[0]):
+                    o_ref = fn(prob, x["t"], Rh[kv]).numpy()
+                    err = np.abs(Wh[kv] - o_ref).max() / max(1e-300, np.abs(o_ref).max())
+                    assert err < otol, (x["o"], x["v"], kv, err)
     finally:
         batch.close()
         for x in inst:
