@@ -925,7 +925,7 @@ void TcGemm::run(const TcOperand& A, int sa, const TcOperand& B, int sb, int64_t
   const int64_t items = mt * nt * splits;
   const int grid = (int)std::min<int64_t>(items, sm_count_);
   const int nk = (int)(A.k_pad / BK);
-  if (variant == 1 && kbs > 4) throw std::runtime_error("tc: eight-warp variant needs <= 4 K blocks");
+
   if (variant == 1)
     k_tc_gemm<3, 8><<<grid, 320, smem_bytes(3, 8), st_>>>(ma, mb, M, N, mt, nt, nfast, items, nk,
                                                           kbs, alpha, C, split_stride, ov,

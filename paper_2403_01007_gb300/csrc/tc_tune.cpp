@@ -36,7 +36,9 @@ TcConfig tc_default_config(const TcShape& s, int64_t m_tiles, int64_t n_tiles, d
     want = std::min<int64_t>((2 * (int64_t)s.sm_count + tiles - 1) / tiles, s.nk / 4);
   split_of(s.nk, want, c);
   c.nfast = (n_tiles > 1 && a_bytes > 4.0 * b_bytes) ? 1 : 0;
-  c.variant = c.kbs <= 4 ? 1 : 0;
+  // eight epilogue warps (three pipeline stages) when an item has at most 16
+  // K blocks: its MMAs then take no longer than its FP64 epilogue
+  c.variant = c.kbs <= 16 ? 1 : 0;
   return c;
 }
 
@@ -54,7 +56,6 @@ std::vector<TcConfig> tc_candidates(const TcShape& s, int64_t m_tiles, int64_t n
     TcConfig c;
     split_of(s.nk, w, c);
     for (int variant = 0; variant < 2; ++variant) {
-      if (variant == 1 && c.kbs > 4) continue;
       for (int nfast = 0; nfast < (n_tiles > 1 ? 2 : 1); ++nfast) {
         TcConfig x = c;
         x.variant = variant;
@@ -76,7 +77,7 @@ bool tc_config_valid(const TcConfig& c, int nk, int64_t n_tiles) {
   } else {
     if (c.splits < 1 || nk < 8 || c.kbs < 4 || c.splits != (nk + c.kbs - 1) / c.kbs) return false;
   }
-  return !(c.variant == 1 && c.kbs > 4);
+  return true;
 }
 
 TcTuneTable& TcTuneTable::global() {

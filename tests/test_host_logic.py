@@ -217,7 +217,7 @@ def _default_rule(M, n_pad, nk, sm, ab, bb):
     split only when the output tiles (128 x 256) cannot fill the SMs and there
     are at least 8 K blocks, into ranges of at least 4 blocks; N tiles are
     walked fastest when A is more than four times larger than B; the
-    eight-warp variant serves items of at most 4 K blocks."""
+    eight-warp variant serves items of at most 16 K blocks."""
     mt, nt = -(-M // 128), n_pad // 256
     tiles = mt * nt
     want = min(-(-2 * sm // tiles), nk // 4) if (tiles < sm and nk >= 8) else 1
@@ -226,7 +226,7 @@ def _default_rule(M, n_pad, nk, sm, ab, bb):
     else:
         kbs = -(-nk // want)
         splits = -(-nk // kbs)
-    return (1 if kbs <= 4 else 0, 1 if (nt > 1 and ab > 4 * bb) else 0, splits, kbs)
+    return (1 if kbs <= 16 else 0, 1 if (nt > 1 and ab > 4 * bb) else 0, splits, kbs)
 
 
 TUNE_SHAPES = [
@@ -258,7 +258,7 @@ def test_autotune_candidates_follow_the_launch_rules():
         assert len(set(c[:4] for c in cands)) == len(cands), shape
         assert any(c[2] == 1 and c[3] == nk for c in cands), shape
         for variant, nfast, splits, kbs, _ in cands:
-            assert variant == 0 or kbs <= 4
+            assert variant in (0, 1)
             assert nfast == 0 or nt > 1
             if splits > 1:
                 assert kbs >= 4 and splits == -(-nk // kbs) and nk >= 8
@@ -266,9 +266,11 @@ def test_autotune_candidates_follow_the_launch_rules():
                 assert kbs == nk
     # one output tile over 1313 K blocks: no split, half the default number of
     # ranges (120 ranges of 11 blocks) and the default (263 ranges of 5, which
-    # is also the finest split with at least 4 blocks per range)
+    # is also the finest split with at least 4 blocks per range), each with
+    # either kernel form
     cands = [tuple(int(x) for x in l.split()) for l in blocks[2].strip().splitlines()]
     assert {(c[2], c[3]) for c in cands} == {(1, 1313), (120, 11), (263, 5)}
+    assert {(c[0], c[2]) for c in cands} == {(v, s) for v in (0, 1) for s in (1, 120, 263)}
 
 
 def test_autotune_table_text(host_lib):
@@ -284,8 +286,11 @@ def test_autotune_table_text(host_lib):
     assert rows == sorted(tuple(l.split()[:11]) for l in good.strip().splitlines())
     B.autotune_import(text, lib)                      # re-import is idempotent
     assert B.autotune_entries(lib) == 2
+    B.autotune_import("126 256 1313 1 1 152 99 1 0 263 5 1.0", lib)   # eight-warp form, 5 blocks
+    assert B.autotune_entries(lib) == 2                                 # replaces the entry
+    B.autotune_import(good, lib)
     bad = [
-        "126 256 1313 1 1 152 99 1 0 263 5 1.0",      # eight-warp variant with 5 K blocks
+        "126 256 1313 1 1 152 99 2 0 263 5 1.0",      # no third kernel form
         "126 256 1313 1 1 152 99 0 0 200 5 1.0",      # split count does not cover K
         "126 256 1313 1 1 152 99 0 1 263 5 1.0",      # N-fastest with one N tile
         "2646 40192 625 1 0 152 1 0 0 1 600 1.0",     # unsplit but K range != K
