@@ -533,6 +533,11 @@ __device__ __forceinline__ void epi_bar() {
   asm volatile("bar.sync 1, %0;" ::"n"(LB_EPI * 32) : "memory");
 }
 
+// HS (one BF16 slice): the upper triangle is kept as BF16, which leaves room
+// for a fourth pipeline stage; phase 2 rewrites G+ in place and stores G- to
+// global memory at once. Otherwise (two slices) it is kept in FP32 and phase 2
+// packs G+ and G- in place.
+template <bool HS>
 __global__ void __launch_bounds__(LB_THREADS, 1)
     k_ladder_build(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    int v, int NB, int two, int nkb, int nprod, int64_t slice_rows, int stages,
@@ -550,6 +555,7 @@ __global__ void __launch_bounds__(LB_THREADS, 1)
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   float* S = (float*)(smem + stages * stage_bytes + 256);
   uint32_t* Su = (uint32_t*)S;
+  __nv_bfloat16* Sh = (__nv_bfloat16*)S;
   const int64_t Pv = (int64_t)v * (v + 1) / 2;
   const int64_t P4 = (Pv + 3) / 4;
   const int H = two ? 2 : 1;
@@ -569,7 +575,12 @@ __global__ void __launch_bounds__(LB_THREADS, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // the padding of the last group of four entries reads as zero in phase 3
-  if (threadIdx.x < 4 && Pv + threadIdx.x < 4 * P4) Su[Pv + threadIdx.x] = 0u;
+  const int64_t P8 = (Pv + 7) / 8;
+  if (HS) {
+    if (threadIdx.x < 8 && Pv + threadIdx.x < 8 * P8) Sh[Pv + threadIdx.x] = __float2bfloat16(0.0f);
+  } else {
+    if (threadIdx.x < 4 && Pv + threadIdx.x < 4 * P4) Su[Pv + threadIdx.x] = 0u;
+  }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
@@ -714,11 +725,20 @@ __global__ void __launch_bounds__(LB_THREADS, 1)
             uint32_t r[32];
             tmem_ld32(tbase + (uint32_t)(ch * 32), r);
             if (c < v) {
-              float* Sr = S + base_c + ch * 32;
+              if (HS) {
+                __nv_bfloat16* Sr = Sh + base_c + ch * 32;
 #pragma unroll
-              for (int j = 0; j < 32; ++j) {
-                const int d = ch * 32 + j;
-                if (d > c && d < v) Sr[j] = __uint_as_float(r[j]);
+                for (int j = 0; j < 32; ++j) {
+                  const int d = ch * 32 + j;
+                  if (d > c && d < v) Sr[j] = __float2bfloat16(__uint_as_float(r[j]));
+                }
+              } else {
+                float* Sr = S + base_c + ch * 32;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                  const int d = ch * 32 + j;
+                  if (d > c && d < v) Sr[j] = __uint_as_float(r[j]);
+                }
               }
             }
           }
@@ -743,16 +763,22 @@ __global__ void __launch_bounds__(LB_THREADS, 1)
                   sp = 2.0f * x;
                   sm = 0.0f;
                 } else {
-                  const float u = S[qi];  // W[d][c]
+                  // W[d][c]
+                  const float u = HS ? __bfloat162float(Sh[qi]) : S[qi];
                   sp = u + x;
                   sm = u - x;
                 }
                 const __nv_bfloat16 hp = __float2bfloat16(sp), hm = __float2bfloat16(sm);
-                Su[qi] = (uint32_t)__bfloat16_as_ushort(hp) |
-                         ((uint32_t)__bfloat16_as_ushort(hm) << 16);
-                if (nsl > 1) {
-                  op[out_sstride + qi] = __float2bfloat16(sp - __bfloat162float(hp));
-                  om[out_sstride + qi] = __float2bfloat16(sm - __bfloat162float(hm));
+                if (HS) {
+                  Sh[qi] = hp;
+                  om[qi] = hm;   // consecutive lanes: consecutive qi
+                } else {
+                  Su[qi] = (uint32_t)__bfloat16_as_ushort(hp) |
+                           ((uint32_t)__bfloat16_as_ushort(hm) << 16);
+                  if (nsl > 1) {
+                    op[out_sstride + qi] = __float2bfloat16(sp - __bfloat162float(hp));
+                    om[out_sstride + qi] = __float2bfloat16(sm - __bfloat162float(hm));
+                  }
                 }
               }
               base_d += v - 1 - d;
@@ -770,15 +796,21 @@ __global__ void __launch_bounds__(LB_THREADS, 1)
       epi_bar();
       if (!dead) {
         const uint4* S4 = (const uint4*)Su;
-        for (int64_t g4 = threadIdx.x; g4 < P4; g4 += LB_EPI * 32) {
-          const uint4 e = S4[g4];
-          uint2 pp, mm;
-          pp.x = (e.x & 0xffffu) | (e.y << 16);
-          pp.y = (e.z & 0xffffu) | (e.w << 16);
-          mm.x = (e.x >> 16) | (e.y & 0xffff0000u);
-          mm.y = (e.z >> 16) | (e.w & 0xffff0000u);
-          *(uint2*)(op + 4 * g4) = pp;
-          *(uint2*)(om + 4 * g4) = mm;
+        if (HS) {
+          // eight G+ values per 16-byte load and store
+          for (int64_t g8 = threadIdx.x; g8 < P8; g8 += LB_EPI * 32)
+            *(uint4*)(op + 8 * g8) = S4[g8];
+        } else {
+          for (int64_t g4 = threadIdx.x; g4 < P4; g4 += LB_EPI * 32) {
+            const uint4 e = S4[g4];
+            uint2 pp, mm;
+            pp.x = (e.x & 0xffffu) | (e.y << 16);
+            pp.y = (e.z & 0xffffu) | (e.w << 16);
+            mm.x = (e.x >> 16) | (e.y & 0xffff0000u);
+            mm.y = (e.z >> 16) | (e.w & 0xffff0000u);
+            *(uint2*)(op + 4 * g4) = pp;
+            *(uint2*)(om + 4 * g4) = mm;
+          }
         }
       }
     }
@@ -1181,17 +1213,22 @@ void TcGemm::prepare_ladder_lt(const double* L, int o, int v, int J, TcOperand& 
 namespace {
 int ladder_nb(int v) { return (int)round_up(v, 16); }
 int ladder_stage_bytes(int v) { return A_BYTES + ladder_nb(v) * BK * 2; }
-int ladder_tri_bytes(int v) { return (int)round_up((int64_t)v * (v + 1) / 2, 4) * 4; }
+// the upper triangle in shared memory: FP32 entries (two slices) or BF16 (one)
+int ladder_tri_bytes(int v, int nsl) {
+  return nsl == 1 ? (int)round_up((int64_t)v * (v + 1) / 2, 8) * 2
+                  : (int)round_up((int64_t)v * (v + 1) / 2, 4) * 4;
+}
 constexpr int kSmemMax = 232448;  // dynamic shared memory a block may opt in to
-int ladder_stages(int v) {
-  const int room = kSmemMax - 1024 - 256 - ladder_tri_bytes(v);
+int ladder_stages(int v, int nsl) {
+  const int room = kSmemMax - 1024 - 256 - ladder_tri_bytes(v, nsl);
   return std::min(6, room / ladder_stage_bytes(v));
 }
 }  // namespace
 
 int TcGemm::ladder_build_max_v() {
+  // the two-slice form has the larger triangle: every v up to this fits both
   int v = 2 * BM;
-  while (v > 1 && ladder_stages(v) < 2) --v;
+  while (v > 1 && ladder_stages(v, 2) < 2) --v;
   return v;
 }
 
@@ -1200,7 +1237,7 @@ void TcGemm::ladder_build(const TcOperand& Lt, int v, const int* pairs, int64_t 
   if (npairs <= 0) return;
   if (v < 1 || v > ladder_build_max_v()) throw std::runtime_error("ladder build: v out of range");
   const int NB = ladder_nb(v), two = v > BM ? 1 : 0;
-  const int stages = ladder_stages(v);
+  const int stages = ladder_stages(v, Lt.slices);
   const int64_t Pv = (int64_t)v * (v + 1) / 2;
   if (Lt.rows != (int64_t)v * v || Lt.rows_pad < Lt.rows + 256)
     throw std::runtime_error("ladder build: Lt operand without its spare rows");
@@ -1212,20 +1249,29 @@ void TcGemm::ladder_build(const TcOperand& Lt, int v, const int* pairs, int64_t 
   // heights 128 (A: rows c) and NB (B: rows d)
   CUtensorMap ma = make_map(Lt.data, (int64_t)Lt.slices * Lt.rows_pad, Lt.k_pad, BM);
   CUtensorMap mb = make_map(Lt.data, (int64_t)Lt.slices * Lt.rows_pad, Lt.k_pad, NB);
-  const int smem = 1024 + stages * ladder_stage_bytes(v) + 256 + ladder_tri_bytes(v);
+  const int smem = 1024 + stages * ladder_stage_bytes(v) + 256 + ladder_tri_bytes(v, Lt.slices);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_ladder_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSmemMax);
+    cudaError_t e = cudaFuncSetAttribute(k_ladder_build<true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_ladder_build<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               kSmemMax);
     if (e != cudaSuccess) throw CudaError(std::string("ladder build smem attribute: ") + cudaGetErrorString(e));
     attr_set = true;
   }
   const int nprod = Lt.slices == 1 ? 1 : 3;
   const int grid = (int)std::min<int64_t>(npairs, sm_count_);
-  k_ladder_build<<<grid, LB_THREADS, smem, st_>>>(
-      ma, mb, v, NB, two, (int)(Lt.k_pad / BK), nprod, Lt.rows_pad, stages, pairs, p_begin, npairs,
-      (__nv_bfloat16*)Gp.data, (__nv_bfloat16*)Gm.data, Gp.k_pad, Gp.rows_pad * Gp.k_pad,
-      Lt.slices, d_err_);
+  if (Lt.slices == 1)
+    k_ladder_build<true><<<grid, LB_THREADS, smem, st_>>>(
+        ma, mb, v, NB, two, (int)(Lt.k_pad / BK), nprod, Lt.rows_pad, stages, pairs, p_begin,
+        npairs, (__nv_bfloat16*)Gp.data, (__nv_bfloat16*)Gm.data, Gp.k_pad,
+        Gp.rows_pad * Gp.k_pad, Lt.slices, d_err_);
+  else
+    k_ladder_build<false><<<grid, LB_THREADS, smem, st_>>>(
+        ma, mb, v, NB, two, (int)(Lt.k_pad / BK), nprod, Lt.rows_pad, stages, pairs, p_begin,
+        npairs, (__nv_bfloat16*)Gp.data, (__nv_bfloat16*)Gm.data, Gp.k_pad,
+        Gp.rows_pad * Gp.k_pad, Lt.slices, d_err_);
   count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw CudaError(std::string("ladder build launch: ") + cudaGetErrorString(e));
