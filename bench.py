@@ -561,6 +561,10 @@ def solve_case(args):
             os.dup2(saved, 2)
             os.close(saved)
         logf.seek(0)
+        if args.solve_log:
+            with open(f"{args.solve_log}.{prec}", "w") as fo:
+                fo.write(logf.read())
+            logf.seek(0)
         done = {}
         for line in logf:
             if line.startswith("{") and ("_done" in line):
@@ -605,7 +609,7 @@ def learned_case(args):
     torch.cuda.set_device(0)
     t0 = time.perf_counter()
     train_sys = [lrn.system(8, 60, k) for k in range(args.n_train)]
-    X, Y = lrn.generate(train_sys, samples_per_instance=20000)
+    X, Y = lrn.generate(train_sys, samples_per_instance=20000, tol=args.gen_tol)
     gen_s = time.perf_counter() - t0
     net = B.Mlp(seed=11)
     t1 = time.perf_counter()
@@ -630,7 +634,8 @@ def learned_case(args):
         "data": "synthetic", "dtype": "bf16 network, bf16->f32->f64 solver with FP64 refinement",
         "config": {"workload": "learned_o8_v60_train_o8-12_v60-110_eval",
                    "n_train": args.n_train, "n_eval": args.n_eval,
-                   "samples_per_train_system": 20000, "epochs": 20},
+                   "samples_per_train_system": 20000, "epochs": 20,
+                   "training_targets_tol": args.gen_tol},
         "plain_iterations_mean": float(np.mean(it0)),
         "learned_iterations_mean": float(np.mean(it1)),
         "iteration_ratio": float(np.mean(it1) / np.mean(it0)),
@@ -670,6 +675,10 @@ def main():
                     help="evaluate the learned guess/preconditioner on fresh systems")
     ap.add_argument("--n-train", type=int, default=24)
     ap.add_argument("--n-eval", type=int, default=12)
+    ap.add_argument("--solve-log", default=None,
+                    help="with --solve: write each arm's solver log to this path + '.<arm>'")
+    ap.add_argument("--gen-tol", type=float, default=1e-8,
+                    help="residual tolerance of the solves that make the training targets")
     ap.add_argument("--projection", default="natural", choices=["natural", "state"],
                     help="with --chain: the SCC projection, SCCSD(E) or SCCSD(K)")
     ap.add_argument("--autotune", action="store_true",

@@ -2,12 +2,24 @@
 // activations, FP32 accumulation, trained and evaluated by these kernels.
 //
 // Network: x[F] -> (Linear + ReLU) x L_hidden -> Linear -> y[n_out].
-// Storage: weights W_l [in][out] BF16 (with FP32 master copies for Adam),
-// biases FP32, activations BF16, pre-activations FP32 (kept for backward).
 // Loss: mean squared error over all outputs.
+//
+// Every layer product runs on the tensor cores (tcgen05 through
+// TcGemm::mlp_gemm) with the elementwise work of the layer fused into the
+// product's epilogue. With A_0 = x, Z_l = A_l W_l + b_l and G_l = dLoss/dZ_l:
+//   forward   A_{l+1} = relu(Z_l), written as BF16 [rows][in] and, when
+//             training, transposed [in][rows]; Y = Z_L in FP32
+//   backward  G_L = dLoss/dY; G_{l-1} = (G_l W_l^T) * [A_l > 0] (BF16, both
+//             layouts); dW_l = A_l^T G_l, a contraction over the rows split
+//             across CTAs (FP32 partial sums, then reduced); db_l = sum_rows G_l
+// Storage: FP32 master weights W_l [in][out] with the Adam moments; BF16
+// copies Wt_l [out][in] (the forward operand) and Wk_l [in][out] (the
+// backward operand), rows padded to 256 and the contraction index to 64,
+// padding zero.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -17,145 +29,113 @@
 #include <vector>
 
 #include "../../include/sccsd.h"
+#include "tc_gemm.h"
 
 namespace {
 
-__device__ __forceinline__ float ld(const float* p, int64_t i) { return p[i]; }
-__device__ __forceinline__ float ld(const __nv_bfloat16* p, int64_t i) { return __bfloat162float(p[i]); }
+int64_t up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
-// C[m][n] (+)= alpha * sum_k A(m,k) B(k,n), FP32 accumulation.
-// A(m,k) = A[m*sam + k*sak], B(k,n) = B[k*sbk + n*sbn], C row-major [M][N].
-// blockIdx.z splits K into chunks of kc; with more than one chunk the
-// results are added atomically (C must be zeroed first).
-template <typename TA, typename TB>
-__global__ void __launch_bounds__(256) k_gemm_f32(int64_t M, int64_t N, int64_t K, int64_t kc,
-                                                  float alpha, const TA* __restrict__ A,
-                                                  int64_t sam, int64_t sak,
-                                                  const TB* __restrict__ B, int64_t sbk,
-                                                  int64_t sbn, float* __restrict__ C,
-                                                  int accumulate) {
-  __shared__ float As[16][65];
-  __shared__ float Bs[16][65];
-  const int64_t m0 = (int64_t)blockIdx.y * 64, n0 = (int64_t)blockIdx.x * 64;
-  const int64_t kbeg = (int64_t)blockIdx.z * kc;
-  const int64_t kend = (K < kbeg + kc) ? K : kbeg + kc;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  float acc[4][4] = {};
-  for (int64_t k0 = kbeg; k0 < kend; k0 += 16) {
-    for (int q = 0; q < 4; ++q) {
-      int e = tid + 256 * q;
-      // A tile: rows fastest when sam == 1, else k fastest
-      int r, kk;
-      if (sam == 1) {
-        r = e & 63;
-        kk = e >> 6;
-      } else {
-        r = e >> 4;
-        kk = e & 15;
-      }
-      int64_t gm = m0 + r, gk = k0 + kk;
-      As[kk][r] = (gm < M && gk < kend) ? ld(A, gm * sam + gk * sak) : 0.f;
-      int c2, k2;
-      if (sbn == 1) {
-        c2 = e & 63;
-        k2 = e >> 6;
-      } else {
-        c2 = e >> 4;
-        k2 = e & 15;
-      }
-      int64_t gn = n0 + c2, gk2 = k0 + k2;
-      Bs[k2][c2] = (gn < N && gk2 < kend) ? ld(B, gk2 * sbk + gn * sbn) : 0.f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < 16; ++kk) {
-      float a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-    }
-    __syncthreads();
+__device__ __forceinline__ uint16_t bf16_bits(float x) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+__device__ __forceinline__ float bf16_val(uint16_t u) {
+  return __bfloat162float(__ushort_as_bfloat16(u));
+}
+
+// A[n][k] = bf16(X[n][k]) for k < n_in, 0 for n_in <= k < lda; when AT is
+// given also AT[k][n] for n < N, and zeros for N <= n < max(N, 64) (the
+// contraction over rows reads whole blocks of 64 there)
+__global__ void k_input(int64_t N, int n_in, const float* __restrict__ X, uint16_t* A,
+                        int64_t lda, uint16_t* AT, int64_t ldt) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N * lda; e += stride) {
+    const int64_t n = e / lda, k = e % lda;
+    const uint16_t b = k < n_in ? bf16_bits(X[n * n_in + k]) : (uint16_t)0;
+    A[e] = b;
+    if (AT && k < n_in) AT[k * ldt + n] = b;
   }
-  const bool atomic = gridDim.z > 1;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    int64_t gm = m0 + ty + 16 * i;
-    if (gm >= M) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int64_t gn = n0 + tx + 16 * j;
-      if (gn >= N) continue;
-      float v = alpha * acc[i][j];
-      float* p = C + gm * N + gn;
-      if (atomic)
-        atomicAdd(p, v);
-      else
-        *p = accumulate ? *p + v : v;
-    }
+  if (AT) {
+    const int64_t tail = N < 64 ? 64 - N : 0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tail * n_in; e += stride)
+      AT[(e / tail) * ldt + N + e % tail] = 0;
   }
 }
 
-// Z[n][m] += b[m]; A = relu(Z) as BF16 (or Z copied to FP32 output for the last layer)
-__global__ void k_bias_act(int64_t N, int64_t M, float* Z, const float* b, __nv_bfloat16* A,
-                           float* Yout, int relu) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N * M;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    float z = Z[e] + b[e % M];
-    Z[e] = z;
-    if (relu)
-      A[e] = __float2bfloat16(z > 0.f ? z : 0.f);
-    else
-      Yout[e] = z;
-  }
-}
-
-// dZ = dA * relu'(Z) (in place on dA)
-__global__ void k_relu_back(int64_t n, const float* Z, float* dA) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x)
-    if (Z[e] <= 0.f) dA[e] = 0.f;
-}
-
-// MSE: dY = 2 (Y - T) / (N * n_out); loss partials accumulated atomically
-__global__ void k_mse(int64_t n, const float* Y, const float* T, float* dY, float* loss) {
+// MSE: G[n][c] = 2 (Y - T) / (N n_out) as BF16 (zeros for n_out <= c < ldg),
+// GT[c][n] likewise (zeros for N <= n < max(N, 64)); loss accumulated atomically
+__global__ void k_mse(int64_t N, int n_out, const float* __restrict__ Y, const float* __restrict__ T,
+                      uint16_t* G, int64_t ldg, uint16_t* GT, int64_t ldt, float* loss) {
   float s = 0.f;
-  const float inv = 1.f / (float)n;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    float d = Y[e] - T[e];
-    dY[e] = 2.f * d * inv;
-    s += d * d * inv;
+  const float inv = 1.f / (float)(N * n_out);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N * ldg; e += stride) {
+    const int64_t n = e / ldg, c = e % ldg;
+    uint16_t b = 0;
+    if (c < n_out) {
+      const float d = Y[n * n_out + c] - T[n * n_out + c];
+      s += d * d * inv;
+      b = bf16_bits(2.f * d * inv);
+      GT[c * ldt + n] = b;
+    }
+    G[e] = b;
   }
+  const int64_t tail = N < 64 ? 64 - N : 0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tail * n_out; e += stride)
+    GT[(e / tail) * ldt + N + e % tail] = 0;
   for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
   if ((threadIdx.x & 31) == 0) atomicAdd(loss, s);
 }
 
-// db[m] = sum_n dZ[n][m]
-__global__ void k_colsum(int64_t N, int64_t M, const float* dZ, float* db) {
-  for (int64_t m = blockIdx.x; m < M; m += gridDim.x) {
+// db[c] = sum_{n < N} GT[c][n]
+__global__ void k_rowsum(int64_t N, int rows, const uint16_t* __restrict__ GT, int64_t ldt,
+                         float* db) {
+  __shared__ float ws[32];
+  for (int c = blockIdx.x; c < rows; c += gridDim.x) {
     float s = 0.f;
-    for (int64_t n = threadIdx.x; n < N; n += blockDim.x) s += dZ[n * M + m];
-    __shared__ float ws[32];
+    for (int64_t n = threadIdx.x; n < N; n += blockDim.x) s += bf16_val(GT[c * ldt + n]);
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
     if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
     __syncthreads();
     if (threadIdx.x < 32) {
       s = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.f;
       for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-      if (threadIdx.x == 0) db[m] = s;
+      if (threadIdx.x == 0) db[c] = s;
     }
     __syncthreads();
   }
 }
 
-// Adam on FP32 master weights; refreshes the BF16 copy
-__global__ void k_adam(int64_t n, float* w, const float* g, float* m1, float* m2, float lr, float b1,
-                       float b2, float eps, float c1, float c2, __nv_bfloat16* wb) {
+// out[e] = sum_z part[z][e] (the split partial sums of a weight gradient)
+__global__ void k_reduce(int splits, int64_t n, const float* __restrict__ part, float* out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int z = 0; z < splits; ++z) s += part[(int64_t)z * n + e];
+    out[e] = s;
+  }
+}
+
+// BF16 operand copies of W [din][dout]: Wt[o][i] (ld ldt) and Wk[i][o] (ld ldk)
+__device__ __forceinline__ void put_w(int64_t e, int dout, float w, uint16_t* Wt, int64_t ldt,
+                                      uint16_t* Wk, int64_t ldk) {
+  const int64_t i = e / dout, o = e % dout;
+  const uint16_t b = bf16_bits(w);
+  Wt[o * ldt + i] = b;
+  Wk[i * ldk + o] = b;
+}
+
+__global__ void k_refresh(int din, int dout, const float* W, uint16_t* Wt, int64_t ldt,
+                          uint16_t* Wk, int64_t ldk) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)din * dout;
+       e += (int64_t)gridDim.x * blockDim.x)
+    put_w(e, dout, W[e], Wt, ldt, Wk, ldk);
+}
+
+// Adam on FP32 master parameters; refreshes the BF16 operand copies of a weight
+// matrix (din > 0) or of nothing (biases: din = 0)
+__global__ void k_adam(int64_t n, int din, int dout, float* w, const float* g, float* m1, float* m2,
+                       float lr, float b1, float b2, float eps, float c1, float c2, uint16_t* Wt,
+                       int64_t ldt, uint16_t* Wk, int64_t ldk) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
     float gg = g[e];
@@ -163,14 +143,8 @@ __global__ void k_adam(int64_t n, float* w, const float* g, float* m1, float* m2
     m2[e] = b2 * m2[e] + (1.f - b2) * gg * gg;
     float mh = m1[e] / c1, vh = m2[e] / c2;
     w[e] -= lr * mh / (sqrtf(vh) + eps);
-    if (wb) wb[e] = __float2bfloat16(w[e]);
+    if (din > 0) put_w(e, dout, w[e], Wt, ldt, Wk, ldk);
   }
-}
-
-__global__ void k_to_bf16(int64_t n, const float* x, __nv_bfloat16* y) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x)
-    y[e] = __float2bfloat16(x[e]);
 }
 
 int grid1(int64_t n) {
@@ -183,127 +157,150 @@ void check(const char* what) {
   if (e != cudaSuccess) throw std::runtime_error(std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-template <typename TA, typename TB>
-void gemm(cudaStream_t st, int64_t M, int64_t N, int64_t K, float alpha, const TA* A, int64_t sam,
-          int64_t sak, const TB* B, int64_t sbk, int64_t sbn, float* C, int accumulate,
-          int64_t splits = 1) {
-  if (M == 0 || N == 0) return;
-  int64_t kc = (K + splits - 1) / splits;
-  kc = (kc + 15) / 16 * 16;
-  splits = (K + kc - 1) / kc;
-  if (splits < 1) splits = 1;
-  if (splits > 1 && !accumulate) cudaMemsetAsync(C, 0, sizeof(float) * M * N, st);
-  dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64), (unsigned)splits);
-  k_gemm_f32<TA, TB><<<grid, 256, 0, st>>>(M, N, K, kc, alpha, A, sam, sak, B, sbk, sbn, C,
-                                          accumulate);
-  check("mlp gemm");
-}
-
 }  // namespace
 
 struct sccsd_mlp {
   cudaStream_t st = nullptr;
+  std::unique_ptr<sccsd::TcGemm> tc;
   int n_in = 0, hidden = 0, layers = 0, n_out = 0;  // layers = number of Linear layers
   std::vector<int> din, dout;
+  std::vector<int64_t> din_p, dout_p, din_r, dout_r;  // padded to 64 (contraction) and 256 (rows)
   std::vector<float*> W, b, gW, gb, mW, vW, mb, vb;   // FP32 master, grads, Adam moments
-  std::vector<__nv_bfloat16*> Wb;                    // BF16 weights used by the kernels
-  int64_t cap = 0;                                   // rows the work buffers hold
-  std::vector<float*> Z;                             // pre-activations [cap][dout]
-  std::vector<__nv_bfloat16*> Act;                   // activations [cap][din] (Act[0] = input)
-  float *Y = nullptr, *dY = nullptr, *dA = nullptr, *dB = nullptr, *loss = nullptr;
+  std::vector<uint16_t*> Wt, Wk;                     // BF16 operand copies
+  int64_t cap = 0;                                   // rows the work buffers hold (multiple of 256)
+  bool cap_train = false;                            // transposed and gradient buffers present
+  std::vector<uint16_t*> A, AT, G, GT;               // per layer: input activations, output grads
+  float *Y = nullptr, *part = nullptr, *loss = nullptr;
+  size_t part_floats = 0;
   int64_t step = 0;
   std::string err;
+  void free_rows() {
+    for (auto* v : {&A, &AT, &G, &GT}) {
+      for (uint16_t* p : *v) cudaFree(p);
+      v->clear();
+    }
+    cudaFree(Y);
+    Y = nullptr;
+    cap = 0;
+    cap_train = false;
+  }
   ~sccsd_mlp() {
-    for (auto* v : {&W, &b, &gW, &gb, &mW, &vW, &mb, &vb, &Z})
+    free_rows();
+    for (auto* v : {&W, &b, &gW, &gb, &mW, &vW, &mb, &vb})
       for (float* p : *v) cudaFree(p);
-    for (auto* p : Wb) cudaFree(p);
-    for (auto* p : Act) cudaFree(p);
-    for (float* p : {Y, dY, dA, dB, loss}) cudaFree(p);
+    for (auto* v : {&Wt, &Wk})
+      for (uint16_t* p : *v) cudaFree(p);
+    cudaFree(part);
+    cudaFree(loss);
   }
 };
 
 namespace {
 
-float* falloc(int64_t n) {
+void* zalloc(size_t bytes) {
   void* p = nullptr;
-  if (cudaMalloc(&p, sizeof(float) * std::max<int64_t>(1, n)) != cudaSuccess) {
+  if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
     cudaGetLastError();
     throw std::runtime_error("mlp allocation failed");
   }
-  cudaMemset(p, 0, sizeof(float) * std::max<int64_t>(1, n));
-  return (float*)p;
-}
-
-__nv_bfloat16* balloc(int64_t n) {
-  void* p = nullptr;
-  if (cudaMalloc(&p, 2 * std::max<int64_t>(1, n)) != cudaSuccess) {
-    cudaGetLastError();
+  if (cudaMemset(p, 0, std::max<size_t>(bytes, 16)) != cudaSuccess)
     throw std::runtime_error("mlp allocation failed");
-  }
-  return (__nv_bfloat16*)p;
+  return p;
 }
+float* falloc(int64_t n) { return (float*)zalloc(sizeof(float) * (size_t)std::max<int64_t>(1, n)); }
+uint16_t* halloc(int64_t n) { return (uint16_t*)zalloc(2 * (size_t)std::max<int64_t>(1, n)); }
 
-void ensure_rows(sccsd_mlp* net, int64_t N) {
-  if (N <= net->cap) return;
-  for (float* p : net->Z) cudaFree(p);
-  for (auto* p : net->Act) cudaFree(p);
-  for (float* p : {net->Y, net->dY, net->dA, net->dB}) cudaFree(p);
-  net->Z.clear();
-  net->Act.clear();
-  int widest = net->n_in;
+// work buffers for N rows (transposed copies and gradients only for training)
+void ensure_rows(sccsd_mlp* net, int64_t N, bool train) {
+  if (N <= net->cap && (!train || net->cap_train)) return;
+  const int64_t cap = std::max(up(std::max<int64_t>(N, 1), 256), net->cap);
+  const bool tr = train || net->cap_train;
+  cudaStreamSynchronize(net->st);
+  net->free_rows();
   for (int l = 0; l < net->layers; ++l) {
-    net->Z.push_back(falloc(N * net->dout[l]));
-    net->Act.push_back(balloc(N * net->din[l]));
-    widest = std::max(widest, net->dout[l]);
+    net->A.push_back(halloc(cap * net->din_p[l]));
+    if (tr) {
+      net->AT.push_back(halloc(net->din_r[l] * cap));
+      net->G.push_back(halloc(cap * net->dout_p[l]));
+      net->GT.push_back(halloc(net->dout_r[l] * cap));
+    }
   }
-  net->Y = falloc(N * net->n_out);
-  net->dY = falloc(N * net->n_out);
-  net->dA = falloc(N * widest);
-  net->dB = falloc(N * widest);
-  net->cap = N;
+  net->Y = falloc(cap * net->n_out);
+  net->cap = cap;
+  net->cap_train = tr;
 }
 
 // forward pass for N rows of X (FP32 features, device); output in net->Y
-void forward(sccsd_mlp* net, const float* X, int64_t N) {
-  ensure_rows(net, N);
+void forward(sccsd_mlp* net, const float* X, int64_t N, bool train) {
+  ensure_rows(net, N, train);
   cudaStream_t st = net->st;
-  k_to_bf16<<<grid1(N * net->n_in), 256, 0, st>>>(N * net->n_in, X, net->Act[0]);
+  const int64_t cap = net->cap;
+  k_input<<<grid1(N * net->din_p[0]), 256, 0, st>>>(N, net->n_in, X, net->A[0], net->din_p[0],
+                                                    train ? net->AT[0] : nullptr, cap);
   check("mlp input");
   for (int l = 0; l < net->layers; ++l) {
-    const int K = net->din[l], M = net->dout[l];
-    gemm(st, N, M, K, 1.f, net->Act[l], (int64_t)K, (int64_t)1, net->Wb[l], (int64_t)M,
-         (int64_t)1, net->Z[l], 0);
     const bool last = l == net->layers - 1;
-    k_bias_act<<<grid1(N * M), 256, 0, st>>>(N, M, net->Z[l], net->b[l],
-                                               last ? nullptr : net->Act[l + 1],
-                                               last ? net->Y : nullptr, last ? 0 : 1);
-    check("mlp bias/act");
+    sccsd::MlpEpi e;
+    e.bias = net->b[l];
+    if (last) {
+      e.outf = net->Y;
+      e.ldf = net->n_out;
+    } else {
+      e.out = net->A[l + 1];
+      e.ldo = net->din_p[l + 1];
+      e.outT = train ? net->AT[l + 1] : nullptr;
+      e.ldt = cap;
+    }
+    net->tc->mlp_gemm(last ? sccsd::MLP_OUTPUT : sccsd::MLP_HIDDEN, net->A[l], cap, net->din_p[l],
+                      net->Wt[l], net->dout_r[l], net->din_p[l], N, net->dout[l], net->din[l], 1, e);
   }
 }
 
 // gradients of the MSE loss w.r.t. all parameters into gW/gb; returns loss
 float backward(sccsd_mlp* net, const float* T, int64_t N) {
   cudaStream_t st = net->st;
+  const int64_t cap = net->cap;
+  const int L = net->layers;
   cudaMemsetAsync(net->loss, 0, sizeof(float), st);
-  k_mse<<<grid1(N * net->n_out), 256, 0, st>>>(N * net->n_out, net->Y, T, net->dY, net->loss);
+  k_mse<<<grid1(N * net->dout_p[L - 1]), 256, 0, st>>>(N, net->n_out, net->Y, T, net->G[L - 1],
+                                                      net->dout_p[L - 1], net->GT[L - 1], cap,
+                                                      net->loss);
   check("mlp loss");
-  float* g = net->dY;  // gradient w.r.t. Z of the current layer
-  for (int l = net->layers - 1; l >= 0; --l) {
-    const int K = net->din[l], M = net->dout[l];
-    // dW = Act_l^T g  (K x M, reduction over N rows)
-    int64_t splits = std::max<int64_t>(1, std::min<int64_t>(256, N / 2048));
-    gemm(st, (int64_t)K, (int64_t)M, N, 1.f, net->Act[l], (int64_t)1, (int64_t)K, g, (int64_t)M,
-         (int64_t)1, net->gW[l], 0, splits);
-    k_colsum<<<std::min(M, 1024), 256, 0, st>>>(N, M, g, net->gb[l]);
-    check("mlp db");
+  for (int l = L - 1; l >= 0; --l) {
+    // dW_l = A_l^T G_l: a contraction over the N rows, split across CTAs
+    const int64_t base = ((net->din[l] + 127) / 128) * ((net->dout[l] + 255) / 256);
+    const int want = (int)std::max<int64_t>(1, net->tc->sm_count() / base);
+    const size_t need = (size_t)want * net->din[l] * net->dout[l];
+    if (net->part_floats < need) {
+      cudaStreamSynchronize(st);
+      cudaFree(net->part);
+      net->part = nullptr;
+      net->part_floats = 0;
+      net->part = falloc((int64_t)need);
+      net->part_floats = need;
+    }
+    sccsd::MlpEpi ep;
+    ep.outf = net->part;
+    ep.ldf = net->dout[l];
+    const int splits = net->tc->mlp_gemm(sccsd::MLP_PARTIAL, net->AT[l], net->din_r[l], cap,
+                                         net->GT[l], net->dout_r[l], cap, net->din[l],
+                                         net->dout[l], N, want, ep);
+    const int64_t nw = (int64_t)net->din[l] * net->dout[l];
+    k_reduce<<<grid1(nw), 256, 0, st>>>(splits, nw, net->part, net->gW[l]);
+    k_rowsum<<<std::min(net->dout[l], 1024), 256, 0, st>>>(N, net->dout[l], net->GT[l], cap,
+                                                          net->gb[l]);
+    check("mlp weight gradient");
     if (l > 0) {
-      // dAct_l = g W_l^T  (N x K), then through ReLU: multiply by [Z_{l-1} > 0]
-      float* dst = (g == net->dA) ? net->dB : net->dA;
-      gemm(st, N, (int64_t)K, (int64_t)M, 1.f, g, (int64_t)M, (int64_t)1, net->Wb[l], (int64_t)1,
-           (int64_t)M, dst, 0);
-      k_relu_back<<<grid1(N * K), 256, 0, st>>>(N * K, net->Z[l - 1], dst);
-      check("mlp relu back");
-      g = dst;
+      // G_{l-1} = (G_l W_l^T) * [A_l > 0]
+      sccsd::MlpEpi eb;
+      eb.out = net->G[l - 1];
+      eb.ldo = net->dout_p[l - 1];
+      eb.outT = net->GT[l - 1];
+      eb.ldt = cap;
+      eb.maskT = net->AT[l];
+      eb.ldm = cap;
+      net->tc->mlp_gemm(sccsd::MLP_RELU_BACK, net->G[l], cap, net->dout_p[l], net->Wk[l],
+                        net->din_r[l], net->dout_p[l], N, net->din[l], net->dout[l], 1, eb);
     }
   }
   float h = 0.f;
@@ -318,11 +315,18 @@ int mlp_guard(sccsd_mlp* net, F&& f) {
     f();
     cudaError_t e = cudaStreamSynchronize(net->st);
     if (e != cudaSuccess) throw std::runtime_error(cudaGetErrorString(e));
+    if (net->tc) net->tc->check_error();
     return SCCSD_OK;
   } catch (const std::exception& e) {
     if (net) net->err = e.what();
     return SCCSD_ECUDA;
   }
+}
+
+void refresh(sccsd_mlp* net, int l) {
+  k_refresh<<<grid1((int64_t)net->din[l] * net->dout[l]), 256, 0, net->st>>>(
+      net->din[l], net->dout[l], net->W[l], net->Wt[l], net->din_p[l], net->Wk[l], net->dout_p[l]);
+  check("mlp weights");
 }
 
 }  // namespace
@@ -349,20 +353,25 @@ int sccsd_mlp_create(sccsd_mlp** out, int n_in, int hidden, int n_hidden_layers,
       z ^= z >> 31;
       return (double)(z >> 11) * (1.0 / 9007199254740992.0);
     };
+    net->tc.reset(new sccsd::TcGemm(net->st, 0));
     for (int l = 0; l < net->layers; ++l) {
       int din = l == 0 ? n_in : hidden;
       int dout = l == net->layers - 1 ? n_out : hidden;
       net->din.push_back(din);
       net->dout.push_back(dout);
+      net->din_p.push_back(up(din, 64));
+      net->dout_p.push_back(up(dout, 64));
+      net->din_r.push_back(up(din, 256));
+      net->dout_r.push_back(up(dout, 256));
       std::vector<float> w((size_t)din * dout);
       double s = std::sqrt(6.0 / din);
       for (auto& x : w) x = (float)((2.0 * next() - 1.0) * s);
       float* W = falloc((int64_t)din * dout);
       cudaMemcpy(W, w.data(), sizeof(float) * w.size(), cudaMemcpyHostToDevice);
       net->W.push_back(W);
-      __nv_bfloat16* Wb = balloc((int64_t)din * dout);
-      k_to_bf16<<<grid1(din * dout), 256, 0, net->st>>>((int64_t)din * dout, W, Wb);
-      net->Wb.push_back(Wb);
+      net->Wt.push_back(halloc(net->dout_r[l] * net->din_p[l]));
+      net->Wk.push_back(halloc(net->din_r[l] * net->dout_p[l]));
+      refresh(net, l);
       net->b.push_back(falloc(dout));
       net->gW.push_back(falloc((int64_t)din * dout));
       net->gb.push_back(falloc(dout));
@@ -414,7 +423,7 @@ int sccsd_mlp_set_params(sccsd_mlp* net, const float* host_in) {
     for (int l = 0; l < net->layers; ++l) {
       int64_t nw = (int64_t)net->din[l] * net->dout[l];
       cudaMemcpy(net->W[l], host_in + off, sizeof(float) * nw, cudaMemcpyHostToDevice);
-      k_to_bf16<<<grid1(nw), 256, 0, net->st>>>(nw, net->W[l], net->Wb[l]);
+      refresh(net, l);
       off += nw;
       cudaMemcpy(net->b[l], host_in + off, sizeof(float) * net->dout[l], cudaMemcpyHostToDevice);
       off += net->dout[l];
@@ -427,7 +436,7 @@ int sccsd_mlp_forward(sccsd_mlp* net, const float* X, long long N, float* Y) {
   if (!net || !X || !Y || N < 0) return SCCSD_EINVAL;
   return mlp_guard(net, [&] {
     if (N == 0) return;
-    forward(net, X, N);
+    forward(net, X, N, false);
     cudaMemcpyAsync(Y, net->Y, sizeof(float) * N * net->n_out, cudaMemcpyDeviceToDevice, net->st);
   });
 }
@@ -438,7 +447,7 @@ int sccsd_mlp_gradient(sccsd_mlp* net, const float* X, const float* T, long long
                        float* loss) {
   if (!net || !X || !T || N < 1) return SCCSD_EINVAL;
   return mlp_guard(net, [&] {
-    forward(net, X, N);
+    forward(net, X, N, true);
     float l = backward(net, T, N);
     if (loss) *loss = l;
     if (grad) {
@@ -459,7 +468,7 @@ int sccsd_mlp_train_step(sccsd_mlp* net, const float* X, const float* T, long lo
                          float* loss) {
   if (!net || !X || !T || N < 1 || !(lr > 0.f)) return SCCSD_EINVAL;
   return mlp_guard(net, [&] {
-    forward(net, X, N);
+    forward(net, X, N, true);
     float l = backward(net, T, N);
     if (loss) *loss = l;
     net->step += 1;
@@ -467,11 +476,13 @@ int sccsd_mlp_train_step(sccsd_mlp* net, const float* X, const float* T, long lo
     const float c1 = 1.f - std::pow(b1, (float)net->step), c2 = 1.f - std::pow(b2, (float)net->step);
     for (int k = 0; k < net->layers; ++k) {
       int64_t nw = (int64_t)net->din[k] * net->dout[k];
-      k_adam<<<grid1(nw), 256, 0, net->st>>>(nw, net->W[k], net->gW[k], net->mW[k], net->vW[k], lr,
-                                              b1, b2, 1e-8f, c1, c2, net->Wb[k]);
-      k_adam<<<grid1(net->dout[k]), 256, 0, net->st>>>(net->dout[k], net->b[k], net->gb[k],
-                                                        net->mb[k], net->vb[k], lr, b1, b2, 1e-8f,
-                                                        c1, c2, nullptr);
+      k_adam<<<grid1(nw), 256, 0, net->st>>>(nw, net->din[k], net->dout[k], net->W[k], net->gW[k],
+                                              net->mW[k], net->vW[k], lr, b1, b2, 1e-8f, c1, c2,
+                                              net->Wt[k], net->din_p[k], net->Wk[k],
+                                              net->dout_p[k]);
+      k_adam<<<grid1(net->dout[k]), 256, 0, net->st>>>(net->dout[k], 0, net->dout[k], net->b[k],
+                                                        net->gb[k], net->mb[k], net->vb[k], lr, b1,
+                                                        b2, 1e-8f, c1, c2, nullptr, 0, nullptr, 0);
     }
     check("mlp adam");
   });

@@ -132,16 +132,69 @@ __device__ __forceinline__ TcItem tc_item(int64_t w, int64_t mt, int64_t nt, int
   return r;
 }
 
+__device__ __forceinline__ bool bf16_positive(uint16_t u) { return (u & 0x8000u) == 0 && u != 0; }
+
+// Epilogue of one 32-column chunk of a learned-part layer (MODE = MlpMode):
+// thread `lane` of the warp holds row `row` of the tile, columns cb .. cb + 31
+// in r. Rows past M write only zeros into the transposed output, so that a
+// later contraction over rows reads zeros there.
+template <int MODE>
+__device__ __forceinline__ void mlp_chunk(const MlpEpi& e, int64_t row, int64_t M, int64_t cb,
+                                          int64_t N, int z, int64_t split_stride,
+                                          const uint32_t* r) {
+  if constexpr (MODE == MLP_HIDDEN || MODE == MLP_RELU_BACK) {
+    const bool rv = row < M;
+    uint32_t pk[16];
+#pragma unroll
+    for (int j = 0; j < 32; j += 2) {
+      const int64_t c0 = cb + j, c1 = cb + j + 1;
+      float x0 = __uint_as_float(r[j]), x1 = __uint_as_float(r[j + 1]);
+      if constexpr (MODE == MLP_HIDDEN) {
+        x0 = c0 < N ? fmaxf(x0 + e.bias[c0], 0.f) : 0.f;
+        x1 = c1 < N ? fmaxf(x1 + e.bias[c1], 0.f) : 0.f;
+      } else {
+        x0 = (rv && c0 < N && bf16_positive(e.maskT[c0 * e.ldm + row])) ? x0 : 0.f;
+        x1 = (rv && c1 < N && bf16_positive(e.maskT[c1 * e.ldm + row])) ? x1 : 0.f;
+      }
+      if (!rv) x0 = x1 = 0.f;
+      __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+      pk[j / 2] = *reinterpret_cast<const uint32_t*>(&h);
+      if (e.outT) {
+        if (c0 < N) e.outT[c0 * e.ldt + row] = (uint16_t)(pk[j / 2] & 0xFFFFu);
+        if (c1 < N) e.outT[c1 * e.ldt + row] = (uint16_t)(pk[j / 2] >> 16);
+      }
+    }
+    if (rv && e.out) {
+      uint4* dst = reinterpret_cast<uint4*>(e.out + row * e.ldo + cb);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        dst[k] = make_uint4(pk[4 * k], pk[4 * k + 1], pk[4 * k + 2], pk[4 * k + 3]);
+    }
+  } else if constexpr (MODE == MLP_OUTPUT) {
+    if (row >= M) return;
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (cb + j < N) e.outf[row * e.ldf + cb + j] = __uint_as_float(r[j]) + e.bias[cb + j];
+  } else {
+    if (row >= M) return;
+    float* p = e.outf + (int64_t)z * split_stride + row * e.ldf;
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (cb + j < N) p[cb + j] = __uint_as_float(r[j]);
+  }
+}
+
 // NST pipeline stages; EW = 4 or 8 epilogue warps (with 8, two groups of four
 // each own one TMEM accumulator and take alternate items: more stores in
-// flight for the epilogue-bound short-K contractions)
-template <int NST, int EW>
+// flight for the epilogue-bound short-K contractions). MODE 0 writes FP64
+// through the output view; MODE 1..4 are the learned part's epilogues.
+template <int NST, int EW, int MODE = 0>
 __global__ void __launch_bounds__((EW + 2) * 32, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               int64_t M, int64_t N, int64_t mt, int64_t nt, int nfast, int64_t items, int nk_total,
               int kbs,
               double alpha, double* __restrict__ C, int64_t split_stride, const OutView ov,
-              int accumulate, int* err) {
+              int accumulate, int* err, const MlpEpi mep) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
@@ -299,7 +352,7 @@ __global__ void __launch_bounds__((EW + 2) * 32, 1)
         *abort_flag = 1;
         break;
       }
-      {
+      if constexpr (MODE == 0) {
         const int64_t row = it.m0 + q * 32 + lane;
         roff[lane] = row < M ? out_row(ov, row) : -1;
       }
@@ -322,6 +375,10 @@ __global__ void __launch_bounds__((EW + 2) * 32, 1)
               "=r"(r[30]), "=r"(r[31])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if constexpr (MODE != 0) {
+          mlp_chunk<MODE>(mep, it.m0 + q * 32 + lane, M, it.n0 + c0, N, it.z, split_stride, r);
+          continue;
+        }
         {
           // output offsets of this chunk's 32 columns, one per lane
           const int64_t col = it.n0 + c0 + lane;
@@ -854,6 +911,29 @@ CUtensorMap make_map(const void* base, int64_t rows_pad, int64_t k_pad, int box_
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+// row-major BF16 [rows][ld] with the contraction index K (extent k_ext) fastest
+CUtensorMap make_map_ld(const void* base, int64_t rows, int64_t k_ext, int64_t ld, int box_rows) {
+  CUtensorMap m;
+  cuuint64_t dims[2] = {(cuuint64_t)k_ext, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+                           strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw CudaError("cuTensorMapEncodeTiled failed: " + std::to_string(r));
+  return m;
+}
+
+template <int MODE>
+void set_mlp_smem() {
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<4, 4, MODE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       smem_bytes(4, 4));
+  if (e != cudaSuccess) throw CudaError(std::string("tc smem attribute: ") + cudaGetErrorString(e));
+}
+
 }  // namespace
 
 TcGemm::TcGemm(cudaStream_t st, int precision) : st_(st) {
@@ -872,6 +952,61 @@ TcGemm::TcGemm(cudaStream_t st, int precision) : st_(st) {
     e = cudaFuncSetAttribute(k_tc_gemm<3, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              smem_bytes(3, 8));
   if (e != cudaSuccess) throw CudaError(std::string("tc smem attribute: ") + cudaGetErrorString(e));
+  set_mlp_smem<MLP_HIDDEN>();
+  set_mlp_smem<MLP_OUTPUT>();
+  set_mlp_smem<MLP_RELU_BACK>();
+  set_mlp_smem<MLP_PARTIAL>();
+}
+
+int TcGemm::mlp_gemm(int mode, const void* A, int64_t a_rows, int64_t lda, const void* B,
+                     int64_t b_rows, int64_t ldb, int64_t M, int64_t N, int64_t K, int splits,
+                     const MlpEpi& e) {
+  if (M < 1 || N < 1 || K < 1 || a_rows < round_up(M, BM) || b_rows < round_up(N, BN) ||
+      lda % 8 || ldb % 8 || lda < std::max<int64_t>(K, BK) || ldb < std::max<int64_t>(K, BK))
+    throw std::runtime_error("mlp_gemm: bad operand shape");
+  if (mode != MLP_PARTIAL) splits = 1;
+  // K >= 64: the map's extent is K and TMA reads zeros past it; K < 64: the
+  // caller has zeroed columns K .. 63
+  const int64_t k_ext = std::max<int64_t>(K, BK);
+  CUtensorMap ma = make_map_ld(A, a_rows, k_ext, lda, BM);
+  CUtensorMap mb = make_map_ld(B, b_rows, k_ext, ldb, BN);
+  const int64_t mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
+  const int nk = (int)((k_ext + BK - 1) / BK);
+  splits = std::max(1, std::min(splits, nk));
+  const int kbs = (nk + splits - 1) / splits;
+  splits = (nk + kbs - 1) / kbs;
+  const int64_t items = mt * nt * splits;
+  const int grid = (int)std::min<int64_t>(items, sm_count_);
+  const int64_t split_stride = M * e.ldf;
+  const size_t sm = smem_bytes(4, 4);
+  switch (mode) {
+    case MLP_HIDDEN:
+      k_tc_gemm<4, 4, MLP_HIDDEN><<<grid, 192, sm, st_>>>(ma, mb, M, N, mt, nt, 0, items, nk, kbs,
+                                                          1.0, nullptr, split_stride, OutView(),
+                                                          0, d_err_, e);
+      break;
+    case MLP_OUTPUT:
+      k_tc_gemm<4, 4, MLP_OUTPUT><<<grid, 192, sm, st_>>>(ma, mb, M, N, mt, nt, 0, items, nk, kbs,
+                                                          1.0, nullptr, split_stride, OutView(),
+                                                          0, d_err_, e);
+      break;
+    case MLP_RELU_BACK:
+      k_tc_gemm<4, 4, MLP_RELU_BACK><<<grid, 192, sm, st_>>>(ma, mb, M, N, mt, nt, 0, items, nk,
+                                                             kbs, 1.0, nullptr, split_stride,
+                                                             OutView(), 0, d_err_, e);
+      break;
+    case MLP_PARTIAL:
+      k_tc_gemm<4, 4, MLP_PARTIAL><<<grid, 192, sm, st_>>>(ma, mb, M, N, mt, nt, 0, items, nk,
+                                                           kbs, 1.0, nullptr, split_stride,
+                                                           OutView(), 0, d_err_, e);
+      break;
+    default:
+      throw std::runtime_error("mlp_gemm: unknown epilogue");
+  }
+  count_launch();
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) throw CudaError(std::string("mlp_gemm launch: ") + cudaGetErrorString(err));
+  return splits;
 }
 
 TcGemm::~TcGemm() {
@@ -961,11 +1096,11 @@ void TcGemm::run(const TcOperand& A, int sa, const TcOperand& B, int sb, int64_t
   if (variant == 1)
     k_tc_gemm<3, 8><<<grid, 320, smem_bytes(3, 8), st_>>>(ma, mb, M, N, mt, nt, nfast, items, nk,
                                                           kbs, alpha, C, split_stride, ov,
-                                                          accumulate ? 1 : 0, d_err_);
+                                                          accumulate ? 1 : 0, d_err_, MlpEpi());
   else
     k_tc_gemm<4, 4><<<grid, 192, smem_bytes(4, 4), st_>>>(ma, mb, M, N, mt, nt, nfast, items, nk,
                                                           kbs, alpha, C, split_stride, ov,
-                                                          accumulate ? 1 : 0, d_err_);
+                                                          accumulate ? 1 : 0, d_err_, MlpEpi());
   count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw CudaError(std::string("tc_gemm launch: ") + cudaGetErrorString(e));

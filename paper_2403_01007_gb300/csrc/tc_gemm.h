@@ -27,6 +27,27 @@ struct TcOperand {
   size_t bytes = 0;
 };
 
+// Epilogue of the learned part's layers (mlp_gemm below): BF16 activations
+// and gradients, FP32 outputs, all dense row-major with the given leading
+// dimensions (elements).
+enum MlpMode {
+  MLP_HIDDEN = 1,   // out = relu(acc + bias) as BF16 in out[row][col] and outT[col][row]
+  MLP_OUTPUT = 2,   // outf[row][col] = acc + bias (FP32)
+  MLP_RELU_BACK = 3,// out = acc where maskT[col][row] > 0, else 0; BF16 in out and outT
+  MLP_PARTIAL = 4,  // outf[z][row][col] = acc of K split z (FP32, split stride rows * ldf)
+};
+struct MlpEpi {
+  const float* bias = nullptr;
+  uint16_t* out = nullptr;          // BF16 bits; may be null (modes 1, 3)
+  int64_t ldo = 0;
+  uint16_t* outT = nullptr;         // BF16 bits, transposed; may be null (modes 1, 3)
+  int64_t ldt = 0;
+  const uint16_t* maskT = nullptr;  // BF16 bits, transposed activations (mode 3)
+  int64_t ldm = 0;
+  float* outf = nullptr;            // modes 2, 4
+  int64_t ldf = 0;
+};
+
 class TcGemm {
  public:
   TcGemm(cudaStream_t st, int precision);
@@ -68,6 +89,17 @@ class TcGemm {
   // K = v (v + 1) / 2 packed (c <= d)); see k_ladder_build
   void ladder_build(const TcOperand& Lt, int v, const int* pairs, int64_t p_begin,
                     int64_t npairs, TcOperand& Gp, TcOperand& Gm);
+  // One layer product of the learned part, C[M][N] = sum_k A[m][k] B[n][k],
+  // with A and B BF16 row-major (leading dimensions lda, ldb elements, a
+  // multiple of 8) holding a_rows >= M and b_rows >= N allocated rows, and the
+  // epilogue `mode` (MlpMode). Contraction columns at or past K are read as
+  // zero when K >= 64; for K < 64 columns K .. 63 must hold zeros. `splits`
+  // splits K over more CTAs (mode MLP_PARTIAL only); returns the split count
+  // used.
+  int mlp_gemm(int mode, const void* A, int64_t a_rows, int64_t lda, const void* B,
+               int64_t b_rows, int64_t ldb, int64_t M, int64_t N, int64_t K, int splits,
+               const MlpEpi& e);
+  int sm_count() const { return sm_count_; }
   int slices() const { return nslices_; }
   void set_precision(int precision) { nslices_ = precision == 1 ? 2 : 1; }
 
