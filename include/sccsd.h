@@ -199,6 +199,37 @@ int sccsd_solve_scc(sccsd_ctx* ctx, double tol, int maxit, double ground_tol, do
                     double* zeta, double* e_corr, double* omega2, double* r0_2, double* Ra,
                     double* Rb, int* iterations);
 
+/* More than two constrained states (Sec. 2.2 with K = {1..n}; the X3 form of
+ * Sec. 2.4.1 for every pair). The cluster operator is
+ *   T + sum_{k<l} zeta_kl X_kl,   X_kl = R1^k R2^l - R1^l R2^k,
+ * for n >= 2 packed kets R[n][dim] (host or device) and zeta[n(n-1)/2] (host)
+ * in the pair order (0,1), (0,2), ..., (0,n-1), (1,2), ... Only
+ * sum_{k<l} zeta_kl <mu~|[Hhat, X_kl]|HF> reaches omega; E0 is unchanged.
+ * With n = 2 this is sccsd_residual with (zeta, Ra, Rb) = (zeta_01, R_0, R_1).
+ * sccsd_residual_states fixes (t, the states) like sccsd_residual: the
+ * transformations, densities and overlaps that follow use it. Errors:
+ * SCCSD_EINVAL for n < 2, NULL arguments or a non-finite zeta. */
+int sccsd_residual_states(sccsd_ctx* ctx, const double* t, int nstates, const double* zeta,
+                          const double* R, double* omega, double* e_corr);
+/* The ground state with the X3 terms of n states (otherwise as
+ * sccsd_solve_ground, including refinement in a mixed precision). */
+int sccsd_solve_ground_states(sccsd_ctx* ctx, const double* t0, int nstates, const double* zeta,
+                              const double* R, double tol, int maxit, double refine_tol,
+                              double* t_out, double* e_corr, int* iterations);
+/* Self-consistent SCCSD for the nstates (2..8) lowest states: zeta_kl for
+ * every pair solves O_kl = 0 (natural projection) by Broyden's method from
+ * zeta = 0 (plain CCSD) with the unit matrix as the first Jacobian estimate;
+ * at every zeta the ground state (ground_tol) and the n lowest right roots
+ * (eom_tol, unit norm, largest component positive) are re-converged.
+ * Converged when max |O_kl| < tol and the last zeta step is below 1e-8.
+ * Outputs (may be NULL): zeta and O [n(n-1)/2], e_corr, omega [n], r0 [n],
+ * R [n][dim] (host or device), iterations. SCCSD_EINVAL with the state
+ * projection set (sccsd_set_projection). Afterwards the fixed state is that of
+ * the last zeta. */
+int sccsd_solve_scc_states(sccsd_ctx* ctx, int nstates, double tol, int maxit, double ground_tol,
+                           double eom_tol, double* zeta, double* O, double* e_corr, double* omega,
+                           double* r0, double* R, int* iterations);
+
 /* Switch the precision of the tensor-core-eligible contractions for later
  * calls (SCCSD_FP64 / SCCSD_BF16X3 / SCCSD_BF16). An implementation choice: the
  * paper's program is FP64 throughout. SCCSD_EINVAL for another value. */

@@ -70,6 +70,15 @@ def _declare(lib):
     lib.sccsd_solve_scc.argtypes = [_dp, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
     lib.sccsd_solve_scc.restype = ctypes.c_int
+    lib.sccsd_residual_states.argtypes = [_dp, _dp, ctypes.c_int, _dp, _dp, _dp, _dp]
+    lib.sccsd_residual_states.restype = ctypes.c_int
+    lib.sccsd_solve_ground_states.argtypes = [_dp, _dp, ctypes.c_int, _dp, _dp, ctypes.c_double,
+                                              ctypes.c_int, ctypes.c_double, _dp, _dp, _dp]
+    lib.sccsd_solve_ground_states.restype = ctypes.c_int
+    lib.sccsd_solve_scc_states.argtypes = [_dp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                           ctypes.c_double, ctypes.c_double, _dp, _dp, _dp, _dp,
+                                           _dp, _dp, _dp]
+    lib.sccsd_solve_scc_states.restype = ctypes.c_int
     # The MLP entry points live in their own translation unit (mlp.cu), which
     # the host test double links without; every entry point the library
     # exports gets its signature (the export test checks that the product
@@ -465,6 +474,45 @@ class Context:
                                              ctypes.addressof(it)))
         return {"zeta": z.value, "e_corr": e.value, "omega": w, "r0": r0, "Ra": Ra, "Rb": Rb,
                 "iterations": it.value}
+
+    def residual_states(self, t, zeta, R, omega=None):
+        """(e_corr, omega) with the X3 terms of several constrained states:
+        zeta[n(n-1)/2] in the pair order (0,1), (0,2), ..., (1,2), ...; R[n][dim]."""
+        if omega is None:
+            omega = np.empty(self.dim)
+        z = np.ascontiguousarray(zeta, dtype=np.float64)
+        R = R if hasattr(R, "data_ptr") else np.ascontiguousarray(R, dtype=np.float64)
+        e = ctypes.c_double()
+        self._check(self.lib.sccsd_residual_states(self.h, _ptr(t), int(R.shape[0]), _ptr(z),
+                                                   _ptr(R), _ptr(omega), ctypes.addressof(e)))
+        return e.value, omega
+
+    def solve_ground_states(self, zeta, R, t0=None, tol=1e-10, maxit=200, refine_tol=1e-4):
+        """Ground state with the X3 terms of several states; (e_corr, t, iterations)."""
+        t_out = np.empty(self.dim)
+        z = np.ascontiguousarray(zeta, dtype=np.float64)
+        R = R if hasattr(R, "data_ptr") else np.ascontiguousarray(R, dtype=np.float64)
+        e, it = ctypes.c_double(), ctypes.c_int()
+        self._check(self.lib.sccsd_solve_ground_states(
+            self.h, _ptr(t0), int(R.shape[0]), _ptr(z), _ptr(R), float(tol), int(maxit),
+            float(refine_tol), _ptr(t_out), ctypes.addressof(e), ctypes.addressof(it)))
+        return e.value, t_out, it.value
+
+    def solve_scc_states(self, nstates, tol=1e-10, maxit=60, ground_tol=1e-11, eom_tol=1e-9):
+        """Self-consistent SCCSD for the nstates lowest states (one zeta per
+        pair, Broyden); returns a dict."""
+        npair = nstates * (nstates - 1) // 2
+        z, O = np.empty(npair), np.empty(npair)
+        w, r0 = np.empty(nstates), np.empty(nstates)
+        R = np.empty((nstates, self.dim))
+        e, it = ctypes.c_double(), ctypes.c_int()
+        self._check(self.lib.sccsd_solve_scc_states(
+            self.h, int(nstates), float(tol), int(maxit), float(ground_tol), float(eom_tol),
+            z.ctypes.data, O.ctypes.data, ctypes.addressof(e), w.ctypes.data, r0.ctypes.data,
+            R.ctypes.data, ctypes.addressof(it)))
+        pairs = [(k, l) for k in range(nstates) for l in range(k + 1, nstates)]
+        return {"zeta": dict(zip(pairs, z.tolist())), "O": dict(zip(pairs, O.tolist())),
+                "e_corr": e.value, "omega": w, "r0": r0, "R": R, "iterations": it.value}
 
     def learned_features(self, X):
         """Features [o^2 v^2][10] (device float32) at the MP2 amplitudes; returns scales."""

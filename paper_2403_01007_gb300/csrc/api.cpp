@@ -11,6 +11,31 @@ using namespace sccsd;
 
 namespace sccsd {
 
+Model& model_states(sccsd_ctx* c, int n) {
+  if (c->multi && c->multi_n != n) {
+    if (c->cur == c->multi.get()) c->cur = nullptr;
+    c->multi.reset();
+    c->multi_set = false;
+  }
+  if (!c->multi) {
+    c->multi = build_model(c->be.get(), c->o, c->v, c->J, false, n);
+    c->multi_n = n;
+    Model* m = c->multi.get();
+    m->g.trace = getenv("SCCSD_TRACE") != nullptr;
+    m->g.set_input(m->L, c->L, true);
+    m->g.set_input(m->h, c->h, true);
+    m->g.set_input(m->delta, c->delta, true);
+    double* z = m->g.t[m->t2zero].data;
+    if (!z) {
+      m->g.t[m->t2zero].data = c->be->alloc(m->g.t[m->t2zero].numel());
+      z = m->g.t[m->t2zero].data;
+    }
+    c->be->fill(z, m->g.t[m->t2zero].numel(), 0.0);
+    m->g.touch(m->t2zero);
+  }
+  return *c->multi;
+}
+
 Model& model(sccsd_ctx* c, bool scc) {
   std::unique_ptr<Model>& m = scc ? c->scc : c->plain;
   if (!m) {

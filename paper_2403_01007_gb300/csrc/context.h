@@ -82,6 +82,9 @@ struct Model {
   int t1, t2, L, h, delta;
   int R1, R2, Lb1, Lb2;
   int zeta = -1, Ra1 = -1, Ra2 = -1, Rb1 = -1, Rb2 = -1, t2zero = -1;
+  // several constrained states: one (R1^k, Y2^k) input pair per state
+  int nslots = 0;
+  std::vector<int> X1s, Y2s;
   int s_l0r0, s_l0, s_r0;
   EnergyResidual er;
   int sig1, sig2, etaR;
@@ -94,7 +97,9 @@ struct Model {
   std::unique_ptr<OvlGradSec> ovg;
 };
 
-std::unique_ptr<Model> build_model(Backend* be, int o, int v, int J, bool scc);
+// scc: the two-state X3 terms (zeta, Ra, Rb); nslots > 0 (with scc false):
+// the X3 terms of nslots constrained states
+std::unique_ptr<Model> build_model(Backend* be, int o, int v, int J, bool scc, int nslots = 0);
 // lazily built graph sections (model.cpp)
 OverlapSec& overlap_section(Model& M);
 OverlapKSec& overlap_k_section(Model& M);
@@ -133,6 +138,9 @@ struct sccsd_ctx {
   int64_t dim = 0;
   std::unique_ptr<sccsd::Backend> be;
   std::unique_ptr<sccsd::Model> plain, scc;
+  std::unique_ptr<sccsd::Model> multi;  // several constrained states (built for multi_n states)
+  int multi_n = 0;
+  bool multi_set = false;  // the packed (R1^k, Y2^k) of the multi-state X3 terms are loaded
   sccsd::Model* cur = nullptr;
   double* L = nullptr;      // device copy of the Cholesky vectors
   double* h = nullptr;      // device one-electron integrals
@@ -154,11 +162,12 @@ struct sccsd_ctx {
   std::string err;
   ~sccsd_ctx() {
     if (getenv("SCCSD_TRACE")) {
-      for (sccsd::Model* m : {plain.get(), scc.get()})
+      for (sccsd::Model* m : {plain.get(), scc.get(), multi.get()})
         if (m) fprintf(stderr, "%s", m->g.trace_report(std::max(60, atoi(getenv("SCCSD_TRACE")))).c_str());
     }
     plain.reset();
     scc.reset();
+    multi.reset();
     if (be) {
       for (double* p : {L, h, delta, stage, stage2, eps_dev, D, Dprec, sv_small})
         if (p) be->release(p);
@@ -200,6 +209,8 @@ int guarded(sccsd_ctx* c, F&& f) {
 
 // marshalling between packed vectors (host or device) and graph tensors (api.cpp)
 Model& model(sccsd_ctx* c, bool scc);
+// the model of n constrained states (rebuilt when n changes)
+Model& model_states(sccsd_ctx* c, int n);
 double* input_buffer(Graph& g, int id);
 void load_packed(sccsd_ctx* c, Graph& g, const double* src, int x1, int x2, bool bra);
 void load_packed_batch(sccsd_ctx* c, Graph& g, const double* src, int64_t nb, int x1, int x2,
@@ -245,8 +256,16 @@ struct Dev {
 double* solver_buf(sccsd_ctx* c, size_t i, int64_t n);
 void ensure_small(sccsd_ctx* c);
 void switch_precision(sccsd_ctx* c, int p);
+// E0 and packed omega at t; with multi the X3 terms of the states set by
+// set_states, else those of (zeta, Ra, Rb) when Ra is given
 double eval_residual(sccsd_ctx* c, const double* t, double zeta, const double* Ra,
-                     const double* Rb, double* om);
+                     const double* Rb, double* om, bool multi = false);
+// the X3 terms of n states R[n][dim] (host or device) with zeta_kl, k < l, in
+// the order (0,1), (0,2), ..., (1,2), ...: packed P_k = (R1^k, sum_l Z_kl R2^l)
+void set_states(sccsd_ctx* c, int n, const double* zeta, const double* R);
+int solve_ground_impl(sccsd_ctx* c, const double* t0, double zeta, const double* Ra,
+                      const double* Rb, bool multi, double tol, int maxit, double refine_tol,
+                      double* t_out, double* e_corr, int* iterations);
 void transform(sccsd_ctx* c, int side, int nvec, const double* V, double* W);
 
 }  // namespace sccsd

@@ -11,7 +11,7 @@ static int node_or_zero(Graph& g, const std::map<int, int>& m, int id) {
   return it != m.end() ? it->second : g.zero(g.t[id].dims);
 }
 
-std::unique_ptr<Model> build_model(Backend* be, int o, int v, int J, bool scc) {
+std::unique_ptr<Model> build_model(Backend* be, int o, int v, int J, bool scc, int nslots) {
   auto M = std::make_unique<Model>();
   Graph& g = M->g;
   g.be = be;
@@ -51,6 +51,27 @@ std::unique_ptr<Model> build_model(Backend* be, int o, int v, int J, bool scc) {
     M->er.O1 = g.add("ai", {{M->er.O1, "ai", 1.0}, {g.contract(M->zeta, "", d1, "ai", "ai"), "ai", 1.0}});
     M->er.O2 = g.add("ijab", {{M->er.O2, "ijab", 1.0},
                               {g.contract(M->zeta, "", d2, "ijab", "ijab"), "ijab", 1.0}});
+  } else if (nslots > 0) {
+    // several constrained states: sum_{k<l} zeta_kl X_kl = sum_k R1^k Y2^k with
+    // Y2^k = sum_l Z_kl R2^l (Z antisymmetric), so the X3 terms are a sum of
+    // one bilinear term per state; the inputs are (R1^k, Y2^k)
+    M->nslots = nslots;
+    M->t2zero = g.input({o, o, v, v}, "t2zero");
+    size_t p0 = g.ops.size();
+    EnergyResidual er0 = build_energy_residual(g, M->t1, M->t2zero, M->L, M->h, M->delta);
+    Graph::Ranges r0 = {{p0, g.ops.size()}};
+    std::vector<Graph::Term> s1 = {{M->er.O1, "ai", 1.0}}, s2 = {{M->er.O2, "ijab", 1.0}};
+    for (int k = 0; k < nslots; ++k) {
+      const int x1 = g.input({v, o}, "X1_" + std::to_string(k));
+      const int y2 = g.input({o, o, v, v}, "Y2_" + std::to_string(k));
+      M->X1s.push_back(x1);
+      M->Y2s.push_back(y2);
+      Xi xk = build_xi(g, M->t1, M->t2zero, er0, r0, x1, y2);
+      s1.push_back({xk.X1, "ai", 1.0});
+      s2.push_back({xk.X2, "ijab", 1.0});
+    }
+    M->er.O1 = g.add("ai", s1);
+    M->er.O2 = g.add("ijab", s2);
   }
   Graph::Ranges fwd = {{0, g.ops.size()}};
   M->fwd = fwd;

@@ -33,13 +33,51 @@ void ensure_small(sccsd_ctx* c) {
 void switch_precision(sccsd_ctx* c, int p) {
   if (c->be->get_precision() == p) return;
   c->be->set_precision(p);
-  for (Model* m : {c->plain.get(), c->scc.get()})
+  for (Model* m : {c->plain.get(), c->scc.get(), c->multi.get()})
     if (m) m->g.invalidate();
+}
+
+void set_states(sccsd_ctx* c, int n, const double* zeta, const double* R) {
+  if (n < 2) throw std::invalid_argument("at least two constrained states");
+  if (!zeta || !R) throw std::invalid_argument("zeta or R is NULL");
+  const int np = n * (n - 1) / 2;
+  for (int p = 0; p < np; ++p)
+    if (!std::isfinite(zeta[p])) throw std::invalid_argument("zeta is not finite");
+  const int64_t dim = c->dim, ov = (int64_t)c->o * c->v;
+  Dev d{c};
+  Model& m = model_states(c, n);
+  double* Rd = solver_buf(c, 90, n * dim);
+  c->be->upload(Rd, R, n * dim, c->be->is_device(R));
+  // coef[l][k] = Z_kl with Z antisymmetric, Z_kl = zeta_kl for k < l
+  std::vector<double> coef((size_t)n * n, 0.0);
+  int p = 0;
+  for (int k = 0; k < n; ++k)
+    for (int l = k + 1; l < n; ++l, ++p) {
+      coef[(size_t)l * n + k] = zeta[p];
+      coef[(size_t)k * n + l] = -zeta[p];
+    }
+  double* cd = solver_buf(c, 91, (int64_t)n * n);
+  c->be->upload(cd, coef.data(), (int64_t)n * n, false);
+  // P_k = (R1^k, sum_l Z_kl R2^l): the doubles of the combination, the singles of R^k
+  double* P = solver_buf(c, 92, n * dim);
+  d.combine(n, n, cd, Rd, P);
+  for (int k = 0; k < n; ++k) d.copy(P + k * dim, Rd + k * dim, ov);
+  for (int k = 0; k < n; ++k) load_packed(c, m.g, P + k * dim, m.X1s[k], m.Y2s[k], false);
+  c->multi_set = true;
 }
 
 // E0 and packed omega (device) at packed amplitudes t (device)
 double eval_residual(sccsd_ctx* c, const double* t, double zeta, const double* Ra,
-                     const double* Rb, double* om) {
+                     const double* Rb, double* om, bool multi) {
+  if (multi) {
+    if (!c->multi || !c->multi_set) throw std::logic_error("no constrained states set");
+    Model& m = *c->multi;
+    load_packed(c, m.g, t, m.t1, m.t2, false);
+    c->cur = &m;
+    m.g.run({m.er.E0, m.er.O1, m.er.O2});
+    store_packed(c, m.g, m.er.O1, m.er.O2, om, false);
+    return get_scalar(c, m.g, m.er.E0);
+  }
   const bool scc = Ra != nullptr;
   Model& m = model(c, scc);
   load_packed(c, m.g, t, m.t1, m.t2, false);
@@ -81,8 +119,17 @@ int sccsd_solve_ground(sccsd_ctx* c, const double* t0, double zeta, const double
                        const double* Rb, double tol, int maxit, double refine_tol, double* t_out,
                        double* e_corr, int* iterations) {
   if (!c) return SCCSD_EINVAL;
-  if (!(tol > 0.0) || maxit < 1) return fail(c, SCCSD_EINVAL, "bad tolerance or iteration limit");
   if ((Ra == nullptr) != (Rb == nullptr)) return fail(c, SCCSD_EINVAL, "give both Ra and Rb or neither");
+  return solve_ground_impl(c, t0, zeta, Ra, Rb, false, tol, maxit, refine_tol, t_out, e_corr,
+                           iterations);
+}
+
+}  // extern "C"
+
+int sccsd::solve_ground_impl(sccsd_ctx* c, const double* t0, double zeta, const double* Ra,
+                             const double* Rb, bool multi, double tol, int maxit,
+                             double refine_tol, double* t_out, double* e_corr, int* iterations) {
+  if (!(tol > 0.0) || maxit < 1) return fail(c, SCCSD_EINVAL, "bad tolerance or iteration limit");
   int status = SCCSD_OK;
   int rc = guarded(c, [&] {
     Dev d{c};
@@ -129,7 +176,7 @@ int sccsd_solve_ground(sccsd_ctx* c, const double* t0, double zeta, const double
     double gate = 1e300;
     int next_refresh = 3;
     for (it = 1; it <= maxit; ++it) {
-      E = eval_residual(c, t, zeta, ra, rb, om);
+      E = eval_residual(c, t, zeta, ra, rb, om, multi);
       nrm = std::sqrt(d.dot(om, om, dim));
       if (getenv("SCCSD_LOG"))
         fprintf(stderr, "{\"solver\": \"ground\", \"iter\": %d, \"fp64\": %d, \"residual\": %.3e, \"e_corr\": %.12f}\n", it,
@@ -166,7 +213,7 @@ int sccsd_solve_ground(sccsd_ctx* c, const double* t0, double zeta, const double
         bool done = false, worse = false;
         for (int round = 0; round < 12 && !done; ++round) {
           switch_precision(c, SCCSD_FP64);
-          E = eval_residual(c, t, zeta, ra, rb, rr);
+          E = eval_residual(c, t, zeta, ra, rb, rr, multi);
           const double rn = std::sqrt(d.dot(rr, rr, dim));
           switch_precision(c, pc);
           ++refine_fp64_evals;
@@ -199,7 +246,7 @@ int sccsd_solve_ground(sccsd_ctx* c, const double* t0, double zeta, const double
           }
           prev = rn;
           // the mixed state at t for the Jacobian transforms
-          eval_residual(c, t, zeta, ra, rb, om);
+          eval_residual(c, t, zeta, ra, rb, om, multi);
           // A d = -r by the Jacobi-preconditioned linear iteration with DIIS
           c->be->fill(dl, dim, 0.0);
           int lh = 0, lhead = 0;
@@ -301,7 +348,7 @@ int sccsd_solve_ground(sccsd_ctx* c, const double* t0, double zeta, const double
       fprintf(stderr, "{\"solver\": \"ground_done\", \"iterations\": %d, \"fp64_refine_residuals\": %d, \"correction_transforms\": %d, \"fp64_phase\": %d}\n",
               std::min(it, maxit), refine_fp64_evals, inner_its, (int)fp64_phase);
     if (refine) switch_precision(c, p0);
-    if (refine) eval_residual(c, t, zeta, ra, rb, om);  // fix the state for later transforms
+    if (refine) eval_residual(c, t, zeta, ra, rb, om, multi);  // fix the state for later transforms
     if (t_out) c->be->download(t_out, t, dim, c->be->is_device(t_out));
     if (e_corr) *e_corr = E - c->e_hf;
     if (iterations) *iterations = std::min(it, maxit);
@@ -311,6 +358,8 @@ int sccsd_solve_ground(sccsd_ctx* c, const double* t0, double zeta, const double
   if (status != SCCSD_OK) return fail(c, status, "ground state not converged within maxit");
   return SCCSD_OK;
 }
+
+extern "C" {
 
 int sccsd_normalize_left(sccsd_ctx* c, int nvec, const double* R, double* L) {
   if (!c) return SCCSD_EINVAL;
@@ -438,39 +487,90 @@ int sccsd_solve_states(sccsd_ctx* c, int nroots, int side, double tol, int maxit
     transform(c, side, m, V, W);
     const int p0 = c->be->get_precision();
     const bool refine = p0 != SCCSD_FP64 && refine_tol > 0.0;
-    bool fp64_phase = !refine;
-    bool pure = false;   // every image in the subspace is an FP64 transform
-    int anchors = 0;
-    int pc = p0;         // precision of the expansion transforms after an anchor
+    int anchors = 0;     // FP64 evaluations of the Ritz vectors' images
+    int restarts = 0;    // of them, restarts of the subspace on FP64 images
+    int pc = p0;         // precision of the expansion transforms
     int complex_run = 0; // consecutive iterations with a complex pair among the wanted roots
     std::vector<double> lam(nroots), res(nroots);
     double best = 1e300;
     int since_best = 0;
-    auto anchor = [&]() {
-      // V = orthonormalised current Ritz vectors, W = their FP64 images
-      have_prev = false;
-      d.copy(V, Xr, (int64_t)nroots * dim);
-      m = 0;
-      for (int k = 0; k < nroots; ++k) {
-        double* vk = V + (int64_t)m * dim;
-        if (k != m) d.copy(vk, Xr + (int64_t)k * dim, dim);
-        orthogonalize(vk, nullptr, m);
-        double nn = std::sqrt(d.dot(vk, vk, dim));
-        if (nn < 1e-10) continue;
-        d.axpby(dim, 0.0, vk, 1.0 / nn, vk);
-        ++m;
-      }
+    double* AXf = solver_buf(c, 93, 12 * dim);
+    double last_true = 1e300;   // FP64 residual at the previous check
+    double target = std::max(tol, refine_tol);  // mixed residual that triggers the next check
+    // Refinement in a mixed precision: the expansion vectors are transformed
+    // in the mixed precision throughout; the FP64 images of the current Ritz
+    // vectors decide convergence (their FP64 residuals must be below tol), and
+    // when the mixed estimate of the residual proves too optimistic (the
+    // subspace images carry more error than the residual is small), the
+    // subspace restarts from the Ritz vectors with their FP64 images, after
+    // which the mixed error scales with the size of the corrections, not of
+    // the roots. Returns 1 when converged, 2 after a restart, 0 otherwise
+    // (then res and Rz hold the FP64 residuals, which the expansion uses).
+    auto anchor = [&](double mixed_worst) -> int {
       switch_precision(c, SCCSD_FP64);
-      transform(c, side, m, V, W);
-      ++anchors;
-      // repeated anchors mean the expansions are too inexact: split BF16
-      // after four, FP64 after eight
-      if (anchors >= 8) pc = SCCSD_FP64;
-      else if (anchors >= 4 && pc == SCCSD_BF16) pc = SCCSD_BF16X3;
+      transform(c, side, nroots, Xr, AXf);
       switch_precision(c, pc);
-      pure = true;
-      best = 1e300;
+      ++anchors;
+      launch_ritz_residual(st, nroots, dim, AXf, Xr, wr, order, Rz);
+      c->be->gemm_tn(1, nroots, nroots, dim, 1.0, Rz, Rz, G, false);
+      c->be->gemm_tn(1, nroots, nroots, dim, 1.0, Xr, Xr, G + 144, false);
+      std::vector<double> g1(nroots * nroots), g2(nroots * nroots);
+      c->be->download(g1.data(), G, nroots * nroots, false);
+      c->be->download(g2.data(), G + 144, nroots * nroots, false);
+      double true_worst = 0.0;
+      for (int k = 0; k < nroots; ++k) {
+        res[k] = std::sqrt(g1[k * nroots + k] / g2[k * nroots + k]);
+        true_worst = std::max(true_worst, res[k]);
+      }
+      if (getenv("SCCSD_LOG"))
+        fprintf(stderr, "{\"solver\": \"davidson_anchor\", \"mixed_res\": %.3e, \"fp64_res\": %.3e}\n",
+                mixed_worst, true_worst);
+      if (true_worst < tol) return 1;
+      best = std::min(best, true_worst);
       since_best = 0;
+      // restart when the mixed estimate is off, or when the FP64 residual
+      // gained less than 30 % since the previous check (a noise floor of the
+      // mixed images)
+      // (before the first restart every image in the subspace is a mixed one,
+      // whose error does not shrink with the residual: always restart then)
+      const bool restart = restarts == 0 || true_worst > 1.5 * mixed_worst ||
+                           true_worst > 0.7 * last_true;
+      // next check when the mixed estimate is below half the FP64 residual
+      // this cycle is expected to reach (the last cycle's gain; 1e-3 before
+      // one is known): deeper mixed iterations would only fit the noise
+      const double gain = last_true < 1e300 ? std::min(1.0, true_worst / last_true) : 1e-3;
+      target = std::max(tol, 0.5 * true_worst * std::max(gain, 1e-6));
+      last_true = true_worst;
+      if (restart) {
+        // restart: V = orthonormalised Ritz vectors, W = their FP64 images
+        have_prev = false;
+        d.copy(V, Xr, (int64_t)nroots * dim);
+        d.copy(W, AXf, (int64_t)nroots * dim);
+        m = 0;
+        for (int k = 0; k < nroots; ++k) {
+          double* vk = V + (int64_t)m * dim;
+          double* wk = W + (int64_t)m * dim;
+          if (k != m) {
+            d.copy(vk, V + (int64_t)k * dim, dim);
+            d.copy(wk, W + (int64_t)k * dim, dim);
+          }
+          orthogonalize(vk, wk, m);
+          double nn = std::sqrt(d.dot(vk, vk, dim));
+          if (nn < 1e-10) continue;
+          d.axpby(dim, 0.0, vk, 1.0 / nn, vk);
+          d.axpby(dim, 0.0, wk, 1.0 / nn, wk);
+          ++m;
+        }
+        ++restarts;
+        // repeated restarts mean the expansions are too inexact: split BF16
+        // after four, FP64 after sixteen
+        if (restarts >= 16) pc = SCCSD_FP64;
+        else if (restarts >= 4 && pc == SCCSD_BF16) pc = SCCSD_BF16X3;
+        switch_precision(c, pc);
+        best = 1e300;
+        return 2;
+      }
+      return 0;
     };
     int it = 0;
     bool converged = false;
@@ -506,8 +606,8 @@ int sccsd_solve_states(sccsd_ctx* c, int nroots, int side, double tol, int maxit
         worst = std::max(worst, res[k]);
       }
       if (getenv("SCCSD_LOG")) {
-        fprintf(stderr, "{\"solver\": \"davidson\", \"iter\": %d, \"space\": %d, \"fp64\": %d, \"max_res\": %.3e, \"omega\": [", it, m,
-                (int)fp64_phase, worst);
+        fprintf(stderr, "{\"solver\": \"davidson\", \"iter\": %d, \"space\": %d, \"precision\": %d, \"max_res\": %.3e, \"omega\": [", it, m,
+                pc, worst);
         for (int k = 0; k < nroots; ++k) fprintf(stderr, "%s%.12f", k ? ", " : "", lam[k]);
         fprintf(stderr, "]}\n");
       }
@@ -517,31 +617,22 @@ int sccsd_solve_states(sccsd_ctx* c, int nroots, int side, double tol, int maxit
       } else {
         ++since_best;
       }
-      // Refinement with FP64 anchors: when the mixed iterations reach
-      // refine_tol (or stall), the subspace restarts from the Ritz vectors
-      // with their FP64 images; the expansion vectors that follow are
-      // transformed in the mixed precision, whose error then scales with the
-      // size of the corrections, not of the roots. Convergence is accepted
-      // only on a subspace of FP64 images alone (after a fresh anchor).
-      // (a stall counts only within 10x of refine_tol: far from convergence a
-      // non-symmetric Davidson can plateau for a while without a noise floor)
-      if (!fp64_phase && (worst < refine_tol || (since_best >= 8 && worst < 10.0 * refine_tol))) {
-        fp64_phase = true;
-        anchor();
-        continue;
+      if (worst < tol && complex_run > 0) throw std::domain_error("complex pair among the lowest roots");
+      if (!refine && worst < tol) {
+        converged = true;
+        break;
       }
-      if (fp64_phase && worst < tol) {
-        if (complex_run > 0) throw std::domain_error("complex pair among the lowest roots");
-        if (!refine || pure) {
+      // mixed estimate below the target (refine_tol at first, then from the
+      // gain of the last cycle, never below tol), or a stall within 100x of
+      // refine_tol: check on FP64 images (far from convergence a stall is a
+      // slow Davidson, not the mixed precision's noise)
+      if (refine && (worst < target || (since_best >= 20 && worst < 100.0 * refine_tol))) {
+        const int a = anchor(worst);
+        if (a == 1) {
           converged = true;
           break;
         }
-        anchor();   // verify: residuals of FP64 images only
-        continue;
-      }
-      if (refine && fp64_phase && since_best >= 12) {
-        anchor();   // the mixed corrections stalled: new FP64 anchor
-        continue;
+        if (a == 2) continue;
       }
       // preconditioned residuals of the unconverged roots
       std::vector<int> want;
@@ -591,13 +682,12 @@ int sccsd_solve_states(sccsd_ctx* c, int nroots, int side, double tol, int maxit
       }
       if (added == 0) throw std::runtime_error("Davidson subspace stagnated");
       transform(c, side, added, V + (int64_t)m * dim, W + (int64_t)m * dim);
-      if (refine && pc != SCCSD_FP64) pure = false;
       m += added;
     }
     if (!converged) status = SCCSD_ENOTCONV;
     if (getenv("SCCSD_LOG") && refine)
-      fprintf(stderr, "{\"solver\": \"davidson_done\", \"iterations\": %d, \"fp64_anchors\": %d}\n",
-              std::min(it, maxit), anchors);
+      fprintf(stderr, "{\"solver\": \"davidson_done\", \"iterations\": %d, \"fp64_anchors\": %d, \"restarts\": %d}\n",
+              std::min(it, maxit), anchors, restarts);
     if (refine) switch_precision(c, p0);
     for (int k = 0; k < nroots; ++k) omega[k] = lam[k];
     if (vecs) {
@@ -737,6 +827,187 @@ int sccsd_solve_scc(sccsd_ctx* c, double tol, int maxit, double ground_tol, doub
         c->be->upload(pr.first, pr.second->data(), dim, false);
       else
         std::memcpy(pr.first, pr.second->data(), sizeof(double) * dim);
+    }
+    if (iterations) *iterations = std::min(it, maxit);
+  });
+  if (rc != SCCSD_OK) return rc;
+  if (status != SCCSD_OK) return fail(c, status, "zeta iteration not converged within maxit");
+  return SCCSD_OK;
+}
+
+}  // extern "C"
+
+// ======================================================================
+// More than two constrained states (Sec. 2.2 with K of n states)
+// ======================================================================
+extern "C" {
+
+int sccsd_residual_states(sccsd_ctx* c, const double* t, int nstates, const double* zeta,
+                          const double* R, double* omega, double* e_corr) {
+  if (!c) return SCCSD_EINVAL;
+  if (!t || !zeta || !R) return fail(c, SCCSD_EINVAL, "NULL argument");
+  if (nstates < 2) return fail(c, SCCSD_EINVAL, "at least two constrained states");
+  return guarded(c, [&] {
+    set_states(c, nstates, zeta, R);
+    Model& m = *c->multi;
+    load_packed(c, m.g, t, m.t1, m.t2, false);
+    c->cur = &m;
+    std::vector<int> targets = {m.er.E0};
+    if (omega) {
+      targets.push_back(m.er.O1);
+      targets.push_back(m.er.O2);
+    }
+    m.g.run(targets);
+    if (omega) store_packed(c, m.g, m.er.O1, m.er.O2, omega, false);
+    if (e_corr) *e_corr = get_scalar(c, m.g, m.er.E0) - c->e_hf;
+    c->be->sync();
+  });
+}
+
+int sccsd_solve_ground_states(sccsd_ctx* c, const double* t0, int nstates, const double* zeta,
+                              const double* R, double tol, int maxit, double refine_tol,
+                              double* t_out, double* e_corr, int* iterations) {
+  if (!c) return SCCSD_EINVAL;
+  if (!zeta || !R) return fail(c, SCCSD_EINVAL, "NULL argument");
+  if (nstates < 2) return fail(c, SCCSD_EINVAL, "at least two constrained states");
+  int rc = guarded(c, [&] { set_states(c, nstates, zeta, R); });
+  if (rc != SCCSD_OK) return rc;
+  return solve_ground_impl(c, t0, 0.0, nullptr, nullptr, true, tol, maxit, refine_tol, t_out,
+                           e_corr, iterations);
+}
+
+// Self-consistent SCCSD for the n lowest states: zeta_kl for every pair k < l
+// solves O_kl = 0 (natural projection) by Broyden's method from zeta = 0
+// (plain CCSD) with the unit matrix as the first Jacobian estimate; at every
+// zeta the ground state and the n lowest right roots are re-converged.
+int sccsd_solve_scc_states(sccsd_ctx* c, int nstates, double tol, int maxit, double ground_tol,
+                           double eom_tol, double* zeta_out, double* O_out, double* e_corr,
+                           double* omega, double* r0_out, double* R_out, int* iterations) {
+  if (!c) return SCCSD_EINVAL;
+  if (nstates < 2 || nstates > 8) return fail(c, SCCSD_EINVAL, "nstates must be 2..8");
+  if (!(tol > 0.0) || maxit < 1 || !(ground_tol > 0.0) || !(eom_tol > 0.0))
+    return fail(c, SCCSD_EINVAL, "bad tolerances or iteration limit");
+  if (c->projection != 0)
+    return fail(c, SCCSD_EINVAL, "several constrained states use the natural projection");
+  int status = SCCSD_OK;
+  int rc = guarded(c, [&] {
+    const int n = nstates, np = n * (n - 1) / 2;
+    const int64_t dim = c->dim;
+    std::vector<double> t(dim), R((size_t)n * dim), w(n), r0(n), zeta(np, 0.0), O(np, 0.0);
+    std::vector<double> Jb((size_t)np * np, 0.0), zprev(np), Oprev(np);
+    for (int p = 0; p < np; ++p) Jb[(size_t)p * np + p] = 1.0;
+    bool have_states = false, have_prev = false;
+    double E = 0.0;
+    auto check = [&](int r) {
+      if (r != SCCSD_OK) throw std::runtime_error("inner solver failed: " + c->err);
+    };
+    int it = 0;
+    for (it = 1; it <= maxit; ++it) {
+      int gi = 0;
+      if (have_states)
+        check(sccsd_solve_ground_states(c, t.data(), n, zeta.data(), R.data(), ground_tol, 1000,
+                                        1e-5, t.data(), &E, &gi));
+      else
+        check(sccsd_solve_ground(c, nullptr, 0.0, nullptr, nullptr, ground_tol, 1000, 1e-5,
+                                 t.data(), &E, &gi));
+      int si = 0;
+      check(sccsd_solve_states(c, n, 0, eom_tol, 1000, 1e-4, w.data(), R.data(), &si));
+      for (int k = 0; k < n; ++k) {
+        // sign convention: largest |component| positive
+        double* x = R.data() + (size_t)k * dim;
+        int64_t im = 0;
+        for (int64_t q = 1; q < dim; ++q)
+          if (std::fabs(x[q]) > std::fabs(x[im])) im = q;
+        if (x[im] < 0)
+          for (int64_t q = 0; q < dim; ++q) x[q] = -x[q];
+      }
+      {
+        // r0 = eta.R / omega and the overlaps decide zeta: FP64 in a mixed context
+        Fp64Scope fp64(c);
+        std::vector<double> etaR(n);
+        for (int k0 = 0; k0 < n; k0 += c->max_batch) {
+          const int nb = std::min(c->max_batch, n - k0);
+          eta_dot(c, nb, R.data() + (size_t)k0 * dim, etaR.data() + k0);
+        }
+        for (int k = 0; k < n; ++k) r0[k] = etaR[k] / w[k];
+        int p = 0;
+        for (int k = 0; k < n; ++k)
+          for (int l = k + 1; l < n; ++l, ++p)
+            check(sccsd_overlap(c, r0[k], R.data() + (size_t)k * dim, r0[l],
+                                R.data() + (size_t)l * dim, &O[p]));
+      }
+      have_states = true;
+      double omax = 0.0, dz = 0.0;
+      for (int p = 0; p < np; ++p) {
+        omax = std::max(omax, std::fabs(O[p]));
+        if (have_prev) dz = std::max(dz, std::fabs(zeta[p] - zprev[p]));
+      }
+      if (getenv("SCCSD_LOG")) {
+        fprintf(stderr, "{\"solver\": \"scc_states\", \"iter\": %d, \"max_O\": %.3e, \"zeta\": [", it,
+                omax);
+        for (int p = 0; p < np; ++p) fprintf(stderr, "%s%.12f", p ? ", " : "", zeta[p]);
+        fprintf(stderr, "]}\n");
+      }
+      if (omax < tol && have_prev && dz < 1e-8) break;
+      if (have_prev) {
+        // Broyden: Jb += (dO - Jb dz) dz^T / (dz . dz)
+        std::vector<double> dzv(np), u(np);
+        double zz = 0.0;
+        for (int p = 0; p < np; ++p) {
+          dzv[p] = zeta[p] - zprev[p];
+          zz += dzv[p] * dzv[p];
+        }
+        if (zz > 0.0) {
+          for (int p = 0; p < np; ++p) {
+            double s = O[p] - Oprev[p];
+            for (int q = 0; q < np; ++q) s -= Jb[(size_t)p * np + q] * dzv[q];
+            u[p] = s / zz;
+          }
+          for (int p = 0; p < np; ++p)
+            for (int q = 0; q < np; ++q) Jb[(size_t)p * np + q] += u[p] * dzv[q];
+        }
+      }
+      zprev = zeta;
+      Oprev = O;
+      have_prev = true;
+      // zeta -= Jb^-1 O (Gaussian elimination with partial pivoting)
+      std::vector<double> A = Jb, b = O;
+      for (int col = 0; col < np; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < np; ++r)
+          if (std::fabs(A[(size_t)r * np + col]) > std::fabs(A[(size_t)piv * np + col])) piv = r;
+        if (!(std::fabs(A[(size_t)piv * np + col]) > 1e-300))
+          throw std::runtime_error("Broyden Jacobian of the overlaps is singular");
+        if (piv != col) {
+          for (int q = 0; q < np; ++q) std::swap(A[(size_t)col * np + q], A[(size_t)piv * np + q]);
+          std::swap(b[col], b[piv]);
+        }
+        for (int r = col + 1; r < np; ++r) {
+          const double f = A[(size_t)r * np + col] / A[(size_t)col * np + col];
+          for (int q = col; q < np; ++q) A[(size_t)r * np + q] -= f * A[(size_t)col * np + q];
+          b[r] -= f * b[col];
+        }
+      }
+      for (int r = np - 1; r >= 0; --r) {
+        double s = b[r];
+        for (int q = r + 1; q < np; ++q) s -= A[(size_t)r * np + q] * b[q];
+        b[r] = s / A[(size_t)r * np + r];
+      }
+      for (int p = 0; p < np; ++p) zeta[p] -= b[p];
+    }
+    if (it > maxit) status = SCCSD_ENOTCONV;
+    // the zeta of the last evaluation (after a non-converged loop, zeta holds an untried step)
+    const std::vector<double>& zfinal = it > maxit ? zprev : zeta;
+    if (zeta_out) std::copy(zfinal.begin(), zfinal.end(), zeta_out);
+    if (O_out) std::copy(O.begin(), O.end(), O_out);
+    if (e_corr) *e_corr = E;
+    if (omega) std::copy(w.begin(), w.end(), omega);
+    if (r0_out) std::copy(r0.begin(), r0.end(), r0_out);
+    if (R_out) {
+      if (c->be->is_device(R_out))
+        c->be->upload(R_out, R.data(), (int64_t)n * dim, false);
+      else
+        std::memcpy(R_out, R.data(), sizeof(double) * n * dim);
     }
     if (iterations) *iterations = std::min(it, maxit);
   });

@@ -148,14 +148,90 @@ def scc_active_verify(stored):
     return out
 
 
+SCC_THREE = dict(o=3, v=6, J=18, sd=0.2, seed=1007)
+
+
+def scc_three_states():
+    """Three constrained states (Sec. 2.2 with K = {1, 2, 3}; X_kl of Sec.
+    2.4.1 for every pair) on the two-irrep system: the oracle's loop (ground
+    state and three Davidson roots re-converged at each zeta, Broyden on the
+    three O_kl from zeta = 0). Two pairs join states of different symmetry,
+    whose zeta stays 0 (Sec. 3.1.1); the pair of equal symmetry is active.
+    The converged t and R_k are stored for the check of the defining
+    equations (the loop takes about twenty minutes)."""
+    from oracle import ccsd as cc
+    from oracle import response as rp
+    from oracle import scc as sc
+    from paper_2403_01007_gb300 import synthetic as syn
+    p = SCC_THREE
+    eps, L, _, _ = syn.symmetric_system(p["o"], p["v"], p["J"], p["sd"], p["seed"], SYM_OCC,
+                                        SYM_VIR)
+    prob = cc.Problem(eps, L, p["o"])
+    s = sc.solve_scc_states(prob, 3, tol=1e-10, ground_tol=1e-11, dense=False, maxit=40)
+    e_hf = float(rp.residual(prob, np.zeros(prob.dim))[0])
+    pairs = [(0, 1), (0, 2), (1, 2)]
+    return {
+        "citation": "Sec. 2.2 (O_kl = 0 for every pair of K, here three states) and "
+                    "Sec. 2.4.1 (X_kl = R1^k R2^l - R1^l R2^k, natural projection); "
+                    "Sec. 3.1.1 (states of different symmetry need no constraint)",
+        "produced_by": "tests/golden/make_golden.py: oracle.scc.solve_scc_states "
+                       "(Davidson roots)",
+        "inputs": {"generator": "synthetic.symmetric_system", **p, "irrep_occ": SYM_OCC,
+                   "irrep_vir": SYM_VIR, "nstates": 3, "projection": "natural"},
+        "values": {"zeta": [float(s["zeta"][kl]) for kl in pairs],
+                   "e_corr": float(s["E0"] - e_hf),
+                   "omega": [float(x) for x in s["omega"][:3]]},
+        "state": {"t": [float(x) for x in s["t"]],
+                  "R": [[float(x) for x in s["R"][k]] for k in range(3)]},
+    }
+
+
+def scc_three_states_verify(stored):
+    """The defining equations at the stored three-state solution, evaluated by
+    the oracle: the ground residual with sum_kl zeta_kl X_kl, the three right
+    eigen-equations, every O_kl with r0_k = eta.R_k / omega_k, and E_corr."""
+    import torch
+    from oracle import ccsd as cc
+    from oracle import response as rp
+    from oracle import scc as sc
+    from paper_2403_01007_gb300 import synthetic as syn
+    p = SCC_THREE
+    eps, L, _, _ = syn.symmetric_system(p["o"], p["v"], p["J"], p["sd"], p["seed"], SYM_OCC,
+                                        SYM_VIR)
+    prob = cc.Problem(eps, L, p["o"])
+    val, st = stored["values"], stored["state"]
+    t = np.array(st["t"])
+    R = [np.array(r) for r in st["R"]]
+    pairs = [(0, 1), (0, 2), (1, 2)]
+    scc = [(z, torch.tensor(R[k]), torch.tensor(R[l])) for z, (k, l) in zip(val["zeta"], pairs)]
+    E0, Om = rp.residual(prob, t, scc=scc)
+    e_hf = float(rp.residual(prob, np.zeros(prob.dim))[0])
+    out = {"ground residual": (float(torch.linalg.norm(Om)), 1e-8),
+           "e_corr": (abs(float(E0) - e_hf - val["e_corr"]), 1e-10)}
+    eta = rp.eta(prob, t, scc=scc).numpy()
+    r0 = []
+    for k in range(3):
+        AR = rp.jacobian_right(prob, t, R[k], scc=scc).numpy()
+        out["eigen-equation %d" % k] = (float(np.linalg.norm(AR - val["omega"][k] * R[k])), 1e-7)
+        r0.append(float(eta @ R[k] / val["omega"][k]))
+    O = sc.overlaps(torch.tensor(t), [(r0[k], torch.tensor(R[k])) for k in range(3)],
+                    prob.o, prob.v, "natural")
+    for kl in pairs:
+        out["O_%d%d" % kl] = (abs(float(O[kl])), 1e-9)
+    out["constraint active"] = (1.0 / max(abs(val["zeta"][1]), 1e-300), 1.0 / 0.3)
+    return out
+
+
 FIXTURES = {"fci_two_electron_o1_v5.json": fci_two_electron,
             "scc_symmetric_o3_v6.json": scc_symmetric,
             "scc_active_o3_v8.json": scc_active,
-            "scc_state_projection_o3_v8.json": lambda: scc_active("state")}
+            "scc_state_projection_o3_v8.json": lambda: scc_active("state"),
+            "scc_three_states_o3_v6.json": scc_three_states}
 # fixtures whose full regeneration is slow: checked through their defining
 # equations instead
 VERIFY = {"scc_active_o3_v8.json": scc_active_verify,
-          "scc_state_projection_o3_v8.json": scc_active_verify}
+          "scc_state_projection_o3_v8.json": scc_active_verify,
+          "scc_three_states_o3_v6.json": scc_three_states_verify}
 
 
 def load(name):

@@ -130,6 +130,69 @@ def test_graph_differentiation_matches_oracle(host_lib, size, with_scc):
     ctx.close()
 
 
+@pytest.mark.parametrize("size", [(2, 3, 6), (3, 4, 7)], ids=lambda s: "o%d_v%d" % s[:2])
+def test_several_constrained_states_match_oracle(host_lib, size):
+    """K of three states (Sec. 2.2; X_kl of Sec. 2.4.1 for every pair): the
+    residual, A R with eta.R, A^T L and the densities through the C ABI with
+    T + sum_kl zeta_kl X_kl against the oracle's sum over the pairs (which the
+    determinant engine pins); with two states the call equals the two-state
+    (zeta, Ra, Rb) call. Bad arguments are refused."""
+    B, lib = host_lib
+    o, v, J = size
+    eps, L = syn.system(o, v, J, 0.3, 91 + o + v)
+    prob = cc.Problem(eps, L, o)
+    t = syn.random_vectors(o, v, 1, 92, scale=0.1)[0]
+    R3 = syn.random_vectors(o, v, 3, 93, normalise=True)
+    Rt = syn.random_vectors(o, v, 2, 94, normalise=True)
+    zeta = np.array([0.37, -0.21, 0.15])
+    pairs = [(0, 1), (0, 2), (1, 2)]
+    scct = [(float(z), torch.tensor(R3[k]), torch.tensor(R3[l])) for z, (k, l) in zip(zeta, pairs)]
+    ctx = B.Context(o, v, J, eps, L, lib=lib)
+    e, om = ctx.residual_states(t, zeta, R3)
+    E0, Om = rp.residual(prob, t, scc=scct)
+    Ehf = float(rp.residual(prob, np.zeros(prob.dim))[0])
+    assert abs(e - (float(E0) - Ehf)) < 1e-12
+    assert np.abs(om - Om.numpy()).max() < 1e-12
+    # the X3 terms are active: they move omega
+    assert np.abs(om - rp.residual(prob, t)[1].numpy()).max() > 1e-3
+    s, eta = ctx.jacobian_right(Rt, with_eta=True)
+    sl = ctx.jacobian_left(Rt)
+    for k in range(2):
+        assert np.abs(s[k] - rp.jacobian_right(prob, t, Rt[k], scc=scct).numpy()).max() < 1e-12
+        assert abs(eta[k] - float(rp.eta(prob, t, scc=scct) @ torch.tensor(Rt[k]))) < 1e-12
+        assert np.abs(sl[k] - rp.jacobian_left(prob, t, Rt[k], scc=scct).numpy()).max() < 1e-12
+    D1, G = ctx.densities(0.5, Rt[0], -0.2, Rt[1])
+    D1r, Gr = rp.densities(prob, t, 0.5, Rt[0], -0.2, Rt[1], scc=scct)
+    assert np.abs(D1 - D1r.numpy()).max() < 1e-12
+    assert np.abs(G - Gr.numpy()).max() < 1e-12
+    # n = 2 is the two-state call
+    e2, om2 = ctx.residual_states(t, [0.4], R3[:2])
+    e2p, om2p = ctx.residual(t, scc=(0.4, R3[0], R3[1]))
+    assert abs(e2 - e2p) < 1e-13
+    assert np.abs(om2 - om2p).max() < 1e-13
+    # back to three states after the model for two was used
+    e3, om3 = ctx.residual_states(t, zeta, R3)
+    assert np.abs(om3 - om).max() < 1e-13
+    # the ground solve with the three-state terms reaches Omega = 0 of the oracle's residual
+    eg, tg, _ = ctx.solve_ground_states(0.1 * zeta, R3, tol=1e-11, maxit=300)
+    sccg = [(0.1 * z, x, y) for z, x, y in scct]
+    assert np.abs(rp.residual(prob, tg, scc=sccg)[1].numpy()).max() < 1e-10
+    # bad arguments: one state, NULL vectors, non-finite zeta
+    d = prob.dim
+    buf = np.zeros(3 * d)
+    z3 = np.zeros(3)
+    assert lib.sccsd_residual_states(ctx.h, buf.ctypes.data, 1, z3.ctypes.data, buf.ctypes.data,
+                                     None, None) == -1
+    assert lib.sccsd_residual_states(ctx.h, buf.ctypes.data, 3, z3.ctypes.data, None, None,
+                                     None) == -1
+    z3[1] = np.nan
+    assert lib.sccsd_residual_states(ctx.h, buf.ctypes.data, 3, z3.ctypes.data, buf.ctypes.data,
+                                     None, None) == -1
+    ctx.set_projection("state")
+    assert lib.sccsd_solve_scc_states(ctx.h, 3, 1e-8, 10, 1e-8, 1e-8, *([None] * 7)) == -1
+    ctx.close()
+
+
 def test_abi_argument_checks(host_lib):
     B, lib = host_lib
     h = ctypes.c_void_p()
@@ -649,6 +712,57 @@ def test_scc_loop_through_the_c_abi(host_lib):
                          torch.tensor(r["Rb"]), p["o"], p["v"]))
     assert abs(O) < 1e-9
     assert abs(r["zeta"]) > 0.3           # the constraint is active
+
+
+def test_broyden_loop_of_several_states_with_two_states_is_the_two_state_solution(host_lib):
+    """sccsd_solve_scc_states with n = 2 runs the several-states model (one
+    X3 term per state) and Broyden's update, which for one unknown is the
+    secant step of the two-state loop (the oracle's loops are pinned to agree,
+    tests/test_oracle_pins.py): it reaches the stored oracle solution of the
+    active two-state system, with O_01 = 0 of the oracle at the returned state."""
+    from oracle import scc as sc
+    B, lib = host_lib
+    g = _golden("scc_active_o3_v8.json")
+    p = g["inputs"]
+    eps, L = syn.system(p["o"], p["v"], p["J"], p["sd"], p["seed"])
+    ctx = B.Context(p["o"], p["v"], p["J"], eps, L, lib=lib)
+    r = ctx.solve_scc_states(2, tol=1e-10)
+    t = ctx.state_amplitudes()
+    ctx.close()
+    assert abs(r["zeta"][(0, 1)] - g["values"]["zeta"]) < 1e-7
+    assert np.abs(r["omega"] - np.array(g["values"]["omega"])).max() < 1e-8
+    assert abs(r["e_corr"] - g["values"]["e_corr"]) < 1e-9
+    O = float(sc.overlap(torch.tensor(t), r["r0"][0], torch.tensor(r["R"][0]), r["r0"][1],
+                         torch.tensor(r["R"][1]), p["o"], p["v"]))
+    assert abs(O) < 1e-9 and abs(r["O"][(0, 1)]) < 1e-9
+
+
+def test_three_constrained_states_reach_the_oracle_solution(host_lib):
+    """sccsd_solve_scc_states with three states on the two-irrep system (the
+    stored oracle solution, Sec. 2.2 with K of three states): the active pair
+    (0, 2) has the oracle's zeta, the pairs of different symmetry stay at
+    zeta = 0 (Sec. 3.1.1), the energies agree, and every O_kl of the oracle
+    vanishes at the returned state."""
+    from oracle import scc as sc
+    B, lib = host_lib
+    g = _golden("scc_three_states_o3_v6.json")
+    p = g["inputs"]
+    eps, L, _, _ = syn.symmetric_system(p["o"], p["v"], p["J"], p["sd"], p["seed"],
+                                        p["irrep_occ"], p["irrep_vir"])
+    ctx = B.Context(p["o"], p["v"], p["J"], eps, L, lib=lib)
+    r = ctx.solve_scc_states(3, tol=1e-10, ground_tol=1e-11, eom_tol=1e-9)
+    t = ctx.state_amplitudes()
+    ctx.close()
+    pairs = [(0, 1), (0, 2), (1, 2)]
+    for kl, z in zip(pairs, g["values"]["zeta"]):
+        assert abs(r["zeta"][kl] - z) < 1e-7, kl
+    assert abs(r["zeta"][(0, 2)]) > 0.3
+    assert np.abs(r["omega"] - np.array(g["values"]["omega"])).max() < 1e-8
+    assert abs(r["e_corr"] - g["values"]["e_corr"]) < 1e-9
+    O = sc.overlaps(torch.tensor(t), [(r["r0"][k], torch.tensor(r["R"][k])) for k in range(3)],
+                    p["o"], p["v"], "natural")
+    for kl in pairs:
+        assert abs(float(O[kl])) < 1e-9, kl
 
 
 def test_davidson_on_small_systems_is_full_ci_for_two_electrons(host_lib):
