@@ -34,6 +34,15 @@ TcConfig tc_default_config(const TcShape& s, int64_t m_tiles, int64_t n_tiles, d
   int64_t want = 1;
   if (tiles < s.sm_count && s.nk >= 8)
     want = std::min<int64_t>((2 * (int64_t)s.sm_count + tiles - 1) / tiles, s.nk / 4);
+  // split only when it shortens the work per SM: waves of the split grid per
+  // unit of work at most 0.85 of the unsplit grid's (a grid that already
+  // fills most SMs in one wave gains nothing and pays for the reduction)
+  if (want > 1) {
+    const int64_t sms = s.sm_count;
+    const double w1 = (double)((tiles + sms - 1) / sms);
+    const double ws = (double)((want * tiles + sms - 1) / sms) / (double)want;
+    if (ws > 0.85 * w1) want = 1;
+  }
   split_of(s.nk, want, c);
   c.nfast = (n_tiles > 1 && a_bytes > 4.0 * b_bytes) ? 1 : 0;
   // eight epilogue warps (three pipeline stages) when an item has at most 16

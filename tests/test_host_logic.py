@@ -278,12 +278,15 @@ def test_multiplier_residual_map_matches_oracle(host_lib, mult_system):
 def _default_rule(M, n_pad, nk, sm, ab, bb):
     """The fixed launch rule of the tensor-core contraction, written out: K is
     split only when the output tiles (128 x 256) cannot fill the SMs and there
-    are at least 8 K blocks, into ranges of at least 4 blocks; N tiles are
-    walked fastest when A is more than four times larger than B; the
-    eight-warp variant serves items of at most 16 K blocks."""
+    are at least 8 K blocks, into ranges of at least 4 blocks, and only when
+    the split grid's waves per unit of work are at most 0.85 of the unsplit
+    grid's; N tiles are walked fastest when A is more than four times larger
+    than B; the eight-warp variant serves items of at most 16 K blocks."""
     mt, nt = -(-M // 128), n_pad // 256
     tiles = mt * nt
     want = min(-(-2 * sm // tiles), nk // 4) if (tiles < sm and nk >= 8) else 1
+    if want > 1 and (-(-want * tiles // sm)) / want > 0.85 * (-(-tiles // sm)):
+        want = 1
     if want <= 1:
         splits, kbs = 1, nk
     else:
@@ -298,6 +301,8 @@ TUNE_SHAPES = [
     (126, 256, 1313, 152, 128 * 84032, 256 * 84032),        # one output tile, long K
     (5000, 768, 11, 152, 5120 * 704, 768 * 704),            # few tiles, short K
     (40000, 512, 2, 152, 40064 * 128, 512 * 128),           # A much larger than B
+    (1386, 3328, 315, 152, 1408 * 20160, 3328 * 20160),     # ladder chunk: 143 tiles, one wave
+    (1200, 2560, 300, 152, 1280 * 19200, 2560 * 19200),     # 100 tiles: a split of 4 pays
 ]
 
 
