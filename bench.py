@@ -623,6 +623,31 @@ def learned_case(args):
         v = int(rng.integers(60, 111))
         evs.append(lrn.system(o, v, 1000 + k))
     rows = lrn.evaluate(net, evs, tol=1e-8)
+    # the network's own throughput: forward over every doubles amplitude of an
+    # o=8 v=60 system (230 400 rows), and one training step on 65 536 rows
+    nrow = 8 * 8 * 60 * 60
+    Xf = X[:nrow].contiguous() if X.shape[0] >= nrow else X.repeat(nrow // X.shape[0] + 1, 1)[:nrow]
+    Yf = torch.empty((nrow, lrn.N_TARGETS), dtype=torch.float32, device=X.device)
+    for _ in range(3):
+        net.forward(Xf, Yf)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(10):
+        net.forward(Xf, Yf)
+    ev1.record()
+    torch.cuda.synchronize()
+    fwd_ms = ev0.elapsed_time(ev1) / 10
+    fwd_flops = 2.0 * nrow * (lrn.N_FEATURES * 256 + 2 * 256 * 256 + 256 * lrn.N_TARGETS)
+    nb = min(65536, X.shape[0])
+    Xb, Yb = X[:nb].contiguous(), Y[:nb].contiguous()
+    net.train_step(Xb, Yb, 1e-6)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    for _ in range(10):
+        net.train_step(Xb, Yb, 1e-6)
+    torch.cuda.synchronize()
+    step_ms = (time.perf_counter() - t3) * 100.0
     net.close()
     it0 = [r["plain_iters"] for r in rows]
     it1 = [r["learned_iters"] for r in rows]
@@ -643,7 +668,11 @@ def learned_case(args):
         "proposal_used": int(sum(r["used_net"] for r in rows)),
         "max_abs_energy_difference": float(max(abs(r["de"]) for r in rows)),
         "training": {"generate_s": gen_s, "train_s": train_s, "loss_first": hist[0],
-                     "loss_last": hist[-1]},
+                     "loss_last": hist[-1], "rows": int(X.shape[0])},
+        "network": {"forward_rows": nrow, "forward_ms": fwd_ms,
+                    "forward_tflops": fwd_flops / (fwd_ms * 1e-3) / 1e12,
+                    "train_step_rows": nb, "train_step_ms": step_ms,
+                    "train_step_tflops": 3.0 * fwd_flops * nb / nrow / (step_ms * 1e-3) / 1e12},
         "rows": rows}))
     return 0
 
@@ -656,7 +685,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["bf16x3", "bf16", "fp64"])
     ap.add_argument("--nvec", type=int, default=6)
-    ap.add_argument("--workload", default="LARGE", choices=["SMALL", "MEDIUM", "LARGE"])
+    ap.add_argument("--workload", default="LARGE", choices=["SMALL", "MEDIUM", "LARGE", "LADDER_O4"],
+                    help="LADDER_O4: the o=21 v=200 J=663 vvvv build with o=4, for profilers")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-fp64-arm", action="store_true")
     ap.add_argument("--no-x3-arm", action="store_true")

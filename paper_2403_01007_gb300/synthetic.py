@@ -54,6 +54,10 @@ MEDIUM = Workload("o10_v90_J300", 10, 90, 300, 0.03, 2)
 # -4022 Eh, FP64 ground iterations still at |Omega| = 8e-3 after 180 steps);
 # the narrower width is the fallback the scope table prescribes for that case.
 LARGE = Workload("o21_v200_J663", 21, 200, 663, 0.02, 3)
+# The vvvv build of o=21 v=200 J=663 (same v, J and entries) with o=4: the
+# same ladder-build launches on a device footprint small enough for profilers
+# that replay each launch many times.
+LADDER_O4 = Workload("o4_v200_J663", 4, 200, 663, 0.02, 3)
 
 
 def seed_of(config: int, instance: int = 0) -> int:
