@@ -60,19 +60,42 @@ struct ViewArgs32 {
   uint32_t istr[kMaxRank];
 };
 
+// Four elements per thread and round, their loads issued before any store, so
+// that a thread keeps four (eight when accumulating) HBM reads in flight;
+// consecutive threads take consecutive linear indices in each of the four
+// slabs of a round. total < 2^31 and the grid holds fewer than 2^22 threads,
+// so lin + 3 * stride cannot wrap.
 __global__ void k_copy_view32(ViewArgs32 a, uint32_t total, double* __restrict__ out,
                               const double* __restrict__ in, double coef, int acc) {
-  for (uint32_t lin = blockIdx.x * blockDim.x + threadIdx.x; lin < total;
-       lin += gridDim.x * blockDim.x) {
-    uint32_t r = lin, oo = 0, ii = 0;
-    for (int k = a.rank - 1; k >= 0; --k) {
-      uint32_t c = r % a.dims[k];
-      r /= a.dims[k];
-      oo += c * a.ostr[k];
-      ii += c * a.istr[k];
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t lin = blockIdx.x * blockDim.x + threadIdx.x; lin < total; lin += 4 * stride) {
+    uint32_t oo[4], ii[4];
+    bool ok[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t l = lin + (uint32_t)u * stride;
+      ok[u] = l < total;
+      uint32_t r = ok[u] ? l : 0, o = 0, i = 0;
+      // compile-time indices keep the view in kernel parameters (no local copy)
+#pragma unroll
+      for (int k = kMaxRank - 1; k >= 0; --k) {
+        if (k >= a.rank) continue;
+        const uint32_t c = r % a.dims[k];
+        r /= a.dims[k];
+        o += c * a.ostr[k];
+        i += c * a.istr[k];
+      }
+      oo[u] = o;
+      ii[u] = i;
     }
-    double v = coef * in[ii];
-    out[oo] = acc ? out[oo] + v : v;
+    double v[4], w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = ok[u] ? in[ii[u]] : 0.0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) w[u] = (acc && ok[u]) ? out[oo[u]] : 0.0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (ok[u]) out[oo[u]] = w[u] + coef * v[u];
   }
 }
 
