@@ -719,6 +719,35 @@ def test_scc_loop_through_the_c_abi(host_lib):
     assert abs(r["zeta"]) > 0.3           # the constraint is active
 
 
+def test_four_constrained_states_and_refined_ground_solve(host_lib):
+    """Four states (six pairs) through the several-states model: the residual
+    and A R against the oracle's sum over the six pairs; and the ground solve
+    with these terms in the emulated split-BF16 precision with FP64 refinement
+    zeroes the oracle's FP64 residual."""
+    B, lib = host_lib
+    o, v, J = 2, 4, 8
+    eps, L = syn.system(o, v, J, 0.3, 97)
+    prob = cc.Problem(eps, L, o)
+    t = syn.random_vectors(o, v, 1, 98, scale=0.1)[0]
+    R4 = syn.random_vectors(o, v, 4, 99, normalise=True)
+    Rt = syn.random_vectors(o, v, 1, 100, normalise=True)
+    pairs = [(k, l) for k in range(4) for l in range(k + 1, 4)]
+    zeta = np.array([0.21, -0.13, 0.08, 0.17, -0.05, 0.11])
+    scct = [(float(z), torch.tensor(R4[k]), torch.tensor(R4[l])) for z, (k, l) in zip(zeta, pairs)]
+    ctx = B.Context(o, v, J, eps, L, lib=lib)
+    _, om = ctx.residual_states(t, zeta, R4)
+    assert np.abs(om - rp.residual(prob, t, scc=scct)[1].numpy()).max() < 1e-12
+    s = ctx.jacobian_right(Rt)
+    assert np.abs(s[0] - rp.jacobian_right(prob, t, Rt[0], scc=scct).numpy()).max() < 1e-12
+    ctx.close()
+    ctx = B.Context(o, v, J, eps, L, precision="bf16x3", lib=lib)
+    z = 0.5 * zeta
+    _, tg, _ = ctx.solve_ground_states(z, R4, tol=1e-10, maxit=300, refine_tol=1e-5)
+    sccg = [(0.5 * zz, x, y) for zz, x, y in scct]
+    assert np.linalg.norm(rp.residual(prob, tg, scc=sccg)[1].numpy()) < 1e-9
+    ctx.close()
+
+
 def test_broyden_loop_of_several_states_with_two_states_is_the_two_state_solution(host_lib):
     """sccsd_solve_scc_states with n = 2 runs the several-states model (one
     X3 term per state) and Broyden's update, which for one unknown is the
