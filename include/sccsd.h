@@ -216,16 +216,25 @@ int sccsd_residual_states(sccsd_ctx* ctx, const double* t, int nstates, const do
 int sccsd_solve_ground_states(sccsd_ctx* ctx, const double* t0, int nstates, const double* zeta,
                               const double* R, double tol, int maxit, double refine_tol,
                               double* t_out, double* e_corr, int* iterations);
+/* O_kl for every pair k < l of nstates states (R0_k = r0[k], packed kets
+ * R[nstates][dim], host or device) at the fixed state, in the pair order of
+ * sccsd_residual_states: projection 0 the natural projection (as
+ * sccsd_overlap), 1 the state projection over all nstates states (Sec. 2.4.1),
+ * O_kl = sum_jm <psi_k|R_j> (S^-1)_jm <R_m|psi_l>, S_jm = <R_j|R_m>, with
+ * psi and the inner product as for sccsd_overlap. SCCSD_EINVAL for linearly
+ * dependent states. */
+int sccsd_overlaps(sccsd_ctx* ctx, int nstates, const double* r0, const double* R, int projection,
+                   double* O);
 /* Self-consistent SCCSD for the nstates (2..8) lowest states: zeta_kl for
- * every pair solves O_kl = 0 (natural projection) by Broyden's method from
+ * every pair solves O_kl = 0 (the projection of sccsd_set_projection: natural,
+ * or the state projection over all nstates states) by Broyden's method from
  * zeta = 0 (plain CCSD) with the unit matrix as the first Jacobian estimate;
  * at every zeta the ground state (ground_tol) and the n lowest right roots
  * (eom_tol, unit norm, largest component positive) are re-converged.
  * Converged when max |O_kl| < tol and the last zeta step is below 1e-8.
  * Outputs (may be NULL): zeta and O [n(n-1)/2], e_corr, omega [n], r0 [n],
- * R [n][dim] (host or device), iterations. SCCSD_EINVAL with the state
- * projection set (sccsd_set_projection). Afterwards the fixed state is that of
- * the last zeta. */
+ * R [n][dim] (host or device), iterations. Afterwards the fixed state is that
+ * of the last zeta. */
 int sccsd_solve_scc_states(sccsd_ctx* ctx, int nstates, double tol, int maxit, double ground_tol,
                            double eom_tol, double* zeta, double* O, double* e_corr, double* omega,
                            double* r0, double* R, int* iterations);

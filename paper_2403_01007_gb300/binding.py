@@ -70,6 +70,8 @@ def _declare(lib):
     lib.sccsd_solve_scc.argtypes = [_dp, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
     lib.sccsd_solve_scc.restype = ctypes.c_int
+    lib.sccsd_overlaps.argtypes = [_dp, ctypes.c_int, _dp, _dp, ctypes.c_int, _dp]
+    lib.sccsd_overlaps.restype = ctypes.c_int
     lib.sccsd_residual_states.argtypes = [_dp, _dp, ctypes.c_int, _dp, _dp, _dp, _dp]
     lib.sccsd_residual_states.restype = ctypes.c_int
     lib.sccsd_solve_ground_states.argtypes = [_dp, _dp, ctypes.c_int, _dp, _dp, ctypes.c_double,
@@ -456,6 +458,19 @@ class Context:
                                                   _ptr(Rb), ctypes.addressof(out)))
         return out.value
 
+    def overlaps(self, r0, R, projection="natural"):
+        """O_kl of every pair k < l of the states (r0[k], R[k]) at the fixed
+        state, natural or state projection over all of them; {(k, l): O_kl}."""
+        p = {"natural": 0, "state": 1}.get(projection, projection)
+        r0 = np.ascontiguousarray(r0, dtype=np.float64)
+        R = R if hasattr(R, "data_ptr") else np.ascontiguousarray(R, dtype=np.float64)
+        n = int(R.shape[0])
+        out = np.empty(n * (n - 1) // 2)
+        self._check(self.lib.sccsd_overlaps(self.h, n, r0.ctypes.data, _ptr(R), int(p),
+                                            out.ctypes.data))
+        pairs = [(k, l) for k in range(n) for l in range(k + 1, n)]
+        return dict(zip(pairs, out.tolist()))
+
     def set_projection(self, projection):
         """0 / "natural": SCCSD(E); 1 / "state": SCCSD(K), for sccsd_solve_scc."""
         p = {"natural": 0, "state": 1}.get(projection, projection)
@@ -500,7 +515,7 @@ class Context:
 
     def solve_scc_states(self, nstates, tol=1e-10, maxit=60, ground_tol=1e-11, eom_tol=1e-9):
         """Self-consistent SCCSD for the nstates lowest states (one zeta per
-        pair, Broyden); returns a dict."""
+        pair, Broyden; the projection of set_projection); returns a dict."""
         npair = nstates * (nstates - 1) // 2
         z, O = np.empty(npair), np.empty(npair)
         w, r0 = np.empty(nstates), np.empty(nstates)

@@ -436,6 +436,88 @@ int sccsd_overlap_states(sccsd_ctx* c, double ra0, const double* Ra, double rb0,
   });
 }
 
+int sccsd_overlaps(sccsd_ctx* c, int nstates, const double* r0, const double* R, int projection,
+                   double* O) {
+  if (!c) return SCCSD_EINVAL;
+  if (!r0 || !R || !O) return fail(c, SCCSD_EINVAL, "NULL argument");
+  if (nstates < 2) return fail(c, SCCSD_EINVAL, "at least two states");
+  if (projection != 0 && projection != 1) return fail(c, SCCSD_EINVAL, "projection must be 0 or 1");
+  if (!c->cur) return fail(c, SCCSD_ESTATE, "call sccsd_residual or a solver first");
+  return guarded(c, [&] {
+    const int n = nstates;
+    const int64_t dim = c->dim;
+    Model& m = *c->cur;
+    OverlapSec& S = overlap_section(m);
+    OverlapKSec* K = projection == 1 ? &overlap_k_section(m) : nullptr;
+    // M[k][j] = <psi_k|R_j>, G[j][l] = <R_j|R_l> (state projection)
+    std::vector<double> M((size_t)n * n, 0.0), G((size_t)n * n, 0.0);
+    int p = 0;
+    for (int k = 0; k < n; ++k)
+      for (int l = k + 1; l < n; ++l, ++p) {
+        set_scalar(c, m.g, S.ra0, r0[k]);
+        set_scalar(c, m.g, S.rb0, r0[l]);
+        load_packed(c, m.g, R + (int64_t)k * dim, S.ra1, S.ra2, false);
+        load_packed(c, m.g, R + (int64_t)l * dim, S.rb1, S.rb2, false);
+        if (!K) {
+          m.g.run({S.O});
+          O[p] = get_scalar(c, m.g, S.O);
+          continue;
+        }
+        const int ids[7] = {K->maa, K->mab, K->nab, K->nbb, K->Saa, K->Sab, K->Sbb};
+        m.g.run(std::vector<int>(ids, ids + 7));
+        double sv[7];
+        for (int i = 0; i < 7; ++i) sv[i] = get_scalar(c, m.g, ids[i]);
+        M[(size_t)k * n + k] = sv[0];
+        M[(size_t)k * n + l] = sv[1];
+        M[(size_t)l * n + k] = sv[2];
+        M[(size_t)l * n + l] = sv[3];
+        G[(size_t)k * n + k] = sv[4];
+        G[(size_t)k * n + l] = G[(size_t)l * n + k] = sv[5];
+        G[(size_t)l * n + l] = sv[6];
+      }
+    if (K) {
+      // O_kl = sum_jm M[k][j] (G^-1)_jm M[l][m]: W = G^-1 M^T by Gaussian
+      // elimination with partial pivoting
+      std::vector<double> A = G, W((size_t)n * n);
+      for (int j = 0; j < n; ++j)
+        for (int l = 0; l < n; ++l) W[(size_t)j * n + l] = M[(size_t)l * n + j];
+      double scale = 0.0;
+      for (double x : G) scale = std::max(scale, std::fabs(x));
+      for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < n; ++r)
+          if (std::fabs(A[(size_t)r * n + col]) > std::fabs(A[(size_t)piv * n + col])) piv = r;
+        if (!(std::fabs(A[(size_t)piv * n + col]) > 1e-14 * std::max(1.0, scale)))
+          throw std::invalid_argument("the states are linearly dependent");
+        if (piv != col)
+          for (int q = 0; q < n; ++q) {
+            std::swap(A[(size_t)col * n + q], A[(size_t)piv * n + q]);
+            std::swap(W[(size_t)col * n + q], W[(size_t)piv * n + q]);
+          }
+        for (int r = 0; r < n; ++r) {
+          if (r == col) continue;
+          const double f = A[(size_t)r * n + col] / A[(size_t)col * n + col];
+          if (f == 0.0) continue;
+          for (int q = 0; q < n; ++q) {
+            A[(size_t)r * n + q] -= f * A[(size_t)col * n + q];
+            W[(size_t)r * n + q] -= f * W[(size_t)col * n + q];
+          }
+        }
+      }
+      for (int r = 0; r < n; ++r)
+        for (int q = 0; q < n; ++q) W[(size_t)r * n + q] /= A[(size_t)r * n + r];
+      p = 0;
+      for (int k = 0; k < n; ++k)
+        for (int l = k + 1; l < n; ++l, ++p) {
+          double o = 0.0;
+          for (int j = 0; j < n; ++j) o += M[(size_t)k * n + j] * W[(size_t)j * n + l];
+          O[p] = o;
+        }
+    }
+    c->be->sync();
+  });
+}
+
 int sccsd_set_projection(sccsd_ctx* c, int projection) {
   if (!c) return SCCSD_EINVAL;
   if (projection != 0 && projection != 1) return fail(c, SCCSD_EINVAL, "projection must be 0 or 1");

@@ -877,7 +877,8 @@ int sccsd_solve_ground_states(sccsd_ctx* c, const double* t0, int nstates, const
 }
 
 // Self-consistent SCCSD for the n lowest states: zeta_kl for every pair k < l
-// solves O_kl = 0 (natural projection) by Broyden's method from zeta = 0
+// solves O_kl = 0 (the context's projection: natural, or the state projection
+// over all n states) by Broyden's method from zeta = 0
 // (plain CCSD) with the unit matrix as the first Jacobian estimate; at every
 // zeta the ground state and the n lowest right roots are re-converged.
 int sccsd_solve_scc_states(sccsd_ctx* c, int nstates, double tol, int maxit, double ground_tol,
@@ -887,8 +888,6 @@ int sccsd_solve_scc_states(sccsd_ctx* c, int nstates, double tol, int maxit, dou
   if (nstates < 2 || nstates > 8) return fail(c, SCCSD_EINVAL, "nstates must be 2..8");
   if (!(tol > 0.0) || maxit < 1 || !(ground_tol > 0.0) || !(eom_tol > 0.0))
     return fail(c, SCCSD_EINVAL, "bad tolerances or iteration limit");
-  if (c->projection != 0)
-    return fail(c, SCCSD_EINVAL, "several constrained states use the natural projection");
   int status = SCCSD_OK;
   int rc = guarded(c, [&] {
     const int n = nstates, np = n * (n - 1) / 2;
@@ -930,11 +929,7 @@ int sccsd_solve_scc_states(sccsd_ctx* c, int nstates, double tol, int maxit, dou
           eta_dot(c, nb, R.data() + (size_t)k0 * dim, etaR.data() + k0);
         }
         for (int k = 0; k < n; ++k) r0[k] = etaR[k] / w[k];
-        int p = 0;
-        for (int k = 0; k < n; ++k)
-          for (int l = k + 1; l < n; ++l, ++p)
-            check(sccsd_overlap(c, r0[k], R.data() + (size_t)k * dim, r0[l],
-                                R.data() + (size_t)l * dim, &O[p]));
+        check(sccsd_overlaps(c, n, r0.data(), R.data(), c->projection, O.data()));
       }
       have_states = true;
       double omax = 0.0, dz = 0.0;

@@ -151,13 +151,14 @@ def scc_active_verify(stored):
 SCC_THREE = dict(o=3, v=6, J=18, sd=0.2, seed=1007)
 
 
-def scc_three_states():
+def scc_three_states(projection="natural"):
     """Three constrained states (Sec. 2.2 with K = {1, 2, 3}; X_kl of Sec.
     2.4.1 for every pair) on the two-irrep system: the oracle's loop (ground
     state and three Davidson roots re-converged at each zeta, Broyden on the
-    three O_kl from zeta = 0). Two pairs join states of different symmetry,
-    whose zeta stays 0 (Sec. 3.1.1); the pair of equal symmetry is active.
-    The converged t and R_k are stored for the check of the defining
+    three O_kl from zeta = 0), with the natural projection or the state
+    projection over all three states. Two pairs join states of different
+    symmetry, whose zeta stays 0 (Sec. 3.1.1); the pair of equal symmetry is
+    active. The converged t and R_k are stored for the check of the defining
     equations (the loop takes about twenty minutes)."""
     from oracle import ccsd as cc
     from oracle import response as rp
@@ -167,17 +168,18 @@ def scc_three_states():
     eps, L, _, _ = syn.symmetric_system(p["o"], p["v"], p["J"], p["sd"], p["seed"], SYM_OCC,
                                         SYM_VIR)
     prob = cc.Problem(eps, L, p["o"])
-    s = sc.solve_scc_states(prob, 3, tol=1e-10, ground_tol=1e-11, dense=False, maxit=40)
+    s = sc.solve_scc_states(prob, 3, tol=1e-10, ground_tol=1e-11, dense=False, maxit=40,
+                            projection=projection)
     e_hf = float(rp.residual(prob, np.zeros(prob.dim))[0])
     pairs = [(0, 1), (0, 2), (1, 2)]
     return {
         "citation": "Sec. 2.2 (O_kl = 0 for every pair of K, here three states) and "
-                    "Sec. 2.4.1 (X_kl = R1^k R2^l - R1^l R2^k, natural projection); "
-                    "Sec. 3.1.1 (states of different symmetry need no constraint)",
+                    "Sec. 2.4.1 (X_kl = R1^k R2^l - R1^l R2^k, %s projection); "
+                    "Sec. 3.1.1 (states of different symmetry need no constraint)" % projection,
         "produced_by": "tests/golden/make_golden.py: oracle.scc.solve_scc_states "
                        "(Davidson roots)",
         "inputs": {"generator": "synthetic.symmetric_system", **p, "irrep_occ": SYM_OCC,
-                   "irrep_vir": SYM_VIR, "nstates": 3, "projection": "natural"},
+                   "irrep_vir": SYM_VIR, "nstates": 3, "projection": projection},
         "values": {"zeta": [float(s["zeta"][kl]) for kl in pairs],
                    "e_corr": float(s["E0"] - e_hf),
                    "omega": [float(x) for x in s["omega"][:3]]},
@@ -215,7 +217,7 @@ def scc_three_states_verify(stored):
         out["eigen-equation %d" % k] = (float(np.linalg.norm(AR - val["omega"][k] * R[k])), 1e-7)
         r0.append(float(eta @ R[k] / val["omega"][k]))
     O = sc.overlaps(torch.tensor(t), [(r0[k], torch.tensor(R[k])) for k in range(3)],
-                    prob.o, prob.v, "natural")
+                    prob.o, prob.v, stored["inputs"]["projection"])
     for kl in pairs:
         out["O_%d%d" % kl] = (abs(float(O[kl])), 1e-9)
     out["constraint active"] = (1.0 / max(abs(val["zeta"][1]), 1e-300), 1.0 / 0.3)
@@ -226,12 +228,14 @@ FIXTURES = {"fci_two_electron_o1_v5.json": fci_two_electron,
             "scc_symmetric_o3_v6.json": scc_symmetric,
             "scc_active_o3_v8.json": scc_active,
             "scc_state_projection_o3_v8.json": lambda: scc_active("state"),
-            "scc_three_states_o3_v6.json": scc_three_states}
+            "scc_three_states_o3_v6.json": scc_three_states,
+            "scc_three_states_state_projection_o3_v6.json": lambda: scc_three_states("state")}
 # fixtures whose full regeneration is slow: checked through their defining
 # equations instead
 VERIFY = {"scc_active_o3_v8.json": scc_active_verify,
           "scc_state_projection_o3_v8.json": scc_active_verify,
-          "scc_three_states_o3_v6.json": scc_three_states_verify}
+          "scc_three_states_o3_v6.json": scc_three_states_verify,
+          "scc_three_states_state_projection_o3_v6.json": scc_three_states_verify}
 
 
 def load(name):

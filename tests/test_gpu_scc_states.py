@@ -7,6 +7,7 @@ X_kl of Sec. 2.4.1 for every pair) against the FP64 oracle at o=5 v=19 J=72.
 * n = 2 through the several-states call equals the two-state call.
 * The ground solve with the three-state X3 terms in the split BF16 precision
   with FP64 refinement: the oracle's residual vanishes at the GPU amplitudes.
+* O_kl of every pair, natural and state projection over all three states.
 """
 import numpy as np
 import pytest
@@ -83,4 +84,24 @@ def test_three_states_split_bf16_against_oracle(small):
     Ehf = float(rp.residual(prob, np.zeros(prob.dim))[0])
     assert np.linalg.norm(Om.numpy()) < 1e-8
     assert abs(e - (float(E0) - Ehf)) < 1e-9
+    ctx.close()
+
+
+def test_overlaps_of_every_pair_against_oracle(small):
+    """O_kl of the three pairs at the fixed (CCSD) state, natural projection
+    and state projection over all three states (Sec. 2.2, 2.4.1), against the
+    oracle; with two states the pair calls."""
+    from oracle import scc as sc
+    B, w, eps, L, prob, t, R3, zeta, scct = small
+    ctx = B.Context(w.o, w.v, w.J, eps, L, precision="fp64")
+    ctx.residual(t)
+    r0 = np.array([0.3, -0.2, 0.1])
+    states = [(float(r0[k]), torch.tensor(R3[k])) for k in range(3)]
+    for proj in ("natural", "state"):
+        got = ctx.overlaps(r0, R3, proj)
+        ref = sc.overlaps(torch.tensor(t), states, w.o, w.v, proj)
+        for kl, val in ref.items():
+            assert abs(got[kl] - float(val)) < 1e-11 * max(1.0, abs(float(val))), (proj, kl)
+    two = ctx.overlaps(r0[:2], R3[:2], "state")
+    assert abs(two[(0, 1)] - ctx.overlap_states(r0[0], R3[0], r0[1], R3[1])) < 1e-12
     ctx.close()

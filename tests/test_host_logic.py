@@ -136,7 +136,10 @@ def test_several_constrained_states_match_oracle(host_lib, size):
     residual, A R with eta.R, A^T L and the densities through the C ABI with
     T + sum_kl zeta_kl X_kl against the oracle's sum over the pairs (which the
     determinant engine pins); with two states the call equals the two-state
-    (zeta, Ra, Rb) call. Bad arguments are refused."""
+    (zeta, Ra, Rb) call. The overlaps O_kl of every pair, natural and state
+    projection over all three states, equal the oracle's (pinned against full
+    determinant vectors). Bad arguments are refused."""
+    from oracle import scc as sc
     B, lib = host_lib
     o, v, J = size
     eps, L = syn.system(o, v, J, 0.3, 91 + o + v)
@@ -188,8 +191,25 @@ def test_several_constrained_states_match_oracle(host_lib, size):
     z3[1] = np.nan
     assert lib.sccsd_residual_states(ctx.h, buf.ctypes.data, 3, z3.ctypes.data, buf.ctypes.data,
                                      None, None) == -1
-    ctx.set_projection("state")
-    assert lib.sccsd_solve_scc_states(ctx.h, 3, 1e-8, 10, 1e-8, 1e-8, *([None] * 7)) == -1
+    # the overlaps of every pair, both projections, against the oracle
+    r0 = np.array([0.3, -0.2, 0.1])
+    ctx.residual(t)
+    states = [(float(r0[k]), torch.tensor(R3[k])) for k in range(3)]
+    for proj in ("natural", "state"):
+        got = ctx.overlaps(r0, R3, proj)
+        ref = sc.overlaps(torch.tensor(t), states, o, v, proj)
+        for kl, val in ref.items():
+            assert abs(got[kl] - float(val)) < 1e-12 * max(1.0, abs(float(val))), (proj, kl)
+    # two states: the pair calls
+    two = ctx.overlaps(r0[:2], R3[:2], "state")
+    assert abs(two[(0, 1)] - ctx.overlap_states(r0[0], R3[0], r0[1], R3[1])) < 1e-13
+    assert abs(ctx.overlaps(r0[:2], R3[:2])[(0, 1)] - ctx.overlap(r0[0], R3[0], r0[1], R3[1])) < 1e-13
+    # linearly dependent states are refused under the state projection
+    Rd = np.stack([R3[0], R3[1], 2.0 * R3[0]])
+    assert lib.sccsd_overlaps(ctx.h, 3, np.array([0.3, -0.2, 0.6]).ctypes.data, Rd.ctypes.data, 1,
+                              np.zeros(3).ctypes.data) == -1
+    assert lib.sccsd_overlaps(ctx.h, 1, r0.ctypes.data, R3.ctypes.data, 0,
+                              np.zeros(3).ctypes.data) == -1
     ctx.close()
 
 
@@ -748,42 +768,53 @@ def test_four_constrained_states_and_refined_ground_solve(host_lib):
     ctx.close()
 
 
-def test_broyden_loop_of_several_states_with_two_states_is_the_two_state_solution(host_lib):
+@pytest.mark.parametrize("fixture", ["scc_active_o3_v8.json", "scc_state_projection_o3_v8.json"],
+                         ids=["natural", "state"])
+def test_broyden_loop_of_several_states_with_two_states_is_the_two_state_solution(host_lib,
+                                                                                  fixture):
     """sccsd_solve_scc_states with n = 2 runs the several-states model (one
     X3 term per state) and Broyden's update, which for one unknown is the
     secant step of the two-state loop (the oracle's loops are pinned to agree,
-    tests/test_oracle_pins.py): it reaches the stored oracle solution of the
-    active two-state system, with O_01 = 0 of the oracle at the returned state."""
+    tests/test_oracle_pins.py): it reaches the stored oracle solutions of the
+    active two-state system, natural and state projection, with O_01 = 0 of
+    the oracle at the returned state."""
     from oracle import scc as sc
     B, lib = host_lib
-    g = _golden("scc_active_o3_v8.json")
+    g = _golden(fixture)
     p = g["inputs"]
     eps, L = syn.system(p["o"], p["v"], p["J"], p["sd"], p["seed"])
     ctx = B.Context(p["o"], p["v"], p["J"], eps, L, lib=lib)
+    ctx.set_projection(p["projection"])
     r = ctx.solve_scc_states(2, tol=1e-10)
     t = ctx.state_amplitudes()
     ctx.close()
     assert abs(r["zeta"][(0, 1)] - g["values"]["zeta"]) < 1e-7
     assert np.abs(r["omega"] - np.array(g["values"]["omega"])).max() < 1e-8
     assert abs(r["e_corr"] - g["values"]["e_corr"]) < 1e-9
-    O = float(sc.overlap(torch.tensor(t), r["r0"][0], torch.tensor(r["R"][0]), r["r0"][1],
-                         torch.tensor(r["R"][1]), p["o"], p["v"]))
+    ovl = sc.overlap_states if p["projection"] == "state" else sc.overlap
+    O = float(ovl(torch.tensor(t), r["r0"][0], torch.tensor(r["R"][0]), r["r0"][1],
+                  torch.tensor(r["R"][1]), p["o"], p["v"]))
     assert abs(O) < 1e-9 and abs(r["O"][(0, 1)]) < 1e-9
 
 
-def test_three_constrained_states_reach_the_oracle_solution(host_lib):
+@pytest.mark.parametrize("fixture", ["scc_three_states_o3_v6.json",
+                                     "scc_three_states_state_projection_o3_v6.json"],
+                         ids=["natural", "state"])
+def test_three_constrained_states_reach_the_oracle_solution(host_lib, fixture):
     """sccsd_solve_scc_states with three states on the two-irrep system (the
-    stored oracle solution, Sec. 2.2 with K of three states): the active pair
-    (0, 2) has the oracle's zeta, the pairs of different symmetry stay at
-    zeta = 0 (Sec. 3.1.1), the energies agree, and every O_kl of the oracle
-    vanishes at the returned state."""
+    stored oracle solutions, Sec. 2.2 with K of three states, natural and
+    state projection over all three): the active pair (0, 2) has the oracle's
+    zeta, the pairs of different symmetry stay at zeta = 0 (Sec. 3.1.1), the
+    energies agree, and every O_kl of the oracle vanishes at the returned
+    state."""
     from oracle import scc as sc
     B, lib = host_lib
-    g = _golden("scc_three_states_o3_v6.json")
+    g = _golden(fixture)
     p = g["inputs"]
     eps, L, _, _ = syn.symmetric_system(p["o"], p["v"], p["J"], p["sd"], p["seed"],
                                         p["irrep_occ"], p["irrep_vir"])
     ctx = B.Context(p["o"], p["v"], p["J"], eps, L, lib=lib)
+    ctx.set_projection(p["projection"])
     r = ctx.solve_scc_states(3, tol=1e-10, ground_tol=1e-11, eom_tol=1e-9)
     t = ctx.state_amplitudes()
     ctx.close()
@@ -794,7 +825,7 @@ def test_three_constrained_states_reach_the_oracle_solution(host_lib):
     assert np.abs(r["omega"] - np.array(g["values"]["omega"])).max() < 1e-8
     assert abs(r["e_corr"] - g["values"]["e_corr"]) < 1e-9
     O = sc.overlaps(torch.tensor(t), [(r["r0"][k], torch.tensor(r["R"][k])) for k in range(3)],
-                    p["o"], p["v"], "natural")
+                    p["o"], p["v"], p["projection"])
     for kl in pairs:
         assert abs(float(O[kl])) < 1e-9, kl
 
