@@ -31,6 +31,18 @@ residual component is the coefficient of one determinant:
 
 A R is the derivative of this residual along R by a 7-point central stencil,
 exact for the quartic residual up to rounding (Sec. 2.3.3: A = dOmega/dt).
+
+The SCC term of Sec. 2.4.1-2.4.2 is written here with explicit triples: the
+singlet X3 = R1^a R2^b - R1^b R2^a becomes the antisymmetric spin-orbital
+triples amplitude
+  x_IJK^ABC = P(I/JK) P(A/BC) [r^a_I^A r^b_JK^BC - r^b_I^A r^a_JK^BC],
+P(I/JK) f(IJK) = f(IJK) - f(JIK) - f(KJI), and the part of
+<mu|exp(-T) H exp(T)|HF> linear in X3 is <mu|(Hhat_N X3)_c|HF> with
+Hhat = exp(-T1) H exp(T1): the triples terms of the CCSDT singles and doubles
+equations, evaluated with the T1-transformed integrals. Those come from the
+orbital transformation exp(-T1) a+_I exp(T1) = a+_I - sum_A t_I^A a+_A,
+exp(-T1) a_A exp(T1) = a_A + sum_I t_I^A a_I (creators of virtual and
+annihilators of occupied orbitals unchanged).
 """
 from __future__ import annotations
 
@@ -185,6 +197,68 @@ class SpinSystem:
         blk = r2[:o, o:2 * o, :v, v:2 * v]                # [i][j][a][b] = r_{i a, j b}^{a a, b b}
         R2 = blk.transpose(2, 0, 3, 1)                    # [a][i][b][j]
         return self.packed_from_closed_shell(R1, R2)
+
+    # ----------------------------------------------------------- SCC term
+    def dressed(self, t1):
+        """(f^, W^): Fock-like one-body part (normal order with respect to HF)
+        and antisymmetrised two-body integrals of exp(-T1) H exp(T1)."""
+        no, N = self.no, self.no + self.nv
+        Lm = np.eye(N)
+        Rm = np.eye(N)
+        Lm[no:, :no] = -t1.T          # a+_I -> a+_I - sum_A t_I^A a+_A
+        Rm[no:, :no] = t1.T           # a_A -> a_A + sum_I t_I^A a_I
+        h = Lm @ self.h @ Rm
+        W = _ein("aP,bQ,PQRS,Rc,Sd->abcd", Lm, Lm, self.W, Rm, Rm)
+        f = h + _ein("pkqk->pq", W[:, :no, :, :no])
+        return f, W
+
+    def triples_of(self, Ra, Rb):
+        """x_IJK^ABC of X3 = R1^a R2^b - R1^b R2^a (packed closed-shell kets)."""
+        r1a, r2a = self.spin_amplitudes(Ra)
+        r1b, r2b = self.spin_amplitudes(Rb)
+        c = _ein("ia,jkbc->ijkabc", r1a, r2b) - _ein("ia,jkbc->ijkabc", r1b, r2a)
+
+        def p_occ(z):   # P(I/JK)
+            return z - z.transpose(1, 0, 2, 3, 4, 5) - z.transpose(2, 1, 0, 3, 4, 5)
+
+        def p_vir(z):   # P(A/BC)
+            return z - z.transpose(0, 1, 2, 4, 3, 5) - z.transpose(0, 1, 2, 5, 4, 3)
+
+        return p_vir(p_occ(c))
+
+    def x3_term_spin(self, t1, x3):
+        """(s1[I][A], s2[I][J][A][B]): <mu|(Hhat_N X3)_c|HF> for singles and
+        doubles, X3 given by its triples amplitude x3[I][J][K][A][B][C]."""
+        no = self.no
+        o, v = slice(0, no), slice(no, None)
+        f, W = self.dressed(t1)
+        s1 = 0.25 * _ein("mnef,imnaef->ia", W[o, o, v, v], x3)
+        s2 = _ein("me,ijmabe->ijab", f[o, v], x3)
+        y = 0.5 * _ein("bmef,ijmaef->ijab", W[v, o, v, v], x3)
+        s2 = s2 + y - y.transpose(0, 1, 3, 2)
+        z = 0.5 * _ein("mnje,imnabe->ijab", W[o, o, o, v], x3)
+        s2 = s2 - (z - z.transpose(1, 0, 2, 3))
+        return s1, s2
+
+    def energy_residual_scc(self, x, zeta, Ra, Rb):
+        """(E0, packed Omega) with the cluster operator T + zeta X3 (Sec. 2.4.1):
+        the CCSD projections plus zeta <mu|(Hhat_N X3)_c|HF> (Sec. 2.4.2)."""
+        t1, t2 = self.spin_amplitudes(x)
+        E0, r1, r2 = self.energy_residual_spin(t1, t2)
+        s1, s2 = self.x3_term_spin(t1, self.triples_of(Ra, Rb))
+        return E0, self.closed_shell_residual(r1 + zeta * s1, r2 + zeta * s2)
+
+    def jacobian_right_scc(self, x, R, zeta, Ra, Rb, h: float = 1.0):
+        """A R of the SCC residual at fixed (zeta, Ra, Rb), by the exact 7-point
+        stencil (the residual is a polynomial of degree <= 6 in t)."""
+        x = np.asarray(x, dtype=np.float64)
+        R = np.asarray(R, dtype=np.float64)
+        w = {1: 45.0, 2: -9.0, 3: 1.0}
+        acc = np.zeros_like(x)
+        for k, c in w.items():
+            acc += c * (self.energy_residual_scc(x + k * h * R, zeta, Ra, Rb)[1]
+                        - self.energy_residual_scc(x - k * h * R, zeta, Ra, Rb)[1])
+        return acc / (60.0 * h)
 
     def jacobian_right(self, x, R, h: float = 1.0):
         """A R by the exact 7-point central stencil of Omega(x + e R)."""

@@ -13,6 +13,10 @@ projections E0 = <HF|Hbar|HF> and Omega_mu = <mu~|Hbar|HF> of Sec. 2.1.
   vectors of that workload (A from the spin-orbital side by an exact 7-point
   stencil, Sec. 2.3.3), and A^T L through <L|A R> = <A^T L|R> with A^T L from
   the closed-shell side, plus single components (A^T L)_nu = L . (A e_nu).
+* The SCC term of Sec. 2.4.2, zeta <mu~|[Hhat, X3]|HF>: the spin-orbital side
+  writes X3 as explicit triples and uses the triples terms of the CCSDT
+  equations with T1-transformed integrals, pinned by the determinant engine at
+  tiny sizes; at o=5 v=19 the closed-shell SCC residual and its A R equal it.
 A mistake made in one factorisation (a dropped term, a wrong sign or index,
 a transposed operand) cannot appear identically in the other.
 """
@@ -107,3 +111,41 @@ def test_jacobians_equal_spin_orbital_stencil_at_o5_v19(c1):
         e[nu] = 1.0
         col = sys_.jacobian_right(x, e)
         assert abs(float(Lb @ col) - ATL[nu]) < 1e-11 * max(1.0, np.abs(col).max())
+
+
+@pytest.mark.parametrize("size", [(2, 3, 6), (2, 4, 7), (3, 3, 8)], ids=lambda s: "o%d_v%d" % s[:2])
+def test_spin_orbital_x3_term_equals_determinant_engine(size):
+    """T + zeta X3 (Sec. 2.4.1): the spin-orbital residual with explicit triples
+    equals the determinant engine's projections with the X3 operator added."""
+    o, v, J = size
+    eps, L = syn.system(o, v, J, 0.3, 11)
+    g = det.full_g(L)
+    S = det.System(det.Space(o, v), det.synthetic_h(eps, g, o), g)
+    sys_ = so.SpinSystem(eps, L, o)
+    x = syn.random_vectors(o, v, 1, 12, scale=0.1)[0]
+    Ra, Rb = syn.random_vectors(o, v, 2, 13, normalise=True)
+    zeta = 0.37
+    E_d, Om_d = S.omega(x, extra=zeta * det.x3_operator(S.S, Ra, Rb))
+    E_s, Om_s = sys_.energy_residual_scc(x, zeta, Ra, Rb)
+    assert abs(E_d - E_s) < 1e-12 * max(1.0, abs(E_d))
+    assert np.abs(Om_d - Om_s).max() < 1e-12 * max(1.0, np.abs(Om_d).max())
+    # the term is present
+    assert np.abs(Om_s - sys_.energy_residual(x)[1]).max() > 1e-3
+
+
+def test_closed_shell_scc_residual_and_jacobian_equal_spin_orbital_at_o5_v19(c1):
+    """At o=5 v=19 J=72 the closed-shell SCC residual (T1-dressed X3 terms) and
+    its A R equal the spin-orbital formulation with explicit triples."""
+    import torch
+    w, prob, sys_, x, R, Lb = c1
+    Ra, Rb = syn.random_vectors(w.o, w.v, 2, syn.seed_of(w.config, 80), normalise=True)
+    zeta = 0.3
+    scc = (zeta, torch.tensor(Ra), torch.tensor(Rb))
+    E_s, Om_s = sys_.energy_residual_scc(x, zeta, Ra, Rb)
+    E_c, Om_c = rp.residual(prob, x, scc=scc)
+    assert abs(float(E_c) - E_s) < 1e-12 * abs(E_s)
+    assert np.abs(Om_c.numpy() - Om_s).max() < 1e-12 * np.abs(Om_s).max()
+    assert np.abs(Om_s - sys_.energy_residual(x)[1]).max() > 1e-3
+    ar_s = sys_.jacobian_right_scc(x, R[0], zeta, Ra, Rb)
+    ar_c = rp.jacobian_right(prob, x, R[0], scc=scc).numpy()
+    assert np.abs(ar_c - ar_s).max() < 1e-11 * np.abs(ar_s).max()
