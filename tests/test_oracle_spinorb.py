@@ -134,8 +134,9 @@ def test_spin_orbital_x3_term_equals_determinant_engine(size):
 
 
 def test_closed_shell_scc_residual_and_jacobian_equal_spin_orbital_at_o5_v19(c1):
-    """At o=5 v=19 J=72 the closed-shell SCC residual (T1-dressed X3 terms) and
-    its A R equal the spin-orbital formulation with explicit triples."""
+    """At o=5 v=19 J=72 the closed-shell SCC residual (T1-dressed X3 terms), its
+    A R and (through <L|A R> = <A^T L|R>) its A^T L equal the spin-orbital
+    formulation with explicit triples."""
     import torch
     w, prob, sys_, x, R, Lb = c1
     Ra, Rb = syn.random_vectors(w.o, w.v, 2, syn.seed_of(w.config, 80), normalise=True)
@@ -149,3 +150,6 @@ def test_closed_shell_scc_residual_and_jacobian_equal_spin_orbital_at_o5_v19(c1)
     ar_s = sys_.jacobian_right_scc(x, R[0], zeta, Ra, Rb)
     ar_c = rp.jacobian_right(prob, x, R[0], scc=scc).numpy()
     assert np.abs(ar_c - ar_s).max() < 1e-11 * np.abs(ar_s).max()
+    # A^T L of the closed-shell SCC residual through <L|A R> with A from the spin side
+    atl = rp.jacobian_left(prob, x, Lb, scc=scc).numpy()
+    assert abs(float(Lb @ ar_s) - float(atl @ R[0])) < 1e-11 * np.abs(Lb).max() * np.abs(ar_s).sum()
