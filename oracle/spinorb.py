@@ -260,6 +260,26 @@ class SpinSystem:
                         - self.energy_residual_scc(x - k * h * R, zeta, Ra, Rb)[1])
         return acc / (60.0 * h)
 
+    # ------------------------------------------------------- SCC overlap
+    def projected_state(self, x, r0, R):
+        """Determinant coefficients (c0, c1[I][A], c2[I][J][A][B]) of
+        exp(T)(r0 + R)|HF> on HF, singles and doubles (T from packed x,
+        without X3): c1 = r1 + r0 t1, c2 = r2 + P(IJ)P(AB) t1 r1 + r0 (t2 + t1^t1)."""
+        t1, t2 = self.spin_amplitudes(x)
+        r1, r2 = self.spin_amplitudes(R)
+        tr = _ein("ia,jb->ijab", t1, r1)
+        ptr = tr - tr.transpose(1, 0, 2, 3) - tr.transpose(0, 1, 3, 2) + tr.transpose(1, 0, 3, 2)
+        tt = _ein("ia,jb->ijab", t1, t1)
+        return r0, r1 + r0 * t1, r2 + ptr + r0 * (t2 + tt - tt.transpose(0, 1, 3, 2))
+
+    def overlap(self, x, ra0, Ra, rb0, Rb):
+        """O_ab = <psi_a|P|psi_b> of the natural projection (Sec. 2.4.2): the
+        plain sum over HF, singles and doubles determinants (each doubles
+        determinant once: 1/4 of the sum over all four-index amplitudes)."""
+        a0, a1, a2 = self.projected_state(x, ra0, Ra)
+        b0, b1, b2 = self.projected_state(x, rb0, Rb)
+        return float(a0 * b0 + np.sum(a1 * b1) + 0.25 * np.sum(a2 * b2))
+
     def jacobian_right(self, x, R, h: float = 1.0):
         """A R by the exact 7-point central stencil of Omega(x + e R)."""
         x = np.asarray(x, dtype=np.float64)

@@ -13,6 +13,9 @@ projections E0 = <HF|Hbar|HF> and Omega_mu = <mu~|Hbar|HF> of Sec. 2.1.
   vectors of that workload (A from the spin-orbital side by an exact 7-point
   stencil, Sec. 2.3.3), and A^T L through <L|A R> = <A^T L|R> with A^T L from
   the closed-shell side, plus single components (A^T L)_nu = L . (A e_nu).
+* The SCC overlap O_ab of the natural projection (Sec. 2.4.2): determinant
+  coefficients of exp(T)(r0 + R)|HF> in spin orbitals and the plain
+  determinant inner product, against the closed-shell metric at o=5 v=19.
 * The SCC term of Sec. 2.4.2, zeta <mu~|[Hhat, X3]|HF>: the spin-orbital side
   writes X3 as explicit triples and uses the triples terms of the CCSDT
   equations with T1-transformed integrals, pinned by the determinant engine at
@@ -153,3 +156,28 @@ def test_closed_shell_scc_residual_and_jacobian_equal_spin_orbital_at_o5_v19(c1)
     # A^T L of the closed-shell SCC residual through <L|A R> with A from the spin side
     atl = rp.jacobian_left(prob, x, Lb, scc=scc).numpy()
     assert abs(float(Lb @ ar_s) - float(atl @ R[0])) < 1e-11 * np.abs(Lb).max() * np.abs(ar_s).sum()
+
+
+@pytest.mark.parametrize("size", [(1, 4, 5), (2, 3, 6), (3, 3, 8)], ids=lambda s: "o%d_v%d" % s[:2])
+def test_spin_orbital_overlap_equals_determinant_engine(size):
+    o, v, J = size
+    eps, L = syn.system(o, v, J, 0.3, 21)
+    g = det.full_g(L)
+    S = det.System(det.Space(o, v), det.synthetic_h(eps, g, o), g)
+    sys_ = so.SpinSystem(eps, L, o)
+    x = syn.random_vectors(o, v, 1, 22, scale=0.1)[0]
+    Ra, Rb = syn.random_vectors(o, v, 2, 23, normalise=True)
+    ref = S.overlap(x, 0.3, Ra, -0.2, Rb)
+    assert abs(sys_.overlap(x, 0.3, Ra, -0.2, Rb) - ref) < 1e-13 * max(1.0, abs(ref))
+
+
+def test_closed_shell_overlap_equals_spin_orbital_at_o5_v19(c1):
+    """O_ab with the closed-shell doubles metric (sum c2 (2 c2' - c2' with
+    i <-> j)) equals the plain determinant inner product in spin orbitals."""
+    import torch
+    from oracle import scc as sc
+    w, prob, sys_, x, R, Lb = c1
+    Ra, Rb = syn.random_vectors(w.o, w.v, 2, syn.seed_of(w.config, 81), normalise=True)
+    a = sys_.overlap(x, 0.3, Ra, -0.2, Rb)
+    b = float(sc.overlap(torch.tensor(x), 0.3, torch.tensor(Ra), -0.2, torch.tensor(Rb), w.o, w.v))
+    assert abs(a - b) < 1e-12 * max(1.0, abs(a))
