@@ -331,8 +331,10 @@ int sccsd_solve_states(sccsd_ctx* ctx, int nroots, int side, double tol, int max
 int sccsd_normalize_left(sccsd_ctx* ctx, int nvec, const double* R, double* L);
 
 /* ---- Learned initial guess and preconditioner ----------------------------
- * A per-amplitude MLP (BF16 weights and activations, FP32 accumulation) maps
- * MP2-level features of each doubles amplitude to (t_ij^ab / s_t,
+ * A per-amplitude MLP (BF16 weights and activations, FP32 accumulation; every
+ * layer product on the tcgen05 tensor cores with bias, ReLU and the backward
+ * mask fused into the product's epilogue) maps MP2-level features of each
+ * doubles amplitude to (t_ij^ab / s_t,
  * log(D'_ij^ab / D_ij^ab)): a guess for the converged amplitude and for the
  * dressed denominator D' (the diagonal of the Jacobian estimated from the
  * intermediates) used as the ground-state preconditioner. The plain solver
